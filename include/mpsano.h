@@ -1,0 +1,162 @@
+/*
+ * mpsano.h -- C ABI of the B300 (sm_103a) MPS-ANO-VQC feature-extraction path.
+ *
+ * What it computes (arxiv 2607.10280):
+ *   p x p image -> one qubit per pixel on a row-major chain (Sec. II.B)
+ *   -> encoding / entangling circuit (Sec. II.B, Eq. 2)
+ *   -> matrix product state with SVD truncation to bond dimension chi (Sec. II.B, Eq. 3)
+ *   -> all 16 two-qubit Pauli expectations of image-local pairs, the Pauli cache
+ *      (Sec. II.C, Eq. 4-5)
+ *   -> adaptive-observable features q = sum_alpha c_alpha <P_alpha> (Eq. 1, 4, 5)
+ *   -> linear reconstruction y = W q + b (Eq. 6).
+ *
+ * Conventions shared by every call
+ *   - Qubit k is pixel (k / p, k % p).  Pauli index alpha = 4a + b with I,X,Y,Z = 0..3,
+ *     P_a on the lower chain index of the pair.
+ *   - Pair order per image: horizontal (r,c)-(r,c+1) row-major by the left pixel,
+ *     then vertical (r,c)-(r+1,c) row-major by the top pixel, then (pair set HVD only)
+ *     diagonal (r,c)-(r+1,c+1) and anti-diagonal (r,c+1)-(r+1,c), each row-major.
+ *   - "device" pointers are CUDA global-memory addresses on the batch's device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns every pointer it
+ *     passes; the library owns only what a mps_batch holds.
+ *   - Every call returns an mps_status.  Argument errors are detected on the host
+ *     and returned synchronously; nothing is launched in that case.  Work is
+ *     enqueued asynchronously on the batch's stream.  Errors raised by device code
+ *     (bounded waits, bounds checks) are recorded in a device status word and are
+ *     returned by the next mps_sync() on that batch.  mps_last_error() gives a
+ *     thread-local message for the last non-OK status.  Nothing throws across
+ *     the ABI.
+ */
+#ifndef MPSANO_H
+#define MPSANO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MPS_OK = 0,
+    MPS_ERR_INVALID_ARG = 1,  /* bad size, pointer or enum value */
+    MPS_ERR_OOM = 2,          /* device allocation failed */
+    MPS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    MPS_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+    MPS_ERR_UNSUPPORTED = 5,  /* valid request outside what this build supports */
+    MPS_ERR_NOT_READY = 6,    /* e.g. Pauli cache requested before a circuit ran */
+    MPS_ERR_DEVICE = 7        /* a device-side check failed (see mps_last_error) */
+} mps_status;
+
+/* Arithmetic of the path.
+ *   MPS_FP64         complex128 everywhere (the plain FP64 path).
+ *   MPS_MIXED        complex64 site tensors, gates, QR splits and environments;
+ *                    FP64 for the Gram matrix, the eigen/singular values and the
+ *                    re-orthogonalisation inside every step that truncates.
+ *   MPS_MIXED_ORTH64 as MPS_MIXED, and every QR/LQ factorisation also in FP64. */
+typedef enum { MPS_FP64 = 0, MPS_MIXED = 1, MPS_MIXED_ORTH64 = 2 } mps_precision;
+
+/* Circuit family.
+ *   MPS_ANSATZ_LADDER  R_Y(pi x_k) once, then L x [R_Y(alpha_{l,k}) then R_Z(beta_{l,k})
+ *                      on every qubit, CNOT(k -> k+1) for k = 0..n-2 in order].
+ *   MPS_ANSATZ_PAPER   L x [H, R_Y(2 pi x_k - pi) (Eq. 2) on every qubit, CNOTs on bonds
+ *                      (0,1),(2,3),... then (1,2),(3,4),..., each sub-layer ascending];
+ *                      Sec. II.B. */
+typedef enum { MPS_ANSATZ_LADDER = 0, MPS_ANSATZ_PAPER = 1 } mps_ansatz;
+
+/* Pair set (Sec. II.C): horizontal + vertical neighbours, or also both diagonals. */
+typedef enum { MPS_PAIRS_HV = 0, MPS_PAIRS_HVD = 1 } mps_pair_set;
+
+typedef struct mps_batch mps_batch;
+
+typedef struct {
+    int32_t ansatz;              /* mps_ansatz */
+    int32_t L;                   /* layers for every image, >= 0 (ignored if L_per_image) */
+    const int32_t* L_per_image;  /* host [n_images] or NULL */
+    const double* params;        /* device [L_max][params_n][2] angles (alpha, beta) in
+                                    radians, LADDER only (NULL for PAPER); image i uses
+                                    params[l][k][.] for l < L_i, k < n_i */
+    int32_t params_n;            /* qubit stride of params, >= max n_i */
+} mps_circuit;
+
+/* Create a batch of n_images independent MPS (Sec. II.B, Eq. 3).
+ *   p        host [n_images], image sides, 2 <= p_i <= 16 (n_i = p_i^2 qubits)
+ *   chi      host [n_images] bond caps, or NULL to use chi_all for every image
+ *   chi_all  bond cap when chi == NULL, 1 <= chi <= 64
+ *   prec     mps_precision
+ *   stream   cudaStream_t (NULL = legacy default stream) used by every later call
+ *   out      receives the handle
+ * The library allocates the MPS arena and its workspace on the current device
+ * (about sum_i n_i * D_i^2 * 2 complex values, D_i the largest bond image i can
+ * reach).  Returns MPS_ERR_OOM if that allocation fails. */
+mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* chi,
+                            int32_t chi_all, int32_t prec, void* stream, mps_batch** out);
+
+/* Release a batch (stream-ordered: waits for its queued work first). NULL is a no-op. */
+mps_status mps_destroy_batch(mps_batch* batch);
+
+/* Run the circuit on every image (Sec. II.B): reset to |0...0>, apply the gate list,
+ * and after every two-qubit gate truncate the bond to chi at the orthogonality
+ * centre (keep the largest min(chi, 2D_left, 2D_right) singular values, renormalise).
+ *   pixels  device, float64, packed [sum_i n_i] in image order, values in [0, 1]
+ *   circ    host, see mps_circuit
+ * Asynchronous. */
+mps_status mps_apply_circuit(mps_batch* batch, const double* pixels, const mps_circuit* circ);
+
+/* Pauli cache (Sec. II.C, Eq. 5): for every image-local pair and every alpha,
+ * <P_a (x) P_b> / <psi|psi>.
+ *   pair_set      mps_pair_set
+ *   out           device, caller-owned, [sum_i m_i][16]; float64 for MPS_FP64,
+ *                 float32 otherwise
+ *   pair_offsets  host [n_images + 1] (may be NULL): receives the prefix sums of m_i
+ * Returns MPS_ERR_NOT_READY if no circuit has run on the batch.  Asynchronous. */
+mps_status mps_pauli_cache(mps_batch* batch, int32_t pair_set, void* out, int64_t* pair_offsets);
+
+/* ANO features and linear reconstruction (Sec. II.A, II.C; Eq. 1, 4, 5, 6) for a batch
+ * of images that share one pair layout of m pairs.
+ *   pauli        device [n_images][m][16], float32 (pauli_f64 = 0) or float64 (= 1)
+ *   abd          device float32 [m][16]: A[6] real off-diagonal, B[6] imaginary
+ *                off-diagonal of H_q for (k,l) = (0,1),(0,2),(0,3),(1,2),(1,3),(2,3),
+ *                D[4] diagonal; c_{q,alpha} = Tr(H_q P_alpha)/4 (Eq. 4)
+ *   W, bias      device float32 [out_dim][m] and [out_dim]; W may be NULL (no linear
+ *                layer, out ignored); bias may be NULL (zero)
+ *   features     device float32 [n_images][m], q_q = sum_alpha c_{q,alpha} <P_alpha>
+ *   out          device float32 [n_images][out_dim], y = W q + b
+ *   stream       cudaStream_t
+ * The linear layer runs on the tcgen05 tensor cores with a three-term TF32 split
+ * (FP32-level accuracy).  Asynchronous. */
+mps_status ano_features(const void* pauli, int32_t pauli_f64, int64_t n_images, int32_t m,
+                        const float* abd, const float* W, const float* bias, int32_t out_dim,
+                        float* features, float* out, void* stream);
+
+/* ---- diagnostics and control ------------------------------------------------ */
+
+/* Wait for the batch's stream and return the first device-side error, if any. */
+mps_status mps_sync(mps_batch* batch);
+
+/* Thread-local text of the last non-OK status (never NULL). */
+const char* mps_last_error(void);
+
+/* Number of pairs of a p x p image for a pair set: 2p(p-1), plus 2(p-1)^2 for HVD. */
+int64_t mps_pair_count(int32_t p, int32_t pair_set);
+
+/* Copy bond dimensions to the host: out [sum_i (n_i + 1)], image i's block holds
+ * D_0 = 1, D_1, ..., D_{n_i} = 1 (D_k = left bond of site k).  Synchronous. */
+mps_status mps_bond_dims(mps_batch* batch, int32_t* out);
+
+/* Copy per-image discarded weight sum_steps sum(dropped sigma^2)/sum(sigma^2) of
+ * the last circuit to the host, out [n_images].  Synchronous. */
+mps_status mps_discarded_weight(mps_batch* batch, double* out);
+
+/* Kernels this library has launched since it was loaded (all batches). */
+uint64_t mps_launch_count(void);
+
+/* Launch-shape knobs used by the autotuner.  images_per_cta: images (one warp each)
+ * per CTA of the circuit kernel, 1..8; pauli_threads: threads per image in the
+ * Pauli kernel, a multiple of 32 in 32..512.  0 leaves a knob unchanged. */
+mps_status mps_set_launch_shape(mps_batch* batch, int32_t images_per_cta, int32_t pauli_threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPSANO_H */

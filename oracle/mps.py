@@ -46,6 +46,7 @@ class MPS:
             self.A.append(t)
         self.centre = 0  # every site of a product state is both left- and right-orthonormal
         self.discarded = []  # per two-qubit gate: relative discarded weight
+        self.min_gap = float("inf")  # smallest (sigma_keep - sigma_keep+1) / sigma_1 at a real cut
 
     # ---- bonds -------------------------------------------------------------
     def bond_dims(self) -> list:
@@ -91,6 +92,8 @@ class MPS:
         keep = min(chi, 2 * Dl, 2 * Dr)
         total = float(np.sum(S ** 2))
         kept = S[:keep]
+        if len(S) > keep and S[keep] > 1e-13 * S[0]:
+            self.min_gap = min(self.min_gap, float((S[keep - 1] - S[keep]) / S[0]))
         self.discarded.append(float(np.sum(S[keep:] ** 2)) / total if total > 0 else 0.0)
         kept = kept / np.linalg.norm(kept)
         self.A[k] = U[:, :keep].reshape(Dl, 2, keep)

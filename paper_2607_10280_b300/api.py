@@ -1,0 +1,160 @@
+"""Python API over the C ABI.  PyTorch provides device memory and streams; every
+step of the path runs in the CUDA library (``_lib``).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import ANSATZ, PAIR_SET, PRECISION, check, lib, mps_circuit
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pair_count(p: int, pair_set: str = "hv") -> int:
+    return int(lib().mps_pair_count(int(p), PAIR_SET[pair_set]))
+
+
+def launch_count() -> int:
+    return int(lib().mps_launch_count())
+
+
+class Batch:
+    """A batch of images, one MPS each (Sec. II.B, Eq. 3), on one CUDA stream."""
+
+    def __init__(self, p, chi, precision: str = "mixed", stream=None):
+        p = np.atleast_1d(np.asarray(p, dtype=np.int32))
+        self.n_images = len(p)
+        self.p = p
+        self.n = p.astype(np.int64) ** 2
+        chi_arr = np.broadcast_to(np.asarray(chi, dtype=np.int32), p.shape).copy()
+        self.chi = chi_arr
+        self.precision = precision
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        handle = ctypes.c_void_p()
+        check(lib().mps_create_batch(
+            self.n_images, p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            chi_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0, PRECISION[precision],
+            _stream_handle(self.stream), ctypes.byref(handle)))
+        self._h = handle
+        self.pixel_offsets = np.concatenate([[0], np.cumsum(self.n)])
+        self.pair_offsets = np.concatenate([[0], np.cumsum([pair_count(int(q)) for q in p])])
+
+    # -- lifetime ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            check(lib().mps_destroy_batch(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the path ------------------------------------------------------------------
+    def apply_circuit(self, pixels: torch.Tensor, L, ansatz: str = "ladder", params: torch.Tensor = None):
+        """pixels: float64 device tensor, packed [sum n_i]; params: float64 device [L][n][2]."""
+        assert pixels.is_cuda and pixels.dtype == torch.float64 and pixels.is_contiguous()
+        if pixels.numel() != int(self.pixel_offsets[-1]):
+            raise ValueError(f"pixels must hold {int(self.pixel_offsets[-1])} values, got {pixels.numel()}")
+        c = mps_circuit()
+        c.ansatz = ANSATZ[ansatz]
+        L_arr = np.broadcast_to(np.asarray(L, dtype=np.int32), self.p.shape).copy()
+        self._L = L_arr
+        c.L = int(L_arr.max()) if len(L_arr) else 0
+        c.L_per_image = L_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        if params is not None:
+            assert params.is_cuda and params.dtype == torch.float64 and params.is_contiguous()
+            if params.dim() != 3 or params.shape[2] != 2 or params.shape[0] < c.L or params.shape[1] < int(self.n.max()):
+                raise ValueError(f"params must be [>= {c.L}][>= {int(self.n.max())}][2], got {tuple(params.shape)}")
+            c.params = params.data_ptr()
+            c.params_n = params.shape[1]
+        else:
+            c.params = None
+            c.params_n = 0
+        self._pixels_ref, self._params_ref = pixels, params   # keep alive while queued
+        check(lib().mps_apply_circuit(self._h, _ptr(pixels), ctypes.byref(c)))
+
+    def pauli_cache(self, out: torch.Tensor = None) -> torch.Tensor:
+        """Pauli cache [sum m_i][16] (Sec. II.C, Eq. 5), float64 (fp64) or float32."""
+        dtype = torch.float64 if self.precision == "fp64" else torch.float32
+        total = int(self.pair_offsets[-1])
+        if out is None:
+            out = torch.empty((total, 16), dtype=dtype, device="cuda")
+        assert out.dtype == dtype and out.shape == (total, 16) and out.is_contiguous()
+        check(lib().mps_pauli_cache(self._h, PAIR_SET["hv"], _ptr(out), None))
+        return out
+
+    def set_launch_shape(self, images_per_cta: int = 0, pauli_threads: int = 0):
+        check(lib().mps_set_launch_shape(self._h, int(images_per_cta), int(pauli_threads)))
+
+    # -- diagnostics -----------------------------------------------------------------
+    def sync(self):
+        check(lib().mps_sync(self._h))
+
+    def bond_dims(self) -> list:
+        buf = np.zeros(int((self.n + 1).sum()), dtype=np.int32)
+        check(lib().mps_bond_dims(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        out, o = [], 0
+        for n in self.n:
+            out.append(buf[o:o + n + 1].tolist())
+            o += n + 1
+        return out
+
+    def discarded_weight(self) -> np.ndarray:
+        buf = np.zeros(self.n_images, dtype=np.float64)
+        check(lib().mps_discarded_weight(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return buf
+
+
+def ano_features(pauli: torch.Tensor, m: int, abd: torch.Tensor, W: torch.Tensor = None,
+                 bias: torch.Tensor = None, stream=None):
+    """Features q (Eq. 5) and, if W is given, y = W q + b (Eq. 6).
+
+    pauli: [n_images * m, 16] float32/float64; abd: float32 [m][16]; W: float32 [out][m].
+    """
+    n_images = pauli.shape[0] // m
+    feats = torch.empty((n_images, m), dtype=torch.float32, device=pauli.device)
+    out = None
+    out_dim = 0
+    if W is not None:
+        out_dim = W.shape[0]
+        out = torch.empty((n_images, out_dim), dtype=torch.float32, device=pauli.device)
+    check(lib().ano_features(_ptr(pauli), 1 if pauli.dtype == torch.float64 else 0, n_images, m,
+                             _ptr(abd), _ptr(W) if W is not None else None,
+                             _ptr(bias) if bias is not None else None, out_dim, _ptr(feats),
+                             _ptr(out) if out is not None else None, _stream_handle(stream)))
+    return feats, out
+
+
+def extract(pixels, p, L: int, chi: int, precision: str = "mixed", ansatz: str = "ladder",
+            params=None, stream=None) -> torch.Tensor:
+    """One-call Pauli cache for a batch of equal-size images.
+
+    pixels: [B][p*p] (host numpy/torch or device tensor, float64); params: [L][p*p][2].
+    Returns a device tensor [B][m][16].
+    """
+    px = torch.as_tensor(pixels, dtype=torch.float64)
+    B = px.shape[0]
+    px = px.reshape(-1).contiguous().cuda()
+    pr = None
+    if params is not None:
+        pr = torch.as_tensor(params, dtype=torch.float64).contiguous().cuda()
+    batch = Batch(np.full(B, p, dtype=np.int32), chi, precision, stream)
+    batch.apply_circuit(px, L, ansatz, pr)
+    out = batch.pauli_cache()
+    batch.sync()
+    batch.close()
+    return out.reshape(B, -1, 16)

@@ -1,0 +1,64 @@
+// Host-side batch handle shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+#include "mpsano.h"
+
+struct mps_batch {
+    int B = 0;
+    int prec = MPS_MIXED;
+    cudaStream_t stream = nullptr;
+    int ld_max = 1;
+    int n_max = 0;
+    size_t elem = 8;                       // bytes per complex element of the state
+    std::vector<mpsano::ImageMeta> meta_h;
+    std::vector<int32_t> units_h;          // (image, column) pairs of the Pauli kernel
+    mpsano::ImageMeta* meta_d = nullptr;
+    mpsano::ImageMeta* meta_pinned = nullptr;
+    int32_t* units_d = nullptr;
+    void* arena = nullptr;                 // sites
+    void* renv = nullptr;                  // right environments
+    int64_t renv_stride = 0;               // complex elements per image
+    void* norms = nullptr;
+    int32_t* bonds_d = nullptr;
+    double* discarded_d = nullptr;
+    int* status_d = nullptr;
+    int64_t total_pairs_hv = 0, total_pairs_hvd = 0;
+    int64_t total_bonds = 0;
+    bool circuit_done = false;
+    int chi_tpl = 0;                       // kernel CHI bucket of the last circuit
+    int images_per_cta = 2;
+    int pauli_warps = 4;
+};
+
+namespace mpsano {
+
+// Record a thread-local error message and return st.
+mps_status fail(mps_status st, const char* fmt, ...);
+// Count one kernel launch (reported by mps_launch_count).
+void count_launch();
+// Opt-in shared-memory limit per block on the current device.
+int smem_optin_limit();
+
+mps_status launch_circuit_fp64(mps_batch* b, int chi_tpl, bool trunc, const double* px, const double* pr,
+                               int pn, int ansatz);
+mps_status launch_circuit_mixed(mps_batch* b, int chi_tpl, bool trunc, const double* px, const double* pr,
+                                int pn, int ansatz);
+mps_status launch_circuit_orth64(mps_batch* b, int chi_tpl, bool trunc, const double* px, const double* pr,
+                                 int pn, int ansatz);
+mps_status launch_pauli_fp64(mps_batch* b, void* out);
+mps_status launch_pauli_mixed(mps_batch* b, void* out);
+
+}  // namespace mpsano
+
+#define CUDA_TRY(expr)                                                                               \
+    do {                                                                                             \
+        cudaError_t e_ = (expr);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return ::mpsano::fail(e_ == cudaErrorMemoryAllocation ? MPS_ERR_OOM : MPS_ERR_CUDA,      \
+                                  "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)

@@ -1,0 +1,516 @@
+// Circuit kernel: one warp owns one image's MPS (Sec. II.B, Eq. 3) for the whole
+// circuit.  The warp sweeps the chain left to right applying the two-qubit gates
+// in their fixed order; the orthogonality centre travels with the sweep.  Each
+// two-qubit step forms theta = A_k A_{k+1} on the fly (with the one-qubit gates of
+// the layer folded into the load of A_{k+1}), applies the gate as a row/column
+// permutation (CNOT) and splits theta back into two sites:
+//
+//   * min(M, N) <= chi (nothing to truncate): exact split.  N <= M: Householder
+//     QR, A_k = Q, A_{k+1} = R.  M < N: A_k = I_M, A_{k+1} = theta.  The state is
+//     the one the SVD split would give, in another gauge of the new bond.
+//   * min(M, N) > chi: SVD truncation at the orthogonality centre.  Gram matrix of
+//     the smaller side in FP64, cyclic Jacobi eigensolver in FP64 (sigma^2 = its
+//     eigenvalues), keep the chi largest, A_k = U_chi (re-orthogonalised by an FP64
+//     Householder QR when it comes from the right Gram), A_{k+1} = U_chi^H theta
+//     rescaled to unit norm.
+//
+// Before a pass in which some step truncates, a right-to-left LQ sweep moves the
+// centre to the first site of the pass so that every truncation happens at the
+// true orthogonality centre (the sites to its right are right-orthonormal).
+// Passes without truncation skip that sweep: their splits are exact in any gauge.
+// After the last pass the MPS is left-canonical with the centre at site n-1,
+// which is the form the Pauli kernel expects.
+//
+// Shared memory is private to each warp; the kernel has no block-wide barriers.
+#pragma once
+#include "common.cuh"
+#include "linalg.cuh"
+
+namespace mpsano {
+
+constexpr int MAX_QUBITS = 256;  // p <= 16
+
+// Per-warp shared-memory layout.  CHI bounds every bond the images reach.
+template <typename T, typename TQ, int CHI, bool TRUNC>
+struct CircuitLayout {
+    static constexpr int CS = CHI + 1;              // row stride of a site: element (l,s,r) at (2l+s)*CS + r
+    static constexpr int SITE = 2 * CHI * CS;       // complex elements of a site buffer
+    static constexpr int LDM = 2 * CHI + 1;         // column stride of theta (column-major)
+    static constexpr int THETA = 2 * CHI * LDM;
+    static constexpr int K = 2 * CHI;               // largest Gram matrix
+    static constexpr int LDK = K + 1;
+    static constexpr size_t off_cur = 0;
+    static constexpr size_t off_nxt = off_cur + sizeof(cx<T>) * SITE;
+    static constexpr size_t off_rb = off_nxt + sizeof(cx<T>) * SITE;
+    static constexpr size_t off_th = (off_rb + sizeof(cx<T>) * CHI * CS + 15) & ~size_t(15);
+    static constexpr size_t off_tau = off_th + sizeof(cx<TQ>) * THETA;
+    static constexpr size_t off_bd = off_tau + sizeof(cx<TQ>) * K;
+    static constexpr size_t off_gram = (off_bd + sizeof(int) * (MAX_QUBITS + 1) + 15) & ~size_t(15);
+    static constexpr size_t off_vec = off_gram + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
+    static constexpr size_t off_taud = off_vec + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
+    static constexpr size_t off_lam = off_taud + (TRUNC ? sizeof(cx<double>) * K : 0);
+    static constexpr size_t off_ord = off_lam + (TRUNC ? sizeof(double) * K : 0);
+    static constexpr size_t bytes = (off_ord + (TRUNC ? sizeof(int) * K : 0) + 15) & ~size_t(15);
+};
+
+// The 2x2 one-qubit gate applied to site k at the start of a layer.
+template <typename T>
+struct Gate1 { cx<T> u00, u01, u10, u11; };
+
+template <typename T>
+__device__ __forceinline__ Gate1<T> layer_gate(int ansatz, const double* params, int params_n,
+                                              int layer, int k, double x) {
+    double u[8];
+    if (ansatz == 0) {
+        // R_Z(beta) R_Y(alpha)
+        const double a = params[((size_t)layer * params_n + k) * 2 + 0];
+        const double b = params[((size_t)layer * params_n + k) * 2 + 1];
+        double sa, ca, sb, cb;
+        sincos(0.5 * a, &sa, &ca);
+        sincos(0.5 * b, &sb, &cb);
+        // e^{-ib/2} = (cb, -sb), e^{ib/2} = (cb, sb)
+        u[0] = cb * ca;  u[1] = -sb * ca;   // u00 = e^{-ib/2} c
+        u[2] = -cb * sa; u[3] = sb * sa;    // u01 = -e^{-ib/2} s
+        u[4] = cb * sa;  u[5] = sb * sa;    // u10 = e^{ib/2} s
+        u[6] = cb * ca;  u[7] = sb * ca;    // u11 = e^{ib/2} c
+    } else {
+        // R_Y(phi) H, phi = 2 pi x - pi (Eq. 2)
+        double s, c;
+        sincos(0.5 * (2.0 * M_PI * x - M_PI), &s, &c);
+        const double h = 0.70710678118654752440;
+        u[0] = h * (c - s); u[1] = 0.0;   // [c -s; s c] [1 1; 1 -1] / sqrt 2
+        u[2] = h * (c + s); u[3] = 0.0;
+        u[4] = h * (s + c); u[5] = 0.0;
+        u[6] = h * (s - c); u[7] = 0.0;
+    }
+    Gate1<T> g;
+    g.u00 = mk<T>(T(u[0]), T(u[1])); g.u01 = mk<T>(T(u[2]), T(u[3]));
+    g.u10 = mk<T>(T(u[4]), T(u[5])); g.u11 = mk<T>(T(u[6]), T(u[7]));
+    return g;
+}
+
+// Global site (Dl x 2 x Dr, padded [ld][2][ld]) -> shared site buffer, optionally
+// applying a one-qubit gate on the physical index.
+template <typename T, int CS>
+__device__ __forceinline__ void load_site(cx<T>* dst, const cx<T>* src, int ld, int Dl, int Dr,
+                                          const Gate1<T>* g, int lane) {
+    for (int o = lane; o < Dl * Dr; o += 32) {
+        const int l = o / Dr, r = o % Dr;
+        const cx<T> a0 = src[(2 * l) * ld + r], a1 = src[(2 * l + 1) * ld + r];
+        if (g) {
+            dst[(2 * l) * CS + r] = g->u00 * a0 + g->u01 * a1;
+            dst[(2 * l + 1) * CS + r] = g->u10 * a0 + g->u11 * a1;
+        } else {
+            dst[(2 * l) * CS + r] = a0;
+            dst[(2 * l + 1) * CS + r] = a1;
+        }
+    }
+}
+
+template <typename T, int CS>
+__device__ __forceinline__ void store_site(cx<T>* dst, const cx<T>* src, int ld, int Dl, int Dr, int lane) {
+    for (int o = lane; o < 2 * Dl * Dr; o += 32) {
+        const int row = o / Dr, r = o % Dr;
+        dst[row * ld + r] = src[row * CS + r];
+    }
+}
+
+template <typename T, int CS>
+__device__ __forceinline__ void apply_gate_smem(cx<T>* site, int Dl, int Dr, const Gate1<T>& g, int lane) {
+    for (int o = lane; o < Dl * Dr; o += 32) {
+        const int l = o / Dr, r = o % Dr;
+        const cx<T> a0 = site[(2 * l) * CS + r], a1 = site[(2 * l + 1) * CS + r];
+        site[(2 * l) * CS + r] = g.u00 * a0 + g.u01 * a1;
+        site[(2 * l + 1) * CS + r] = g.u10 * a0 + g.u11 * a1;
+    }
+}
+
+template <typename T, typename TQ, int CHI, bool TRUNC>
+struct CircuitWarp {
+    using Lay = CircuitLayout<T, TQ, CHI, TRUNC>;
+    static constexpr int CS = Lay::CS, LDM = Lay::LDM, LDK = Lay::LDK;
+
+    cx<T>* cur;   // centre tensor of the sweep
+    cx<T>* nxt;   // next site
+    cx<T>* rb;    // small triangular factor
+    cx<TQ>* th;   // theta, column-major M x N, rows (l,s), columns (t,r)
+    cx<TQ>* tau;
+    int* bd;      // bd[k] = left bond of site k, k = 0..n
+    cx<double>* G;
+    cx<double>* V;
+    cx<double>* taud;
+    double* lam;
+    int* ord;
+    int lane, n, chi, ld;
+    cx<T>* sites;        // this image's site 0 in the arena
+    double discarded;
+    int* status;
+
+    __device__ cx<T>* site_ptr(int k) const { return sites + (size_t)k * (2 * ld * ld); }
+
+    // ---- theta = cur(Dl x 2 x Dm) nxt(Dm x 2 x Dr), CNOT(control = left) folded in ----
+    __device__ void form_theta(int Dl, int Dm, int Dr, bool cnot) {
+        const int M = 2 * Dl, N = 2 * Dr;
+        for (int o = lane; o < M * N; o += 32) {
+            const int row = o / N, c = o % N;
+            const int s = row & 1;
+            int t = c / Dr;
+            const int r = c % Dr;
+            if (cnot && s) t ^= 1;
+            cx<T> acc = czero<T>();
+            const cx<T>* a = cur + row * CS;
+            const cx<T>* b = nxt + t * CS + r;
+#pragma unroll 4
+            for (int m = 0; m < Dm; ++m) cmac(acc, a[m], b[2 * m * CS]);
+            th[c * LDM + row] = cvt<TQ>(acc);
+        }
+        __syncwarp();
+    }
+
+    // ---- split theta (M x N) into site k (written to global) and cur (new centre) ----
+    // Returns the new bond dimension.
+    __device__ int split(int k, int Dl, int Dr, bool allow_trunc) {
+        const int M = 2 * Dl, N = 2 * Dr;
+        const int mn = M < N ? M : N;
+        if (mn <= chi || !allow_trunc) {
+            if (N <= M) {
+                // Householder QR: A_k = Q (M x N), cur = R (N x N) reshaped (N, 2, Dr)
+                warp_qr<TQ>(th, LDM, M, N, tau, lane);
+                for (int o = lane; o < N * N; o += 32) {
+                    const int i = o / N, c = o % N;
+                    const int t = c / Dr, r = c % Dr;
+                    const cx<TQ> v = (i <= c) ? th[c * LDM + i] : czero<TQ>();
+                    cur[(2 * i + t) * CS + r] = cvt<T>(v);
+                }
+                __syncwarp();
+                warp_form_q<TQ>(th, LDM, M, N, tau, lane);
+                cx<T>* dst = site_ptr(k);
+                for (int o = lane; o < M * N; o += 32) {
+                    const int row = o / N, c = o % N;
+                    dst[row * ld + c] = cvt<T>(th[c * LDM + row]);
+                }
+                __syncwarp();
+                return N;
+            }
+            // M < N: A_k = I_M, cur = theta reshaped (M, 2, Dr)
+            cx<T>* dst = site_ptr(k);
+            for (int o = lane; o < M * M; o += 32) {
+                const int row = o / M, c = o % M;
+                dst[row * ld + c] = mk<T>(T(row == c ? 1 : 0), T(0));
+            }
+            for (int o = lane; o < M * N; o += 32) {
+                const int i = o / N, c = o % N;
+                const int t = c / Dr, r = c % Dr;
+                cur[(2 * i + t) * CS + r] = cvt<T>(th[c * LDM + i]);
+            }
+            __syncwarp();
+            return M;
+        }
+        if constexpr (TRUNC) {
+            return svd_truncate(k, Dl, Dr);
+        } else {
+            raise_status(status, DEV_BAD_SHAPE);
+            return chi;
+        }
+    }
+
+    // SVD truncation to chi of theta (M x N), min(M, N) > chi.
+    __device__ int svd_truncate(int k, int Dl, int Dr) {
+        const int M = 2 * Dl, N = 2 * Dr;
+        const bool left = M <= N;      // Gram of the row space (M x M) or column space (N x N)
+        const int K = left ? M : N;
+        // G = theta theta^H (left) or theta^H theta, accumulated in FP64
+        for (int o = lane; o < K * K; o += 32) {
+            const int i = o / K, j = o % K;   // G[i][j], column-major store G[j*LDK + i]
+            if (j < i) continue;
+            cx<double> acc = czero<double>();
+            if (left) {
+                for (int c = 0; c < N; ++c)
+                    cmac(acc, cvt<double>(th[c * LDM + i]), conj(cvt<double>(th[c * LDM + j])));
+            } else {
+                for (int r = 0; r < M; ++r)
+                    cmac_cj(acc, cvt<double>(th[i * LDM + r]), cvt<double>(th[j * LDM + r]));
+            }
+            G[j * LDK + i] = acc;
+            G[i * LDK + j] = conj(acc);
+        }
+        __syncwarp();
+        warp_jacobi_eigh(G, V, LDK, K, lane, 40);
+        // rank the eigenvalues (descending, ties by index) and record the discarded weight
+        for (int i = lane; i < K; i += 32) lam[i] = G[i * LDK + i].re;
+        __syncwarp();
+        double tot = 0.0, drop = 0.0;
+        for (int i = lane; i < K; i += 32) {
+            const double li = lam[i];
+            int rank = 0;
+            for (int j = 0; j < K; ++j) rank += (lam[j] > li) || (lam[j] == li && j < i);
+            ord[rank] = i;
+            const double w = li > 0.0 ? li : 0.0;
+            tot += w;
+            if (rank >= chi) drop += w;
+        }
+        tot = warp_sum(tot);
+        drop = warp_sum(drop);
+        if (tot > 0.0) discarded += drop / tot;
+        __syncwarp();
+        const int D = chi;
+        // U_chi (M x D, FP64) into the Gram buffer
+        cx<double>* U = G;
+        if (left) {
+            for (int o = lane; o < M * D; o += 32) {
+                const int r = o % M, c = o / M;
+                U[c * LDK + r] = V[ord[c] * LDK + r];
+            }
+            __syncwarp();
+        } else {
+            // X = theta V_chi (M x D), then U = Q of its FP64 Householder QR
+            for (int o = lane; o < M * D; o += 32) {
+                const int r = o % M, c = o / M;
+                const cx<double>* v = V + ord[c] * LDK;
+                cx<double> acc = czero<double>();
+                for (int j = 0; j < N; ++j) cmac(acc, cvt<double>(th[j * LDM + r]), v[j]);
+                U[c * LDK + r] = acc;
+            }
+            __syncwarp();
+            warp_qr<double>(U, LDK, M, D, taud, lane);
+            warp_form_q<double>(U, LDK, M, D, taud, lane);
+        }
+        // A_k = U (Dl x 2 x D)
+        cx<T>* dst = site_ptr(k);
+        for (int o = lane; o < M * D; o += 32) {
+            const int row = o / D, c = o % D;
+            dst[row * ld + c] = cvt<T>(U[c * LDK + row]);
+        }
+        // cur = U^H theta (D x N), FP64 accumulation, then unit Frobenius norm
+        double nrm = 0.0;
+        for (int o = lane; o < D * N; o += 32) {
+            const int i = o / N, c = o % N;
+            cx<double> acc = czero<double>();
+            for (int r = 0; r < M; ++r) cmac_cj(acc, U[i * LDK + r], cvt<double>(th[c * LDM + r]));
+            nrm += norm2(acc);
+            V[c * LDK + i] = acc;   // V is free now
+        }
+        nrm = warp_sum(nrm);
+        __syncwarp();
+        const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+        for (int o = lane; o < D * N; o += 32) {
+            const int i = o / N, c = o % N;
+            const int t = c / Dr, r = c % Dr;
+            cur[(2 * i + t) * CS + r] = cvt<T>(inv * V[c * LDK + i]);
+        }
+        __syncwarp();
+        return D;
+    }
+
+    // Exact centre move one site right: cur (Dl x 2 x Dm) = Q R, site k = Q,
+    // cur <- R * nxt.  Returns the new bond min(2 Dl, Dm).
+    __device__ int move_right(int k, int Dl, int Dm, int Dr) {
+        const int M = 2 * Dl, N = Dm;
+        for (int o = lane; o < M * N; o += 32) {
+            const int row = o / N, c = o % N;
+            th[c * LDM + row] = cvt<TQ>(cur[row * CS + c]);
+        }
+        __syncwarp();
+        warp_qr<TQ>(th, LDM, M, N, tau, lane);
+        const int Kd = M < N ? M : N;
+        for (int o = lane; o < Kd * N; o += 32) {
+            const int i = o / N, c = o % N;
+            rb[i * CS + c] = cvt<T>(i <= c ? th[c * LDM + i] : czero<TQ>());
+        }
+        __syncwarp();
+        warp_form_q<TQ>(th, LDM, M, Kd, tau, lane);
+        cx<T>* dst = site_ptr(k);
+        for (int o = lane; o < M * Kd; o += 32) {
+            const int row = o / Kd, c = o % Kd;
+            dst[row * ld + c] = cvt<T>(th[c * LDM + row]);
+        }
+        // cur(i, t, r) = sum_m R(i, m) nxt(m, t, r)
+        for (int o = lane; o < Kd * 2 * Dr; o += 32) {
+            const int i = o / (2 * Dr), tr = o % (2 * Dr);
+            const int t = tr / Dr, r = tr % Dr;
+            cx<T> acc = czero<T>();
+            for (int m = i; m < N; ++m) cmac(acc, rb[i * CS + m], nxt[(2 * m + t) * CS + r]);
+            cur[(2 * i + t) * CS + r] = acc;
+        }
+        __syncwarp();
+        return Kd;
+    }
+
+    // Exact centre move one site left (LQ): site k (held in cur, Dl x 2 x Dr) = L Q,
+    // site k = Q, cur <- site_{k-1} L.  Returns the new bond min(Dl, 2 Dr).
+    __device__ int move_left(int k, int Dlm, int Dl, int Dr) {
+        const int M = 2 * Dr, N = Dl;   // A^H is (2 Dr) x Dl
+        for (int o = lane; o < M * N; o += 32) {
+            const int l = o / M, sr = o % M;
+            const int s = sr / Dr, r = sr % Dr;
+            th[l * LDM + sr] = conj(cvt<TQ>(cur[(2 * l + s) * CS + r]));
+        }
+        __syncwarp();
+        warp_qr<TQ>(th, LDM, M, N, tau, lane);
+        const int Kd = M < N ? M : N;
+        for (int o = lane; o < Kd * N; o += 32) {
+            const int i = o / N, c = o % N;
+            rb[i * CS + c] = cvt<T>(i <= c ? th[c * LDM + i] : czero<TQ>());   // R'(i, c)
+        }
+        __syncwarp();
+        warp_form_q<TQ>(th, LDM, M, Kd, tau, lane);
+        // site k = Q'^H : (Kd x 2 x Dr), element (m, s, r) = conj(Q'(s*Dr + r, m))
+        cx<T>* dst = site_ptr(k);
+        for (int o = lane; o < Kd * M; o += 32) {
+            const int m = o / M, sr = o % M;
+            const int s = sr / Dr, r = sr % Dr;
+            dst[(2 * m + s) * ld + r] = conj(cvt<T>(th[m * LDM + sr]));
+        }
+        __syncwarp();
+        // cur <- site_{k-1} (Dlm x 2 x Dl) times L = R'^H (Dl x Kd)
+        load_site<T, CS>(nxt, site_ptr(k - 1), ld, Dlm, Dl, nullptr, lane);
+        __syncwarp();
+        for (int o = lane; o < 2 * Dlm * Kd; o += 32) {
+            const int row = o / Kd, m = o % Kd;
+            cx<T> acc = czero<T>();
+            for (int l = m; l < Dl; ++l) cmac_cj(acc, rb[m * CS + l], nxt[row * CS + l]);
+            cur[row * CS + m] = acc;
+        }
+        __syncwarp();
+        return Kd;
+    }
+};
+
+// Pass description: bonds first..n-2; at bond k a CNOT if (k - first) % stride == 0
+// (ladder: stride 1), otherwise an exact centre move.
+template <typename T, typename TQ, int CHI, bool TRUNC>
+__device__ bool run_pass(CircuitWarp<T, TQ, CHI, TRUNC>& w, int first, int stride,
+                         int ansatz, const double* params, int params_n, int layer,
+                         const double* px, bool gates_on_load, bool fresh) {
+    constexpr int CS = CircuitWarp<T, TQ, CHI, TRUNC>::CS;
+    const int n = w.n, lane = w.lane;
+    int* bd = w.bd;
+    // does any step of this pass truncate?  (bond dimensions only; lane 0)
+    int trunc = 0;
+    if (lane == 0) {
+        int dl = bd[first];
+        for (int k = first; k < n - 1; ++k) {
+            if ((k - first) % stride == 0) {
+                const int m = 2 * dl, nn = 2 * bd[k + 2];
+                const int mn = m < nn ? m : nn;
+                if (mn > w.chi) trunc = 1;
+                dl = mn < w.chi ? mn : w.chi;
+            } else {
+                const int m = 2 * dl;
+                dl = m < bd[k + 1] ? m : bd[k + 1];
+            }
+        }
+    }
+    trunc = __shfl_sync(0xffffffffu, trunc, 0);
+    if (trunc && TRUNC && !fresh) {
+        // right-to-left LQ sweep: centre from n-1 (held in cur) to `first`.  A fresh
+        // product state needs none: its normalised sites are right-orthonormal.
+        for (int k = n - 1; k > first; --k) {
+            const int nb = w.move_left(k, bd[k - 1], bd[k], bd[k + 1]);
+            if (lane == 0) bd[k] = nb;
+            __syncwarp();
+        }
+    } else {
+        // the centre stays where it is; the pass starts from the stored site `first`
+        load_site<T, CS>(w.cur, w.site_ptr(first), w.ld, bd[first], bd[first + 1], nullptr, lane);
+        __syncwarp();
+    }
+    if (gates_on_load) {
+        const Gate1<T> g = layer_gate<T>(ansatz, params, params_n, layer, first, px[first]);
+        apply_gate_smem<T, CS>(w.cur, bd[first], bd[first + 1], g, lane);
+        __syncwarp();
+    }
+    for (int k = first; k < n - 1; ++k) {
+        const int Dl = bd[k], Dm = bd[k + 1], Dr = bd[k + 2];
+        if (gates_on_load) {
+            const Gate1<T> g = layer_gate<T>(ansatz, params, params_n, layer, k + 1, px[k + 1]);
+            load_site<T, CS>(w.nxt, w.site_ptr(k + 1), w.ld, Dm, Dr, &g, lane);
+        } else {
+            load_site<T, CS>(w.nxt, w.site_ptr(k + 1), w.ld, Dm, Dr, nullptr, lane);
+        }
+        __syncwarp();
+        int nb;
+        if ((k - first) % stride == 0) {
+            w.form_theta(Dl, Dm, Dr, true);
+            nb = w.split(k, Dl, Dr, trunc != 0);
+        } else {
+            nb = w.move_right(k, Dl, Dm, Dr);
+        }
+        if (nb > CHI || nb > w.ld) {  // never expected: the host sizes CHI and ld from a dry run
+            raise_status(w.status, DEV_BOND_OVERFLOW);
+            return false;
+        }
+        if (lane == 0) bd[k + 1] = nb;
+        __syncwarp();
+    }
+    store_site<T, CS>(w.site_ptr(n - 1), w.cur, w.ld, bd[n - 1], bd[n], lane);
+    __syncwarp();
+    return true;
+}
+
+template <typename T, typename TQ, int CHI, bool TRUNC>
+__global__ void __launch_bounds__(256) circuit_kernel(
+    const ImageMeta* __restrict__ meta, int n_images, const double* __restrict__ pixels,
+    const double* __restrict__ params, int params_n, int ansatz,
+    cx<T>* __restrict__ arena, int32_t* __restrict__ bonds_out,
+    double* __restrict__ discarded_out, int* status) {
+    using Lay = CircuitLayout<T, TQ, CHI, TRUNC>;
+    constexpr int CS = Lay::CS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int img = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (img >= n_images) return;
+    unsigned char* base = smem_raw + (size_t)warp * Lay::bytes;
+
+    const ImageMeta mt = meta[img];
+    CircuitWarp<T, TQ, CHI, TRUNC> w;
+    w.cur = reinterpret_cast<cx<T>*>(base + Lay::off_cur);
+    w.nxt = reinterpret_cast<cx<T>*>(base + Lay::off_nxt);
+    w.rb = reinterpret_cast<cx<T>*>(base + Lay::off_rb);
+    w.th = reinterpret_cast<cx<TQ>*>(base + Lay::off_th);
+    w.tau = reinterpret_cast<cx<TQ>*>(base + Lay::off_tau);
+    w.bd = reinterpret_cast<int*>(base + Lay::off_bd);
+    w.G = reinterpret_cast<cx<double>*>(base + Lay::off_gram);
+    w.V = reinterpret_cast<cx<double>*>(base + Lay::off_vec);
+    w.taud = reinterpret_cast<cx<double>*>(base + Lay::off_taud);
+    w.lam = reinterpret_cast<double*>(base + Lay::off_lam);
+    w.ord = reinterpret_cast<int*>(base + Lay::off_ord);
+    w.lane = lane;
+    w.n = mt.n;
+    w.chi = mt.chi < CHI ? mt.chi : CHI;
+    w.ld = mt.ld;
+    w.sites = arena + mt.site_off;
+    w.discarded = 0.0;
+    w.status = status;
+    const double* px = pixels + mt.pixel_off;
+    const int n = mt.n;
+
+    // |0...0> then the encoding R_Y(pi x) (ladder); every bond is 1
+    for (int k = lane; k <= n; k += 32) w.bd[k] = 1;
+    for (int k = lane; k < n; k += 32) {
+        cx<T>* s = w.site_ptr(k);
+        double sn = 0.0, cs = 1.0;
+        if (ansatz == 0) sincos(0.5 * M_PI * px[k], &sn, &cs);
+        s[0] = mk<T>(T(cs), T(0));
+        s[w.ld] = mk<T>(T(sn), T(0));
+    }
+    __syncwarp();
+    for (int layer = 0; layer < mt.L; ++layer) {
+        bool ok;
+        if (ansatz == 0) {
+            ok = run_pass<T, TQ, CHI, TRUNC>(w, 0, 1, ansatz, params, params_n, layer, px, true, layer == 0);
+        } else {
+            ok = run_pass<T, TQ, CHI, TRUNC>(w, 0, 2, ansatz, params, params_n, layer, px, true, layer == 0);
+            if (ok && n > 2) ok = run_pass<T, TQ, CHI, TRUNC>(w, 1, 2, ansatz, params, params_n, layer, px, false, false);
+        }
+        if (!ok) return;
+    }
+    // A pass ends with the centre at n-1.  The paper ansatz's second pass leaves
+    // site 0 as written by the first pass (left-orthonormal), so the whole chain is
+    // left-canonical either way.
+    for (int k = lane; k <= n; k += 32) bonds_out[mt.bond_off + k] = w.bd[k];
+    if (lane == 0) discarded_out[img] = w.discarded;
+    (void)CS;
+}
+
+}  // namespace mpsano

@@ -1,0 +1,64 @@
+// Device-side helpers shared by the MPS kernels: a minimal complex type, warp
+// reductions and the per-image metadata record.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpsano {
+
+template <typename T>
+struct __align__(2 * sizeof(T)) cx {
+    T re, im;
+};
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { cx<T> z; z.re = r; z.im = i; return z; }
+template <typename T> __device__ __forceinline__ cx<T> czero() { return mk<T>(T(0), T(0)); }
+template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk<T>(a.re + b.re, a.im + b.im); }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk<T>(a.re - b.re, a.im - b.im); }
+template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return mk<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk<T>(s * a.re, s * a.im); }
+template <typename T> __device__ __forceinline__ cx<T> conj(cx<T> a) { return mk<T>(a.re, -a.im); }
+template <typename T> __device__ __forceinline__ T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+// acc += a * b
+template <typename T> __device__ __forceinline__ void cmac(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re); acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im); acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename T> __device__ __forceinline__ void cmac_cj(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re); acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im); acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename To, typename Ti> __device__ __forceinline__ cx<To> cvt(cx<Ti> a) {
+    return mk<To>(To(a.re), To(a.im));
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per-image record, built on the host, read by every kernel.
+struct ImageMeta {
+    int32_t p;          // image side
+    int32_t n;          // qubits = p*p
+    int32_t chi;        // bond cap
+    int32_t L;          // layers of the last circuit
+    int32_t ld;         // site-tensor padding: a site is [ld][2][ld], element (l,s,r) at (2l+s)*ld+r
+    int32_t bond_off;   // offset of this image's bond array (n+1 entries)
+    int64_t site_off;   // offset (in complex elements) of site 0 in the arena
+    int64_t pixel_off;  // offset of the image's pixels in the packed pixel array
+    int64_t pair_off;   // offset (in pairs) of the image's Pauli-cache block
+};
+
+// Device status word: first error wins.
+enum : int { DEV_OK = 0, DEV_BOND_OVERFLOW = 1, DEV_SMEM_OVERFLOW = 2, DEV_BAD_SHAPE = 3 };
+
+__device__ __forceinline__ void raise_status(int* status, int code) {
+    if (status) atomicCAS(status, DEV_OK, code);
+}
+
+}  // namespace mpsano

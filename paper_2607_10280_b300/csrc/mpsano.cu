@@ -1,0 +1,359 @@
+// Host side of the C ABI declared in include/mpsano.h: batch handles, metadata,
+// launch-shape selection and template dispatch of the kernels.
+#include "mpsano.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "batch.h"
+#include "common.cuh"
+#include "epilogue.cuh"
+
+using namespace mpsano;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+std::atomic<uint64_t> g_launches{0};
+
+}  // namespace
+
+namespace mpsano {
+
+void count_launch() { g_launches.fetch_add(1); }
+
+mps_status fail(mps_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+
+
+int smem_optin_limit() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v > 0 ? v : 48 * 1024;
+}
+
+}  // namespace mpsano
+
+namespace {
+
+// Bond dimensions reachable by one image, simulated on dimensions only with the
+// same rules as the circuit kernel.  Returns the largest bond; sets *trunc if any
+// two-qubit step must truncate.
+int dry_run_bonds(int n, int L, int chi, int ansatz, bool* trunc) {
+    std::vector<int> bd(n + 1, 1);
+    int mx = 1;
+    bool any = false;
+    auto pass = [&](int first, int stride) {
+        bool t = false;
+        int dl = bd[first];
+        for (int k = first; k < n - 1; ++k) {
+            if ((k - first) % stride == 0) {
+                const int m = 2 * dl, nn = 2 * bd[k + 2];
+                const int mn = std::min(m, nn);
+                if (mn > chi) t = true;
+                dl = std::min(mn, chi);
+            } else {
+                dl = std::min(2 * dl, bd[k + 1]);
+            }
+        }
+        if (t) {  // centre moves right-to-left (LQ) before the pass
+            for (int k = n - 1; k > first; --k) bd[k] = std::min(bd[k], 2 * bd[k + 1]);
+        }
+        for (int k = first; k < n - 1; ++k) {
+            int nb;
+            if ((k - first) % stride == 0) {
+                const int m = 2 * bd[k], nn = 2 * bd[k + 2];
+                nb = std::min(chi, std::min(m, nn));
+            } else {
+                nb = std::min(2 * bd[k], bd[k + 1]);
+            }
+            bd[k + 1] = nb;
+            mx = std::max(mx, nb);
+        }
+        any = any || t;
+    };
+    for (int l = 0; l < L; ++l) {
+        if (ansatz == MPS_ANSATZ_LADDER) {
+            pass(0, 1);
+        } else {
+            pass(0, 2);
+            if (n > 2) pass(1, 2);
+        }
+    }
+    *trunc = any;
+    return mx;
+}
+
+int chi_bucket(int mx) {
+    for (int c : {4, 8, 16, 32})
+        if (mx <= c) return c;
+    return -1;
+}
+
+}  // namespace
+
+
+
+namespace {
+
+void free_batch(mps_batch* b) {
+    if (!b) return;
+    cudaFree(b->meta_d);
+    cudaFreeHost(b->meta_pinned);
+    cudaFree(b->units_d);
+    cudaFree(b->arena);
+    cudaFree(b->renv);
+    cudaFree(b->norms);
+    cudaFree(b->bonds_d);
+    cudaFree(b->discarded_d);
+    cudaFree(b->status_d);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mps_last_error(void) { return g_err.c_str(); }
+
+uint64_t mps_launch_count(void) { return g_launches.load(); }
+
+int64_t mps_pair_count(int32_t p, int32_t pair_set) {
+    if (p < 1) return 0;
+    int64_t m = 2LL * p * (p - 1);
+    if (pair_set == MPS_PAIRS_HVD) m += 2LL * (p - 1) * (p - 1);
+    return m;
+}
+
+mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* chi, int32_t chi_all,
+                            int32_t prec, void* stream, mps_batch** out) {
+    if (!out) return fail(MPS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_images <= 0) return fail(MPS_ERR_INVALID_ARG, "n_images must be positive, got %d", n_images);
+    if (!p) return fail(MPS_ERR_INVALID_ARG, "p is NULL");
+    if (prec != MPS_FP64 && prec != MPS_MIXED && prec != MPS_MIXED_ORTH64)
+        return fail(MPS_ERR_INVALID_ARG, "unknown precision %d", prec);
+    mps_batch* b = new (std::nothrow) mps_batch();
+    if (!b) return fail(MPS_ERR_OOM, "host allocation failed");
+    b->B = n_images;
+    b->prec = prec;
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    b->elem = prec == MPS_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
+    b->meta_h.resize(n_images);
+    int64_t site_off = 0, pix = 0, pair = 0, bond = 0, renv_max = 0;
+    for (int i = 0; i < n_images; ++i) {
+        const int pi = p[i];
+        const int ci = chi ? chi[i] : chi_all;
+        if (pi < 2 || pi > 16) { delete b; return fail(MPS_ERR_INVALID_ARG, "p[%d] = %d outside 2..16", i, pi); }
+        if (ci < 1 || ci > 64) { delete b; return fail(MPS_ERR_INVALID_ARG, "chi[%d] = %d outside 1..64", i, ci); }
+        const int n = pi * pi;
+        // largest bond any circuit can reach: min(chi, 2^floor(n/2))
+        int cap = 1;
+        while (cap < ci && cap < (1 << std::min(n / 2, 20))) cap <<= 1;
+        cap = std::min(cap, ci);
+        int ld = 4;
+        while (ld < cap) ld <<= 1;
+        ImageMeta& m = b->meta_h[i];
+        m.p = pi; m.n = n; m.chi = ci; m.L = 0; m.ld = ld;
+        m.bond_off = (int32_t)bond;
+        m.site_off = site_off;
+        m.pixel_off = pix;
+        m.pair_off = pair;
+        site_off += (int64_t)n * 2 * ld * ld;
+        pix += n;
+        pair += mps_pair_count(pi, MPS_PAIRS_HV);
+        bond += n + 1;
+        b->ld_max = std::max(b->ld_max, ld);
+        b->n_max = std::max(b->n_max, n);
+        for (int c = 0; c < pi; ++c) { b->units_h.push_back(i); b->units_h.push_back(c); }
+    }
+    renv_max = (int64_t)b->n_max * b->ld_max * b->ld_max;  // R_j of any image at any kernel bucket
+    b->total_pairs_hv = pair;
+    b->total_bonds = bond;
+    b->renv_stride = renv_max;
+    auto bail = [&](mps_status st) { free_batch(b); return st; };
+#define TRY_ALLOC(expr)                                                                         \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            fail(e_ == cudaErrorMemoryAllocation ? MPS_ERR_OOM : MPS_ERR_CUDA, "%s: %s", #expr, \
+                 cudaGetErrorString(e_));                                                       \
+            return bail(e_ == cudaErrorMemoryAllocation ? MPS_ERR_OOM : MPS_ERR_CUDA);          \
+        }                                                                                       \
+    } while (0)
+    TRY_ALLOC(cudaMalloc(&b->meta_d, sizeof(ImageMeta) * n_images));
+    TRY_ALLOC(cudaMallocHost(&b->meta_pinned, sizeof(ImageMeta) * n_images));
+    TRY_ALLOC(cudaMalloc(&b->units_d, sizeof(int32_t) * b->units_h.size()));
+    TRY_ALLOC(cudaMalloc(&b->arena, b->elem * site_off));
+    TRY_ALLOC(cudaMalloc(&b->renv, b->elem * renv_max * n_images));
+    TRY_ALLOC(cudaMalloc(&b->norms, sizeof(double) * n_images));
+    TRY_ALLOC(cudaMalloc(&b->bonds_d, sizeof(int32_t) * bond));
+    TRY_ALLOC(cudaMalloc(&b->discarded_d, sizeof(double) * n_images));
+    TRY_ALLOC(cudaMalloc(&b->status_d, sizeof(int)));
+    TRY_ALLOC(cudaMemsetAsync(b->status_d, 0, sizeof(int), b->stream));
+    TRY_ALLOC(cudaMemsetAsync(b->discarded_d, 0, sizeof(double) * n_images, b->stream));
+    TRY_ALLOC(cudaMemcpyAsync(b->units_d, b->units_h.data(), sizeof(int32_t) * b->units_h.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+    std::memcpy(b->meta_pinned, b->meta_h.data(), sizeof(ImageMeta) * n_images);
+    TRY_ALLOC(cudaMemcpyAsync(b->meta_d, b->meta_pinned, sizeof(ImageMeta) * n_images,
+                              cudaMemcpyHostToDevice, b->stream));
+    TRY_ALLOC(cudaStreamSynchronize(b->stream));
+#undef TRY_ALLOC
+    *out = b;
+    return MPS_OK;
+}
+
+mps_status mps_destroy_batch(mps_batch* b) {
+    if (!b) return MPS_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return MPS_OK;
+}
+
+mps_status mps_set_launch_shape(mps_batch* b, int32_t images_per_cta, int32_t pauli_threads) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    if (images_per_cta < 0 || images_per_cta > 8) return fail(MPS_ERR_INVALID_ARG, "images_per_cta %d", images_per_cta);
+    if (pauli_threads < 0 || pauli_threads > 512 || pauli_threads % 32)
+        return fail(MPS_ERR_INVALID_ARG, "pauli_threads %d", pauli_threads);
+    if (images_per_cta) b->images_per_cta = images_per_cta;
+    if (pauli_threads) b->pauli_warps = pauli_threads / 32;
+    return MPS_OK;
+}
+
+mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circuit* circ) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    if (!pixels) return fail(MPS_ERR_INVALID_ARG, "pixels is NULL");
+    if (!circ) return fail(MPS_ERR_INVALID_ARG, "circuit is NULL");
+    if (circ->ansatz != MPS_ANSATZ_LADDER && circ->ansatz != MPS_ANSATZ_PAPER)
+        return fail(MPS_ERR_INVALID_ARG, "unknown ansatz %d", circ->ansatz);
+    int L_max = 0;
+    for (int i = 0; i < b->B; ++i) {
+        const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
+        if (L < 0 || L > 64) return fail(MPS_ERR_INVALID_ARG, "L[%d] = %d outside 0..64", i, L);
+        L_max = std::max(L_max, L);
+    }
+    if (circ->ansatz == MPS_ANSATZ_LADDER && L_max > 0) {
+        if (!circ->params) return fail(MPS_ERR_INVALID_ARG, "ladder ansatz needs params");
+        if (circ->params_n < b->n_max)
+            return fail(MPS_ERR_INVALID_ARG, "params_n = %d < largest n = %d", circ->params_n, b->n_max);
+    }
+    // bond dimensions, shared-memory bucket and truncation per image
+    int mx = 1;
+    bool trunc = false;
+    bool changed = false;
+    for (int i = 0; i < b->B; ++i) {
+        ImageMeta& m = b->meta_h[i];
+        const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
+        if (m.L != L) { m.L = L; changed = true; }
+        bool t = false;
+        const int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
+        if (bi > m.ld) return fail(MPS_ERR_UNSUPPORTED, "image %d reaches bond %d > padding %d", i, bi, m.ld);
+        mx = std::max(mx, bi);
+        trunc = trunc || t;
+    }
+    const int chi_tpl = chi_bucket(mx);
+    if (chi_tpl < 0) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > 32 not supported", mx);
+    if (changed) {
+        CUDA_TRY(cudaStreamSynchronize(b->stream));  // pinned staging may still be in flight
+        std::memcpy(b->meta_pinned, b->meta_h.data(), sizeof(ImageMeta) * b->B);
+        CUDA_TRY(cudaMemcpyAsync(b->meta_d, b->meta_pinned, sizeof(ImageMeta) * b->B,
+                                 cudaMemcpyHostToDevice, b->stream));
+    }
+    mps_status st;
+    const double* pr = circ->ansatz == MPS_ANSATZ_LADDER ? circ->params : nullptr;
+    switch (b->prec) {
+        case MPS_FP64: st = launch_circuit_fp64(b, chi_tpl, trunc, pixels, pr, circ->params_n, circ->ansatz); break;
+        case MPS_MIXED: st = launch_circuit_mixed(b, chi_tpl, trunc, pixels, pr, circ->params_n, circ->ansatz); break;
+        default: st = launch_circuit_orth64(b, chi_tpl, trunc, pixels, pr, circ->params_n, circ->ansatz); break;
+    }
+    if (st != MPS_OK) return st;
+    b->chi_tpl = chi_tpl;
+    b->circuit_done = true;
+    return MPS_OK;
+}
+
+mps_status mps_pauli_cache(mps_batch* b, int32_t pair_set, void* out, int64_t* pair_offsets) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    if (!out) return fail(MPS_ERR_INVALID_ARG, "out is NULL");
+    if (pair_set != MPS_PAIRS_HV && pair_set != MPS_PAIRS_HVD)
+        return fail(MPS_ERR_INVALID_ARG, "unknown pair set %d", pair_set);
+    if (pair_set == MPS_PAIRS_HVD) return fail(MPS_ERR_UNSUPPORTED, "diagonal pairs are not built yet");
+    if (!b->circuit_done) return fail(MPS_ERR_NOT_READY, "no circuit has run on this batch");
+    if (pair_offsets) {
+        pair_offsets[0] = 0;
+        for (int i = 0; i < b->B; ++i) pair_offsets[i + 1] = pair_offsets[i] + mps_pair_count(b->meta_h[i].p, pair_set);
+    }
+    if (b->prec == MPS_FP64) return launch_pauli_fp64(b, out);
+    return launch_pauli_mixed(b, out);
+}
+
+mps_status ano_features(const void* pauli, int32_t pauli_f64, int64_t n_images, int32_t m, const float* abd,
+                        const float* W, const float* bias, int32_t out_dim, float* features, float* out,
+                        void* stream) {
+    if (!pauli || !abd || !features) return fail(MPS_ERR_INVALID_ARG, "pauli, abd and features must be non-NULL");
+    if (n_images <= 0 || m <= 0) return fail(MPS_ERR_INVALID_ARG, "n_images and m must be positive");
+    if (W && (!out || out_dim <= 0)) return fail(MPS_ERR_INVALID_ARG, "linear layer needs out and out_dim > 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t tot = n_images * (int64_t)m;
+    const int threads = 256;
+    const int64_t blocks = (tot + threads - 1) / threads;
+    if (pauli_f64)
+        ano_kernel<double><<<(unsigned)blocks, threads, 0, s>>>(static_cast<const double*>(pauli), n_images, m, abd, features);
+    else
+        ano_kernel<float><<<(unsigned)blocks, threads, 0, s>>>(static_cast<const float*>(pauli), n_images, m, abd, features);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    if (W) {
+        dim3 grid((out_dim + 15) / 16, (unsigned)((n_images + 15) / 16));
+        linear_fp32_kernel<<<grid, 256, 0, s>>>(features, n_images, m, W, bias, out_dim, out);
+        CUDA_TRY(cudaGetLastError());
+        count_launch();
+    }
+    return MPS_OK;
+}
+
+mps_status mps_sync(mps_batch* b) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    int st = 0;
+    CUDA_TRY(cudaMemcpy(&st, b->status_d, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != DEV_OK) {
+        cudaMemset(b->status_d, 0, sizeof(int));
+        return fail(MPS_ERR_DEVICE, "device check failed with code %d (%s)", st,
+                    st == DEV_BOND_OVERFLOW ? "bond overflow" : st == DEV_BAD_SHAPE ? "bad shape" : "other");
+    }
+    return MPS_OK;
+}
+
+mps_status mps_bond_dims(mps_batch* b, int32_t* out) {
+    if (!b || !out) return fail(MPS_ERR_INVALID_ARG, "batch and out must be non-NULL");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    CUDA_TRY(cudaMemcpy(out, b->bonds_d, sizeof(int32_t) * b->total_bonds, cudaMemcpyDeviceToHost));
+    return MPS_OK;
+}
+
+mps_status mps_discarded_weight(mps_batch* b, double* out) {
+    if (!b || !out) return fail(MPS_ERR_INVALID_ARG, "batch and out must be non-NULL");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    CUDA_TRY(cudaMemcpy(out, b->discarded_d, sizeof(double) * b->B, cudaMemcpyDeviceToHost));
+    return MPS_OK;
+}
+
+}  // extern "C"

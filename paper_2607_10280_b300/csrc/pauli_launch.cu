@@ -1,0 +1,54 @@
+// Right-environment and Pauli-cache kernel launches.
+#include <algorithm>
+
+#include "batch.h"
+#include "pauli.cuh"
+
+namespace mpsano {
+namespace {
+
+template <typename T, int CHI>
+mps_status launch_pauli(mps_batch* b, void* out) {
+    using Lay = PauliLayout<T, CHI>;
+    const int limit = smem_optin_limit();
+    int w = std::max(1, b->pauli_warps);
+    while (w > 1 && (size_t)w * Lay::bytes > (size_t)limit) --w;
+    const size_t smem = (size_t)w * Lay::bytes;
+    if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "Pauli kernel shared memory %zu B", smem);
+    auto rk = renv_kernel<T, CHI>;
+    auto pk = pauli_kernel<T, CHI>;
+    CUDA_TRY(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    rk<<<(b->B + w - 1) / w, 32 * w, smem, b->stream>>>(
+        b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
+        reinterpret_cast<cx<T>*>(b->renv), b->renv_stride, reinterpret_cast<T*>(b->norms));
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    const int units = (int)(b->units_h.size() / 2);
+    pk<<<(units + w - 1) / w, 32 * w, smem, b->stream>>>(
+        b->meta_d, units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
+        reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
+        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out));
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return MPS_OK;
+}
+
+template <typename T>
+mps_status dispatch_pauli(mps_batch* b, void* out) {
+    switch (b->chi_tpl) {
+        case 4: return launch_pauli<T, 4>(b, out);
+        case 8: return launch_pauli<T, 8>(b, out);
+        case 16: return launch_pauli<T, 16>(b, out);
+        case 32: return launch_pauli<T, 32>(b, out);
+    }
+    return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", b->chi_tpl);
+}
+
+
+}  // namespace
+
+mps_status launch_pauli_fp64(mps_batch* b, void* out) { return dispatch_pauli<double>(b, out); }
+mps_status launch_pauli_mixed(mps_batch* b, void* out) { return dispatch_pauli<float>(b, out); }
+
+}  // namespace mpsano

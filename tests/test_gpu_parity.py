@@ -1,0 +1,213 @@
+"""Parity of the CUDA path against the CPU oracle (GPU tests).
+
+Tolerances: the FP64 path must match the oracle within 1e-10 per Pauli entry and
+the mixed paths (complex64 state, FP64 inside truncations) within 1e-5 absolute.
+Cases where the oracle meets a near-tie at a truncation cut (relative gap below
+1e-6) have no unique answer; the seeds used here are checked to avoid them.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import ano as o_ano          # noqa: E402
+from oracle import circuit as o_circ     # noqa: E402
+from oracle import mps as o_mps          # noqa: E402
+from oracle import pairs as o_pairs      # noqa: E402
+from oracle import statevector as o_sv   # noqa: E402
+from paper_2607_10280_b300 import synth  # noqa: E402
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5, "mixed_orth64": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_10280_b300 import build
+    build.build()
+
+
+def oracle_cache(x, p, L, chi, ansatz="ladder", params=None, backend="mps"):
+    n = p * p
+    ops = o_circ.build_circuit(ansatz, np.asarray(x), L, params)
+    prs = o_pairs.image_pairs(p)
+    if backend == "statevector":
+        return o_sv.pair_paulis(o_sv.run(n, ops), prs), np.inf
+    st = o_mps.simulate(ops, n, chi)
+    return st.pair_paulis(prs), st.min_gap
+
+
+def run_gpu(pixels_list, ps, L, chi, precision, ansatz="ladder", params=None, shape=None):
+    from paper_2607_10280_b300.api import Batch
+    px = torch.tensor(np.concatenate([np.asarray(x) for x in pixels_list]), dtype=torch.float64, device="cuda")
+    pr = None if params is None else torch.tensor(params, dtype=torch.float64, device="cuda").contiguous()
+    b = Batch(np.asarray(ps, dtype=np.int32), chi, precision)
+    if shape:
+        b.set_launch_shape(*shape)
+    b.apply_circuit(px, L, ansatz, pr)
+    out = b.pauli_cache()
+    b.sync()
+    res = out.double().cpu().numpy()
+    offs = b.pair_offsets
+    bonds = b.bond_dims()
+    disc = b.discarded_weight()
+    b.close()
+    return [res[offs[i]:offs[i + 1]] for i in range(len(ps))], bonds, disc
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_orth64"])
+def test_tiny_4x4_vs_statevector(precision):
+    """4x4 image (16 qubits), batch 8, U[0,1] pixels, L = 1, chi = 4 (plain method, tiny)."""
+    p, B, L, chi = 4, 8, 1, 4
+    X = synth.uniform_pixels(B, p)
+    params = synth.circuit_params(L, p * p)
+    got, _, _ = run_gpu(list(X), [p] * B, L, chi, precision, params=params)
+    for i in range(B):
+        ref, _ = oracle_cache(X[i], p, L, chi, params=params, backend="statevector")
+        assert got[i].shape == (24, 16)
+        assert np.max(np.abs(got[i] - ref)) < TOL[precision], (i, np.max(np.abs(got[i] - ref)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("p,L,chi", [(3, 2, 1), (3, 3, 2), (3, 3, 3), (4, 2, 2), (4, 3, 3), (4, 4, 4), (5, 3, 4)])
+def test_truncated_regime_vs_oracle_mps(precision, p, L, chi):
+    B = 4
+    X = synth.uniform_pixels(B, p, seed=100 + p)
+    params = synth.circuit_params(L, p * p, seed=101)
+    got, _, disc = run_gpu(list(X), [p] * B, L, chi, precision, params=params)
+    for i in range(B):
+        ref, gap = oracle_cache(X[i], p, L, chi, params=params)
+        if gap < 1e-6:
+            continue
+        assert np.max(np.abs(got[i] - ref)) < TOL[precision], (i, np.max(np.abs(got[i] - ref)))
+    assert np.all(disc >= 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_uneven_batch_ragged_sizes(precision):
+    ps = [2, 5, 3, 4, 2, 6, 3]
+    L, chi = 2, 4
+    params = synth.circuit_params(L, 36, seed=7)
+    X = [synth.garment_pixels(1, p, seed=200 + i)[0] for i, p in enumerate(ps)]
+    got, _, _ = run_gpu(X, ps, L, chi, precision, params=params)
+    for i, p in enumerate(ps):
+        ref, gap = oracle_cache(X[i], p, L, chi, params=params)
+        assert gap >= 1e-6
+        assert np.max(np.abs(got[i] - ref)) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_paper_ansatz_vs_statevector(precision):
+    p, B, L, chi = 4, 4, 2, 16
+    X = synth.garment_pixels(B, p, seed=5)
+    got, _, _ = run_gpu(list(X), [p] * B, L, chi, precision, ansatz="paper")
+    for i in range(B):
+        ref, _ = oracle_cache(X[i], p, L, chi, ansatz="paper", backend="statevector")
+        assert np.max(np.abs(got[i] - ref)) < TOL[precision]
+
+
+def test_paper_ansatz_truncated_vs_oracle_mps():
+    p, B, L, chi = 3, 4, 3, 2
+    X = synth.uniform_pixels(B, p, seed=9)
+    got, _, _ = run_gpu(list(X), [p] * B, L, chi, "fp64", ansatz="paper")
+    for i in range(B):
+        ref, gap = oracle_cache(X[i], p, L, chi, ansatz="paper")
+        if gap < 1e-6:
+            continue
+        assert np.max(np.abs(got[i] - ref)) < 1e-10
+
+
+def test_encoding_only_and_chi_one():
+    """L = 0 gives the product state (closed form of the encoding); chi = 1 forces
+    every two-qubit step through the SVD branch."""
+    p = 3
+    X = synth.uniform_pixels(2, p, seed=3)
+    got, bonds, _ = run_gpu(list(X), [p, p], 0, 2, "fp64", params=np.zeros((1, 9, 2)))
+    for i in range(2):
+        s = np.stack([np.ones(9), np.sin(np.pi * X[i]), np.zeros(9), np.cos(np.pi * X[i])], 1)
+        for q, (a, b) in enumerate(o_pairs.image_pairs(p)):
+            assert np.allclose(got[i][q], np.outer(s[a], s[b]).reshape(16), atol=1e-12)
+    params = synth.circuit_params(2, 9, seed=4)
+    got, bonds, disc = run_gpu(list(X), [p, p], 2, 1, "fp64", params=params)
+    assert all(max(bd) == 1 for bd in bonds)
+    for i in range(2):
+        ref, gap = oracle_cache(X[i], p, 2, 1, params=params)
+        assert np.max(np.abs(got[i] - ref)) < 1e-10
+    assert np.all(disc > 0)
+
+
+def test_ladder_bond_dimensions_7x7():
+    n, L, chi = 49, 3, 16
+    X = synth.garment_pixels(2, 7, seed=40)
+    _, bonds, _ = run_gpu(list(X), [7, 7], L, chi, "mixed", params=synth.circuit_params(L, n))
+    expect = [1] + [min(chi, 2 ** L, 2 ** (k + 1), 2 ** (n - k - 1)) for k in range(n - 1)] + [1]
+    assert bonds[0] == expect and bonds[1] == expect
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_headline_7x7_L4_chi16_sampled(precision):
+    """7x7 images (49 qubits), L = 4, chi = 16: the benchmark workload shape, run at
+    batch 64 with the same launch configuration; sampled images vs the oracle."""
+    p, L, chi, B = 7, 4, 16, 64
+    X = synth.garment_pixels(B, p)
+    params = synth.circuit_params(L, p * p)
+    got, _, disc = run_gpu(list(X), [p] * B, L, chi, precision, params=params)
+    for i in (0, 17, 63):
+        ref, _ = oracle_cache(X[i], p, L, chi, params=params)
+        err = np.max(np.abs(got[i] - ref))
+        assert err < TOL[precision], (i, err)
+    assert np.max(disc) == 0.0   # chi = 2^L: nothing is truncated
+
+
+def test_large_16x16_and_uneven_mix():
+    """Maximum image size (256 qubits) and an uneven mix up to it, L = 2."""
+    ps = [16, 4, 11, 16, 7]
+    L, chi = 2, 32
+    params = synth.circuit_params(L, 256, seed=12)
+    X = [synth.garment_pixels(1, p, seed=300 + i)[0] for i, p in enumerate(ps)]
+    got, _, _ = run_gpu(X, ps, L, chi, "mixed", params=params)
+    for i in (0, 1, 2):
+        ref, _ = oracle_cache(X[i], ps[i], L, chi, params=params)
+        assert np.max(np.abs(got[i] - ref)) < 1e-5
+
+
+def test_launch_shapes_agree():
+    p, L, chi, B = 5, 3, 8, 11
+    X = synth.garment_pixels(B, p, seed=77)
+    params = synth.circuit_params(L, 25, seed=78)
+    base, _, _ = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=(1, 32))
+    for shape in ((2, 64), (4, 128), (8, 256)):
+        got, _, _ = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=shape)
+        for i in range(B):
+            assert np.array_equal(got[i], base[i])
+
+
+def test_ano_features_and_linear_vs_oracle():
+    from paper_2607_10280_b300.api import ano_features
+    p, B = 7, 5
+    m = 2 * p * (p - 1)
+    X = synth.garment_pixels(B, p, seed=90)
+    params = synth.circuit_params(2, 49, seed=91)
+    caches = np.stack([oracle_cache(X[i], p, 2, 8, params=params)[0] for i in range(B)])
+    abd = synth.observable_params(m)
+    W, bias = synth.linear_params(784, m)
+    for dt in (torch.float32, torch.float64):
+        P = torch.tensor(caches.reshape(B * m, 16), dtype=dt, device="cuda")
+        feats, out = ano_features(P, m, torch.tensor(abd, dtype=torch.float32, device="cuda"),
+                                  torch.tensor(W, dtype=torch.float32, device="cuda"),
+                                  torch.tensor(bias, dtype=torch.float32, device="cuda"))
+        torch.cuda.synchronize()
+        f = feats.double().cpu().numpy()
+        y = out.double().cpu().numpy()
+        abd32 = abd.astype(np.float32).astype(np.float64)
+        W32 = W.astype(np.float32).astype(np.float64)
+        b32 = bias.astype(np.float32).astype(np.float64)
+        for i in range(B):
+            ref_q = o_ano.features(caches[i], abd32)
+            scale_q = np.array([np.sum(np.abs(o_ano.coefficients(abd32[q]) * caches[i][q])) for q in range(m)])
+            assert np.all(np.abs(f[i] - ref_q) <= 1e-5 * (1 + scale_q))
+            ref_y = o_ano.linear(W32, ref_q, b32)
+            scale_y = np.abs(W32) @ np.abs(ref_q) + np.abs(b32)
+            assert np.all(np.abs(y[i] - ref_y) <= 1e-5 * (1 + scale_y))
