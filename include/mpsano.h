@@ -156,6 +156,15 @@ uint64_t mps_launch_count(void);
  * Pauli kernel, a multiple of 32 in 32..512.  0 leaves a knob unchanged. */
 mps_status mps_set_launch_shape(mps_batch* batch, int32_t images_per_cta, int32_t pauli_threads);
 
+/* Per-launch timing with CUDA events recorded on the batch's stream around each
+ * kernel the batch launches (enable != 0 turns it on; off by default). */
+mps_status mps_set_timing(mps_batch* batch, int32_t enable);
+
+/* Sum of the recorded launch durations since the last call, per kernel kind
+ * (0 circuit, 1 right environments, 2 Pauli cache): ms [3], launches [3].
+ * Synchronises the batch's stream, then clears the records. */
+mps_status mps_kernel_times(mps_batch* batch, double* ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -113,6 +113,16 @@ class Batch:
             o += n + 1
         return out
 
+    def set_timing(self, enable: bool = True):
+        check(lib().mps_set_timing(self._h, 1 if enable else 0))
+
+    def kernel_times(self) -> dict:
+        """{kind: (total ms, launches)} since the last call, from the library's events."""
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_int64 * 3)()
+        check(lib().mps_kernel_times(self._h, ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.KERNEL_KINDS)}
+
     def discarded_weight(self) -> np.ndarray:
         buf = np.zeros(self.n_images, dtype=np.float64)
         check(lib().mps_discarded_weight(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
@@ -158,3 +168,48 @@ def extract(pixels, p, L: int, chi: int, precision: str = "mixed", ansatz: str =
     batch.sync()
     batch.close()
     return out.reshape(B, -1, 16)
+
+
+class Pipeline:
+    """End-to-end path for a fixed batch layout: host pixels in, host results out.
+
+    Every run copies the pixels from (pinned) host memory to the device, runs the
+    circuit, the Pauli cache, the ANO features and the linear layer, and copies the
+    Pauli cache, the features and the reconstruction back to pinned host buffers.
+    All steps are enqueued on one stream; run() returns after the copies finish.
+    """
+
+    def __init__(self, p, chi, L, precision, params, abd, W=None, bias=None, ansatz="ladder", stream=None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.batch = Batch(p, chi, precision, self.stream)
+        self.L, self.ansatz = L, ansatz
+        self.params, self.abd, self.W, self.bias = params, abd, W, bias
+        p = np.atleast_1d(np.asarray(p))
+        if len(set(p.tolist())) != 1:
+            raise ValueError("Pipeline needs images of one size (one pair layout for the ANO layer)")
+        self.m = pair_count(int(p[0]))
+        n_px = int(self.batch.pixel_offsets[-1])
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.px_dev = torch.empty(n_px, dtype=torch.float64, device=dev)
+        dt = torch.float64 if precision == "fp64" else torch.float32
+        self.pauli_dev = torch.empty((int(self.batch.pair_offsets[-1]), 16), dtype=dt, device=dev)
+        B = self.batch.n_images
+        self.pauli_host = torch.empty(self.pauli_dev.shape, dtype=dt).pin_memory()
+        self.feat_host = torch.empty((B, self.m), dtype=torch.float32).pin_memory()
+        self.out_host = None if W is None else torch.empty((B, W.shape[0]), dtype=torch.float32).pin_memory()
+        self.h2d_bytes = n_px * 8
+        self.d2h_bytes = (self.pauli_host.numel() * self.pauli_host.element_size() + self.feat_host.numel() * 4
+                          + (0 if self.out_host is None else self.out_host.numel() * 4))
+
+    def run(self, host_pixels: torch.Tensor):
+        with torch.cuda.stream(self.stream):
+            self.px_dev.copy_(host_pixels, non_blocking=True)
+            self.batch.apply_circuit(self.px_dev, self.L, self.ansatz, self.params)
+            self.batch.pauli_cache(self.pauli_dev)
+            feats, out = ano_features(self.pauli_dev, self.m, self.abd, self.W, self.bias, self.stream)
+            self.pauli_host.copy_(self.pauli_dev, non_blocking=True)
+            self.feat_host.copy_(feats, non_blocking=True)
+            if out is not None:
+                self.out_host.copy_(out, non_blocking=True)
+        self.stream.synchronize()
+        return self.pauli_host, self.feat_host, self.out_host

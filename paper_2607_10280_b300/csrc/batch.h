@@ -33,6 +33,11 @@ struct mps_batch {
     int chi_tpl = 0;                       // kernel CHI bucket of the last circuit
     int images_per_cta = 2;
     int pauli_warps = 4;
+    // optional per-launch event timing (mps_set_timing / mps_kernel_times)
+    bool timing = false;
+    struct TimedLaunch { int kind; cudaEvent_t start, stop; };
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
 };
 
 namespace mpsano {
@@ -41,6 +46,11 @@ namespace mpsano {
 mps_status fail(mps_status st, const char* fmt, ...);
 // Count one kernel launch (reported by mps_launch_count).
 void count_launch();
+// Kernel kinds reported by mps_kernel_times.
+enum KernelKind { KIND_CIRCUIT = 0, KIND_RENV = 1, KIND_PAULI = 2, KIND_COUNT = 3 };
+// Record a start event for a timed launch on the batch stream (no-op unless timing).
+void timing_begin(mps_batch* b, int kind);
+void timing_end(mps_batch* b);
 // Opt-in shared-memory limit per block on the current device.
 int smem_optin_limit();
 

@@ -21,9 +21,11 @@ mps_status launch_circuit(mps_batch* b, const double* pixels, const double* para
     auto kern = circuit_kernel<T, TQ, CHI, TRUNC>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (b->B + ipc - 1) / ipc;
+    timing_begin(b, KIND_CIRCUIT);
     kern<<<grid, 32 * ipc, smem, b->stream>>>(b->meta_d, b->B, pixels, params, params_n, ansatz,
                                                 reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
                                                 b->discarded_d, b->status_d);
+    timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
     return MPS_OK;

@@ -30,6 +30,31 @@ namespace mpsano {
 
 void count_launch() { g_launches.fetch_add(1); }
 
+namespace {
+cudaEvent_t pooled_event(mps_batch* b) {
+    if (!b->event_pool.empty()) {
+        cudaEvent_t e = b->event_pool.back();
+        b->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+void timing_begin(mps_batch* b, int kind) {
+    if (!b->timing) return;
+    mps_batch::TimedLaunch t{kind, pooled_event(b), pooled_event(b)};
+    cudaEventRecord(t.start, b->stream);
+    b->timed.push_back(t);
+}
+
+void timing_end(mps_batch* b) {
+    if (!b->timing || b->timed.empty()) return;
+    cudaEventRecord(b->timed.back().stop, b->stream);
+}
+
 mps_status fail(mps_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -115,6 +140,8 @@ namespace {
 
 void free_batch(mps_batch* b) {
     if (!b) return;
+    for (auto& t : b->timed) { cudaEventDestroy(t.start); cudaEventDestroy(t.stop); }
+    for (auto e : b->event_pool) cudaEventDestroy(e);
     cudaFree(b->meta_d);
     cudaFreeHost(b->meta_pinned);
     cudaFree(b->units_d);
@@ -346,6 +373,28 @@ mps_status mps_bond_dims(mps_batch* b, int32_t* out) {
     if (!b || !out) return fail(MPS_ERR_INVALID_ARG, "batch and out must be non-NULL");
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     CUDA_TRY(cudaMemcpy(out, b->bonds_d, sizeof(int32_t) * b->total_bonds, cudaMemcpyDeviceToHost));
+    return MPS_OK;
+}
+
+mps_status mps_set_timing(mps_batch* b, int32_t enable) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    b->timing = enable != 0;
+    return MPS_OK;
+}
+
+mps_status mps_kernel_times(mps_batch* b, double* ms, int64_t* launches) {
+    if (!b || !ms || !launches) return fail(MPS_ERR_INVALID_ARG, "batch, ms and launches must be non-NULL");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < KIND_COUNT; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    for (auto& t : b->timed) {
+        float e = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&e, t.start, t.stop));
+        ms[t.kind] += e;
+        launches[t.kind] += 1;
+        b->event_pool.push_back(t.start);
+        b->event_pool.push_back(t.stop);
+    }
+    b->timed.clear();
     return MPS_OK;
 }
 

@@ -19,16 +19,20 @@ mps_status launch_pauli(mps_batch* b, void* out) {
     auto pk = pauli_kernel<T, CHI>;
     CUDA_TRY(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    timing_begin(b, KIND_RENV);
     rk<<<(b->B + w - 1) / w, 32 * w, smem, b->stream>>>(
         b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<cx<T>*>(b->renv), b->renv_stride, reinterpret_cast<T*>(b->norms));
+    timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
     const int units = (int)(b->units_h.size() / 2);
+    timing_begin(b, KIND_PAULI);
     pk<<<(units + w - 1) / w, 32 * w, smem, b->stream>>>(
         b->meta_d, units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
         reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out));
+    timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
     return MPS_OK;

@@ -1,0 +1,135 @@
+"""Algorithmic flop counts of the CUDA kernels, per image, from the bond schedule.
+
+Real flops; a complex multiply-add counts 8.  The counts follow the work each
+kernel performs on the true bond dimensions (no padding, no idle lanes):
+
+circuit  per two-qubit step on theta = (2 Dl) x (2 Dr) with inner bond Dm:
+           one-qubit gate on the loaded site      8 * 4 * Dm * Dr
+           theta = A_k A_{k+1}                    8 * M * N * Dm       (M = 2 Dl, N = 2 Dr)
+           exact split, N <= M (Householder QR and explicit Q)
+                                                  2 * 8 * (M N^2 - N^3 / 3)
+           exact split, M < N                     0                    (A_k = identity)
+           truncated split (K = min(M, N) > chi)  Gram 4 K^2 max(M, N), Jacobi
+                                                  48 K per rotation over the measured
+                                                  sweeps (6 assumed), U^H theta 8 chi M N
+         per centre move of a (2 Dl) x Dm site     QR + Q + R * next site
+renv     per site                                 8 * (2 Dl Dr^2 + 2 Dl^2 Dr)
+pauli    per column unit: E_a and closings at its sites, the carried closing
+         matrices through p - 1 sites per row     3 * 8 * (2 Dl Dr^2 + 2 Dl^2 Dr)
+"""
+from __future__ import annotations
+
+from functools import lru_cache
+
+
+def _qr_flops(M: int, N: int) -> float:
+    K = min(M, N)
+    # complex Householder QR of M x N with K reflectors, plus forming the M x K factor
+    return 8.0 * (M * N * K - (M + N) * K * K / 2 + K ** 3 / 3) * 2
+
+
+@lru_cache(maxsize=None)
+def circuit_schedule(n: int, L: int, chi: int, ansatz: str = "ladder") -> tuple:
+    """Steps of the circuit kernel: tuples (kind, Dl, Dm, Dr, new_bond), kind in
+    {'gate', 'move', 'lq'}; plus the final bond dimensions."""
+    bd = [1] * (n + 1)
+    steps = []
+
+    def run_pass(first: int, stride: int, fresh: bool):
+        trunc = False
+        dl = bd[first]
+        for k in range(first, n - 1):
+            if (k - first) % stride == 0:
+                mn = min(2 * dl, 2 * bd[k + 2])
+                trunc |= mn > chi
+                dl = min(mn, chi)
+            else:
+                dl = min(2 * dl, bd[k + 1])
+        if trunc and not fresh:
+            for k in range(n - 1, first, -1):
+                nb = min(bd[k], 2 * bd[k + 1])
+                steps.append(("lq", bd[k - 1], bd[k], bd[k + 1], nb))
+                bd[k] = nb
+        for k in range(first, n - 1):
+            if (k - first) % stride == 0:
+                M, N = 2 * bd[k], 2 * bd[k + 2]
+                nb = min(chi, M, N)
+                steps.append(("gate", bd[k], bd[k + 1], bd[k + 2], nb))
+            else:
+                nb = min(2 * bd[k], bd[k + 1])
+                steps.append(("move", bd[k], bd[k + 1], bd[k + 2], nb))
+            bd[k + 1] = nb
+
+    for layer in range(L):
+        if ansatz == "ladder":
+            run_pass(0, 1, layer == 0)
+        else:
+            run_pass(0, 2, layer == 0)
+            if n > 2:
+                run_pass(1, 2, False)
+    return tuple(steps), tuple(bd)
+
+
+def circuit_flops(n: int, L: int, chi: int, ansatz: str = "ladder", jacobi_sweeps: int = 6) -> float:
+    steps, _ = circuit_schedule(n, L, chi, ansatz)
+    f = 0.0
+    for kind, Dl, Dm, Dr, nb in steps:
+        if kind == "gate":
+            M, N = 2 * Dl, 2 * Dr
+            f += 32.0 * Dm * Dr + 8.0 * M * N * Dm
+            if min(M, N) <= chi:
+                if N <= M:
+                    f += _qr_flops(M, N)
+            else:
+                K = min(M, N)
+                f += 4.0 * K * K * max(M, N) + jacobi_sweeps * (K * (K - 1) / 2) * 48.0 * K
+                f += 8.0 * chi * M * N
+                if M > N:
+                    f += 8.0 * M * chi * N + _qr_flops(M, chi)
+        elif kind == "move":
+            M, N = 2 * Dl, Dm
+            f += _qr_flops(M, N) + 8.0 * nb * Dm * 2 * Dr
+        else:  # lq of site (Dl x 2 Dr) and site_{k-1} * L
+            f += _qr_flops(2 * Dr, Dm) + 8.0 * 2 * Dl * Dm * nb
+    return f
+
+
+def renv_flops(bonds) -> float:
+    n = len(bonds) - 1
+    return sum(8.0 * (2 * bonds[j] * bonds[j + 1] ** 2 + 2 * bonds[j] ** 2 * bonds[j + 1]) for j in range(n))
+
+
+def pauli_flops(p: int, bonds) -> float:
+    """Flops of the Pauli kernel for one image (all p column units)."""
+    f = 0.0
+
+    def transfer(Dl, Dr):  # C <- sum_s conj(A^s) C A^{sT}
+        return 8.0 * (2 * Dl * Dr * Dr + 2 * Dl * Dl * Dr)
+
+    for c in range(p):
+        for row in range(p - 1, -1, -1):
+            j = row * p + c
+            Dl, Dr = bonds[j], bonds[j + 1]
+            f += 3 * 8.0 * Dr * Dr * 2 * Dl          # E_a
+            f += 3 * 8.0 * Dr * Dr                   # <E_a, R>
+            if row < p - 1:
+                f += 9 * 8.0 * Dr * Dr               # vertical closing
+            f += 8.0 * (2 * Dl * Dr * Dr + 3 * Dl * Dl * Dr)   # right closings
+            if c == 0 and row == 0:
+                break
+            k0 = j - 1
+            if c > 0:
+                D0 = bonds[k0]
+                f += 3 * 8.0 * Dl * Dl * 2 * D0 + 12 * 8.0 * Dl * Dl
+            if row == 0:
+                break
+            for k in range(k0, j - p, -1):
+                f += 3 * transfer(bonds[k], bonds[k + 1])
+    return f
+
+
+def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder") -> dict:
+    n = p * p
+    _, bonds = circuit_schedule(n, L, chi, ansatz)
+    return {"circuit": circuit_flops(n, L, chi, ansatz), "renv": renv_flops(bonds),
+            "pauli": pauli_flops(p, bonds)}
