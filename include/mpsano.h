@@ -165,6 +165,43 @@ mps_status mps_set_timing(mps_batch* batch, int32_t enable);
  * Synchronises the batch's stream, then clears the records. */
 mps_status mps_kernel_times(mps_batch* batch, double* ms, int64_t* launches);
 
+/* ---- Pauli cache without device allocation ------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory themselves or through this library:
+ *   - plug-ins inside a host application whose GPU memory is owned by another
+ *     allocator or a fixed pool, where an extra cudaMalloc fails or breaks that
+ *     application's accounting;
+ *   - processes whose framework reserves the whole GPU at start-up, so that any
+ *     later cudaMalloc runs out of memory;
+ *   - latency-bound serving loops, where cudaMalloc/cudaFree can synchronise the
+ *     device and stall every stream.
+ * It computes the same Pauli cache as mps_create_batch + mps_apply_circuit +
+ * mps_pauli_cache for n_images images of one size, MPS_MIXED precision, the
+ * ladder ansatz and the horizontal + vertical pair set, using the same kernels.
+ * All working memory (site tensors, environments, bond dimensions, per-image
+ * records) lives in one fixed array inside this library's device memory (about
+ * 18 MiB, held on every GPU that loads the library until the process exits).
+ *   n_images  1..64
+ *   p, chi, L image side 2..16, bond cap 1..32, layers >= 0
+ *   pixels    device float64 [n_images][p*p], values in [0, 1]
+ *   params    device float64 [>= L][params_n][2] angles, params_n >= p*p (may be NULL if L == 0)
+ *   out       device float32 [n_images][2p(p-1)][16], caller-owned
+ *   stream    cudaStream_t
+ * Limits: with ld the smallest power of two >= 4 that holds the largest bond the
+ * circuit reaches, n_images * p^2 * 2 * ld^2 * 8 bytes <= 12 MiB of site storage and
+ * n_images * p^2 * ld^2 * 8 bytes <= 6 MiB of environments (e.g. up to 62 images of
+ * 7x7 at chi = 16, L = 4).  Larger requests return MPS_ERR_INVALID_ARG with a message.
+ * No cudaMalloc, cudaFree or other allocating routine is called.  The first call on a
+ * device looks up the array's device address with that device current; make that
+ * first call before any stream capture.  Every call reuses the same array and
+ * overwrites the previous call's contents (per-call state is cleared at its start),
+ * so calls that overlap on the GPU -- on different streams or from different
+ * threads -- race and corrupt each other: keep them on one stream.  Device-side
+ * checks are not reported by this call.  Asynchronous on stream. */
+mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32_t chi, int32_t L,
+                                   const double* pixels, const double* params, int32_t params_n,
+                                   float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

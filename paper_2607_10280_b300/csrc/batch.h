@@ -17,6 +17,7 @@ struct mps_batch {
     size_t elem = 8;                       // bytes per complex element of the state
     std::vector<mpsano::ImageMeta> meta_h;
     std::vector<int32_t> units_h;          // (image, column) pairs of the Pauli kernel
+    int n_units = 0;                       // = units_h.size() / 2 when units_h is used
     mpsano::ImageMeta* meta_d = nullptr;
     mpsano::ImageMeta* meta_pinned = nullptr;
     int32_t* units_d = nullptr;

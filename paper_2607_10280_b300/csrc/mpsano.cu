@@ -212,6 +212,7 @@ mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* c
         for (int c = 0; c < pi; ++c) { b->units_h.push_back(i); b->units_h.push_back(c); }
     }
     renv_max = (int64_t)b->n_max * b->ld_max * b->ld_max;  // R_j of any image at any kernel bucket
+    b->n_units = (int)(b->units_h.size() / 2);
     b->total_pairs_hv = pair;
     b->total_bonds = bond;
     b->renv_stride = renv_max;

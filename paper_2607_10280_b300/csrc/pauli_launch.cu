@@ -26,7 +26,7 @@ mps_status launch_pauli(mps_batch* b, void* out) {
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
-    const int units = (int)(b->units_h.size() / 2);
+    const int units = b->n_units;
     timing_begin(b, KIND_PAULI);
     pk<<<(units + w - 1) / w, 32 * w, smem, b->stream>>>(
         b->meta_d, units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
