@@ -151,10 +151,17 @@ mps_status mps_discarded_weight(mps_batch* batch, double* out);
 /* Kernels this library has launched since it was loaded (all batches). */
 uint64_t mps_launch_count(void);
 
-/* Launch-shape knobs used by the autotuner.  images_per_cta: images (one warp each)
- * per CTA of the circuit kernel, 1..8; pauli_threads: threads per image in the
- * Pauli kernel, a multiple of 32 in 32..512.  0 leaves a knob unchanged. */
-mps_status mps_set_launch_shape(mps_batch* batch, int32_t images_per_cta, int32_t pauli_threads);
+/* Launch-shape knobs used by the autotuner (0 leaves a knob unchanged).
+ *   images_per_cta   images per CTA of the circuit kernel when it runs one warp per
+ *                    image, 1..8
+ *   circuit_threads  threads that share one image in the circuit kernel: 32, 64 or 128
+ *                    (wider teams apply to the mixed path at bond buckets 16 and 32)
+ *   pauli_threads    threads that share one (image, grid column) unit of the Pauli
+ *                    kernel: 32, 64 or 128
+ * images_per_cta and pauli_threads leave every result bit-identical; circuit_threads
+ * changes the summation order inside the QR splits (results agree to rounding). */
+mps_status mps_set_launch_shape(mps_batch* batch, int32_t images_per_cta, int32_t circuit_threads,
+                                int32_t pauli_threads);
 
 /* Per-launch timing with CUDA events recorded on the batch's stream around each
  * kernel the batch launches (enable != 0 turns it on; off by default). */
@@ -180,7 +187,7 @@ mps_status mps_kernel_times(mps_batch* batch, double* ms, int64_t* launches);
  * ladder ansatz and the horizontal + vertical pair set, using the same kernels.
  * All working memory (site tensors, environments, bond dimensions, per-image
  * records) lives in one fixed array inside this library's device memory (about
- * 18 MiB, held on every GPU that loads the library until the process exits).
+ * 18.5 MiB, held on every GPU that loads the library until the process exits).
  *   n_images  1..64
  *   p, chi, L image side 2..16, bond cap 1..32, layers >= 0
  *   pixels    device float64 [n_images][p*p], values in [0, 1]

@@ -97,8 +97,8 @@ class Batch:
         check(lib().mps_pauli_cache(self._h, PAIR_SET["hv"], _ptr(out), None))
         return out
 
-    def set_launch_shape(self, images_per_cta: int = 0, pauli_threads: int = 0):
-        check(lib().mps_set_launch_shape(self._h, int(images_per_cta), int(pauli_threads)))
+    def set_launch_shape(self, images_per_cta: int = 0, circuit_threads: int = 0, pauli_threads: int = 0):
+        check(lib().mps_set_launch_shape(self._h, int(images_per_cta), int(circuit_threads), int(pauli_threads)))
 
     # -- diagnostics -----------------------------------------------------------------
     def sync(self):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmpsano.so")
-SOURCES = ["mpsano.cu", "circuit_fp64.cu", "circuit_mixed.cu", "circuit_orth64.cu", "pauli_launch.cu", "noalloc.cu"]
+SOURCES = ["mpsano.cu", "pauli_launch.cu", "noalloc.cu"] + [f"circuit_{p}_t{t}.cu" for p in ("mixed", "fp64", "orth64") for t in (0, 1)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -31,9 +31,14 @@ struct mps_batch {
     int64_t total_pairs_hv = 0, total_pairs_hvd = 0;
     int64_t total_bonds = 0;
     bool circuit_done = false;
+    void* gates = nullptr;                 // one-qubit gate table of the last circuit
+    size_t gates_bytes = 0;
+    int gate_n = 0;                        // qubit stride of the gate table
+    bool gates_owned = true;               // false when gates points into static scratch
+    int circuit_threads = 32;              // threads per image in the circuit kernel
     int chi_tpl = 0;                       // kernel CHI bucket of the last circuit
     int images_per_cta = 2;
-    int pauli_warps = 4;
+    int pauli_warps = 2;
     // optional per-launch event timing (mps_set_timing / mps_kernel_times)
     bool timing = false;
     struct TimedLaunch { int kind; cudaEvent_t start, stop; };
@@ -55,12 +60,24 @@ void timing_end(mps_batch* b);
 // Opt-in shared-memory limit per block on the current device.
 int smem_optin_limit();
 
-mps_status launch_circuit_fp64(mps_batch* b, int chi_tpl, bool trunc, const double* px, const double* pr,
-                               int pn, int ansatz);
-mps_status launch_circuit_mixed(mps_batch* b, int chi_tpl, bool trunc, const double* px, const double* pr,
-                                int pn, int ansatz);
-mps_status launch_circuit_orth64(mps_batch* b, int chi_tpl, bool trunc, const double* px, const double* pr,
-                                 int pn, int ansatz);
+mps_status launch_circuit_fp64_t0(mps_batch* b, int chi_tpl, const double* px, int ansatz);
+mps_status launch_circuit_fp64_t1(mps_batch* b, int chi_tpl, const double* px, int ansatz);
+inline mps_status launch_circuit_fp64(mps_batch* b, int chi_tpl, bool trunc, const double* px, int ansatz) {
+    return trunc ? launch_circuit_fp64_t1(b, chi_tpl, px, ansatz) : launch_circuit_fp64_t0(b, chi_tpl, px, ansatz);
+}
+mps_status launch_circuit_mixed_t0(mps_batch* b, int chi_tpl, const double* px, int ansatz);
+mps_status launch_circuit_mixed_t1(mps_batch* b, int chi_tpl, const double* px, int ansatz);
+inline mps_status launch_circuit_mixed(mps_batch* b, int chi_tpl, bool trunc, const double* px, int ansatz) {
+    return trunc ? launch_circuit_mixed_t1(b, chi_tpl, px, ansatz) : launch_circuit_mixed_t0(b, chi_tpl, px, ansatz);
+}
+mps_status launch_circuit_orth64_t0(mps_batch* b, int chi_tpl, const double* px, int ansatz);
+mps_status launch_circuit_orth64_t1(mps_batch* b, int chi_tpl, const double* px, int ansatz);
+inline mps_status launch_circuit_orth64(mps_batch* b, int chi_tpl, bool trunc, const double* px, int ansatz) {
+    return trunc ? launch_circuit_orth64_t1(b, chi_tpl, px, ansatz) : launch_circuit_orth64_t0(b, chi_tpl, px, ansatz);
+}
+// Fill b->gates (allocated by the caller) with the one-qubit gate table of a circuit.
+mps_status launch_gate_table(mps_batch* b, int ansatz, int L_max, const double* params, int params_n,
+                             const double* pixels);
 mps_status launch_pauli_fp64(mps_batch* b, void* out);
 mps_status launch_pauli_mixed(mps_batch* b, void* out);
 

@@ -50,52 +50,69 @@ struct CircuitLayout {
     static constexpr size_t off_taud = off_vec + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_lam = off_taud + (TRUNC ? sizeof(cx<double>) * K : 0);
     static constexpr size_t off_ord = off_lam + (TRUNC ? sizeof(double) * K : 0);
-    static constexpr size_t bytes = (off_ord + (TRUNC ? sizeof(int) * K : 0) + 15) & ~size_t(15);
+    static constexpr size_t off_red = (off_ord + (TRUNC ? sizeof(int) * K : 0) + 15) & ~size_t(15);
+    static constexpr size_t off_flag = off_red + sizeof(double) * 4;   // team reductions (<= 128 threads)
+    static constexpr size_t bytes = (off_flag + sizeof(int) + 15) & ~size_t(15);
 };
 
 // The 2x2 one-qubit gate applied to site k at the start of a layer.
 template <typename T>
 struct Gate1 { cx<T> u00, u01, u10, u11; };
 
+// One-qubit gate of (layer, site k) from the table written by gate_table_kernel:
+// ladder ansatz gates[(layer * gn + k) * 4 + e], paper ansatz gates[(img * gn + k) * 4 + e]
+// (the paper layer gate depends on the pixel, not on the layer).
 template <typename T>
-__device__ __forceinline__ Gate1<T> layer_gate(int ansatz, const double* params, int params_n,
-                                              int layer, int k, double x) {
+__device__ __forceinline__ Gate1<T> table_gate(const cx<T>* gates, int gn, int ansatz, int layer, int img, int k) {
+    const cx<T>* g = gates + ((size_t)(ansatz == 0 ? layer : img) * gn + k) * 4;
+    Gate1<T> u;
+    u.u00 = g[0]; u.u01 = g[1]; u.u10 = g[2]; u.u11 = g[3];
+    return u;
+}
+
+// Gate table in FP64, rounded to the state type once per launch.
+//   ladder: entry (layer, k) = R_Z(beta_{layer,k}) R_Y(alpha_{layer,k})
+//   paper:  entry (img, k)   = R_Y(2 pi x_k - pi) H   (Eq. 2)
+template <typename T>
+__global__ void gate_table_kernel(int ansatz, int rows, int gn, const double* __restrict__ params, int params_n,
+                                  const ImageMeta* __restrict__ meta, const double* __restrict__ pixels,
+                                  cx<T>* __restrict__ gates) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * gn) return;
+    const int row = t / gn, k = t % gn;
     double u[8];
     if (ansatz == 0) {
-        // R_Z(beta) R_Y(alpha)
-        const double a = params[((size_t)layer * params_n + k) * 2 + 0];
-        const double b = params[((size_t)layer * params_n + k) * 2 + 1];
+        const double a = params[((size_t)row * params_n + k) * 2 + 0];
+        const double b = params[((size_t)row * params_n + k) * 2 + 1];
         double sa, ca, sb, cb;
         sincos(0.5 * a, &sa, &ca);
         sincos(0.5 * b, &sb, &cb);
-        // e^{-ib/2} = (cb, -sb), e^{ib/2} = (cb, sb)
-        u[0] = cb * ca;  u[1] = -sb * ca;   // u00 = e^{-ib/2} c
-        u[2] = -cb * sa; u[3] = sb * sa;    // u01 = -e^{-ib/2} s
-        u[4] = cb * sa;  u[5] = sb * sa;    // u10 = e^{ib/2} s
-        u[6] = cb * ca;  u[7] = sb * ca;    // u11 = e^{ib/2} c
+        // e^{-ib/2} = (cb, -sb), e^{ib/2} = (cb, sb), R_Y(a) = [[ca, -sa], [sa, ca]]
+        u[0] = cb * ca;  u[1] = -sb * ca;
+        u[2] = -cb * sa; u[3] = sb * sa;
+        u[4] = cb * sa;  u[5] = sb * sa;
+        u[6] = cb * ca;  u[7] = sb * ca;
     } else {
-        // R_Y(phi) H, phi = 2 pi x - pi (Eq. 2)
-        double s, c;
-        sincos(0.5 * (2.0 * M_PI * x - M_PI), &s, &c);
+        const ImageMeta m = meta[row];
+        const double x = k < m.n ? pixels[m.pixel_off + k] : 0.0;
+        double sn, c;
+        sincos(0.5 * (2.0 * M_PI * x - M_PI), &sn, &c);
         const double h = 0.70710678118654752440;
-        u[0] = h * (c - s); u[1] = 0.0;   // [c -s; s c] [1 1; 1 -1] / sqrt 2
-        u[2] = h * (c + s); u[3] = 0.0;
-        u[4] = h * (s + c); u[5] = 0.0;
-        u[6] = h * (s - c); u[7] = 0.0;
+        u[0] = h * (c - sn); u[1] = 0.0;   // [c -s; s c] [1 1; 1 -1] / sqrt 2
+        u[2] = h * (c + sn); u[3] = 0.0;
+        u[4] = h * (sn + c); u[5] = 0.0;
+        u[6] = h * (sn - c); u[7] = 0.0;
     }
-    Gate1<T> g;
-    g.u00 = mk<T>(T(u[0]), T(u[1])); g.u01 = mk<T>(T(u[2]), T(u[3]));
-    g.u10 = mk<T>(T(u[4]), T(u[5])); g.u11 = mk<T>(T(u[6]), T(u[7]));
-    return g;
+    cx<T>* g = gates + (size_t)t * 4;
+    for (int e = 0; e < 4; ++e) g[e] = mk<T>(T(u[2 * e]), T(u[2 * e + 1]));
 }
 
 // Global site (Dl x 2 x Dr, padded [ld][2][ld]) -> shared site buffer, optionally
 // applying a one-qubit gate on the physical index.
-template <typename T, int CS>
+template <typename T, int CS, int NTHR>
 __device__ __forceinline__ void load_site(cx<T>* dst, const cx<T>* src, int ld, int Dl, int Dr,
                                           const Gate1<T>* g, int lane) {
-    for (int o = lane; o < Dl * Dr; o += 32) {
-        const int l = o / Dr, r = o % Dr;
+    team_for_2d<NTHR>(Dl, Dr, lane, [&](int l, int r) {
         const cx<T> a0 = src[(2 * l) * ld + r], a1 = src[(2 * l + 1) * ld + r];
         if (g) {
             dst[(2 * l) * CS + r] = g->u00 * a0 + g->u01 * a1;
@@ -104,29 +121,25 @@ __device__ __forceinline__ void load_site(cx<T>* dst, const cx<T>* src, int ld, 
             dst[(2 * l) * CS + r] = a0;
             dst[(2 * l + 1) * CS + r] = a1;
         }
-    }
+    });
 }
 
-template <typename T, int CS>
+template <typename T, int CS, int NTHR>
 __device__ __forceinline__ void store_site(cx<T>* dst, const cx<T>* src, int ld, int Dl, int Dr, int lane) {
-    for (int o = lane; o < 2 * Dl * Dr; o += 32) {
-        const int row = o / Dr, r = o % Dr;
-        dst[row * ld + r] = src[row * CS + r];
-    }
+    team_for_2d<NTHR>(2 * Dl, Dr, lane, [&](int row, int r) { dst[row * ld + r] = src[row * CS + r]; });
 }
 
-template <typename T, int CS>
+template <typename T, int CS, int NTHR>
 __device__ __forceinline__ void apply_gate_smem(cx<T>* site, int Dl, int Dr, const Gate1<T>& g, int lane) {
-    for (int o = lane; o < Dl * Dr; o += 32) {
-        const int l = o / Dr, r = o % Dr;
+    team_for_2d<NTHR>(Dl, Dr, lane, [&](int l, int r) {
         const cx<T> a0 = site[(2 * l) * CS + r], a1 = site[(2 * l + 1) * CS + r];
         site[(2 * l) * CS + r] = g.u00 * a0 + g.u01 * a1;
         site[(2 * l + 1) * CS + r] = g.u10 * a0 + g.u11 * a1;
-    }
+    });
 }
 
-template <typename T, typename TQ, int CHI, bool TRUNC>
-struct CircuitWarp {
+template <typename T, typename TQ, int CHI, bool TRUNC, int NTHR>
+struct CircuitTeam {
     using Lay = CircuitLayout<T, TQ, CHI, TRUNC>;
     static constexpr int CS = Lay::CS, LDM = Lay::LDM, LDK = Lay::LDK;
 
@@ -141,6 +154,8 @@ struct CircuitWarp {
     cx<double>* taud;
     double* lam;
     int* ord;
+    double* red;  // team reductions
+    int* flag;    // team broadcast
     int lane, n, chi, ld;
     cx<T>* sites;        // this image's site 0 in the arena
     double discarded;
@@ -151,20 +166,23 @@ struct CircuitWarp {
     // ---- theta = cur(Dl x 2 x Dm) nxt(Dm x 2 x Dr), CNOT(control = left) folded in ----
     __device__ void form_theta(int Dl, int Dm, int Dr, bool cnot) {
         const int M = 2 * Dl, N = 2 * Dr;
-        for (int o = lane; o < M * N; o += 32) {
-            const int row = o / N, c = o % N;
+        team_for_2d<NTHR>(M, N, lane, [&](int row, int c) {
             const int s = row & 1;
-            int t = c / Dr;
-            const int r = c % Dr;
+            int t = c >= Dr ? 1 : 0;
+            const int r = c - t * Dr;
             if (cnot && s) t ^= 1;
-            cx<T> acc = czero<T>();
+            cx<T> acc0 = czero<T>(), acc1 = czero<T>();
             const cx<T>* a = cur + row * CS;
             const cx<T>* b = nxt + t * CS + r;
-#pragma unroll 4
-            for (int m = 0; m < Dm; ++m) cmac(acc, a[m], b[2 * m * CS]);
-            th[c * LDM + row] = cvt<TQ>(acc);
-        }
-        __syncwarp();
+            int m = 0;
+            for (; m + 1 < Dm; m += 2) {
+                cmac(acc0, a[m], b[2 * m * CS]);
+                cmac(acc1, a[m + 1], b[2 * (m + 1) * CS]);
+            }
+            if (m < Dm) cmac(acc0, a[m], b[2 * m * CS]);
+            th[c * LDM + row] = cvt<TQ>(acc0 + acc1);
+        });
+        tsync<NTHR>();
     }
 
     // ---- split theta (M x N) into site k (written to global) and cur (new centre) ----
@@ -175,35 +193,27 @@ struct CircuitWarp {
         if (mn <= chi || !allow_trunc) {
             if (N <= M) {
                 // Householder QR: A_k = Q (M x N), cur = R (N x N) reshaped (N, 2, Dr)
-                warp_qr<TQ>(th, LDM, M, N, tau, lane);
-                for (int o = lane; o < N * N; o += 32) {
-                    const int i = o / N, c = o % N;
-                    const int t = c / Dr, r = c % Dr;
+                team_qr<NTHR>(th, LDM, M, N, tau, red, lane);
+                team_for_2d<NTHR>(N, N, lane, [&](int i, int c) {
+                    const int t = c >= Dr ? 1 : 0, r = c - t * Dr;
                     const cx<TQ> v = (i <= c) ? th[c * LDM + i] : czero<TQ>();
                     cur[(2 * i + t) * CS + r] = cvt<T>(v);
-                }
-                __syncwarp();
-                warp_form_q<TQ>(th, LDM, M, N, tau, lane);
+                });
+                tsync<NTHR>();
+                team_form_q<NTHR>(th, LDM, M, N, tau, lane);
                 cx<T>* dst = site_ptr(k);
-                for (int o = lane; o < M * N; o += 32) {
-                    const int row = o / N, c = o % N;
-                    dst[row * ld + c] = cvt<T>(th[c * LDM + row]);
-                }
-                __syncwarp();
+                team_for_2d<NTHR>(M, N, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
+                tsync<NTHR>();
                 return N;
             }
             // M < N: A_k = I_M, cur = theta reshaped (M, 2, Dr)
             cx<T>* dst = site_ptr(k);
-            for (int o = lane; o < M * M; o += 32) {
-                const int row = o / M, c = o % M;
-                dst[row * ld + c] = mk<T>(T(row == c ? 1 : 0), T(0));
-            }
-            for (int o = lane; o < M * N; o += 32) {
-                const int i = o / N, c = o % N;
-                const int t = c / Dr, r = c % Dr;
+            team_for_2d<NTHR>(M, M, lane, [&](int row, int c) { dst[row * ld + c] = mk<T>(T(row == c ? 1 : 0), T(0)); });
+            team_for_2d<NTHR>(M, N, lane, [&](int i, int c) {
+                const int t = c >= Dr ? 1 : 0, r = c - t * Dr;
                 cur[(2 * i + t) * CS + r] = cvt<T>(th[c * LDM + i]);
-            }
-            __syncwarp();
+            });
+            tsync<NTHR>();
             return M;
         }
         if constexpr (TRUNC) {
@@ -220,9 +230,8 @@ struct CircuitWarp {
         const bool left = M <= N;      // Gram of the row space (M x M) or column space (N x N)
         const int K = left ? M : N;
         // G = theta theta^H (left) or theta^H theta, accumulated in FP64
-        for (int o = lane; o < K * K; o += 32) {
-            const int i = o / K, j = o % K;   // G[i][j], column-major store G[j*LDK + i]
-            if (j < i) continue;
+        team_for_2d<NTHR>(K, K, lane, [&](int i, int j) {   // G[i][j], column-major store G[j*LDK + i]
+            if (j < i) return;
             cx<double> acc = czero<double>();
             if (left) {
                 for (int c = 0; c < N; ++c)
@@ -233,14 +242,15 @@ struct CircuitWarp {
             }
             G[j * LDK + i] = acc;
             G[i * LDK + j] = conj(acc);
-        }
-        __syncwarp();
-        warp_jacobi_eigh(G, V, LDK, K, lane, 40);
+        });
+        tsync<NTHR>();
+        if (lane < 32) warp_jacobi_eigh(G, V, LDK, K, lane, 40);
+        tsync<NTHR>();
         // rank the eigenvalues (descending, ties by index) and record the discarded weight
-        for (int i = lane; i < K; i += 32) lam[i] = G[i * LDK + i].re;
-        __syncwarp();
+        for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
+        tsync<NTHR>();
         double tot = 0.0, drop = 0.0;
-        for (int i = lane; i < K; i += 32) {
+        for (int i = lane; i < K; i += NTHR) {
             const double li = lam[i];
             int rank = 0;
             for (int j = 0; j < K; ++j) rank += (lam[j] > li) || (lam[j] == li && j < i);
@@ -249,56 +259,47 @@ struct CircuitWarp {
             tot += w;
             if (rank >= chi) drop += w;
         }
-        tot = warp_sum(tot);
-        drop = warp_sum(drop);
+        tot = team_sum<NTHR>(tot, red, lane);
+        drop = team_sum<NTHR>(drop, red, lane);
         if (tot > 0.0) discarded += drop / tot;
-        __syncwarp();
+        tsync<NTHR>();
         const int D = chi;
         // U_chi (M x D, FP64) into the Gram buffer
         cx<double>* U = G;
         if (left) {
-            for (int o = lane; o < M * D; o += 32) {
-                const int r = o % M, c = o / M;
-                U[c * LDK + r] = V[ord[c] * LDK + r];
-            }
-            __syncwarp();
+            team_for_2d<NTHR>(D, M, lane, [&](int c, int r) { U[c * LDK + r] = V[ord[c] * LDK + r]; });
+            tsync<NTHR>();
         } else {
             // X = theta V_chi (M x D), then U = Q of its FP64 Householder QR
-            for (int o = lane; o < M * D; o += 32) {
-                const int r = o % M, c = o / M;
+            team_for_2d<NTHR>(D, M, lane, [&](int c, int r) {
                 const cx<double>* v = V + ord[c] * LDK;
                 cx<double> acc = czero<double>();
                 for (int j = 0; j < N; ++j) cmac(acc, cvt<double>(th[j * LDM + r]), v[j]);
                 U[c * LDK + r] = acc;
-            }
-            __syncwarp();
-            warp_qr<double>(U, LDK, M, D, taud, lane);
-            warp_form_q<double>(U, LDK, M, D, taud, lane);
+            });
+            tsync<NTHR>();
+            team_qr<NTHR>(U, LDK, M, D, taud, red, lane);
+            team_form_q<NTHR>(U, LDK, M, D, taud, lane);
         }
         // A_k = U (Dl x 2 x D)
         cx<T>* dst = site_ptr(k);
-        for (int o = lane; o < M * D; o += 32) {
-            const int row = o / D, c = o % D;
-            dst[row * ld + c] = cvt<T>(U[c * LDK + row]);
-        }
+        team_for_2d<NTHR>(M, D, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(U[c * LDK + row]); });
         // cur = U^H theta (D x N), FP64 accumulation, then unit Frobenius norm
         double nrm = 0.0;
-        for (int o = lane; o < D * N; o += 32) {
-            const int i = o / N, c = o % N;
+        team_for_2d<NTHR>(D, N, lane, [&](int i, int c) {
             cx<double> acc = czero<double>();
             for (int r = 0; r < M; ++r) cmac_cj(acc, U[i * LDK + r], cvt<double>(th[c * LDM + r]));
             nrm += norm2(acc);
             V[c * LDK + i] = acc;   // V is free now
-        }
-        nrm = warp_sum(nrm);
-        __syncwarp();
+        });
+        nrm = team_sum<NTHR>(nrm, red, lane);
+        tsync<NTHR>();
         const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-        for (int o = lane; o < D * N; o += 32) {
-            const int i = o / N, c = o % N;
-            const int t = c / Dr, r = c % Dr;
+        team_for_2d<NTHR>(D, N, lane, [&](int i, int c) {
+            const int t = c >= Dr ? 1 : 0, r = c - t * Dr;
             cur[(2 * i + t) * CS + r] = cvt<T>(inv * V[c * LDK + i]);
-        }
-        __syncwarp();
+        });
+        tsync<NTHR>();
         return D;
     }
 
@@ -306,33 +307,23 @@ struct CircuitWarp {
     // cur <- R * nxt.  Returns the new bond min(2 Dl, Dm).
     __device__ int move_right(int k, int Dl, int Dm, int Dr) {
         const int M = 2 * Dl, N = Dm;
-        for (int o = lane; o < M * N; o += 32) {
-            const int row = o / N, c = o % N;
-            th[c * LDM + row] = cvt<TQ>(cur[row * CS + c]);
-        }
-        __syncwarp();
-        warp_qr<TQ>(th, LDM, M, N, tau, lane);
+        team_for_2d<NTHR>(M, N, lane, [&](int row, int c) { th[c * LDM + row] = cvt<TQ>(cur[row * CS + c]); });
+        tsync<NTHR>();
+        team_qr<NTHR>(th, LDM, M, N, tau, red, lane);
         const int Kd = M < N ? M : N;
-        for (int o = lane; o < Kd * N; o += 32) {
-            const int i = o / N, c = o % N;
-            rb[i * CS + c] = cvt<T>(i <= c ? th[c * LDM + i] : czero<TQ>());
-        }
-        __syncwarp();
-        warp_form_q<TQ>(th, LDM, M, Kd, tau, lane);
+        team_for_2d<NTHR>(Kd, N, lane, [&](int i, int c) { rb[i * CS + c] = cvt<T>(i <= c ? th[c * LDM + i] : czero<TQ>()); });
+        tsync<NTHR>();
+        team_form_q<NTHR>(th, LDM, M, Kd, tau, lane);
         cx<T>* dst = site_ptr(k);
-        for (int o = lane; o < M * Kd; o += 32) {
-            const int row = o / Kd, c = o % Kd;
-            dst[row * ld + c] = cvt<T>(th[c * LDM + row]);
-        }
+        team_for_2d<NTHR>(M, Kd, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
         // cur(i, t, r) = sum_m R(i, m) nxt(m, t, r)
-        for (int o = lane; o < Kd * 2 * Dr; o += 32) {
-            const int i = o / (2 * Dr), tr = o % (2 * Dr);
-            const int t = tr / Dr, r = tr % Dr;
+        team_for_2d<NTHR>(Kd, 2 * Dr, lane, [&](int i, int tr) {
+            const int t = tr >= Dr ? 1 : 0, r = tr - t * Dr;
             cx<T> acc = czero<T>();
             for (int m = i; m < N; ++m) cmac(acc, rb[i * CS + m], nxt[(2 * m + t) * CS + r]);
             cur[(2 * i + t) * CS + r] = acc;
-        }
-        __syncwarp();
+        });
+        tsync<NTHR>();
         return Kd;
     }
 
@@ -340,54 +331,51 @@ struct CircuitWarp {
     // site k = Q, cur <- site_{k-1} L.  Returns the new bond min(Dl, 2 Dr).
     __device__ int move_left(int k, int Dlm, int Dl, int Dr) {
         const int M = 2 * Dr, N = Dl;   // A^H is (2 Dr) x Dl
-        for (int o = lane; o < M * N; o += 32) {
-            const int l = o / M, sr = o % M;
-            const int s = sr / Dr, r = sr % Dr;
+        team_for_2d<NTHR>(N, M, lane, [&](int l, int sr) {
+            const int s = sr >= Dr ? 1 : 0, r = sr - s * Dr;
             th[l * LDM + sr] = conj(cvt<TQ>(cur[(2 * l + s) * CS + r]));
-        }
-        __syncwarp();
-        warp_qr<TQ>(th, LDM, M, N, tau, lane);
+        });
+        tsync<NTHR>();
+        team_qr<NTHR>(th, LDM, M, N, tau, red, lane);
         const int Kd = M < N ? M : N;
-        for (int o = lane; o < Kd * N; o += 32) {
-            const int i = o / N, c = o % N;
+        team_for_2d<NTHR>(Kd, N, lane, [&](int i, int c) {
             rb[i * CS + c] = cvt<T>(i <= c ? th[c * LDM + i] : czero<TQ>());   // R'(i, c)
-        }
-        __syncwarp();
-        warp_form_q<TQ>(th, LDM, M, Kd, tau, lane);
+        });
+        tsync<NTHR>();
+        team_form_q<NTHR>(th, LDM, M, Kd, tau, lane);
         // site k = Q'^H : (Kd x 2 x Dr), element (m, s, r) = conj(Q'(s*Dr + r, m))
         cx<T>* dst = site_ptr(k);
-        for (int o = lane; o < Kd * M; o += 32) {
-            const int m = o / M, sr = o % M;
-            const int s = sr / Dr, r = sr % Dr;
+        team_for_2d<NTHR>(Kd, M, lane, [&](int m, int sr) {
+            const int s = sr >= Dr ? 1 : 0, r = sr - s * Dr;
             dst[(2 * m + s) * ld + r] = conj(cvt<T>(th[m * LDM + sr]));
-        }
-        __syncwarp();
+        });
+        tsync<NTHR>();
         // cur <- site_{k-1} (Dlm x 2 x Dl) times L = R'^H (Dl x Kd)
-        load_site<T, CS>(nxt, site_ptr(k - 1), ld, Dlm, Dl, nullptr, lane);
-        __syncwarp();
-        for (int o = lane; o < 2 * Dlm * Kd; o += 32) {
-            const int row = o / Kd, m = o % Kd;
+        load_site<T, CS, NTHR>(nxt, site_ptr(k - 1), ld, Dlm, Dl, nullptr, lane);
+        tsync<NTHR>();
+        team_for_2d<NTHR>(2 * Dlm, Kd, lane, [&](int row, int m) {
             cx<T> acc = czero<T>();
             for (int l = m; l < Dl; ++l) cmac_cj(acc, rb[m * CS + l], nxt[row * CS + l]);
             cur[row * CS + m] = acc;
-        }
-        __syncwarp();
+        });
+        tsync<NTHR>();
         return Kd;
     }
 };
 
 // Pass description: bonds first..n-2; at bond k a CNOT if (k - first) % stride == 0
-// (ladder: stride 1), otherwise an exact centre move.
-template <typename T, typename TQ, int CHI, bool TRUNC>
-__device__ bool run_pass(CircuitWarp<T, TQ, CHI, TRUNC>& w, int first, int stride,
-                         int ansatz, const double* params, int params_n, int layer,
-                         const double* px, bool gates_on_load, bool fresh) {
-    constexpr int CS = CircuitWarp<T, TQ, CHI, TRUNC>::CS;
+// (ladder: stride 1), otherwise an exact centre move.  gates_on_load applies the
+// layer's one-qubit gates as the sites are loaded.  fresh: the state is the
+// initial product state (its normalised sites are already right-orthonormal).
+template <typename T, typename TQ, int CHI, bool TRUNC, int NTHR>
+__device__ bool run_pass(CircuitTeam<T, TQ, CHI, TRUNC, NTHR>& w, int first, int stride, int ansatz,
+                         const cx<T>* gates, int gn, int img, int layer, bool gates_on_load, bool fresh) {
+    constexpr int CS = CircuitTeam<T, TQ, CHI, TRUNC, NTHR>::CS;
     const int n = w.n, lane = w.lane;
     int* bd = w.bd;
-    // does any step of this pass truncate?  (bond dimensions only; lane 0)
-    int trunc = 0;
+    // does any step of this pass truncate?  (bond dimensions only; thread 0)
     if (lane == 0) {
+        int trunc = 0;
         int dl = bd[first];
         for (int k = first; k < n - 1; ++k) {
             if ((k - first) % stride == 0) {
@@ -400,35 +388,37 @@ __device__ bool run_pass(CircuitWarp<T, TQ, CHI, TRUNC>& w, int first, int strid
                 dl = m < bd[k + 1] ? m : bd[k + 1];
             }
         }
+        *w.flag = trunc;
     }
-    trunc = __shfl_sync(0xffffffffu, trunc, 0);
+    tsync<NTHR>();
+    const int trunc = *w.flag;
+    tsync<NTHR>();
     if (trunc && TRUNC && !fresh) {
-        // right-to-left LQ sweep: centre from n-1 (held in cur) to `first`.  A fresh
-        // product state needs none: its normalised sites are right-orthonormal.
+        // right-to-left LQ sweep: centre from n-1 (held in cur) to `first`
         for (int k = n - 1; k > first; --k) {
             const int nb = w.move_left(k, bd[k - 1], bd[k], bd[k + 1]);
             if (lane == 0) bd[k] = nb;
-            __syncwarp();
+            tsync<NTHR>();
         }
     } else {
         // the centre stays where it is; the pass starts from the stored site `first`
-        load_site<T, CS>(w.cur, w.site_ptr(first), w.ld, bd[first], bd[first + 1], nullptr, lane);
-        __syncwarp();
+        load_site<T, CS, NTHR>(w.cur, w.site_ptr(first), w.ld, bd[first], bd[first + 1], nullptr, lane);
+        tsync<NTHR>();
     }
     if (gates_on_load) {
-        const Gate1<T> g = layer_gate<T>(ansatz, params, params_n, layer, first, px[first]);
-        apply_gate_smem<T, CS>(w.cur, bd[first], bd[first + 1], g, lane);
-        __syncwarp();
+        const Gate1<T> g = table_gate<T>(gates, gn, ansatz, layer, img, first);
+        apply_gate_smem<T, CS, NTHR>(w.cur, bd[first], bd[first + 1], g, lane);
+        tsync<NTHR>();
     }
     for (int k = first; k < n - 1; ++k) {
         const int Dl = bd[k], Dm = bd[k + 1], Dr = bd[k + 2];
         if (gates_on_load) {
-            const Gate1<T> g = layer_gate<T>(ansatz, params, params_n, layer, k + 1, px[k + 1]);
-            load_site<T, CS>(w.nxt, w.site_ptr(k + 1), w.ld, Dm, Dr, &g, lane);
+            const Gate1<T> g = table_gate<T>(gates, gn, ansatz, layer, img, k + 1);
+            load_site<T, CS, NTHR>(w.nxt, w.site_ptr(k + 1), w.ld, Dm, Dr, &g, lane);
         } else {
-            load_site<T, CS>(w.nxt, w.site_ptr(k + 1), w.ld, Dm, Dr, nullptr, lane);
+            load_site<T, CS, NTHR>(w.nxt, w.site_ptr(k + 1), w.ld, Dm, Dr, nullptr, lane);
         }
-        __syncwarp();
+        tsync<NTHR>();
         int nb;
         if ((k - first) % stride == 0) {
             w.form_theta(Dl, Dm, Dr, true);
@@ -441,29 +431,30 @@ __device__ bool run_pass(CircuitWarp<T, TQ, CHI, TRUNC>& w, int first, int strid
             return false;
         }
         if (lane == 0) bd[k + 1] = nb;
-        __syncwarp();
+        tsync<NTHR>();
     }
-    store_site<T, CS>(w.site_ptr(n - 1), w.cur, w.ld, bd[n - 1], bd[n], lane);
-    __syncwarp();
+    store_site<T, CS, NTHR>(w.site_ptr(n - 1), w.cur, w.ld, bd[n - 1], bd[n], lane);
+    tsync<NTHR>();
     return true;
 }
 
-template <typename T, typename TQ, int CHI, bool TRUNC>
-__global__ void __launch_bounds__(256) circuit_kernel(
+// One team of NTHR threads per image.  NTHR = 32: a CTA holds blockDim/32 images
+// (one warp each, no block barriers); NTHR > 32: a CTA is one image.
+template <typename T, typename TQ, int CHI, bool TRUNC, int NTHR>
+__global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024 / NTHR / 2) circuit_kernel(
     const ImageMeta* __restrict__ meta, int n_images, const double* __restrict__ pixels,
-    const double* __restrict__ params, int params_n, int ansatz,
+    const cx<T>* __restrict__ gates, int gn, int ansatz,
     cx<T>* __restrict__ arena, int32_t* __restrict__ bonds_out,
     double* __restrict__ discarded_out, int* status) {
     using Lay = CircuitLayout<T, TQ, CHI, TRUNC>;
-    constexpr int CS = Lay::CS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int img = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int team = threadIdx.x / NTHR, lane = threadIdx.x % NTHR;
+    const int img = blockIdx.x * (blockDim.x / NTHR) + team;
     if (img >= n_images) return;
-    unsigned char* base = smem_raw + (size_t)warp * Lay::bytes;
+    unsigned char* base = smem_raw + (size_t)team * Lay::bytes;
 
     const ImageMeta mt = meta[img];
-    CircuitWarp<T, TQ, CHI, TRUNC> w;
+    CircuitTeam<T, TQ, CHI, TRUNC, NTHR> w;
     w.cur = reinterpret_cast<cx<T>*>(base + Lay::off_cur);
     w.nxt = reinterpret_cast<cx<T>*>(base + Lay::off_nxt);
     w.rb = reinterpret_cast<cx<T>*>(base + Lay::off_rb);
@@ -475,6 +466,8 @@ __global__ void __launch_bounds__(256) circuit_kernel(
     w.taud = reinterpret_cast<cx<double>*>(base + Lay::off_taud);
     w.lam = reinterpret_cast<double*>(base + Lay::off_lam);
     w.ord = reinterpret_cast<int*>(base + Lay::off_ord);
+    w.red = reinterpret_cast<double*>(base + Lay::off_red);
+    w.flag = reinterpret_cast<int*>(base + Lay::off_flag);
     w.lane = lane;
     w.n = mt.n;
     w.chi = mt.chi < CHI ? mt.chi : CHI;
@@ -486,31 +479,31 @@ __global__ void __launch_bounds__(256) circuit_kernel(
     const int n = mt.n;
 
     // |0...0> then the encoding R_Y(pi x) (ladder); every bond is 1
-    for (int k = lane; k <= n; k += 32) w.bd[k] = 1;
-    for (int k = lane; k < n; k += 32) {
+    for (int k = lane; k <= n; k += NTHR) w.bd[k] = 1;
+    for (int k = lane; k < n; k += NTHR) {
         cx<T>* s = w.site_ptr(k);
         double sn = 0.0, cs = 1.0;
         if (ansatz == 0) sincos(0.5 * M_PI * px[k], &sn, &cs);
         s[0] = mk<T>(T(cs), T(0));
         s[w.ld] = mk<T>(T(sn), T(0));
     }
-    __syncwarp();
+    tsync<NTHR>();
     for (int layer = 0; layer < mt.L; ++layer) {
         bool ok;
         if (ansatz == 0) {
-            ok = run_pass<T, TQ, CHI, TRUNC>(w, 0, 1, ansatz, params, params_n, layer, px, true, layer == 0);
+            ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 0, 1, ansatz, gates, gn, img, layer, true, layer == 0);
         } else {
-            ok = run_pass<T, TQ, CHI, TRUNC>(w, 0, 2, ansatz, params, params_n, layer, px, true, layer == 0);
-            if (ok && n > 2) ok = run_pass<T, TQ, CHI, TRUNC>(w, 1, 2, ansatz, params, params_n, layer, px, false, false);
+            ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 0, 2, ansatz, gates, gn, img, layer, true, layer == 0);
+            if (ok && n > 2)
+                ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 1, 2, ansatz, gates, gn, img, layer, false, false);
         }
         if (!ok) return;
     }
     // A pass ends with the centre at n-1.  The paper ansatz's second pass leaves
     // site 0 as written by the first pass (left-orthonormal), so the whole chain is
     // left-canonical either way.
-    for (int k = lane; k <= n; k += 32) bonds_out[mt.bond_off + k] = w.bd[k];
+    for (int k = lane; k <= n; k += NTHR) bonds_out[mt.bond_off + k] = w.bd[k];
     if (lane == 0) discarded_out[img] = w.discarded;
-    (void)CS;
 }
 
 }  // namespace mpsano

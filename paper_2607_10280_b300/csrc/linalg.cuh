@@ -1,38 +1,91 @@
-// Warp-level small dense linear algebra on shared memory: Householder QR,
-// explicit Q, and a cyclic Jacobi eigensolver for Hermitian matrices.
+// Small dense linear algebra on shared memory for a team of NTHR threads (one
+// warp, or the whole CTA when NTHR > 32): Householder QR, the explicit Q factor,
+// and a cyclic Jacobi eigensolver for Hermitian matrices (run by warp 0).
 // Matrices are column-major: element (r, c) at A[c * ld + r].
 #pragma once
 #include "common.cuh"
 
 namespace mpsano {
 
-// Largest power of two G <= 32 with G * nc <= 32 (at least 1): lanes per column
-// when nc columns are processed by one warp.
-__device__ __forceinline__ int lanes_per_col(int nc) {
+template <int NTHR>
+__device__ __forceinline__ void tsync() {
+    if (NTHR == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// Sum of v over the team; every thread gets the result.  red: NTHR/32 doubles.
+template <int NTHR, typename T>
+__device__ __forceinline__ T team_sum(T v, double* red, int tid) {
+    v = warp_sum(v);
+    if (NTHR == 32) return v;
+    if ((tid & 31) == 0) red[tid >> 5] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NTHR / 32; ++w) s += red[w];
+    __syncthreads();
+    return (T)s;
+}
+
+// Calls f(row, col) for every row < R and col < C, spreading the pairs over the
+// NTHR threads without integer division: columns are padded to a power of two cp,
+// thread -> (col = tid % cp, first row = tid / cp).
+template <int NTHR, class F>
+__device__ __forceinline__ void team_for_2d(int R, int C, int tid, F f) {
+    if (C <= 0 || R <= 0) return;
+    const int cp = C <= 1 ? 1 : 1 << (32 - __clz(C - 1));
+    if (cp >= NTHR) {
+        for (int row = 0; row < R; ++row)
+            for (int col = tid; col < C; col += NTHR) f(row, col);
+    } else {
+        const int shift = __ffs(cp) - 1;
+        const int col = tid & (cp - 1);
+        const int rstep = NTHR >> shift;
+        if (col < C) {
+#pragma unroll 4
+            for (int row = tid >> shift; row < R; row += rstep) f(row, col);
+        }
+    }
+}
+
+// Largest power of two G <= 32 with G * nc <= NTHR (at least 1): threads per column
+// when nc columns are processed by the team.
+template <int NTHR>
+__device__ __forceinline__ int threads_per_col(int nc) {
     int G = 32;
-    while (G > 1 && G * nc > 32) G >>= 1;
+    while (G > 1 && G * nc > NTHR) G >>= 1;
     return G;
 }
 
 // A(j:M, j+1:N) <- (I - t v v^H) A(j:M, j+1:N), v = [1; A(j+1:M, j)] stored in column j.
-// Rows are split over G lanes per column; partial dot products are combined with
-// xor-shuffles inside each aligned lane group.
-template <typename T>
-__device__ __forceinline__ void apply_reflector(cx<T>* A, int ld, int M, int N, int j, cx<T> t, int lane) {
+// Rows are split over G threads per column; partial dot products are combined with
+// xor-shuffles inside each aligned group of G lanes.
+template <int NTHR, typename T>
+__device__ __forceinline__ void apply_reflector(cx<T>* A, int ld, int M, int N, int j, cx<T> t, int tid) {
     const int nc = N - j - 1;
     if (nc <= 0) return;
     const cx<T>* v = A + j * ld;
-    const int G = lanes_per_col(nc);
-    const int cg = lane / G, g = lane % G;
-    const int per_pass = 32 / G;
+    const int G = threads_per_col<NTHR>(nc);
+    const int cg = tid / G, g = tid % G;
+    const int per_pass = NTHR / G;
     for (int c0 = 0; c0 < nc; c0 += per_pass) {
         const int cc = c0 + cg;
         const bool active = cc < nc;
         cx<T>* a = A + (j + 1 + (active ? cc : 0)) * ld;
         cx<T> w = czero<T>();
         if (active) {
+            // four independent partial sums keep the FMA chains short
+            cx<T> w1 = czero<T>(), w2 = czero<T>(), w3 = czero<T>();
             if (g == 0) w = a[j];
-            for (int r = j + 1 + g; r < M; r += G) cmac_cj(w, v[r], a[r]);
+            int r = j + 1 + g;
+            for (; r + 3 * G < M; r += 4 * G) {
+                cmac_cj(w, v[r], a[r]);
+                cmac_cj(w1, v[r + G], a[r + G]);
+                cmac_cj(w2, v[r + 2 * G], a[r + 2 * G]);
+                cmac_cj(w3, v[r + 3 * G], a[r + 3 * G]);
+            }
+            for (; r < M; r += G) cmac_cj(w, v[r], a[r]);
+            w = (w + w1) + (w2 + w3);
         }
         for (int o = G >> 1; o > 0; o >>= 1) {
             w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
@@ -41,6 +94,7 @@ __device__ __forceinline__ void apply_reflector(cx<T>* A, int ld, int M, int N, 
         if (active) {
             w = t * w;
             if (g == 0) a[j] = a[j] - w;
+#pragma unroll 4
             for (int r = j + 1 + g; r < M; r += G) a[r] = a[r] - v[r] * w;
         }
     }
@@ -49,15 +103,15 @@ __device__ __forceinline__ void apply_reflector(cx<T>* A, int ld, int M, int N, 
 // Householder QR of the M x N matrix A (LAPACK geqr2 convention, K = min(M, N)
 // reflectors H_j = I - tau_j v_j v_j^H, A = H_0 ... H_{K-1} R).  On return the
 // upper trapezoid holds R (real diagonal), the strict lower part the reflector
-// tails, tau[0..K) the scalars.
-template <typename T>
-__device__ void warp_qr(cx<T>* A, int ld, int M, int N, cx<T>* tau, int lane) {
+// tails, tau[0..K) the scalars.  red: NTHR/32 doubles of scratch.
+template <int NTHR, typename T>
+__device__ void team_qr(cx<T>* A, int ld, int M, int N, cx<T>* tau, double* red, int tid) {
     const int K = M < N ? M : N;
     for (int j = 0; j < K; ++j) {
         cx<T>* col = A + j * ld;
         T s = T(0);
-        for (int r = j + 1 + lane; r < M; r += 32) s += norm2(col[r]);
-        s = warp_sum(s);
+        for (int r = j + 1 + tid; r < M; r += NTHR) s += norm2(col[r]);
+        s = team_sum<NTHR>(s, red, tid);
         const cx<T> alpha = col[j];
         const bool trivial = (s == T(0)) && (alpha.im == T(0));
         cx<T> t = czero<T>();
@@ -71,45 +125,46 @@ __device__ void warp_qr(cx<T>* A, int ld, int M, int N, cx<T>* tau, int lane) {
             const T dd = norm2(d);
             scale = mk<T>(d.re / dd, -d.im / dd);
         }
-        __syncwarp();
+        tsync<NTHR>();
         if (!trivial) {
-            for (int r = j + 1 + lane; r < M; r += 32) col[r] = col[r] * scale;
+            for (int r = j + 1 + tid; r < M; r += NTHR) col[r] = col[r] * scale;
         }
-        if (lane == 0) {
+        if (tid == 0) {
             col[j] = mk<T>(beta, T(0));
             tau[j] = t;
         }
-        __syncwarp();
-        if (!trivial) apply_reflector(A, ld, M, N, j, conj(t), lane);
-        __syncwarp();
+        tsync<NTHR>();
+        if (!trivial) apply_reflector<NTHR>(A, ld, M, N, j, conj(t), tid);
+        tsync<NTHR>();
     }
 }
 
-// Overwrite the reflectors left by warp_qr with the explicit M x K factor Q
+// Overwrite the reflectors left by team_qr with the explicit M x K factor Q
 // (LAPACK ung2r): Q = H_0 ... H_{K-1} [I_K; 0].
-template <typename T>
-__device__ void warp_form_q(cx<T>* A, int ld, int M, int K, const cx<T>* tau, int lane) {
+template <int NTHR, typename T>
+__device__ void team_form_q(cx<T>* A, int ld, int M, int K, const cx<T>* tau, int tid) {
     for (int i = K - 1; i >= 0; --i) {
         const cx<T> t = tau[i];
-        if (t.re != T(0) || t.im != T(0)) apply_reflector(A, ld, M, K, i, t, lane);
-        __syncwarp();
+        if (t.re != T(0) || t.im != T(0)) apply_reflector<NTHR>(A, ld, M, K, i, t, tid);
+        tsync<NTHR>();
         cx<T>* v = A + i * ld;
-        for (int r = lane; r < M; r += 32) {
+        for (int r = tid; r < M; r += NTHR) {
             cx<T> val;
             if (r < i) val = czero<T>();
             else if (r == i) val = mk<T>(T(1) - t.re, -t.im);
             else val = czero<T>() - t * v[r];
             v[r] = val;
         }
-        __syncwarp();
+        tsync<NTHR>();
     }
 }
 
 // Cyclic parallel (round-robin) Jacobi eigensolver for the K x K Hermitian matrix G
-// (column-major, ld), K <= 64.  On return diag(G) holds the eigenvalues and the
-// columns of V (K x K, ld) the eigenvectors: G_in = V diag(lambda) V^H.  Each lane
-// owns one disjoint index pair per round; a round applies all rotations to the
-// columns of G and V, then to the rows of G.  Returns the sweeps used.
+// (column-major, ld), K <= 64, run by one warp.  On return diag(G) holds the
+// eigenvalues and the columns of V (K x K, ld) the eigenvectors:
+// G_in = V diag(lambda) V^H.  Each lane owns one disjoint index pair per round; a
+// round applies all rotations to the columns of G and V, then to the rows of G.
+// Returns the sweeps used.
 static __device__ int warp_jacobi_eigh(cx<double>* G, cx<double>* V, int ld, int K, int lane, int max_sweeps) {
     for (int c = 0; c < K; ++c)
         for (int r = lane; r < K; r += 32) V[c * ld + r] = mk<double>(r == c ? 1.0 : 0.0, 0.0);

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "batch.h"
+#include "circuit.cuh"
 #include "common.cuh"
 #include "epilogue.cuh"
 
@@ -48,6 +49,23 @@ void timing_begin(mps_batch* b, int kind) {
     mps_batch::TimedLaunch t{kind, pooled_event(b), pooled_event(b)};
     cudaEventRecord(t.start, b->stream);
     b->timed.push_back(t);
+}
+
+mps_status launch_gate_table(mps_batch* b, int ansatz, int L_max, const double* params, int params_n,
+                             const double* pixels) {
+    const int rows = ansatz == MPS_ANSATZ_LADDER ? L_max : b->B;
+    const int total = rows * b->gate_n;
+    if (total <= 0) return MPS_OK;
+    const int threads = 128;
+    if (b->prec == MPS_FP64)
+        gate_table_kernel<double><<<(total + threads - 1) / threads, threads, 0, b->stream>>>(
+            ansatz, rows, b->gate_n, params, params_n, b->meta_d, pixels, static_cast<cx<double>*>(b->gates));
+    else
+        gate_table_kernel<float><<<(total + threads - 1) / threads, threads, 0, b->stream>>>(
+            ansatz, rows, b->gate_n, params, params_n, b->meta_d, pixels, static_cast<cx<float>*>(b->gates));
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return MPS_OK;
 }
 
 void timing_end(mps_batch* b) {
@@ -151,6 +169,7 @@ void free_batch(mps_batch* b) {
     cudaFree(b->bonds_d);
     cudaFree(b->discarded_d);
     cudaFree(b->status_d);
+    if (b->gates_owned) cudaFree(b->gates);
     delete b;
 }
 
@@ -255,11 +274,15 @@ mps_status mps_destroy_batch(mps_batch* b) {
     return MPS_OK;
 }
 
-mps_status mps_set_launch_shape(mps_batch* b, int32_t images_per_cta, int32_t pauli_threads) {
+mps_status mps_set_launch_shape(mps_batch* b, int32_t images_per_cta, int32_t circuit_threads,
+                                int32_t pauli_threads) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    if (circuit_threads != 0 && circuit_threads != 32 && circuit_threads != 64 && circuit_threads != 128)
+        return fail(MPS_ERR_INVALID_ARG, "circuit_threads %d (32, 64 or 128)", circuit_threads);
+    if (circuit_threads) b->circuit_threads = circuit_threads;
     if (images_per_cta < 0 || images_per_cta > 8) return fail(MPS_ERR_INVALID_ARG, "images_per_cta %d", images_per_cta);
-    if (pauli_threads < 0 || pauli_threads > 512 || pauli_threads % 32)
-        return fail(MPS_ERR_INVALID_ARG, "pauli_threads %d", pauli_threads);
+    if (pauli_threads != 0 && pauli_threads != 32 && pauli_threads != 64 && pauli_threads != 128)
+        return fail(MPS_ERR_INVALID_ARG, "pauli_threads %d (32, 64 or 128)", pauli_threads);
     if (images_per_cta) b->images_per_cta = images_per_cta;
     if (pauli_threads) b->pauli_warps = pauli_threads / 32;
     return MPS_OK;
@@ -304,12 +327,25 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         CUDA_TRY(cudaMemcpyAsync(b->meta_d, b->meta_pinned, sizeof(ImageMeta) * b->B,
                                  cudaMemcpyHostToDevice, b->stream));
     }
-    mps_status st;
+    // one-qubit gate table (FP64 math, rounded to the state type)
+    const int rows = circ->ansatz == MPS_ANSATZ_LADDER ? L_max : b->B;
+    const size_t gbytes = (size_t)std::max(rows, 1) * b->n_max * 4 * b->elem;
+    if (gbytes > b->gates_bytes) {
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        cudaFree(b->gates);
+        b->gates = nullptr;
+        b->gates_bytes = 0;
+        CUDA_TRY(cudaMalloc(&b->gates, gbytes));
+        b->gates_bytes = gbytes;
+    }
+    b->gate_n = b->n_max;
     const double* pr = circ->ansatz == MPS_ANSATZ_LADDER ? circ->params : nullptr;
+    mps_status st = launch_gate_table(b, circ->ansatz, L_max, pr, circ->params_n, pixels);
+    if (st != MPS_OK) return st;
     switch (b->prec) {
-        case MPS_FP64: st = launch_circuit_fp64(b, chi_tpl, trunc, pixels, pr, circ->params_n, circ->ansatz); break;
-        case MPS_MIXED: st = launch_circuit_mixed(b, chi_tpl, trunc, pixels, pr, circ->params_n, circ->ansatz); break;
-        default: st = launch_circuit_orth64(b, chi_tpl, trunc, pixels, pr, circ->params_n, circ->ansatz); break;
+        case MPS_FP64: st = launch_circuit_fp64(b, chi_tpl, trunc, pixels, circ->ansatz); break;
+        case MPS_MIXED: st = launch_circuit_mixed(b, chi_tpl, trunc, pixels, circ->ansatz); break;
+        default: st = launch_circuit_orth64(b, chi_tpl, trunc, pixels, circ->ansatz); break;
     }
     if (st != MPS_OK) return st;
     b->chi_tpl = chi_tpl;

@@ -18,6 +18,7 @@ constexpr int NA_MAX_IMAGES = 64;
 constexpr int NA_MAX_DEVICES = 64;
 constexpr size_t NA_ARENA_BYTES = size_t(12) << 20;   // site tensors
 constexpr size_t NA_RENV_BYTES = size_t(6) << 20;     // right environments
+constexpr size_t NA_GATE_BYTES = size_t(512) << 10;   // one-qubit gate table
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t OFF_META = 0;
@@ -28,11 +29,12 @@ constexpr size_t OFF_DISC = align256(OFF_NORMS + sizeof(double) * NA_MAX_IMAGES)
 constexpr size_t OFF_STATUS = align256(OFF_DISC + sizeof(double) * NA_MAX_IMAGES);
 constexpr size_t OFF_ARENA = align256(OFF_STATUS + sizeof(int));
 constexpr size_t OFF_RENV = align256(OFF_ARENA + NA_ARENA_BYTES);
-constexpr size_t NA_TOTAL = align256(OFF_RENV + NA_RENV_BYTES);
+constexpr size_t OFF_GATES = align256(OFF_RENV + NA_RENV_BYTES);
+constexpr size_t NA_TOTAL = align256(OFF_GATES + NA_GATE_BYTES);
 
 }  // namespace
 
-// The scratch array.  Every GPU that loads this library holds it (about 18 MiB)
+// The scratch array.  Every GPU that loads this library holds it (about 18.5 MiB)
 // until the process exits.  Host code must not use its name as an address: the
 // device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_TOTAL];
@@ -131,6 +133,10 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
     if (chi_tpl > 32) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > 32", mx);
     const size_t arena = (size_t)n_images * n * 2 * ld * ld * sizeof(cx<float>);
     const size_t renv = (size_t)n_images * n * ld * ld * sizeof(cx<float>);
+    const size_t gate_bytes = (size_t)(L > 0 ? L : 1) * n * 4 * sizeof(cx<float>);
+    if (gate_bytes > NA_GATE_BYTES)
+        return fail(MPS_ERR_INVALID_ARG, "L * p^2 = %d gate-table entries exceed the limit of %zu in the "
+                    "no-allocation entry point", L * n, NA_GATE_BYTES / (4 * sizeof(cx<float>)));
     if (arena > NA_ARENA_BYTES || renv > NA_RENV_BYTES)
         return fail(MPS_ERR_INVALID_ARG,
                     "%d images of %dx%d at bond %d need %zu B of site storage (limit %zu) and %zu B of "
@@ -157,6 +163,10 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
     b.bonds_d = reinterpret_cast<int32_t*>(base + OFF_BONDS);
     b.discarded_d = reinterpret_cast<double*>(base + OFF_DISC);
     b.status_d = reinterpret_cast<int*>(base + OFF_STATUS);
+    b.gates = base + OFF_GATES;
+    b.gates_bytes = NA_GATE_BYTES;
+    b.gates_owned = false;
+    b.gate_n = n;
 
     const int threads = 128;
     const int work = std::max(n_images * p, n_images);
@@ -164,7 +174,9 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
         b.meta_d, b.units_d, b.discarded_d, b.status_d, n_images, p, chi, L, ld);
     CUDA_TRY(cudaGetLastError());
     count_launch();
-    st = launch_circuit_mixed(&b, chi_tpl, trunc, pixels, params, params_n, MPS_ANSATZ_LADDER);
+    st = launch_gate_table(&b, MPS_ANSATZ_LADDER, L, params, params_n, pixels);
+    if (st != MPS_OK) return st;
+    st = launch_circuit_mixed(&b, chi_tpl, trunc, pixels, MPS_ANSATZ_LADDER);
     if (st != MPS_OK) return st;
     b.chi_tpl = chi_tpl;
     return launch_pauli_mixed(&b, out);

@@ -20,7 +20,11 @@
 //                 P_a[s][s'] A[l,s',r'] and <P_a (x) P_b> = <E_a, C_b> / <psi|psi>,
 //                 <P_a> = <E_a, R_i> / <psi|psi> (elementwise product summed).
 //
-// D x D matrices live in per-warp shared memory with row stride CS = CHI + 1.
+// Every contraction is a small complex GEMM done by a team of UW warps (one
+// (image, column) unit per CTA) with a register tile of TM x TN outputs per thread;
+// threads take interleaved rows (tm + MT*i) and columns (tn + NT*j) so that the shared-memory reads of a k-step hit distinct banks or
+// broadcast.  D x D matrices use row stride CS = CHI + 1; the GEMM scratch S has
+// 3*CHI rows of stride ZS = 2*CHI + 1.
 #pragma once
 #include "common.cuh"
 
@@ -30,132 +34,228 @@ template <typename T, int CHI>
 struct PauliLayout {
     static constexpr int CS = CHI + 1;
     static constexpr int MAT = CHI * CS;
-    // A (2 MAT), R, Z (2 MAT), C (3 MAT), E
-    static constexpr int NMAT = 9;
-    static constexpr size_t bytes = sizeof(cx<T>) * NMAT * MAT;
+    static constexpr int ZS = 2 * CHI + 1;
+    static constexpr int SROWS = 3 * CHI;
+    // A (2 MAT), R (1 MAT), C (3 MAT), S (3 CHI rows x ZS)
+    static constexpr int ELEMS = 6 * MAT + SROWS * ZS;
+    static constexpr size_t bytes = sizeof(cx<T>) * ELEMS;
+    // plus the cross-warp reduction buffer of a UW-warp team
+    static constexpr size_t team_bytes(int uw) { return bytes + sizeof(T) * 12 * uw; }
 };
 
-// Z_s[r][l'] = sum_{r'} M[r][r'] A[l', s, r'] for s = 0, 1  (M is Dr x Dr, Z is Dr x Dl)
-template <typename T, int CS>
-__device__ __forceinline__ void prod_MAt(const cx<T>* M, const cx<T>* A, cx<T>* Z0, cx<T>* Z1,
-                                         int Dl, int Dr, int lane) {
-    const int tot = 2 * Dl * Dr;
-    for (int o = lane; o < tot; o += 32) {
-        const int r = o % Dr;
-        const int rest = o / Dr;
-        const int lp = rest % Dl, s = rest / Dl;
-        const cx<T>* m = M + r * CS;
-        const cx<T>* a = A + (2 * lp + s) * CS;
-        cx<T> acc = czero<T>();
-#pragma unroll 4
-        for (int rp = 0; rp < Dr; ++rp) cmac(acc, m[rp], a[rp]);
-        (s ? Z1 : Z0)[r * CS + lp] = acc;
-    }
-}
+// Register-tile shape for an M x N output (compile-time bounds) computed by NTHR
+// threads: MT x NT threads, TM x TN complex accumulators per thread, at most 48
+// (float) or 24 (double).
+template <typename T, int M_HINT, int N_HINT, int NTHR = 32>
+struct Tile {
+    static constexpr int MT = (NTHR == 32) ? ((M_HINT >= 2 * N_HINT) ? 8 : 4)
+                                           : ((M_HINT >= 2 * N_HINT) ? 16 : (M_HINT * 2 > N_HINT ? 8 : 4));
+    static constexpr int NT = NTHR / MT;
+    static constexpr int CAP = sizeof(T) == 4 ? 48 : 24;
+    static constexpr int TM0 = (M_HINT + MT - 1) / MT;
+    static constexpr int TM = TM0 < 1 ? 1 : (TM0 > CAP ? CAP : TM0);
+    static constexpr int TN0 = (N_HINT + NT - 1) / NT;
+    static constexpr int TN1 = TN0 < 1 ? 1 : TN0;
+    static constexpr int TN = TM * TN1 <= CAP ? TN1 : (CAP / TM < 1 ? 1 : CAP / TM);
+};
 
-// out[l][l'] = sum_r conj(A[l, sa, r]) Za[r][l'] (+ conj(A[l, sb, r]) Zb[r][l'] if Zb)
-template <typename T, int CS>
-__device__ __forceinline__ void prod_AhZ(const cx<T>* A, int sa, const cx<T>* Za, int sb, const cx<T>* Zb,
-                                         cx<T>* out, int Dl, int Dr, int lane) {
-    for (int o = lane; o < Dl * Dl; o += 32) {
-        const int l = o / Dl, lp = o % Dl;
-        cx<T> acc = czero<T>();
-        const cx<T>* aa = A + (2 * l + sa) * CS;
-#pragma unroll 4
-        for (int r = 0; r < Dr; ++r) cmac_cj(acc, aa[r], Za[r * CS + lp]);
-        if (Zb) {
-            const cx<T>* ab = A + (2 * l + sb) * CS;
-#pragma unroll 4
-            for (int r = 0; r < Dr; ++r) cmac_cj(acc, ab[r], Zb[r * CS + lp]);
+// out[m][n] = sum_{seg < NSEG} sum_{k < K} opA(Ab[ao(m) + seg*as_seg + k*as])
+//                                          * Bb[bo(n) + seg*bs_seg + k*bs]
+// for m < M, n < N, delivered through store(m, n, value).
+template <typename T, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, class AO, class BO, class ST>
+__device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as_seg,
+                                          const cx<T>* Bb, BO bo, int bs, int bs_seg,
+                                          int M, int N, int K, ST store, int lane) {
+    const int tm = lane / NT, tn = lane % NT;
+    for (int m0 = 0; m0 < M; m0 += MT * TM) {
+        for (int n0 = 0; n0 < N; n0 += NT * TN) {
+            int aoff[TM], boff[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                const int m = m0 + tm + MT * i;
+                aoff[i] = ao(m < M ? m : M - 1);
+            }
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int n = n0 + tn + NT * j;
+                boff[j] = bo(n < N ? n : N - 1);
+            }
+            cx<T> acc[TM][TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = czero<T>();
+#pragma unroll
+            for (int seg = 0; seg < NSEG; ++seg) {
+                const cx<T>* As = Ab + seg * as_seg;
+                const cx<T>* Bs = Bb + seg * bs_seg;
+#pragma unroll 2
+                for (int k = 0; k < K; ++k) {
+                    cx<T> a[TM], b[TN];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i) a[i] = As[aoff[i] + k * as];
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) b[j] = Bs[boff[j] + k * bs];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) {
+                            if (CONJA) cmac_cj(acc[i][j], a[i], b[j]);
+                            else cmac(acc[i][j], a[i], b[j]);
+                        }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                const int m = m0 + tm + MT * i;
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    const int n = n0 + tn + NT * j;
+                    if (m < M && n < N) store(m, n, acc[i][j]);
+                }
+            }
         }
-        out[l * CS + lp] = acc;
     }
 }
 
-template <typename T, int CS>
+// S[b*Dr + r][n] = sum_k C_b[r][k] A[n][k]: NB source matrices (Dr x Dr, stride MAT)
+// times the transposed site rows n = 2l + s < 2 Dl.
+__device__ __forceinline__ void team_sync() { __syncthreads(); }
+
+template <typename T, int CHI, int NB, int NTHR>
+__device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane) {
+    using Lay = PauliLayout<T, CHI>;
+    constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
+    using Tl = Tile<T, NB * CHI, 2 * CHI, NTHR>;
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false>(
+        C, [Dr](int m) { return (m / Dr) * MAT + (m % Dr) * CS; }, 1, 0,
+        A, [](int n) { return n * CS; }, 1, 0, NB * Dr, 2 * Dl, Dr,
+        [S](int m, int n, cx<T> v) { S[m * ZS + n] = v; }, lane);
+}
+
+// Transfer of NB matrices through a site A (Dl x 2 x Dr), in place:
+//   C_b <- sum_s conj(A^s) C_b A^{sT}     (C_b: Dr x Dr in, Dl x Dl out)
+// with S[b*Dr + r][2l'+s] = (C_b A^{sT})[r][l'] as the intermediate.
+template <typename T, int CHI, int NB, int NTHR>
+__device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane) {
+    using Lay = PauliLayout<T, CHI>;
+    constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
+    times_site_t<T, CHI, NB, NTHR>(C, A, S, Dl, Dr, lane);
+    team_sync();
+    using Tl = Tile<T, CHI, NB * CHI, NTHR>;
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true>(
+        A, [](int l) { return 2 * l * CS; }, 1, CS,
+        S, [Dl, Dr](int n) { return (n / Dl) * Dr * ZS + 2 * (n % Dl); }, ZS, 1, Dl, NB * Dl, Dr,
+        [C, Dl](int l, int n, cx<T> v) { C[(n / Dl) * MAT + l * CS + (n % Dl)] = v; }, lane);
+    team_sync();
+}
+
+// F[m][n] = sum_l conj(A[2l+s_m][r_m]) A[2l+s_n][r_n], m = s_m*Dr + r_m, n = s_n*Dr + r_n:
+// the four physical blocks F_{ss'} of a left site, into S rows CHI .. CHI + 2 Dr.
+template <typename T, int CHI, int NTHR>
+__device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane) {
+    using Lay = PauliLayout<T, CHI>;
+    constexpr int CS = Lay::CS, ZS = Lay::ZS;
+    using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
+    cx<T>* F = S + CHI * ZS;
+    auto off = [Dr](int m) { return (m / Dr) * CS + (m % Dr); };
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true>(
+        A, off, 2 * CS, 0, A, off, 2 * CS, 0, 2 * Dr, 2 * Dr, Dl,
+        [F](int m, int n, cx<T> v) { F[m * ZS + n] = v; }, lane);
+}
+
+// <E_a, Y> for a = X, Y, Z (from the blocks F_{ss'} in S) and Y in {C_X, C_Y, C_Z, R}:
+// out[4(a-1) + y].  C may be null (then only the R column is formed).  Warp 0 alone
+// forms the sums, so the summation order (and every bit of the result) does not
+// depend on the team size; the other warps read the sums from red.
+template <typename T, int CHI, int NTHR>
+__device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const cx<T>* R, int D, T* out,
+                                          T* red, int lane) {
+    using Lay = PauliLayout<T, CHI>;
+    constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
+    const cx<T>* F = S + CHI * ZS;
+    if (lane < 32) {
+        T acc[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) acc[i] = T(0);
+        for (int o = lane; o < D * D; o += 32) {
+            const int r = o / D, rp = o % D;
+            const cx<T> f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
+            const cx<T> f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
+            cx<T> e[3];
+            e[0] = f01 + f10;                                     // X
+            e[1] = mk<T>(f01.im - f10.im, f10.re - f01.re);       // Y: i (F10 - F01)
+            e[2] = f00 - f11;                                     // Z
+            cx<T> y[4];
+            y[3] = R[r * CS + rp];
+            if (C) {
+#pragma unroll
+                for (int b = 0; b < 3; ++b) y[b] = C[b * MAT + r * CS + rp];
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (C || b == 3) acc[4 * a + b] += e[a].re * y[b].re - e[a].im * y[b].im;
+        }
+#pragma unroll
+        for (int i = 0; i < 12; ++i) out[i] = warp_sum(acc[i]);
+        if (NTHR > 32 && lane == 0)
+#pragma unroll
+            for (int i = 0; i < 12; ++i) red[i] = out[i];
+    }
+    if (NTHR > 32) {
+        team_sync();
+        if (lane >= 32)
+#pragma unroll
+            for (int i = 0; i < 12; ++i) out[i] = red[i];
+        team_sync();
+    }
+}
+
+// Closings of a right site A (Dl x 2 x Dr) with right environment R:
+//   G[2l+s][2l'+s'] = sum_r conj(A[2l+s][r]) (R A^{s'T})[r][l'],
+//   C_X = G01 + G10, C_Y = i (G10 - G01), C_Z = G00 - G11  (Dl x Dl each, into C).
+template <typename T, int CHI, int NTHR>
+__device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* R, cx<T>* C, cx<T>* S,
+                                               int Dl, int Dr, int lane) {
+    using Lay = PauliLayout<T, CHI>;
+    constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
+    times_site_t<T, CHI, 1, NTHR>(R, A, S, Dl, Dr, lane);   // S[r][n] = (R A^T)[r][n]
+    team_sync();
+    cx<T>* G = S + CHI * ZS;
+    using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true>(
+        A, [](int m) { return m * CS; }, 1, 0, S, [](int n) { return n; }, ZS, 0, 2 * Dl, 2 * Dl, Dr,
+        [G](int m, int n, cx<T> v) { G[m * ZS + n] = v; }, lane);
+    team_sync();
+    for (int o = lane; o < Dl * Dl; o += NTHR) {
+        const int l = o / Dl, lp = o % Dl;
+        const cx<T> g00 = G[(2 * l) * ZS + 2 * lp], g01 = G[(2 * l) * ZS + 2 * lp + 1];
+        const cx<T> g10 = G[(2 * l + 1) * ZS + 2 * lp], g11 = G[(2 * l + 1) * ZS + 2 * lp + 1];
+        const cx<T> d = g10 - g01;
+        C[l * CS + lp] = g01 + g10;
+        C[MAT + l * CS + lp] = mk<T>(-d.im, d.re);
+        C[2 * MAT + l * CS + lp] = g00 - g11;
+    }
+    team_sync();
+}
+
+template <typename T, int CS, int NTHR = 32>
 __device__ __forceinline__ void load_site_p(cx<T>* dst, const cx<T>* src, int ld, int Dl, int Dr, int lane) {
-    for (int o = lane; o < 2 * Dl * Dr; o += 32) {
+    for (int o = lane; o < 2 * Dl * Dr; o += NTHR) {
         const int row = o / Dr, r = o % Dr;
         dst[row * CS + r] = src[row * ld + r];
     }
 }
 
-template <typename T, int CS>
+template <typename T, int CS, int NTHR = 32>
 __device__ __forceinline__ void load_mat(cx<T>* dst, const cx<T>* src, int ld, int D, int lane) {
-    for (int o = lane; o < D * D; o += 32) dst[(o / D) * CS + (o % D)] = src[(o / D) * ld + (o % D)];
-}
-
-// sum_{r,r'} X[r][r'] Y[r][r'] (real part), full-warp result
-template <typename T, int CS>
-__device__ __forceinline__ T dot_re(const cx<T>* X, const cx<T>* Y, int D, int lane) {
-    T acc = T(0);
-    for (int o = lane; o < D * D; o += 32) {
-        const int i = (o / D) * CS + (o % D);
-        acc = fma(X[i].re, Y[i].re, acc);
-        acc = fma(-X[i].im, Y[i].im, acc);
-    }
-    return warp_sum(acc);
-}
-
-// E_a (a = 1..3: X, Y, Z) of a left site A (Dl x 2 x Dr) with identity left
-// environment: E_a = sum_{s,s'} P_a[s][s'] F_{ss'}, F_{ss'}[r][r'] = sum_l conj(A[l,s,r]) A[l,s',r'].
-template <typename T, int CS>
-__device__ __forceinline__ void left_pauli_env(const cx<T>* A, int a, cx<T>* E, int Dl, int Dr, int lane) {
-    for (int o = lane; o < Dr * Dr; o += 32) {
-        const int r = o / Dr, rp = o % Dr;
-        cx<T> v = czero<T>();
-        if (a == 3) {  // Z: F00 - F11
-            cx<T> f0 = czero<T>(), f1 = czero<T>();
-            for (int l = 0; l < Dl; ++l) {
-                cmac_cj(f0, A[(2 * l) * CS + r], A[(2 * l) * CS + rp]);
-                cmac_cj(f1, A[(2 * l + 1) * CS + r], A[(2 * l + 1) * CS + rp]);
-            }
-            v = f0 - f1;
-        } else {
-            cx<T> f01 = czero<T>(), f10 = czero<T>();
-            for (int l = 0; l < Dl; ++l) {
-                cmac_cj(f01, A[(2 * l) * CS + r], A[(2 * l + 1) * CS + rp]);
-                cmac_cj(f10, A[(2 * l + 1) * CS + r], A[(2 * l) * CS + rp]);
-            }
-            if (a == 1) v = f01 + f10;                       // X
-            else v = mk<T>(f01.im - f10.im, f10.re - f01.re);  // Y: -i f01 + i f10
-        }
-        E[r * CS + rp] = v;
-    }
-}
-
-// Closings of a right site: from G_{ss'} = conj(A^s) R A^{s'T}:
-//   C_X = G01 + G10, C_Y = -i G01 + i G10, C_Z = G00 - G11, R_new = G00 + G11.
-// Z0, Z1 hold R A^{sT}.  G10 = G01^H because R is Hermitian.
-template <typename T, int CS>
-__device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* Z0, const cx<T>* Z1,
-                                               cx<T>* CX, cx<T>* CY, cx<T>* CZ, cx<T>* Rnew,
-                                               int Dl, int Dr, int lane) {
-    // G00 -> CZ, G11 -> CX, G01 -> CY (scratch), then combine in place
-    prod_AhZ<T, CS>(A, 0, Z0, 0, nullptr, CZ, Dl, Dr, lane);
-    prod_AhZ<T, CS>(A, 1, Z1, 0, nullptr, CX, Dl, Dr, lane);
-    prod_AhZ<T, CS>(A, 0, Z1, 0, nullptr, CY, Dl, Dr, lane);
-    __syncwarp();
-    // element-wise combine; G10[l][l'] = conj(G01[l'][l]) needs the transpose, so
-    // read everything first into registers per (l, l') pair with l <= l'
-    for (int o = lane; o < Dl * Dl; o += 32) {
-        const int l = o / Dl, lp = o % Dl;
-        if (lp < l) continue;
-        const cx<T> g00a = CZ[l * CS + lp], g00b = CZ[lp * CS + l];
-        const cx<T> g11a = CX[l * CS + lp], g11b = CX[lp * CS + l];
-        const cx<T> g01a = CY[l * CS + lp], g01b = CY[lp * CS + l];
-        const cx<T> g10a = conj(g01b), g10b = conj(g01a);   // G10[l][l'], G10[l'][l]
-        if (Rnew) { Rnew[l * CS + lp] = g00a + g11a; Rnew[lp * CS + l] = g00b + g11b; }
-        CZ[l * CS + lp] = g00a - g11a; CZ[lp * CS + l] = g00b - g11b;
-        CX[l * CS + lp] = g01a + g10a; CX[lp * CS + l] = g01b + g10b;
-        const cx<T> da = g10a - g01a, db = g10b - g01b;       // -i G01 + i G10 = i (G10 - G01)
-        CY[l * CS + lp] = mk<T>(-da.im, da.re); CY[lp * CS + l] = mk<T>(-db.im, db.re);
-    }
-    __syncwarp();
+    for (int o = lane; o < D * D; o += NTHR) dst[(o / D) * CS + (o % D)] = src[(o / D) * ld + (o % D)];
 }
 
 template <typename T, int CHI>
-__global__ void __launch_bounds__(512) renv_kernel(const ImageMeta* __restrict__ meta, int n_images,
+__global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ meta, int n_images,
                                                    const cx<T>* __restrict__ arena,
                                                    const int32_t* __restrict__ bonds,
                                                    cx<T>* __restrict__ renv, int64_t renv_stride,
@@ -163,14 +263,14 @@ __global__ void __launch_bounds__(512) renv_kernel(const ImageMeta* __restrict__
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int img = blockIdx.x * (blockDim.x >> 5) + warp;
+    // one warp per image and one image per CTA (block-wide syncs are warp syncs)
+    const int lane = threadIdx.x;
+    const int img = blockIdx.x;
     if (img >= n_images) return;
-    cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw + (size_t)warp * Lay::bytes);
+    cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
     cx<T>* A = base;
     cx<T>* R = base + 2 * MAT;
-    cx<T>* Z0 = base + 3 * MAT;
-    cx<T>* Z1 = base + 4 * MAT;
+    cx<T>* S = base + 6 * MAT;
     const ImageMeta mt = meta[img];
     const int n = mt.n, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
@@ -180,21 +280,17 @@ __global__ void __launch_bounds__(512) renv_kernel(const ImageMeta* __restrict__
     __syncwarp();
     for (int j = n - 1; j >= 0; --j) {
         const int Dl = bd[j], Dr = bd[j + 1];
-        // store R_j
         cx<T>* dst = rg + (size_t)j * CHI * CHI;
         for (int o = lane; o < Dr * Dr; o += 32) dst[(o / Dr) * CHI + (o % Dr)] = R[(o / Dr) * CS + (o % Dr)];
         load_site_p<T, CS>(A, sites + (size_t)j * 2 * ld * ld, ld, Dl, Dr, lane);
         __syncwarp();
-        prod_MAt<T, CS>(R, A, Z0, Z1, Dl, Dr, lane);
-        __syncwarp();
-        prod_AhZ<T, CS>(A, 0, Z0, 1, Z1, R, Dl, Dr, lane);
-        __syncwarp();
+        transfer<T, CHI, 1, 32>(R, A, S, Dl, Dr, lane);
     }
     if (lane == 0) norm_out[img] = R[0].re;
 }
 
-template <typename T, int CHI>
-__global__ void __launch_bounds__(512) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
+template <typename T, int CHI, int UW>
+__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
                                                     const int32_t* __restrict__ unit_image,
                                                     const cx<T>* __restrict__ arena,
                                                     const int32_t* __restrict__ bonds,
@@ -203,17 +299,18 @@ __global__ void __launch_bounds__(512) pauli_kernel(const ImageMeta* __restrict_
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
+    constexpr int NTHR = 32 * UW;
+    // one (image, column) unit per CTA, worked on by UW warps
+    const int lane = threadIdx.x;
+    const int unit = blockIdx.x;
     if (unit >= n_units) return;
     const int img = unit_image[2 * unit], c = unit_image[2 * unit + 1];
-    cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw + (size_t)warp * Lay::bytes);
+    cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
+    T* red = reinterpret_cast<T*>(base + Lay::ELEMS);
     cx<T>* A = base;               // 2 MAT
     cx<T>* R = base + 2 * MAT;
-    cx<T>* Z0 = base + 3 * MAT;
-    cx<T>* Z1 = base + 4 * MAT;
-    cx<T>* C = base + 5 * MAT;     // 3 MAT: C_X, C_Y, C_Z
-    cx<T>* E = base + 8 * MAT;
+    cx<T>* C = base + 3 * MAT;     // 3 MAT: C_X, C_Y, C_Z
+    cx<T>* S = base + 6 * MAT;     // GEMM scratch
     const ImageMeta mt = meta[img];
     const int p = mt.p, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
@@ -224,82 +321,64 @@ __global__ void __launch_bounds__(512) pauli_kernel(const ImageMeta* __restrict_
     const int nh = p * (p - 1);  // horizontal pairs come first
 
     T single_up[3] = {T(0), T(0), T(0)};   // <P_b> of the site that created the carried C
+    T d[12];
     for (int row = p - 1; row >= 0; --row) {
         const int j = row * p + c;
         const int Dl = bd[j], Dr = bd[j + 1];
-        load_site_p<T, CS>(A, sites + (size_t)j * 2 * ld * ld, ld, Dl, Dr, lane);
-        load_mat<T, CS>(R, rg + (size_t)j * CHI * CHI, CHI, Dr, lane);
-        __syncwarp();
+        load_site_p<T, CS, NTHR>(A, sites + (size_t)j * 2 * ld * ld, ld, Dl, Dr, lane);
+        load_mat<T, CS, NTHR>(R, rg + (size_t)j * CHI * CHI, CHI, Dr, lane);
+        team_sync();
         // site j as the left site: single-site terms and the vertical pair (j, j+p)
-        T single_j[3], vert[9];
-        for (int a = 1; a <= 3; ++a) {
-            left_pauli_env<T, CS>(A, a, E, Dl, Dr, lane);
-            __syncwarp();
-            single_j[a - 1] = dot_re<T, CS>(E, R, Dr, lane) * inv_norm;
-            if (row < p - 1)
-                for (int b = 0; b < 3; ++b) vert[(a - 1) * 3 + b] = dot_re<T, CS>(E, C + b * MAT, Dr, lane) * inv_norm;
-            __syncwarp();
+        left_blocks<T, CHI, NTHR>(A, S, Dl, Dr, lane);
+        team_sync();
+        left_dots<T, CHI, NTHR>(S, row < p - 1 ? C : nullptr, R, Dr, d, red, lane);
+        T single_j[3];
+        for (int a = 0; a < 3; ++a) single_j[a] = d[4 * a + 3] * inv_norm;
+        if (row < p - 1 && lane < 16) {
+            const int a = lane >> 2, b = lane & 3;
+            T v;
+            if (a == 0 && b == 0) v = T(1);
+            else if (b == 0) v = single_j[a - 1];
+            else if (a == 0) v = single_up[b - 1];
+            else v = d[4 * (a - 1) + (b - 1)] * inv_norm;
+            outp[(size_t)(nh + j) * 16 + lane] = v;
         }
-        if (row < p - 1) {
-            T* o = outp + (size_t)(nh + j) * 16;
-            for (int e = lane; e < 16; e += 32) {
-                const int a = e >> 2, b = e & 3;
-                T v;
-                if (a == 0 && b == 0) v = T(1);
-                else if (b == 0) v = single_j[a - 1];
-                else if (a == 0) v = single_up[b - 1];
-                else v = vert[(a - 1) * 3 + (b - 1)];
-                o[e] = v;
-            }
-        }
-        // closings of site j as a right site (R_{j-1} is not needed here)
-        prod_MAt<T, CS>(R, A, Z0, Z1, Dl, Dr, lane);
-        __syncwarp();
-        right_closings<T, CS>(A, Z0, Z1, C, C + MAT, C + 2 * MAT, nullptr, Dl, Dr, lane);
+        team_sync();
+        // closings of site j as a right site
+        right_closings<T, CHI, NTHR>(A, R, C, S, Dl, Dr, lane);
         for (int b = 0; b < 3; ++b) single_up[b] = single_j[b];
         if (c == 0 && row == 0) break;
         // next site to the left: horizontal pair (j-1, j) and the first carry step
         const int k0 = j - 1;
-        const int Dl0 = bd[k0];   // bond between k0-1 and k0; Dr of k0 is Dl
-        load_site_p<T, CS>(A, sites + (size_t)k0 * 2 * ld * ld, ld, Dl0, Dl, lane);
-        __syncwarp();
+        const int Dl0 = bd[k0];   // left bond of site k0; its right bond is Dl
+        load_site_p<T, CS, NTHR>(A, sites + (size_t)k0 * 2 * ld * ld, ld, Dl0, Dl, lane);
+        team_sync();
         if (c > 0) {
-            load_mat<T, CS>(R, rg + (size_t)k0 * CHI * CHI, CHI, Dl, lane);
-            __syncwarp();
-            T single_k[3], hor[9];
-            for (int a = 1; a <= 3; ++a) {
-                left_pauli_env<T, CS>(A, a, E, Dl0, Dl, lane);
-                __syncwarp();
-                single_k[a - 1] = dot_re<T, CS>(E, R, Dl, lane) * inv_norm;
-                for (int b = 0; b < 3; ++b) hor[(a - 1) * 3 + b] = dot_re<T, CS>(E, C + b * MAT, Dl, lane) * inv_norm;
-                __syncwarp();
-            }
-            T* o = outp + (size_t)(row * (p - 1) + (c - 1)) * 16;
-            for (int e = lane; e < 16; e += 32) {
-                const int a = e >> 2, b = e & 3;
+            load_mat<T, CS, NTHR>(R, rg + (size_t)k0 * CHI * CHI, CHI, Dl, lane);
+            team_sync();
+            left_blocks<T, CHI, NTHR>(A, S, Dl0, Dl, lane);
+            team_sync();
+            left_dots<T, CHI, NTHR>(S, C, R, Dl, d, red, lane);
+            if (lane < 16) {
+                const int a = lane >> 2, b = lane & 3;
                 T v;
                 if (a == 0 && b == 0) v = T(1);
-                else if (b == 0) v = single_k[a - 1];
+                else if (b == 0) v = d[4 * (a - 1) + 3] * inv_norm;
                 else if (a == 0) v = single_j[b - 1];
-                else v = hor[(a - 1) * 3 + (b - 1)];
-                o[e] = v;
+                else v = d[4 * (a - 1) + (b - 1)] * inv_norm;
+                outp[(size_t)(row * (p - 1) + (c - 1)) * 16 + lane] = v;
             }
+            team_sync();
         }
         if (row == 0) break;
         // carry C_X, C_Y, C_Z through sites j-1 .. j-p+1
         for (int k = k0; k > j - p; --k) {
             const int Dlk = bd[k], Drk = bd[k + 1];
             if (k != k0) {
-                load_site_p<T, CS>(A, sites + (size_t)k * 2 * ld * ld, ld, Dlk, Drk, lane);
-                __syncwarp();
+                load_site_p<T, CS, NTHR>(A, sites + (size_t)k * 2 * ld * ld, ld, Dlk, Drk, lane);
+                team_sync();
             }
-            for (int b = 0; b < 3; ++b) {
-                cx<T>* Cb = C + b * MAT;
-                prod_MAt<T, CS>(Cb, A, Z0, Z1, Dlk, Drk, lane);
-                __syncwarp();
-                prod_AhZ<T, CS>(A, 0, Z0, 1, Z1, Cb, Dlk, Drk, lane);
-                __syncwarp();
-            }
+            transfer<T, CHI, 3, NTHR>(C, A, S, Dlk, Drk, lane);
         }
     }
 }

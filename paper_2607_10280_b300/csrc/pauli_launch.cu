@@ -7,35 +7,45 @@
 namespace mpsano {
 namespace {
 
-template <typename T, int CHI>
-mps_status launch_pauli(mps_batch* b, void* out) {
+template <typename T, int CHI, int UW>
+mps_status launch_pauli_uw(mps_batch* b, void* out) {
     using Lay = PauliLayout<T, CHI>;
     const int limit = smem_optin_limit();
-    int w = std::max(1, b->pauli_warps);
-    while (w > 1 && (size_t)w * Lay::bytes > (size_t)limit) --w;
-    const size_t smem = (size_t)w * Lay::bytes;
+    const size_t smem = Lay::team_bytes(UW);
     if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "Pauli kernel shared memory %zu B", smem);
-    auto rk = renv_kernel<T, CHI>;
-    auto pk = pauli_kernel<T, CHI>;
-    CUDA_TRY(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto pk = pauli_kernel<T, CHI, UW>;
     CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    timing_begin(b, KIND_RENV);
-    rk<<<(b->B + w - 1) / w, 32 * w, smem, b->stream>>>(
-        b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
-        reinterpret_cast<cx<T>*>(b->renv), b->renv_stride, reinterpret_cast<T*>(b->norms));
-    timing_end(b);
-    CUDA_TRY(cudaGetLastError());
-    count_launch();
-    const int units = b->n_units;
     timing_begin(b, KIND_PAULI);
-    pk<<<(units + w - 1) / w, 32 * w, smem, b->stream>>>(
-        b->meta_d, units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
+    pk<<<b->n_units, 32 * UW, smem, b->stream>>>(
+        b->meta_d, b->n_units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
         reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out));
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
     return MPS_OK;
+}
+
+template <typename T, int CHI>
+mps_status launch_pauli(mps_batch* b, void* out) {
+    using Lay = PauliLayout<T, CHI>;
+    const int limit = smem_optin_limit();
+    const size_t smem = Lay::bytes;
+    if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "environment kernel shared memory %zu B", smem);
+    auto rk = renv_kernel<T, CHI>;
+    CUDA_TRY(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    timing_begin(b, KIND_RENV);
+    rk<<<b->B, 32, smem, b->stream>>>(
+        b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
+        reinterpret_cast<cx<T>*>(b->renv), b->renv_stride, reinterpret_cast<T*>(b->norms));
+    timing_end(b);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    switch (b->pauli_warps) {
+        case 1: return launch_pauli_uw<T, CHI, 1>(b, out);
+        case 4: return launch_pauli_uw<T, CHI, 4>(b, out);
+        default: return launch_pauli_uw<T, CHI, 2>(b, out);
+    }
 }
 
 template <typename T>

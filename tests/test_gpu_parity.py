@@ -177,11 +177,24 @@ def test_launch_shapes_agree():
     p, L, chi, B = 5, 3, 8, 11
     X = synth.garment_pixels(B, p, seed=77)
     params = synth.circuit_params(L, 25, seed=78)
-    base, _, _ = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=(1, 32))
-    for shape in ((2, 64), (4, 128), (8, 256)):
+    base, _, _ = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=(1, 32, 32))
+    for shape in ((2, 32, 64), (4, 32, 128), (8, 32, 32), (3, 32, 64)):
         got, _, _ = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=shape)
         for i in range(B):
-            assert np.array_equal(got[i], base[i])
+            assert np.array_equal(got[i], base[i])   # these knobs keep every bit
+    # wider circuit teams change the QR summation order only
+    for shape in ((1, 64, 64), (1, 128, 128)):
+        got, _, _ = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=shape)
+        for i in range(B):
+            assert np.max(np.abs(got[i] - base[i])) < 2e-6
+    p2, L2, chi2, B2 = 7, 4, 16, 6    # bucket 16, where the wider teams are compiled
+    X2 = synth.garment_pixels(B2, p2, seed=79)
+    params2 = synth.circuit_params(L2, 49, seed=80)
+    base2, _, _ = run_gpu(list(X2), [p2] * B2, L2, chi2, "mixed", params=params2, shape=(2, 32, 64))
+    for shape in ((1, 64, 64), (1, 128, 128)):
+        got, _, _ = run_gpu(list(X2), [p2] * B2, L2, chi2, "mixed", params=params2, shape=shape)
+        for i in range(B2):
+            assert np.max(np.abs(got[i] - base2[i])) < 2e-6
 
 
 def test_ano_features_and_linear_vs_oracle():
