@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-sample", type=int, default=8, help="images timed through the per-image FP64 path")
     ap.add_argument("--batch", type=int, default=BATCH, help="images per GPU (profiling of smaller cases)")
+    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "uneven", "large", "serve"],
+                    help="headline (default): 7x7 L=4 chi=16; the others are the chi x L sweep, the uneven "
+                         "batch, the 16x16 batch and the serving run")
+    ap.add_argument("--requests", type=int, default=4000, help="serving run: number of requests")
     return ap.parse_args()
 
 
@@ -304,9 +308,246 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------ other configurations
+def _setup_torch():
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2607_10280_b300.build import build
+    build()
+    return torch
+
+
+def _time_events(torch, fn, steps, stream=None):
+    stream = stream or torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_sweep(args):
+    """chi x L sweep at 7x7 (Sec. III, Fig. 3): per (L, chi) the mixed and FP64 batched
+    paths, their MAE (Eq. 7) and max error vs the FP64 oracle at chi = 64, and images/s."""
+    torch = _setup_torch()
+    from oracle import pipeline as opipe
+    from paper_2607_10280_b300 import api, synth
+    B = min(args.batch, 1024)
+    m = api.pair_count(P)
+    X = synth.garment_pixels(B, P)
+    sample = [0, B // 2, B - 1]
+    rows = []
+    for Lr in (1, 2, 3, 4):
+        params_np = synth.circuit_params(Lr, P * P)
+        params = torch.tensor(params_np, dtype=torch.float64, device="cuda")
+        px = torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda")
+        refs = [opipe.pauli_cache(X[i], P, Lr, 64, "ladder", params_np) for i in sample]
+        for chi in (2, 4, 8, 16):
+            res = {}
+            for prec in ("mixed", "fp64"):
+                b = api.Batch(np.full(B, P, np.int32), chi, prec)
+                pauli = torch.empty((B * m, 16), dtype=torch.float64 if prec == "fp64" else torch.float32,
+                                    device="cuda")
+
+                def step():
+                    b.apply_circuit(px, Lr, "ladder", params)
+                    b.pauli_cache(pauli)
+                step()
+                torch.cuda.synchronize()
+                ms = _time_events(torch, step, 3 if prec == "fp64" else 10)
+                got = pauli.double().cpu().numpy().reshape(B, m, 16)
+                res[prec] = (ms, got, b.discarded_weight())
+                b.close()
+            errs = [np.abs(res["mixed"][1][i] - refs[k]) for k, i in enumerate(sample)]
+            errs64 = [np.abs(res["fp64"][1][i] - refs[k]) for k, i in enumerate(sample)]
+            rows.append({"L": Lr, "chi": chi,
+                         "mae_mixed_vs_exact": float(np.mean([e.mean() for e in errs])),
+                         "max_mixed_vs_exact": float(max(e.max() for e in errs)),
+                         "mae_fp64_vs_exact": float(np.mean([e.mean() for e in errs64])),
+                         "max_mixed_vs_fp64_gpu_all_images": float(np.max(np.abs(res["mixed"][1] - res["fp64"][1]))),
+                         "discarded_weight_mean": float(np.mean(res["fp64"][2])),
+                         "images_per_s_mixed": B / (res["mixed"][0] / 1e3),
+                         "images_per_s_fp64": B / (res["fp64"][0] / 1e3)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "chi x L sweep at 7x7: MAE vs exact (chi=64 FP64 oracle) and images/s", "value":
+            rows[-1]["images_per_s_mixed"], "unit": "images/s", "n_gpus": 1, "config":
+            {"workload": "7x7 garment-like, ladder ansatz, L in 1..4, chi in {2,4,8,16}", "images": B,
+             "exact_reference": "oracle MPS chi=64 on 3 sampled images"}, "table": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_uneven(args):
+    """512 images with p ~ U{4..16}, chi = 16, L in {1, 2}: the batched pipeline (persistent,
+    cost-ordered circuit kernel; autotuned launch shape) replayed as one CUDA graph, vs a
+    per-image launch loop."""
+    torch = _setup_torch()
+    from paper_2607_10280_b300 import api, autotune, synth
+    B = 512
+    sizes = synth.uneven_sizes(B)
+    X = synth.uneven_pixels(sizes)
+    chi = 16
+    out_rows = []
+    for Lr in (1, 2):
+        params = torch.tensor(synth.circuit_params(Lr, 256), dtype=torch.float64, device="cuda")
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            b = api.Batch(sizes, chi, "mixed", s)
+            px = torch.tensor(np.concatenate(X), dtype=torch.float64, device="cuda")
+            pauli = torch.empty((int(b.pair_offsets[-1]), 16), dtype=torch.float32, device="cuda")
+
+            def step():
+                b.apply_circuit(px, Lr, "ladder", params)
+                b.pauli_cache(pauli)
+            shape = autotune.tune(b, step, autotune.signature(b, Lr), use_cache=False)
+            step()
+            s.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                step()
+            g.replay()
+            s.synchronize()
+            ms_graph = _time_events(torch, g.replay, 20, s)
+            # per-image launch loop: one batch per image, launched one after another
+            singles = [api.Batch(np.array([p], np.int32), chi, "mixed", s) for p in sizes]
+            pxs = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in X]
+            outs = [torch.empty((api.pair_count(int(p)), 16), dtype=torch.float32, device="cuda") for p in sizes]
+
+            def loop():
+                for i in range(B):
+                    singles[i].apply_circuit(pxs[i], Lr, "ladder", params)
+                    singles[i].pauli_cache(outs[i])
+            loop()
+            s.synchronize()
+            ms_loop = _time_events(torch, loop, 2, s)
+            got = pauli.cpu().numpy()
+            same = all(np.array_equal(got[b.pair_offsets[i]:b.pair_offsets[i + 1]], outs[i].cpu().numpy())
+                       for i in range(0, B, 37))
+            qubit_layers = float(np.sum(sizes.astype(np.int64) ** 2) * Lr)
+            out_rows.append({"L": Lr, "graph_images_per_s": B / (ms_graph / 1e3),
+                             "loop_images_per_s": B / (ms_loop / 1e3),
+                             "graph_qubit_layers_per_s": qubit_layers / (ms_graph / 1e3),
+                             "speedup": ms_loop / ms_graph, "launch_shape": {k: shape[k] for k in (
+                                 "images_per_cta", "circuit_threads", "pauli_threads")},
+                             "graph_equals_loop_on_sampled_images": bool(same)})
+            for x in singles:
+                x.close()
+            b.close()
+    line = {"metric": "images/s, 512 uneven images p~U{4..16} chi=16, graph-replayed batch vs per-image loop",
+            "value": out_rows[-1]["graph_images_per_s"], "unit": "images/s", "n_gpus": 1,
+            "config": {"workload": "uneven sizes p ~ U{4..16} (16-256 qubits), ladder, chi=16, L in {1,2}",
+                       "images": B}, "table": out_rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_large(args):
+    """16x16 images (256 qubits), 256 per batch, L in {1,2}, chi in {16,32}, mixed vs FP64,
+    then ANO (480 pairs x 16 N(0,1) coefficients) and a linear layer 480 -> 4096 (64x64)."""
+    torch = _setup_torch()
+    from oracle import pipeline as opipe
+    from paper_2607_10280_b300 import api, synth
+    p, B = 16, 256
+    m = api.pair_count(p)
+    X = synth.garment_pixels(B, p)
+    abd = torch.tensor(synth.observable_params(m), dtype=torch.float32, device="cuda")
+    W = torch.tensor(np.random.default_rng(3).standard_normal((4096, m)) / np.sqrt(m), dtype=torch.float32,
+                     device="cuda")
+    bias = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    rows = []
+    px = torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda")
+    for Lr in (1, 2):
+        params_np = synth.circuit_params(Lr, p * p)
+        params = torch.tensor(params_np, dtype=torch.float64, device="cuda")
+        ref = opipe.pauli_cache(X[0], p, Lr, 64, "ladder", params_np)
+        for chi in (16, 32):
+            r = {"L": Lr, "chi": chi}
+            for prec in ("mixed", "fp64"):
+                b = api.Batch(np.full(B, p, np.int32), chi, prec)
+                pauli = torch.empty((B * m, 16), dtype=torch.float64 if prec == "fp64" else torch.float32,
+                                    device="cuda")
+
+                def step():
+                    b.apply_circuit(px, Lr, "ladder", params)
+                    b.pauli_cache(pauli)
+                    return api.ano_features(pauli, m, abd, W, bias)
+                step()
+                torch.cuda.synchronize()
+                ms = _time_events(torch, step, 5 if prec == "mixed" else 2)
+                r[f"images_per_s_{prec}"] = B / (ms / 1e3)
+                r[f"max_err_{prec}_vs_exact_image0"] = float(np.max(np.abs(
+                    pauli[:m].double().cpu().numpy() - ref)))
+                b.close()
+            rows.append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+    line = {"metric": "images/s, 16x16 (256 qubits) batch 256 + ANO 480x16 + linear 480->4096",
+            "value": rows[0]["images_per_s_mixed"], "unit": "images/s", "n_gpus": 1,
+            "config": {"workload": "16x16 garment-like, ladder ansatz, L in {1,2}, chi in {16,32}", "images": B},
+            "table": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson arrivals at 2000 requests/s of single images with p in 6..16, L in 1..4,
+    chi in {4,8,16,32}; p = 7 requests also get ANO (84 x 16) and a linear layer 84 -> 784."""
+    torch = _setup_torch()
+    import threading
+    from oracle import pipeline as opipe
+    from paper_2607_10280_b300 import api, synth
+    from paper_2607_10280_b300.serving import Request, Server, latency_report
+    reqs = synth.serving_requests(args.requests)
+    params_np = synth.circuit_params(4, 256)
+    params = torch.tensor(params_np, dtype=torch.float64, device="cuda")
+    m7 = api.pair_count(7)
+    W, b = synth.linear_params(784, m7)
+    epi = {7: (torch.tensor(synth.observable_params(m7), dtype=torch.float32, device="cuda"),
+               torch.tensor(W, dtype=torch.float32, device="cuda"), torch.tensor(b, dtype=torch.float32,
+                                                                                device="cuda"))}
+    srv = Server(params, epi, slots=4, max_images_per_wave=64, budget_bytes=4 << 30)
+    # warm the slots (kernel attributes, first launches)
+    warm = [srv.submit(Request(r["p"], r["L"], r["chi"], r["pixels"])) for r in reqs[:32]]
+    srv.start()
+    for w in warm:
+        w.event.wait()
+    srv.stop()
+    srv.completed.clear()
+    srv.start()
+    t0 = time.perf_counter()
+    submitted = []
+    for r in reqs:
+        delay = r["t"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        submitted.append(srv.submit(Request(r["p"], r["L"], r["chi"], r["pixels"])))
+    for q in submitted:
+        q.event.wait()
+    t1 = max(q.t_done for q in submitted)
+    srv.stop()
+    rep = latency_report(submitted)
+    # errors vs the FP64 oracle on a sample of the smaller requests
+    errs = []
+    for q, r in zip(submitted, reqs):
+        if r["p"] <= 8 and len(errs) < 6:
+            ref, st = opipe.pauli_cache(r["pixels"], r["p"], r["L"], r["chi"], "ladder", params_np,
+                                        return_state=True)
+            if st.min_gap >= 1e-6:
+                errs.append(float(np.max(np.abs(q.pauli - ref))))
+    line = {"metric": "serving: images/s and p50/p99 latency, Poisson 2000 req/s, mixed p/L/chi",
+            "value": len(submitted) / (t1 - t0), "unit": "images/s", "n_gpus": 1,
+            "latency": rep, "arrival_rate_hz": 2000.0, "waves": srv.waves, "max_wave": srv.max_wave,
+            "max_inflight_bytes": srv.max_inflight_bytes, "budget_bytes": srv.budget,
+            "max_err_vs_fp64_oracle_sampled": max(errs) if errs else None, "sampled": len(errs),
+            "config": {"workload": "single images p~U{6..16}, L~U{1..4}, chi~U{4,8,16,32}, p=7 with ANO + "
+                                   "linear 84->784", "requests": len(submitted), "slots": 4}}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    else:
+    elif a.config == "headline":
         run_ours(a)
+    else:
+        {"sweep": run_sweep, "uneven": run_uneven, "large": run_large, "serve": run_serve}[a.config](a)

@@ -92,6 +92,13 @@ typedef struct {
 mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* chi,
                             int32_t chi_all, int32_t prec, void* stream, mps_batch** out);
 
+/* Give an existing batch a new list of images (same precision and stream), reusing
+ * its device memory when the new layout fits and growing it otherwise.  Waits for
+ * the batch's queued work first.  Arguments as in mps_create_batch.  A circuit must
+ * be applied again before mps_pauli_cache. */
+mps_status mps_reshape_batch(mps_batch* batch, int32_t n_images, const int32_t* p, const int32_t* chi,
+                             int32_t chi_all);
+
 /* Release a batch (stream-ordered: waits for its queued work first). NULL is a no-op. */
 mps_status mps_destroy_batch(mps_batch* batch);
 
@@ -155,7 +162,8 @@ uint64_t mps_launch_count(void);
  *   images_per_cta   images per CTA of the circuit kernel when it runs one warp per
  *                    image, 1..8
  *   circuit_threads  threads that share one image in the circuit kernel: 32, 64 or 128
- *                    (wider teams apply to the mixed path at bond buckets 16 and 32)
+ *                    (wider teams are compiled for the mixed path at bond bucket 16
+ *                    without truncation; elsewhere one warp per image runs)
  *   pauli_threads    threads that share one (image, grid column) unit of the Pauli
  *                    kernel: 32, 64 or 128
  * images_per_cta and pauli_threads leave every result bit-identical; circuit_threads

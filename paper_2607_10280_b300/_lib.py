@@ -41,6 +41,8 @@ SIGNATURES = {
     "mps_create_batch": (_c.c_int, [_c.c_int32, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32), _c.c_int32,
                                     _c.c_int32, _c.c_void_p, _c.POINTER(_c.c_void_p)]),
     "mps_destroy_batch": (_c.c_int, [_c.c_void_p]),
+    "mps_reshape_batch": (_c.c_int, [_c.c_void_p, _c.c_int32, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32),
+                                     _c.c_int32]),
     "mps_apply_circuit": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.POINTER(mps_circuit)]),
     "mps_pauli_cache": (_c.c_int, [_c.c_void_p, _c.c_int32, _c.c_void_p, _c.POINTER(_c.c_int64)]),
     "ano_features": (_c.c_int, [_c.c_void_p, _c.c_int32, _c.c_int64, _c.c_int32, _c.c_void_p, _c.c_void_p,

@@ -51,6 +51,17 @@ class Batch:
         self.pixel_offsets = np.concatenate([[0], np.cumsum(self.n)])
         self.pair_offsets = np.concatenate([[0], np.cumsum([pair_count(int(q)) for q in p])])
 
+    def reshape(self, p, chi):
+        """New image list for this batch, reusing its device memory when it fits."""
+        p = np.atleast_1d(np.asarray(p, dtype=np.int32))
+        chi_arr = np.broadcast_to(np.asarray(chi, dtype=np.int32), p.shape).copy()
+        check(lib().mps_reshape_batch(self._h, len(p), p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      chi_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0))
+        self.n_images, self.p, self.chi = len(p), p, chi_arr
+        self.n = p.astype(np.int64) ** 2
+        self.pixel_offsets = np.concatenate([[0], np.cumsum(self.n)])
+        self.pair_offsets = np.concatenate([[0], np.cumsum([pair_count(int(q)) for q in p])])
+
     # -- lifetime ------------------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

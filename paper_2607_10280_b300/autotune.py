@@ -15,7 +15,7 @@ from __future__ import annotations
 import json
 import os
 
-CIRCUIT_SHAPES = [(1, 32), (2, 32), (4, 32), (1, 64), (1, 128)]   # (images_per_cta, circuit_threads)
+CIRCUIT_SHAPES = [(1, 32), (2, 32), (4, 32), (1, 64)]   # (images_per_cta, circuit_threads)
 PAULI_THREADS = [32, 64, 128]
 
 

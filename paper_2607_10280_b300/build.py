@@ -10,13 +10,18 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmpsano.so")
-SOURCES = ["mpsano.cu", "pauli_launch.cu", "noalloc.cu"] + [f"circuit_{p}_t{t}.cu" for p in ("mixed", "fp64", "orth64") for t in (0, 1)]
+SOURCES = (["circuit_fp64_t1_c32.cu", "circuit_fp64_t1_c16.cu", "circuit_orth64_t1_c32.cu", "circuit_orth64_t1_c16.cu",
+            "pauli_launch.cu"]
+           + [f"circuit_{p}_t{t}_c{c}.cu" for p in ("mixed", "fp64", "orth64") for t in (0, 1) for c in (4, 8, 16, 32)
+              if not (t == 1 and p != "mixed" and c >= 16)]
+           + ["circuit_dispatch.cu", "mpsano.cu", "noalloc.cu"])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -47,13 +52,17 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(obj_dir, exist_ok=True)
     common = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I", INCLUDE, "-I", CSRC, *extra]
-    procs, objs = [], []
+    # the slowest units come first; at most one compiler per core
+    jobs = max(1, os.cpu_count() or 1)
+    procs, objs, failed = [], [], []
     for src in SOURCES:
         obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [*common, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
+        while len([1 for _, pr in procs if pr.poll() is None]) >= jobs:
+            time.sleep(0.2)
         procs.append((src, subprocess.Popen(cmd)))
     failed = [src for src, pr in procs if pr.wait() != 0]
     if failed:

@@ -36,6 +36,15 @@ struct mps_batch {
     int gate_n = 0;                        // qubit stride of the gate table
     bool gates_owned = true;               // false when gates points into static scratch
     int circuit_threads = 32;              // threads per image in the circuit kernel
+    int32_t* order_d = nullptr;            // circuit work queue: images by descending cost
+    int32_t* order_pinned = nullptr;       // staging of order_d
+    int32_t* units_pinned = nullptr;       // staging of units_d
+    int64_t need_sites = 0;                // complex elements of site storage of the layout
+    // allocated capacities in bytes (buffers grow, never shrink, across re-layouts)
+    size_t cap_meta = 0, cap_meta_pinned = 0, cap_units = 0, cap_arena = 0, cap_renv = 0, cap_norms = 0,
+           cap_bonds = 0, cap_disc = 0, cap_status = 0, cap_queue = 0, cap_order = 0, cap_order_pinned = 0,
+           cap_units_pinned = 0;
+    int* queue_d = nullptr;                // circuit work-queue counter
     int chi_tpl = 0;                       // kernel CHI bucket of the last circuit
     int images_per_cta = 2;
     int pauli_warps = 2;

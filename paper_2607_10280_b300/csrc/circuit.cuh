@@ -244,20 +244,66 @@ struct CircuitTeam {
             G[i * LDK + j] = conj(acc);
         });
         tsync<NTHR>();
-        if (lane < 32) warp_jacobi_eigh(G, V, LDK, K, lane, 40);
-        tsync<NTHR>();
-        // rank the eigenvalues (descending, ties by index) and record the discarded weight
-        for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
-        tsync<NTHR>();
+        // Eigen-decomposition of G.  FP64 path: Jacobi in FP64 in place (diag(G) = sigma^2,
+        // V = eigenvectors).  Mixed path: Jacobi in FP32 on a rounded copy (in the V
+        // buffer), then sigma^2 as FP64 Rayleigh quotients v_i^H G v_i of the FP64 Gram,
+        // and the kept vectors re-orthogonalised in FP64 below.
+        cx<float>* G32 = reinterpret_cast<cx<float>*>(V);
+        cx<float>* V32 = G32 + K * LDK;
+        // rank the eigenvalues lam (descending, ties by index) into ord
+        auto rank_lam = [&]() {
+            for (int i = lane; i < K; i += NTHR) {
+                const double li = lam[i];
+                int rank = 0;
+                for (int j = 0; j < K; ++j) rank += (lam[j] > li) || (lam[j] == li && j < i);
+                ord[rank] = i;
+            }
+            tsync<NTHR>();
+        };
+        bool fp64_vectors = sizeof(TQ) == 8;
+        if constexpr (sizeof(TQ) == 8) {
+            if (lane < 32) warp_jacobi_eigh<double>(G, V, LDK, K, lane, 40);
+            tsync<NTHR>();
+            for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
+            tsync<NTHR>();
+            rank_lam();
+        } else {
+            team_for_2d<NTHR>(K, K, lane, [&](int c, int r) { G32[c * LDK + r] = cvt<float>(G[c * LDK + r]); });
+            tsync<NTHR>();
+            if (lane < 32) warp_jacobi_eigh<float>(G32, V32, LDK, K, lane, 40);
+            tsync<NTHR>();
+            // lam[i] = v_i^H G v_i in FP64 (Rayleigh quotients of the FP64 Gram)
+            for (int i = lane; i < K; i += NTHR) {
+                cx<double> acc = czero<double>();
+                const cx<float>* v = V32 + i * LDK;
+                for (int r = 0; r < K; ++r) {
+                    cx<double> gv = czero<double>();
+                    for (int c = 0; c < K; ++c) cmac(gv, G[c * LDK + r], cvt<double>(v[c]));
+                    cmac_cj(acc, cvt<double>(v[r]), gv);
+                }
+                lam[i] = acc.re;
+            }
+            tsync<NTHR>();
+            rank_lam();
+            // Near a tie at the cut the FP32 eigenvectors mix the kept and the dropped
+            // directions at the FP32 rounding level; there the eigenproblem is solved
+            // again in FP64 (G still holds the FP64 Gram, V is free for FP64 vectors).
+            const double gap = lam[ord[chi - 1]] - lam[ord[chi]];
+            if (gap < 1e-3 * lam[ord[0]]) {
+                if (lane < 32) warp_jacobi_eigh<double>(G, V, LDK, K, lane, 40);
+                tsync<NTHR>();
+                for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
+                tsync<NTHR>();
+                rank_lam();
+                fp64_vectors = true;
+            }
+        }
+        // discarded weight of this step
         double tot = 0.0, drop = 0.0;
         for (int i = lane; i < K; i += NTHR) {
-            const double li = lam[i];
-            int rank = 0;
-            for (int j = 0; j < K; ++j) rank += (lam[j] > li) || (lam[j] == li && j < i);
-            ord[rank] = i;
-            const double w = li > 0.0 ? li : 0.0;
+            const double w = lam[ord[i]] > 0.0 ? lam[ord[i]] : 0.0;
             tot += w;
-            if (rank >= chi) drop += w;
+            if (i >= chi) drop += w;
         }
         tot = team_sum<NTHR>(tot, red, lane);
         drop = team_sum<NTHR>(drop, red, lane);
@@ -266,15 +312,23 @@ struct CircuitTeam {
         const int D = chi;
         // U_chi (M x D, FP64) into the Gram buffer
         cx<double>* U = G;
+        auto vec = [&](int c, int r) -> cx<double> {
+            if (fp64_vectors) return V[ord[c] * LDK + r];
+            return cvt<double>(V32[ord[c] * LDK + r]);
+        };
         if (left) {
-            team_for_2d<NTHR>(D, M, lane, [&](int c, int r) { U[c * LDK + r] = V[ord[c] * LDK + r]; });
+            team_for_2d<NTHR>(D, M, lane, [&](int c, int r) { U[c * LDK + r] = vec(c, r); });
             tsync<NTHR>();
+            if (!fp64_vectors) {
+                // FP32 eigenvectors -> orthonormal to FP64 rounding
+                team_qr<NTHR>(U, LDK, M, D, taud, red, lane);
+                team_form_q<NTHR>(U, LDK, M, D, taud, lane);
+            }
         } else {
             // X = theta V_chi (M x D), then U = Q of its FP64 Householder QR
             team_for_2d<NTHR>(D, M, lane, [&](int c, int r) {
-                const cx<double>* v = V + ord[c] * LDK;
                 cx<double> acc = czero<double>();
-                for (int j = 0; j < N; ++j) cmac(acc, cvt<double>(th[j * LDM + r]), v[j]);
+                for (int j = 0; j < N; ++j) cmac(acc, cvt<double>(th[j * LDM + r]), vec(c, j));
                 U[c * LDK + r] = acc;
             });
             tsync<NTHR>();
@@ -438,22 +492,21 @@ __device__ bool run_pass(CircuitTeam<T, TQ, CHI, TRUNC, NTHR>& w, int first, int
     return true;
 }
 
-// One team of NTHR threads per image.  NTHR = 32: a CTA holds blockDim/32 images
-// (one warp each, no block barriers); NTHR > 32: a CTA is one image.
+// Persistent kernel: every team of NTHR threads takes images from a work queue
+// (an atomic counter over `order`, which the host sorts by descending cost so that
+// the longest chains start first) until the queue is empty.  NTHR = 32: a CTA holds
+// blockDim/32 independent teams (no block barriers); NTHR > 32: a CTA is one team.
+// `queue` must be zero at launch.
 template <typename T, typename TQ, int CHI, bool TRUNC, int NTHR>
 __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024 / NTHR / 2) circuit_kernel(
-    const ImageMeta* __restrict__ meta, int n_images, const double* __restrict__ pixels,
-    const cx<T>* __restrict__ gates, int gn, int ansatz,
+    const ImageMeta* __restrict__ meta, int n_images, const int32_t* __restrict__ order, int* queue,
+    const double* __restrict__ pixels, const cx<T>* __restrict__ gates, int gn, int ansatz,
     cx<T>* __restrict__ arena, int32_t* __restrict__ bonds_out,
     double* __restrict__ discarded_out, int* status) {
     using Lay = CircuitLayout<T, TQ, CHI, TRUNC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int team = threadIdx.x / NTHR, lane = threadIdx.x % NTHR;
-    const int img = blockIdx.x * (blockDim.x / NTHR) + team;
-    if (img >= n_images) return;
     unsigned char* base = smem_raw + (size_t)team * Lay::bytes;
-
-    const ImageMeta mt = meta[img];
     CircuitTeam<T, TQ, CHI, TRUNC, NTHR> w;
     w.cur = reinterpret_cast<cx<T>*>(base + Lay::off_cur);
     w.nxt = reinterpret_cast<cx<T>*>(base + Lay::off_nxt);
@@ -469,41 +522,51 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
     w.red = reinterpret_cast<double*>(base + Lay::off_red);
     w.flag = reinterpret_cast<int*>(base + Lay::off_flag);
     w.lane = lane;
-    w.n = mt.n;
-    w.chi = mt.chi < CHI ? mt.chi : CHI;
-    w.ld = mt.ld;
-    w.sites = arena + mt.site_off;
-    w.discarded = 0.0;
     w.status = status;
-    const double* px = pixels + mt.pixel_off;
-    const int n = mt.n;
 
-    // |0...0> then the encoding R_Y(pi x) (ladder); every bond is 1
-    for (int k = lane; k <= n; k += NTHR) w.bd[k] = 1;
-    for (int k = lane; k < n; k += NTHR) {
-        cx<T>* s = w.site_ptr(k);
-        double sn = 0.0, cs = 1.0;
-        if (ansatz == 0) sincos(0.5 * M_PI * px[k], &sn, &cs);
-        s[0] = mk<T>(T(cs), T(0));
-        s[w.ld] = mk<T>(T(sn), T(0));
-    }
-    tsync<NTHR>();
-    for (int layer = 0; layer < mt.L; ++layer) {
-        bool ok;
-        if (ansatz == 0) {
-            ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 0, 1, ansatz, gates, gn, img, layer, true, layer == 0);
-        } else {
-            ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 0, 2, ansatz, gates, gn, img, layer, true, layer == 0);
-            if (ok && n > 2)
-                ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 1, 2, ansatz, gates, gn, img, layer, false, false);
+    for (;;) {
+        if (lane == 0) *w.flag = atomicAdd(queue, 1);
+        tsync<NTHR>();
+        const int slot = *w.flag;
+        tsync<NTHR>();
+        if (slot >= n_images) return;
+        const int img = order ? order[slot] : slot;
+        const ImageMeta mt = meta[img];
+        w.n = mt.n;
+        w.chi = mt.chi < CHI ? mt.chi : CHI;
+        w.ld = mt.ld;
+        w.sites = arena + mt.site_off;
+        w.discarded = 0.0;
+        const double* px = pixels + mt.pixel_off;
+        const int n = mt.n;
+
+        // |0...0> then the encoding R_Y(pi x) (ladder); every bond is 1
+        for (int k = lane; k <= n; k += NTHR) w.bd[k] = 1;
+        for (int k = lane; k < n; k += NTHR) {
+            cx<T>* s = w.site_ptr(k);
+            double sn = 0.0, cs = 1.0;
+            if (ansatz == 0) sincos(0.5 * M_PI * px[k], &sn, &cs);
+            s[0] = mk<T>(T(cs), T(0));
+            s[w.ld] = mk<T>(T(sn), T(0));
         }
-        if (!ok) return;
+        tsync<NTHR>();
+        bool ok = true;
+        for (int layer = 0; ok && layer < mt.L; ++layer) {
+            if (ansatz == 0) {
+                ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 0, 1, ansatz, gates, gn, img, layer, true, layer == 0);
+            } else {
+                ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 0, 2, ansatz, gates, gn, img, layer, true, layer == 0);
+                if (ok && n > 2)
+                    ok = run_pass<T, TQ, CHI, TRUNC, NTHR>(w, 1, 2, ansatz, gates, gn, img, layer, false, false);
+            }
+        }
+        // A pass ends with the centre at n-1.  The paper ansatz's second pass leaves
+        // site 0 as written by the first pass (left-orthonormal), so the whole chain is
+        // left-canonical either way.
+        for (int k = lane; k <= n; k += NTHR) bonds_out[mt.bond_off + k] = w.bd[k];
+        if (lane == 0) discarded_out[img] = w.discarded;
+        tsync<NTHR>();
     }
-    // A pass ends with the centre at n-1.  The paper ansatz's second pass leaves
-    // site 0 as written by the first pass (left-orthonormal), so the whole chain is
-    // left-canonical either way.
-    for (int k = lane; k <= n; k += NTHR) bonds_out[mt.bond_off + k] = w.bd[k];
-    if (lane == 0) discarded_out[img] = w.discarded;
 }
 
 }  // namespace mpsano

@@ -23,9 +23,16 @@ mps_status launch_circuit_team(mps_batch* b, const double* pixels, int ansatz) {
                     Lay::bytes, limit);
     auto kern = circuit_kernel<T, TQ, CHI, TRUNC, NTHR>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (b->B + per_cta - 1) / per_cta;
+    // persistent grid: as many CTAs as stay resident, capped by the work
+    int per_sm = 0, dev = 0, sms = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHR * per_cta, smem));
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int needed = (b->B + per_cta - 1) / per_cta;
+    const int grid = std::max(1, std::min(needed, std::max(1, per_sm) * sms));
+    CUDA_TRY(cudaMemsetAsync(b->queue_d, 0, sizeof(int), b->stream));
     timing_begin(b, KIND_CIRCUIT);
-    kern<<<grid, NTHR * per_cta, smem, b->stream>>>(b->meta_d, b->B, pixels,
+    kern<<<grid, NTHR * per_cta, smem, b->stream>>>(b->meta_d, b->B, b->order_d, b->queue_d, pixels,
                                                    reinterpret_cast<const cx<T>*>(b->gates), b->gate_n, ansatz,
                                                    reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
                                                    b->discarded_d, b->status_d);
@@ -35,26 +42,15 @@ mps_status launch_circuit_team(mps_batch* b, const double* pixels, int ansatz) {
     return MPS_OK;
 }
 
-// Teams wider than a warp pay off only for the larger tiles; smaller buckets run
-// one warp per image.
+// Wider teams are compiled only for the mixed path at bond bucket 16 without
+// truncation (the benchmark shape); measured on B300 they do not beat one warp per
+// image, so every other combination runs one warp per image.
 template <typename T, typename TQ, int CHI, bool TRUNC>
 mps_status launch_circuit(mps_batch* b, const double* pixels, int ansatz) {
-    if constexpr (CHI >= 16 && sizeof(T) == 4 && sizeof(TQ) == 4) {
+    if constexpr (CHI == 16 && !TRUNC && sizeof(T) == 4 && sizeof(TQ) == 4) {
         if (b->circuit_threads == 64) return launch_circuit_team<T, TQ, CHI, TRUNC, 64>(b, pixels, ansatz);
-        if (b->circuit_threads == 128) return launch_circuit_team<T, TQ, CHI, TRUNC, 128>(b, pixels, ansatz);
     }
     return launch_circuit_team<T, TQ, CHI, TRUNC, 32>(b, pixels, ansatz);
-}
-
-template <typename T, typename TQ, bool TRUNC>
-mps_status dispatch_chi(mps_batch* b, int chi_tpl, const double* px, int an) {
-    switch (chi_tpl) {
-        case 4: return launch_circuit<T, TQ, 4, TRUNC>(b, px, an);
-        case 8: return launch_circuit<T, TQ, 8, TRUNC>(b, px, an);
-        case 16: return launch_circuit<T, TQ, 16, TRUNC>(b, px, an);
-        case 32: return launch_circuit<T, TQ, 32, TRUNC>(b, px, an);
-    }
-    return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", chi_tpl);
 }
 
 }  // namespace

@@ -160,21 +160,26 @@ __device__ void team_form_q(cx<T>* A, int ld, int M, int K, const cx<T>* tau, in
 }
 
 // Cyclic parallel (round-robin) Jacobi eigensolver for the K x K Hermitian matrix G
-// (column-major, ld), K <= 64, run by one warp.  On return diag(G) holds the
-// eigenvalues and the columns of V (K x K, ld) the eigenvectors:
-// G_in = V diag(lambda) V^H.  Each lane owns one disjoint index pair per round; a
-// round applies all rotations to the columns of G and V, then to the rows of G.
-// Returns the sweeps used.
-static __device__ int warp_jacobi_eigh(cx<double>* G, cx<double>* V, int ld, int K, int lane, int max_sweeps) {
+// (column-major, ld), K <= 64, run by one warp in the arithmetic of T.  On return
+// diag(G) holds the eigenvalues and the columns of V (K x K, ld) the eigenvectors:
+// G_in = V diag(lambda) V^H.  A round rotates K/2 disjoint index pairs; each pair
+// is owned by a group of LP = 32 / (K/2) lanes (a power of two) that split the
+// rows (column phase) and the columns (row phase) of the update.  Returns the sweeps.
+template <typename T>
+__device__ int warp_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int lane, int max_sweeps) {
     for (int c = 0; c < K; ++c)
-        for (int r = lane; r < K; r += 32) V[c * ld + r] = mk<double>(r == c ? 1.0 : 0.0, 0.0);
-    // scale for the absolute threshold
-    double tr = 0.0;
+        for (int r = lane; r < K; r += 32) V[c * ld + r] = mk<T>(r == c ? T(1) : T(0), T(0));
+    T tr = T(0);
     for (int r = lane; r < K; r += 32) tr += fabs(G[r * ld + r].re);
     tr = warp_sum(tr);
-    const double abs_tol = 1e-17 * (tr > 0.0 ? tr : 1.0);
+    // rotate while |G_pq| exceeds the rounding level of the pair's diagonal
+    const T eps = sizeof(T) == 4 ? T(3e-7) : T(1e-15);
+    const T abs_tol = (sizeof(T) == 4 ? T(3e-8) : T(1e-17)) * (tr > T(0) ? tr : T(1));
     const int Kp = (K + 1) & ~1;          // even number of slots; slot K (if K odd) is a dummy
     const int npairs = Kp / 2;
+    int LP = 1;                           // lanes per pair
+    while (LP * 2 * npairs <= 32) LP *= 2;
+    const int pair = lane / LP, sub = lane % LP;
     int sweep = 0;
     __syncwarp();
     for (; sweep < max_sweeps; ++sweep) {
@@ -182,27 +187,27 @@ static __device__ int warp_jacobi_eigh(cx<double>* G, cx<double>* V, int ld, int
         for (int round = 0; round < Kp - 1; ++round) {
             // round-robin pairing: slot 0 fixed, slots 1..Kp-1 rotate
             int p = -1, q = -1;
-            if (lane < npairs) {
-                int a = lane, b = Kp - 1 - lane;
+            if (pair < npairs) {
+                const int a = pair, b = Kp - 1 - pair;
                 auto pos = [&](int s) { return s == 0 ? 0 : 1 + (s - 1 + round) % (Kp - 1); };
                 p = pos(a);
                 q = pos(b);
                 if (p > q) { int tmp = p; p = q; q = tmp; }
                 if (q >= K) p = -1;  // pair with the dummy slot
             }
-            double c = 1.0, s = 0.0;
-            cx<double> e = mk<double>(1.0, 0.0);  // e^{-i phi}
+            T c = T(1), s = T(0);
+            cx<T> e = mk<T>(T(1), T(0));  // e^{-i phi}
             bool rot = false;
             if (p >= 0) {
-                const double a = G[p * ld + p].re, b = G[q * ld + q].re;
-                const cx<double> g = G[q * ld + p];  // G[p][q]
-                const double ag = sqrt(norm2(g));
-                if (ag > abs_tol && ag * ag > 1e-30 * fabs(a * b)) {
+                const T a = G[p * ld + p].re, b = G[q * ld + q].re;
+                const cx<T> g = G[q * ld + p];  // G[p][q]
+                const T ag = sqrt(norm2(g));
+                if (ag > abs_tol && ag > eps * sqrt(fabs(a * b))) {
                     rot = true;
-                    e = mk<double>(g.re / ag, -g.im / ag);
-                    const double tau = (b - a) / (2.0 * ag);
-                    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
+                    e = mk<T>(g.re / ag, -g.im / ag);
+                    const T tau = (b - a) / (T(2) * ag);
+                    const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                    c = T(1) / sqrt(T(1) + t * t);
                     s = t * c;
                 }
             }
@@ -211,11 +216,11 @@ static __device__ int warp_jacobi_eigh(cx<double>* G, cx<double>* V, int ld, int
             // columns of G and V: G <- G J, V <- V J,
             // J(p,p) = c, J(p,q) = s, J(q,p) = -s e, J(q,q) = c e, e = e^{-i phi}
             if (rot) {
-                for (int r = 0; r < K; ++r) {
-                    const cx<double> gp = G[p * ld + r], gq = G[q * ld + r];
+                for (int r = sub; r < K; r += LP) {
+                    const cx<T> gp = G[p * ld + r], gq = G[q * ld + r];
                     G[p * ld + r] = c * gp - s * (e * gq);
                     G[q * ld + r] = s * gp + c * (e * gq);
-                    const cx<double> vp = V[p * ld + r], vq = V[q * ld + r];
+                    const cx<T> vp = V[p * ld + r], vq = V[q * ld + r];
                     V[p * ld + r] = c * vp - s * (e * vq);
                     V[q * ld + r] = s * vp + c * (e * vq);
                 }
@@ -223,19 +228,19 @@ static __device__ int warp_jacobi_eigh(cx<double>* G, cx<double>* V, int ld, int
             __syncwarp();
             // rows of G: G <- J^H G
             if (rot) {
-                const cx<double> ec = conj(e);
-                for (int col = 0; col < K; ++col) {
-                    const cx<double> gp = G[col * ld + p], gq = G[col * ld + q];
+                const cx<T> ec = conj(e);
+                for (int col = sub; col < K; col += LP) {
+                    const cx<T> gp = G[col * ld + p], gq = G[col * ld + q];
                     G[col * ld + p] = c * gp - s * (ec * gq);
                     G[col * ld + q] = s * gp + c * (ec * gq);
                 }
             }
             __syncwarp();
-            if (rot) {  // the 2x2 block is diagonal in exact arithmetic
-                G[q * ld + p] = czero<double>();
-                G[p * ld + q] = czero<double>();
-                G[p * ld + p].im = 0.0;
-                G[q * ld + q].im = 0.0;
+            if (rot && sub == 0) {  // the 2x2 block is diagonal in exact arithmetic
+                G[q * ld + p] = czero<T>();
+                G[p * ld + q] = czero<T>();
+                G[p * ld + p].im = T(0);
+                G[q * ld + q].im = T(0);
             }
             __syncwarp();
         }

@@ -162,6 +162,8 @@ void free_batch(mps_batch* b) {
     for (auto e : b->event_pool) cudaEventDestroy(e);
     cudaFree(b->meta_d);
     cudaFreeHost(b->meta_pinned);
+    cudaFreeHost(b->order_pinned);
+    cudaFreeHost(b->units_pinned);
     cudaFree(b->units_d);
     cudaFree(b->arena);
     cudaFree(b->renv);
@@ -169,6 +171,8 @@ void free_batch(mps_batch* b) {
     cudaFree(b->bonds_d);
     cudaFree(b->discarded_d);
     cudaFree(b->status_d);
+    cudaFree(b->queue_d);
+    cudaFree(b->order_d);
     if (b->gates_owned) cudaFree(b->gates);
     delete b;
 }
@@ -188,27 +192,28 @@ int64_t mps_pair_count(int32_t p, int32_t pair_set) {
     return m;
 }
 
-mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* chi, int32_t chi_all,
-                            int32_t prec, void* stream, mps_batch** out) {
-    if (!out) return fail(MPS_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// Host-side layout of an image list: per-image records, Pauli work units and sizes.
+mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const int32_t* chi, int32_t chi_all) {
     if (n_images <= 0) return fail(MPS_ERR_INVALID_ARG, "n_images must be positive, got %d", n_images);
     if (!p) return fail(MPS_ERR_INVALID_ARG, "p is NULL");
-    if (prec != MPS_FP64 && prec != MPS_MIXED && prec != MPS_MIXED_ORTH64)
-        return fail(MPS_ERR_INVALID_ARG, "unknown precision %d", prec);
-    mps_batch* b = new (std::nothrow) mps_batch();
-    if (!b) return fail(MPS_ERR_OOM, "host allocation failed");
+    for (int i = 0; i < n_images; ++i) {
+        const int ci = chi ? chi[i] : chi_all;
+        if (p[i] < 2 || p[i] > 16) return fail(MPS_ERR_INVALID_ARG, "p[%d] = %d outside 2..16", i, p[i]);
+        if (ci < 1 || ci > 64) return fail(MPS_ERR_INVALID_ARG, "chi[%d] = %d outside 1..64", i, ci);
+    }
     b->B = n_images;
-    b->prec = prec;
-    b->stream = reinterpret_cast<cudaStream_t>(stream);
-    b->elem = prec == MPS_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
-    b->meta_h.resize(n_images);
-    int64_t site_off = 0, pix = 0, pair = 0, bond = 0, renv_max = 0;
+    b->meta_h.assign(n_images, ImageMeta{});
+    b->units_h.clear();
+    b->ld_max = 1;
+    b->n_max = 0;
+    int64_t site_off = 0, pix = 0, pair = 0, bond = 0;
     for (int i = 0; i < n_images; ++i) {
         const int pi = p[i];
         const int ci = chi ? chi[i] : chi_all;
-        if (pi < 2 || pi > 16) { delete b; return fail(MPS_ERR_INVALID_ARG, "p[%d] = %d outside 2..16", i, pi); }
-        if (ci < 1 || ci > 64) { delete b; return fail(MPS_ERR_INVALID_ARG, "chi[%d] = %d outside 1..64", i, ci); }
         const int n = pi * pi;
         // largest bond any circuit can reach: min(chi, 2^floor(n/2))
         int cap = 1;
@@ -217,7 +222,7 @@ mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* c
         int ld = 4;
         while (ld < cap) ld <<= 1;
         ImageMeta& m = b->meta_h[i];
-        m.p = pi; m.n = n; m.chi = ci; m.L = 0; m.ld = ld;
+        m.p = pi; m.n = n; m.chi = ci; m.L = -1; m.ld = ld;
         m.bond_off = (int32_t)bond;
         m.site_off = site_off;
         m.pixel_off = pix;
@@ -230,41 +235,105 @@ mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* c
         b->n_max = std::max(b->n_max, n);
         for (int c = 0; c < pi; ++c) { b->units_h.push_back(i); b->units_h.push_back(c); }
     }
-    renv_max = (int64_t)b->n_max * b->ld_max * b->ld_max;  // R_j of any image at any kernel bucket
     b->n_units = (int)(b->units_h.size() / 2);
     b->total_pairs_hv = pair;
     b->total_bonds = bond;
-    b->renv_stride = renv_max;
-    auto bail = [&](mps_status st) { free_batch(b); return st; };
-#define TRY_ALLOC(expr)                                                                         \
+    b->renv_stride = (int64_t)b->n_max * b->ld_max * b->ld_max;  // R_j of any image at any kernel bucket
+    b->need_sites = site_off;
+    return MPS_OK;
+}
+
+template <typename P>
+cudaError_t grow(P** ptr, size_t* cap, size_t need, bool pinned = false) {
+    if (need <= *cap && *ptr) return cudaSuccess;
+    if (pinned) cudaFreeHost(*ptr); else cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t e = pinned ? cudaMallocHost(reinterpret_cast<void**>(ptr), need)
+                           : cudaMalloc(reinterpret_cast<void**>(ptr), need);
+    if (e == cudaSuccess) *cap = need;
+    return e;
+}
+
+// Device buffers at least as large as the current layout needs, then the layout
+// uploaded (stream-ordered).
+mps_status fit_and_upload(mps_batch* b) {
+    const int B = b->B;
+#define TRY_GROW(expr)                                                                          \
     do {                                                                                        \
         cudaError_t e_ = (expr);                                                                \
-        if (e_ != cudaSuccess) {                                                                \
-            fail(e_ == cudaErrorMemoryAllocation ? MPS_ERR_OOM : MPS_ERR_CUDA, "%s: %s", #expr, \
-                 cudaGetErrorString(e_));                                                       \
-            return bail(e_ == cudaErrorMemoryAllocation ? MPS_ERR_OOM : MPS_ERR_CUDA);          \
-        }                                                                                       \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? MPS_ERR_OOM : MPS_ERR_CUDA, "%s: %s", \
+                        #expr, cudaGetErrorString(e_));                                         \
     } while (0)
-    TRY_ALLOC(cudaMalloc(&b->meta_d, sizeof(ImageMeta) * n_images));
-    TRY_ALLOC(cudaMallocHost(&b->meta_pinned, sizeof(ImageMeta) * n_images));
-    TRY_ALLOC(cudaMalloc(&b->units_d, sizeof(int32_t) * b->units_h.size()));
-    TRY_ALLOC(cudaMalloc(&b->arena, b->elem * site_off));
-    TRY_ALLOC(cudaMalloc(&b->renv, b->elem * renv_max * n_images));
-    TRY_ALLOC(cudaMalloc(&b->norms, sizeof(double) * n_images));
-    TRY_ALLOC(cudaMalloc(&b->bonds_d, sizeof(int32_t) * bond));
-    TRY_ALLOC(cudaMalloc(&b->discarded_d, sizeof(double) * n_images));
-    TRY_ALLOC(cudaMalloc(&b->status_d, sizeof(int)));
-    TRY_ALLOC(cudaMemsetAsync(b->status_d, 0, sizeof(int), b->stream));
-    TRY_ALLOC(cudaMemsetAsync(b->discarded_d, 0, sizeof(double) * n_images, b->stream));
-    TRY_ALLOC(cudaMemcpyAsync(b->units_d, b->units_h.data(), sizeof(int32_t) * b->units_h.size(),
-                              cudaMemcpyHostToDevice, b->stream));
-    std::memcpy(b->meta_pinned, b->meta_h.data(), sizeof(ImageMeta) * n_images);
-    TRY_ALLOC(cudaMemcpyAsync(b->meta_d, b->meta_pinned, sizeof(ImageMeta) * n_images,
-                              cudaMemcpyHostToDevice, b->stream));
-    TRY_ALLOC(cudaStreamSynchronize(b->stream));
-#undef TRY_ALLOC
+    TRY_GROW(grow(&b->meta_d, &b->cap_meta, sizeof(ImageMeta) * B));
+    TRY_GROW(grow(&b->meta_pinned, &b->cap_meta_pinned, sizeof(ImageMeta) * B, true));
+    TRY_GROW(grow(&b->units_d, &b->cap_units, sizeof(int32_t) * b->units_h.size()));
+    TRY_GROW(grow(reinterpret_cast<unsigned char**>(&b->arena), &b->cap_arena, b->elem * b->need_sites));
+    TRY_GROW(grow(reinterpret_cast<unsigned char**>(&b->renv), &b->cap_renv, b->elem * b->renv_stride * B));
+    TRY_GROW(grow(reinterpret_cast<unsigned char**>(&b->norms), &b->cap_norms, sizeof(double) * B));
+    TRY_GROW(grow(&b->bonds_d, &b->cap_bonds, sizeof(int32_t) * b->total_bonds));
+    TRY_GROW(grow(&b->discarded_d, &b->cap_disc, sizeof(double) * B));
+    TRY_GROW(grow(&b->status_d, &b->cap_status, sizeof(int)));
+    TRY_GROW(grow(&b->queue_d, &b->cap_queue, sizeof(int)));
+    TRY_GROW(grow(&b->order_d, &b->cap_order, sizeof(int32_t) * B));
+    TRY_GROW(grow(&b->order_pinned, &b->cap_order_pinned, sizeof(int32_t) * B, true));
+    TRY_GROW(grow(&b->units_pinned, &b->cap_units_pinned, sizeof(int32_t) * b->units_h.size(), true));
+    // work queue: images by descending cost n * ld^3 (largest chains first)
+    for (int i = 0; i < B; ++i) b->order_pinned[i] = i;
+    std::stable_sort(b->order_pinned, b->order_pinned + B, [&](int a, int c) {
+        const ImageMeta& ma = b->meta_h[a];
+        const ImageMeta& mc = b->meta_h[c];
+        return (int64_t)ma.n * ma.ld * ma.ld * ma.ld > (int64_t)mc.n * mc.ld * mc.ld * mc.ld;
+    });
+    std::memcpy(b->units_pinned, b->units_h.data(), sizeof(int32_t) * b->units_h.size());
+    std::memcpy(b->meta_pinned, b->meta_h.data(), sizeof(ImageMeta) * B);
+    TRY_GROW(cudaMemsetAsync(b->status_d, 0, sizeof(int), b->stream));
+    TRY_GROW(cudaMemsetAsync(b->discarded_d, 0, sizeof(double) * B, b->stream));
+    TRY_GROW(cudaMemcpyAsync(b->order_d, b->order_pinned, sizeof(int32_t) * B, cudaMemcpyHostToDevice, b->stream));
+    TRY_GROW(cudaMemcpyAsync(b->units_d, b->units_pinned, sizeof(int32_t) * b->units_h.size(),
+                             cudaMemcpyHostToDevice, b->stream));
+    TRY_GROW(cudaMemcpyAsync(b->meta_d, b->meta_pinned, sizeof(ImageMeta) * B, cudaMemcpyHostToDevice, b->stream));
+#undef TRY_GROW
+    b->circuit_done = false;
+    return MPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* chi, int32_t chi_all,
+                            int32_t prec, void* stream, mps_batch** out) {
+    if (!out) return fail(MPS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (prec != MPS_FP64 && prec != MPS_MIXED && prec != MPS_MIXED_ORTH64)
+        return fail(MPS_ERR_INVALID_ARG, "unknown precision %d", prec);
+    mps_batch* b = new (std::nothrow) mps_batch();
+    if (!b) return fail(MPS_ERR_OOM, "host allocation failed");
+    b->prec = prec;
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    b->elem = prec == MPS_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
+    mps_status st = layout_images(b, n_images, p, chi, chi_all);
+    if (st == MPS_OK) st = fit_and_upload(b);
+    if (st == MPS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess)
+        st = fail(MPS_ERR_CUDA, "stream synchronisation failed after batch creation");
+    if (st != MPS_OK) {
+        free_batch(b);
+        return st;
+    }
     *out = b;
     return MPS_OK;
+}
+
+mps_status mps_reshape_batch(mps_batch* b, int32_t n_images, const int32_t* p, const int32_t* chi,
+                             int32_t chi_all) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    // the previous layout's work and its pinned staging must be finished before reuse
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    mps_status st = layout_images(b, n_images, p, chi, chi_all);
+    if (st != MPS_OK) return st;
+    return fit_and_upload(b);
 }
 
 mps_status mps_destroy_batch(mps_batch* b) {

@@ -27,7 +27,8 @@ constexpr size_t OFF_BONDS = align256(OFF_UNITS + sizeof(int32_t) * 2 * NA_MAX_I
 constexpr size_t OFF_NORMS = align256(OFF_BONDS + sizeof(int32_t) * NA_MAX_IMAGES * 257);
 constexpr size_t OFF_DISC = align256(OFF_NORMS + sizeof(double) * NA_MAX_IMAGES);
 constexpr size_t OFF_STATUS = align256(OFF_DISC + sizeof(double) * NA_MAX_IMAGES);
-constexpr size_t OFF_ARENA = align256(OFF_STATUS + sizeof(int));
+constexpr size_t OFF_QUEUE = align256(OFF_STATUS + sizeof(int));
+constexpr size_t OFF_ARENA = align256(OFF_QUEUE + sizeof(int));
 constexpr size_t OFF_RENV = align256(OFF_ARENA + NA_ARENA_BYTES);
 constexpr size_t OFF_GATES = align256(OFF_RENV + NA_RENV_BYTES);
 constexpr size_t NA_TOTAL = align256(OFF_GATES + NA_GATE_BYTES);
@@ -167,6 +168,8 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
     b.gates_bytes = NA_GATE_BYTES;
     b.gates_owned = false;
     b.gate_n = n;
+    b.queue_d = reinterpret_cast<int*>(base + OFF_QUEUE);
+    b.order_d = nullptr;   // equal sizes: images in index order
 
     const int threads = 128;
     const int work = std::max(n_images * p, n_images);

@@ -183,7 +183,7 @@ def test_launch_shapes_agree():
         for i in range(B):
             assert np.array_equal(got[i], base[i])   # these knobs keep every bit
     # wider circuit teams change the QR summation order only
-    for shape in ((1, 64, 64), (1, 128, 128)):
+    for shape in ((1, 64, 64), (1, 128, 128)):   # bucket 8: runs one warp per image
         got, _, _ = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=shape)
         for i in range(B):
             assert np.max(np.abs(got[i] - base[i])) < 2e-6
