@@ -136,6 +136,12 @@ mps_status ano_features(const void* pauli, int32_t pauli_f64, int64_t n_images, 
                         const float* abd, const float* W, const float* bias, int32_t out_dim,
                         float* features, float* out, void* stream);
 
+/* Wait for the device and report whether a bounded wait inside the tensor-core
+ * linear layer of ano_features gave up since the last call (MPS_ERR_TIMEOUT; the
+ * flag is then cleared).  Setting the environment variable MPSANO_LINEAR=fp32
+ * makes ano_features use a plain FP32 CUDA-core GEMM instead. */
+mps_status ano_status(void);
+
 /* ---- diagnostics and control ------------------------------------------------ */
 
 /* Wait for the batch's stream and return the first device-side error, if any. */

@@ -48,6 +48,7 @@ SIGNATURES = {
     "ano_features": (_c.c_int, [_c.c_void_p, _c.c_int32, _c.c_int64, _c.c_int32, _c.c_void_p, _c.c_void_p,
                                 _c.c_void_p, _c.c_int32, _c.c_void_p, _c.c_void_p, _c.c_void_p]),
     "mps_sync": (_c.c_int, [_c.c_void_p]),
+    "ano_status": (_c.c_int, []),
     "mps_last_error": (_c.c_char_p, []),
     "mps_pair_count": (_c.c_int64, [_c.c_int32, _c.c_int32]),
     "mps_bond_dims": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_int32)]),

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -17,12 +18,14 @@
 #include "circuit.cuh"
 #include "common.cuh"
 #include "epilogue.cuh"
+#include "gemm_tc.cuh"
 
 using namespace mpsano;
 
 namespace {
 
 thread_local std::string g_err = "no error";
+__device__ int g_epilogue_status = 0;   // first failure code of a tensor-core wait
 std::atomic<uint64_t> g_launches{0};
 
 }  // namespace
@@ -454,10 +457,36 @@ mps_status ano_features(const void* pauli, int32_t pauli_f64, int64_t n_images, 
     CUDA_TRY(cudaGetLastError());
     count_launch();
     if (W) {
-        dim3 grid((out_dim + 15) / 16, (unsigned)((n_images + 15) / 16));
-        linear_fp32_kernel<<<grid, 256, 0, s>>>(features, n_images, m, W, bias, out_dim, out);
+        const char* force = getenv("MPSANO_LINEAR");
+        if (force && strcmp(force, "fp32") == 0) {
+            // plain FP32 CUDA-core GEMM (kept for comparison)
+            dim3 grid((out_dim + 15) / 16, (unsigned)((n_images + 15) / 16));
+            linear_fp32_kernel<<<grid, 256, 0, s>>>(features, n_images, m, W, bias, out_dim, out);
+        } else {
+            static bool attr_set = false;
+            if (!attr_set) {
+                CUDA_TRY(cudaFuncSetAttribute(linear_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)TC_SMEM_BYTES));
+                attr_set = true;
+            }
+            int* st = nullptr;
+            CUDA_TRY(cudaGetSymbolAddress((void**)&st, g_epilogue_status));
+            dim3 grid((out_dim + TC_N - 1) / TC_N, (unsigned)((n_images + TC_M - 1) / TC_M));
+            linear_tc_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(features, (int)n_images, m, W, bias, out_dim, out, st);
+        }
         CUDA_TRY(cudaGetLastError());
         count_launch();
+    }
+    return MPS_OK;
+}
+
+mps_status ano_status(void) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    int st = 0, zero = 0;
+    CUDA_TRY(cudaMemcpyFromSymbol(&st, g_epilogue_status, sizeof(int)));
+    if (st != 0) {
+        CUDA_TRY(cudaMemcpyToSymbol(g_epilogue_status, &zero, sizeof(int)));
+        return fail(MPS_ERR_TIMEOUT, "a tensor-core wait of the linear layer gave up (code %d)", st);
     }
     return MPS_OK;
 }

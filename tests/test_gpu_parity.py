@@ -224,3 +224,24 @@ def test_ano_features_and_linear_vs_oracle():
             ref_y = o_ano.linear(W32, ref_q, b32)
             scale_y = np.abs(W32) @ np.abs(ref_q) + np.abs(b32)
             assert np.all(np.abs(y[i] - ref_y) <= 1e-5 * (1 + scale_y))
+
+
+def test_linear_layer_tensor_cores_partial_tiles():
+    """y = W q + b (Eq. 6) for the 16x16 pair count (480 features) into 1000 outputs
+    and 300 images: partial 128 x 128 tiles in both directions and a K tail."""
+    from paper_2607_10280_b300 import _lib
+    from paper_2607_10280_b300.api import ano_features
+    rng = np.random.default_rng(5)
+    B, m, O = 300, 480, 1000
+    P = rng.uniform(-1, 1, size=(B * m, 16)).astype(np.float32)
+    P[:, 0] = 1.0
+    abd = synth.observable_params(m)
+    W = (rng.standard_normal((O, m)) / np.sqrt(m)).astype(np.float32)
+    bias = rng.standard_normal(O).astype(np.float32)
+    feats, out = ano_features(torch.tensor(P, device="cuda"), m, torch.tensor(abd, dtype=torch.float32, device="cuda"),
+                              torch.tensor(W, device="cuda"), torch.tensor(bias, device="cuda"))
+    _lib.check(_lib.lib().ano_status())
+    q = feats.double().cpu().numpy()
+    ref = q @ W.astype(np.float64).T + bias.astype(np.float64)
+    scale = np.abs(q) @ np.abs(W.astype(np.float64)).T + np.abs(bias)
+    assert np.all(np.abs(out.double().cpu().numpy() - ref) <= 1e-5 * (1 + scale))
