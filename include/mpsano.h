@@ -64,7 +64,8 @@ typedef enum { MPS_FP64 = 0, MPS_MIXED = 1, MPS_MIXED_ORTH64 = 2 } mps_precision
  *                      Sec. II.B. */
 typedef enum { MPS_ANSATZ_LADDER = 0, MPS_ANSATZ_PAPER = 1 } mps_ansatz;
 
-/* Pair set (Sec. II.C): horizontal + vertical neighbours, or also both diagonals. */
+/* Pair set (Sec. II.C): horizontal + vertical neighbours (2p(p-1) pairs), or also
+ * both diagonals (2p(p-1) + 2(p-1)^2 pairs: 156 at p = 7). */
 typedef enum { MPS_PAIRS_HV = 0, MPS_PAIRS_HVD = 1 } mps_pair_set;
 
 typedef struct mps_batch mps_batch;

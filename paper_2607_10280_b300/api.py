@@ -98,14 +98,18 @@ class Batch:
         self._pixels_ref, self._params_ref = pixels, params   # keep alive while queued
         check(lib().mps_apply_circuit(self._h, _ptr(pixels), ctypes.byref(c)))
 
-    def pauli_cache(self, out: torch.Tensor = None) -> torch.Tensor:
-        """Pauli cache [sum m_i][16] (Sec. II.C, Eq. 5), float64 (fp64) or float32."""
+    def pair_offsets_for(self, pair_set: str = "hv") -> np.ndarray:
+        return np.concatenate([[0], np.cumsum([pair_count(int(q), pair_set) for q in self.p])])
+
+    def pauli_cache(self, out: torch.Tensor = None, pair_set: str = "hv") -> torch.Tensor:
+        """Pauli cache [sum m_i][16] (Sec. II.C, Eq. 5), float64 (fp64) or float32.
+        pair_set "hv": horizontal + vertical neighbours; "hvd": also both diagonals."""
         dtype = torch.float64 if self.precision == "fp64" else torch.float32
-        total = int(self.pair_offsets[-1])
+        total = int(self.pair_offsets_for(pair_set)[-1])
         if out is None:
             out = torch.empty((total, 16), dtype=dtype, device="cuda")
         assert out.dtype == dtype and out.shape == (total, 16) and out.is_contiguous()
-        check(lib().mps_pauli_cache(self._h, PAIR_SET["hv"], _ptr(out), None))
+        check(lib().mps_pauli_cache(self._h, PAIR_SET[pair_set], _ptr(out), None))
         return out
 
     def set_launch_shape(self, images_per_cta: int = 0, circuit_threads: int = 0, pauli_threads: int = 0):

@@ -87,8 +87,8 @@ inline mps_status launch_circuit_orth64(mps_batch* b, int chi_tpl, bool trunc, c
 // Fill b->gates (allocated by the caller) with the one-qubit gate table of a circuit.
 mps_status launch_gate_table(mps_batch* b, int ansatz, int L_max, const double* params, int params_n,
                              const double* pixels);
-mps_status launch_pauli_fp64(mps_batch* b, void* out);
-mps_status launch_pauli_mixed(mps_batch* b, void* out);
+mps_status launch_pauli_fp64(mps_batch* b, void* out, bool diag = false);
+mps_status launch_pauli_mixed(mps_batch* b, void* out, bool diag = false);
 
 }  // namespace mpsano
 

@@ -51,7 +51,8 @@ struct ImageMeta {
     int32_t bond_off;   // offset of this image's bond array (n+1 entries)
     int64_t site_off;   // offset (in complex elements) of site 0 in the arena
     int64_t pixel_off;  // offset of the image's pixels in the packed pixel array
-    int64_t pair_off;   // offset (in pairs) of the image's Pauli-cache block
+    int64_t pair_off;   // offset (in pairs) of the image's Pauli-cache block, horizontal + vertical
+    int64_t pair_off_d; // the same with both diagonal pair sets
 };
 
 // Device status word: first error wins.

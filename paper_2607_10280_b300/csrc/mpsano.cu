@@ -213,7 +213,7 @@ mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const
     b->units_h.clear();
     b->ld_max = 1;
     b->n_max = 0;
-    int64_t site_off = 0, pix = 0, pair = 0, bond = 0;
+    int64_t site_off = 0, pix = 0, pair = 0, pair_d = 0, bond = 0;
     for (int i = 0; i < n_images; ++i) {
         const int pi = p[i];
         const int ci = chi ? chi[i] : chi_all;
@@ -230,9 +230,11 @@ mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const
         m.site_off = site_off;
         m.pixel_off = pix;
         m.pair_off = pair;
+        m.pair_off_d = pair_d;
         site_off += (int64_t)n * 2 * ld * ld;
         pix += n;
         pair += mps_pair_count(pi, MPS_PAIRS_HV);
+        pair_d += mps_pair_count(pi, MPS_PAIRS_HVD);
         bond += n + 1;
         b->ld_max = std::max(b->ld_max, ld);
         b->n_max = std::max(b->n_max, n);
@@ -430,14 +432,14 @@ mps_status mps_pauli_cache(mps_batch* b, int32_t pair_set, void* out, int64_t* p
     if (!out) return fail(MPS_ERR_INVALID_ARG, "out is NULL");
     if (pair_set != MPS_PAIRS_HV && pair_set != MPS_PAIRS_HVD)
         return fail(MPS_ERR_INVALID_ARG, "unknown pair set %d", pair_set);
-    if (pair_set == MPS_PAIRS_HVD) return fail(MPS_ERR_UNSUPPORTED, "diagonal pairs are not built yet");
     if (!b->circuit_done) return fail(MPS_ERR_NOT_READY, "no circuit has run on this batch");
     if (pair_offsets) {
         pair_offsets[0] = 0;
         for (int i = 0; i < b->B; ++i) pair_offsets[i + 1] = pair_offsets[i] + mps_pair_count(b->meta_h[i].p, pair_set);
     }
-    if (b->prec == MPS_FP64) return launch_pauli_fp64(b, out);
-    return launch_pauli_mixed(b, out);
+    const bool diag = pair_set == MPS_PAIRS_HVD;
+    if (b->prec == MPS_FP64) return launch_pauli_fp64(b, out, diag);
+    return launch_pauli_mixed(b, out, diag);
 }
 
 mps_status ano_features(const void* pauli, int32_t pauli_f64, int64_t n_images, int32_t m, const float* abd,

@@ -73,6 +73,7 @@ __global__ void noalloc_setup_kernel(ImageMeta* meta, int32_t* units, double* di
         m.site_off = (int64_t)t * n * 2 * ld * ld;
         m.pixel_off = (int64_t)t * n;
         m.pair_off = (int64_t)t * 2 * p * (p - 1);
+        m.pair_off_d = (int64_t)t * (2 * p * (p - 1) + 2 * (p - 1) * (p - 1));
         meta[t] = m;
         discarded[t] = 0.0;
     }

@@ -36,11 +36,15 @@ struct PauliLayout {
     static constexpr int MAT = CHI * CS;
     static constexpr int ZS = 2 * CHI + 1;
     static constexpr int SROWS = 3 * CHI;
-    // A (2 MAT), R (1 MAT), C (3 MAT), S (3 CHI rows x ZS)
+    // A (2 MAT), R (1 MAT), C (3 MAT), S (3 CHI rows x ZS); with diagonal pairs also
+    // Cd (3 MAT, the carried closings one site further)
     static constexpr int ELEMS = 6 * MAT + SROWS * ZS;
     static constexpr size_t bytes = sizeof(cx<T>) * ELEMS;
+    static constexpr size_t elems(bool diag) { return ELEMS + (diag ? 3 * MAT : 0); }
     // plus the cross-warp reduction buffer of a UW-warp team
-    static constexpr size_t team_bytes(int uw) { return bytes + sizeof(T) * 12 * uw; }
+    static constexpr size_t team_bytes(int uw, bool diag = false) {
+        return sizeof(cx<T>) * elems(diag) + sizeof(T) * 12 * uw;
+    }
 };
 
 // Register-tile shape for an M x N output (compile-time bounds) computed by NTHR
@@ -295,33 +299,50 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8)) pauli_kernel(const
                                                     const cx<T>* __restrict__ arena,
                                                     const int32_t* __restrict__ bonds,
                                                     const cx<T>* __restrict__ renv, int64_t renv_stride,
-                                                    const T* __restrict__ norms, T* __restrict__ out) {
+                                                    const T* __restrict__ norms, T* __restrict__ out,
+                                                    int diag_pairs) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NTHR = 32 * UW;
+    const bool diag = diag_pairs != 0;
     // one (image, column) unit per CTA, worked on by UW warps
     const int lane = threadIdx.x;
     const int unit = blockIdx.x;
     if (unit >= n_units) return;
     const int img = unit_image[2 * unit], c = unit_image[2 * unit + 1];
     cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
-    T* red = reinterpret_cast<T*>(base + Lay::ELEMS);
+    T* red = reinterpret_cast<T*>(base + Lay::ELEMS + (diag ? 3 * MAT : 0));
     cx<T>* A = base;               // 2 MAT
     cx<T>* R = base + 2 * MAT;
     cx<T>* C = base + 3 * MAT;     // 3 MAT: C_X, C_Y, C_Z
     cx<T>* S = base + 6 * MAT;     // GEMM scratch
+    cx<T>* Cd = base + Lay::ELEMS; // 3 MAT (diagonal pairs only)
     const ImageMeta mt = meta[img];
     const int p = mt.p, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
     const cx<T>* sites = arena + mt.site_off;
     const cx<T>* rg = renv + (size_t)img * renv_stride;
     const T inv_norm = T(1) / norms[img];
-    T* outp = out + (size_t)mt.pair_off * 16;
-    const int nh = p * (p - 1);  // horizontal pairs come first
+    T* outp = out + (size_t)(diag ? mt.pair_off_d : mt.pair_off) * 16;
+    const int nh = p * (p - 1);                  // horizontal pairs come first, then vertical,
+    const int base_dd = 2 * p * (p - 1);         // then (r,c)-(r+1,c+1),
+    const int base_da = base_dd + (p - 1) * (p - 1);   // then (r,c+1)-(r+1,c)
+    auto write_pair = [&](int q, const T* sa, const T* sb, const T* dv) {
+        // sa: <P_a> of the lower-index site, sb: <P_b> of the other, dv: the 9 two-body sums
+        if (lane < 16) {
+            const int a = lane >> 2, b = lane & 3;
+            T v;
+            if (a == 0 && b == 0) v = T(1);
+            else if (b == 0) v = sa[a - 1];
+            else if (a == 0) v = sb[b - 1];
+            else v = dv[4 * (a - 1) + (b - 1)] * inv_norm;
+            outp[(size_t)q * 16 + lane] = v;
+        }
+    };
 
     T single_up[3] = {T(0), T(0), T(0)};   // <P_b> of the site that created the carried C
-    T d[12];
+    T d[12], dd[12];
     for (int row = p - 1; row >= 0; --row) {
         const int j = row * p + c;
         const int Dl = bd[j], Dr = bd[j + 1];
@@ -334,19 +355,19 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8)) pauli_kernel(const
         left_dots<T, CHI, NTHR>(S, row < p - 1 ? C : nullptr, R, Dr, d, red, lane);
         T single_j[3];
         for (int a = 0; a < 3; ++a) single_j[a] = d[4 * a + 3] * inv_norm;
-        if (row < p - 1 && lane < 16) {
-            const int a = lane >> 2, b = lane & 3;
-            T v;
-            if (a == 0 && b == 0) v = T(1);
-            else if (b == 0) v = single_j[a - 1];
-            else if (a == 0) v = single_up[b - 1];
-            else v = d[4 * (a - 1) + (b - 1)] * inv_norm;
-            outp[(size_t)(nh + j) * 16 + lane] = v;
-        }
+        if (row < p - 1) write_pair(nh + j, single_j, single_up, d);
         team_sync();
+        // diagonal (row, c-1)-(row+1, c): the closings carried from j+p, one site further
+        const bool has_dd = diag && row < p - 1 && c >= 1;
+        if (has_dd) {
+            for (int o = lane; o < 3 * MAT; o += NTHR) Cd[o] = C[o];
+            team_sync();
+            transfer<T, CHI, 3, NTHR>(Cd, A, S, Dl, Dr, lane);
+        }
         // closings of site j as a right site
         right_closings<T, CHI, NTHR>(A, R, C, S, Dl, Dr, lane);
-        for (int b = 0; b < 3; ++b) single_up[b] = single_j[b];
+        T single_prev[3];
+        for (int b = 0; b < 3; ++b) { single_prev[b] = single_up[b]; single_up[b] = single_j[b]; }
         if (c == 0 && row == 0) break;
         // next site to the left: horizontal pair (j-1, j) and the first carry step
         const int k0 = j - 1;
@@ -359,14 +380,12 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8)) pauli_kernel(const
             left_blocks<T, CHI, NTHR>(A, S, Dl0, Dl, lane);
             team_sync();
             left_dots<T, CHI, NTHR>(S, C, R, Dl, d, red, lane);
-            if (lane < 16) {
-                const int a = lane >> 2, b = lane & 3;
-                T v;
-                if (a == 0 && b == 0) v = T(1);
-                else if (b == 0) v = d[4 * (a - 1) + 3] * inv_norm;
-                else if (a == 0) v = single_j[b - 1];
-                else v = d[4 * (a - 1) + (b - 1)] * inv_norm;
-                outp[(size_t)(row * (p - 1) + (c - 1)) * 16 + lane] = v;
+            T single_k[3];
+            for (int a = 0; a < 3; ++a) single_k[a] = d[4 * a + 3] * inv_norm;
+            write_pair(row * (p - 1) + (c - 1), single_k, single_j, d);
+            if (has_dd) {
+                left_dots<T, CHI, NTHR>(S, Cd, R, Dl, dd, red, lane);
+                write_pair(base_dd + row * (p - 1) + (c - 1), single_k, single_prev, dd);
             }
             team_sync();
         }
@@ -376,6 +395,18 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8)) pauli_kernel(const
             const int Dlk = bd[k], Drk = bd[k + 1];
             if (k != k0) {
                 load_site_p<T, CS, NTHR>(A, sites + (size_t)k * 2 * ld * ld, ld, Dlk, Drk, lane);
+                team_sync();
+            }
+            if (diag && k == j - p + 1 && c <= p - 2) {
+                // anti-diagonal (row-1, c+1)-(row, c): site k is the left site
+                load_mat<T, CS, NTHR>(R, rg + (size_t)k * CHI * CHI, CHI, Drk, lane);
+                team_sync();
+                left_blocks<T, CHI, NTHR>(A, S, Dlk, Drk, lane);
+                team_sync();
+                left_dots<T, CHI, NTHR>(S, C, R, Drk, dd, red, lane);
+                T single_k[3];
+                for (int a = 0; a < 3; ++a) single_k[a] = dd[4 * a + 3] * inv_norm;
+                write_pair(base_da + (row - 1) * (p - 1) + c, single_k, single_j, dd);
                 team_sync();
             }
             transfer<T, CHI, 3, NTHR>(C, A, S, Dlk, Drk, lane);

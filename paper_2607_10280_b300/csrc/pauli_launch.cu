@@ -8,10 +8,10 @@ namespace mpsano {
 namespace {
 
 template <typename T, int CHI, int UW>
-mps_status launch_pauli_uw(mps_batch* b, void* out) {
+mps_status launch_pauli_uw(mps_batch* b, void* out, bool diag) {
     using Lay = PauliLayout<T, CHI>;
     const int limit = smem_optin_limit();
-    const size_t smem = Lay::team_bytes(UW);
+    const size_t smem = Lay::team_bytes(UW, diag);
     if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "Pauli kernel shared memory %zu B", smem);
     auto pk = pauli_kernel<T, CHI, UW>;
     CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -19,7 +19,7 @@ mps_status launch_pauli_uw(mps_batch* b, void* out) {
     pk<<<b->n_units, 32 * UW, smem, b->stream>>>(
         b->meta_d, b->n_units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
-        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out));
+        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out), diag ? 1 : 0);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
@@ -27,7 +27,7 @@ mps_status launch_pauli_uw(mps_batch* b, void* out) {
 }
 
 template <typename T, int CHI>
-mps_status launch_pauli(mps_batch* b, void* out) {
+mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
     using Lay = PauliLayout<T, CHI>;
     const int limit = smem_optin_limit();
     const size_t smem = Lay::bytes;
@@ -42,19 +42,19 @@ mps_status launch_pauli(mps_batch* b, void* out) {
     CUDA_TRY(cudaGetLastError());
     count_launch();
     switch (b->pauli_warps) {
-        case 1: return launch_pauli_uw<T, CHI, 1>(b, out);
-        case 4: return launch_pauli_uw<T, CHI, 4>(b, out);
-        default: return launch_pauli_uw<T, CHI, 2>(b, out);
+        case 1: return launch_pauli_uw<T, CHI, 1>(b, out, diag);
+        case 4: return launch_pauli_uw<T, CHI, 4>(b, out, diag);
+        default: return launch_pauli_uw<T, CHI, 2>(b, out, diag);
     }
 }
 
 template <typename T>
-mps_status dispatch_pauli(mps_batch* b, void* out) {
+mps_status dispatch_pauli(mps_batch* b, void* out, bool diag) {
     switch (b->chi_tpl) {
-        case 4: return launch_pauli<T, 4>(b, out);
-        case 8: return launch_pauli<T, 8>(b, out);
-        case 16: return launch_pauli<T, 16>(b, out);
-        case 32: return launch_pauli<T, 32>(b, out);
+        case 4: return launch_pauli<T, 4>(b, out, diag);
+        case 8: return launch_pauli<T, 8>(b, out, diag);
+        case 16: return launch_pauli<T, 16>(b, out, diag);
+        case 32: return launch_pauli<T, 32>(b, out, diag);
     }
     return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", b->chi_tpl);
 }
@@ -62,7 +62,7 @@ mps_status dispatch_pauli(mps_batch* b, void* out) {
 
 }  // namespace
 
-mps_status launch_pauli_fp64(mps_batch* b, void* out) { return dispatch_pauli<double>(b, out); }
-mps_status launch_pauli_mixed(mps_batch* b, void* out) { return dispatch_pauli<float>(b, out); }
+mps_status launch_pauli_fp64(mps_batch* b, void* out, bool diag) { return dispatch_pauli<double>(b, out, diag); }
+mps_status launch_pauli_mixed(mps_batch* b, void* out, bool diag) { return dispatch_pauli<float>(b, out, diag); }
 
 }  // namespace mpsano
