@@ -172,11 +172,22 @@ uint64_t mps_launch_count(void);
  *                    (wider teams are compiled for the mixed path at bond bucket 16
  *                    without truncation; elsewhere one warp per image runs)
  *   pauli_threads    threads that share one (image, grid column) unit of the Pauli
- *                    kernel: 32, 64 or 128
+ *                    kernel: 32, 64 or 128 (the pair set with diagonals always runs
+ *                    with 64)
  * images_per_cta and pauli_threads leave every result bit-identical; circuit_threads
  * changes the summation order inside the QR splits (results agree to rounding). */
 mps_status mps_set_launch_shape(mps_batch* batch, int32_t images_per_cta, int32_t circuit_threads,
                                 int32_t pauli_threads);
+
+/* Layer pipelining of the circuit kernel (enable != 0: on, the default).  When the
+ * ansatz is the ladder, no step of any image truncates (min(2 D_left, 2 D_right) <= chi
+ * at every two-qubit gate) and no image has more than 4 layers, one warp per layer
+ * works on each image and layer l applies its gate at bond k as soon as layer l-1
+ * has finished bond k+1 (Sec. II.B's gate order is kept for every qubit).  Every
+ * split is then exact, so the resulting MPS equals the one of the sequential sweep;
+ * other circuits always run the sequential sweep.  Takes effect at the next
+ * mps_apply_circuit. */
+mps_status mps_set_layer_pipeline(mps_batch* batch, int32_t enable);
 
 /* Per-launch timing with CUDA events recorded on the batch's stream around each
  * kernel the batch launches (enable != 0 turns it on; off by default). */

@@ -128,6 +128,10 @@ class Batch:
             o += n + 1
         return out
 
+    def set_layer_pipeline(self, enable: bool = True):
+        """Layer-pipelined circuit kernel where it applies (ladder, no truncation, L <= 4)."""
+        check(lib().mps_set_layer_pipeline(self._h, 1 if enable else 0))
+
     def set_timing(self, enable: bool = True):
         check(lib().mps_set_timing(self._h, 1 if enable else 0))
 

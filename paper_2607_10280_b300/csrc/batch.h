@@ -36,6 +36,8 @@ struct mps_batch {
     int gate_n = 0;                        // qubit stride of the gate table
     bool gates_owned = true;               // false when gates points into static scratch
     int circuit_threads = 32;              // threads per image in the circuit kernel
+    bool layer_pipeline = true;            // layer-pipelined kernel where it applies
+    int L_max = 0;                         // most layers of any image in the last circuit
     int32_t* order_d = nullptr;            // circuit work queue: images by descending cost
     int32_t* order_pinned = nullptr;       // staging of order_d
     int32_t* units_pinned = nullptr;       // staging of units_d

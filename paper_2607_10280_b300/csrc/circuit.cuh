@@ -9,10 +9,12 @@
 //     QR, A_k = Q, A_{k+1} = R.  M < N: A_k = I_M, A_{k+1} = theta.  The state is
 //     the one the SVD split would give, in another gauge of the new bond.
 //   * min(M, N) > chi: SVD truncation at the orthogonality centre.  Gram matrix of
-//     the smaller side in FP64, cyclic Jacobi eigensolver in FP64 (sigma^2 = its
-//     eigenvalues), keep the chi largest, A_k = U_chi (re-orthogonalised by an FP64
-//     Householder QR when it comes from the right Gram), A_{k+1} = U_chi^H theta
-//     rescaled to unit norm.
+//     the smaller side in FP64; cyclic Jacobi eigensolver (FP64 path: in FP64;
+//     mixed path: in FP32 on the rounded Gram, sigma^2 then taken as FP64 Rayleigh
+//     quotients, and solved again in FP64 when the gap at the cut is below 1e-3 of
+//     the largest); keep the chi largest, A_k = U_chi (re-orthogonalised by an FP64
+//     Householder QR unless it came from an FP64 solve of the left Gram),
+//     A_{k+1} = U_chi^H theta rescaled to unit norm.
 //
 // Before a pass in which some step truncates, a right-to-left LQ sweep moves the
 // centre to the first site of the pass so that every truncation happens at the
@@ -567,6 +569,152 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
         if (lane == 0) discarded_out[img] = w.discarded;
         tsync<NTHR>();
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// Layer-pipelined circuit kernel: ladder ansatz, no step truncates, L <= 4.
+//
+// One CTA per image and one warp per layer.  Layer j's step at bond k runs in
+// super-step t = k + 2j, so it starts once layer j-1 has finished its steps at
+// bonds k and k+1: sites k and k+1 then hold exactly what the sequential sweep
+// would hand to layer j, and the gates still pending in layer j-1 (bonds >= k+2)
+// act on other qubits.  Every split of a pass without truncation is exact (QR or
+// identity), so no step needs the orthogonality centre; each step also runs the
+// same arithmetic as in circuit_kernel, so the two kernels give the same state.
+// A CTA barrier ends every super-step (no spin waits).
+//
+// After layer l of a ladder every bond is at most 2^l (one CNOT crosses each cut
+// per layer), so layer l's buffers are sized for a left bond <= CL = min(2^l, CHI)
+// and middle/right bonds <= CLR = min(2^(l-1), CHI); a step whose bonds exceed
+// them raises DEV_BOND_OVERFLOW before touching the buffers.
+constexpr int WAVE_LAYERS = 4;
+
+template <typename T, typename TQ, int CL, int CLR>
+struct WaveBuf {
+    static constexpr int CS = CL + 1, LDM = 2 * CL + 1;
+    static constexpr size_t off_cur = 0;
+    static constexpr size_t off_nxt = off_cur + sizeof(cx<T>) * 2 * CL * CS;
+    static constexpr size_t off_th = (off_nxt + sizeof(cx<T>) * 2 * CLR * CS + 15) & ~size_t(15);
+    static constexpr size_t off_tau = off_th + sizeof(cx<TQ>) * 2 * CLR * LDM;
+    static constexpr size_t bytes = (off_tau + sizeof(cx<TQ>) * 2 * CLR + 15) & ~size_t(15);
+};
+
+template <int CHI, int J> struct WaveDims {
+    static constexpr int CL = (2 << J) < CHI ? (2 << J) : CHI;
+    static constexpr int CLR = (1 << J) < CHI ? (1 << J) : CHI;
+};
+
+template <typename T, typename TQ, int CHI>
+struct WaveLayout {
+    static constexpr size_t off_bd = 0;                                  // MAX_QUBITS + 1 bonds
+    static constexpr size_t off_w0 = (sizeof(int) * (MAX_QUBITS + 1) + 15) & ~size_t(15);
+    static constexpr size_t b0 = WaveBuf<T, TQ, WaveDims<CHI, 0>::CL, WaveDims<CHI, 0>::CLR>::bytes;
+    static constexpr size_t b1 = WaveBuf<T, TQ, WaveDims<CHI, 1>::CL, WaveDims<CHI, 1>::CLR>::bytes;
+    static constexpr size_t b2 = WaveBuf<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>::bytes;
+    static constexpr size_t b3 = WaveBuf<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>::bytes;
+    static constexpr size_t off_w1 = off_w0 + b0, off_w2 = off_w1 + b1, off_w3 = off_w2 + b2;
+    static constexpr size_t bytes = off_w3 + b3;
+};
+
+// One step (bond k) of layer `layer` for the warp that owns it.  Returns false
+// (after raising the status) when a bond exceeds the layer's buffers.
+template <typename T, typename TQ, int CL, int CLR>
+__device__ bool wave_step(unsigned char* buf, int* bd, int k, int n, int ld, cx<T>* sites,
+                          const cx<T>* gates, int gn, int layer, int lane, int* status) {
+    using B = WaveBuf<T, TQ, CL, CLR>;
+    constexpr int CS = B::CS;
+    CircuitTeam<T, TQ, CL, false, 32> w;
+    w.cur = reinterpret_cast<cx<T>*>(buf + B::off_cur);
+    w.nxt = reinterpret_cast<cx<T>*>(buf + B::off_nxt);
+    w.th = reinterpret_cast<cx<TQ>*>(buf + B::off_th);
+    w.tau = reinterpret_cast<cx<TQ>*>(buf + B::off_tau);
+    w.rb = nullptr; w.G = nullptr; w.V = nullptr; w.taud = nullptr; w.lam = nullptr; w.ord = nullptr;
+    w.red = nullptr; w.flag = nullptr;
+    w.bd = bd;
+    w.lane = lane;
+    w.n = n;
+    w.chi = CL;
+    w.ld = ld;
+    w.sites = sites;
+    w.discarded = 0.0;
+    w.status = status;
+    const int Dl = bd[k], Dm = bd[k + 1], Dr = bd[k + 2];
+    const int nb = 2 * Dl < 2 * Dr ? 2 * Dl : 2 * Dr;
+    if (Dl > CL || Dm > CLR || Dr > CLR || nb > CL || nb > ld) {
+        raise_status(status, DEV_BOND_OVERFLOW);
+        return false;
+    }
+    if (k == 0) {
+        // the pass starts from the stored site 0 with the layer's one-qubit gate
+        load_site<T, CS, 32>(w.cur, w.site_ptr(0), ld, Dl, Dm, nullptr, lane);
+        __syncwarp();
+        const Gate1<T> g = table_gate<T>(gates, gn, 0, layer, 0, 0);
+        apply_gate_smem<T, CS, 32>(w.cur, Dl, Dm, g, lane);
+        __syncwarp();
+    }
+    const Gate1<T> g = table_gate<T>(gates, gn, 0, layer, 0, k + 1);
+    load_site<T, CS, 32>(w.nxt, w.site_ptr(k + 1), ld, Dm, Dr, &g, lane);
+    __syncwarp();
+    w.form_theta(Dl, Dm, Dr, true);
+    w.split(k, Dl, Dr, false);
+    if (k == n - 2) {
+        store_site<T, CS, 32>(w.site_ptr(n - 1), w.cur, ld, nb, Dr, lane);
+    }
+    __syncwarp();
+    if (lane == 0) bd[k + 1] = nb;
+    return true;
+}
+
+template <typename T, typename TQ, int CHI>
+__global__ void __launch_bounds__(32 * WAVE_LAYERS, 8) circuit_wave_kernel(
+    const ImageMeta* __restrict__ meta, int n_images, const int32_t* __restrict__ order,
+    const double* __restrict__ pixels, const cx<T>* __restrict__ gates, int gn,
+    cx<T>* __restrict__ arena, int32_t* __restrict__ bonds_out, double* __restrict__ discarded_out,
+    int* status) {
+    using Lay = WaveLayout<T, TQ, CHI>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int slot = blockIdx.x;
+    if (slot >= n_images) return;
+    const int img = order ? order[slot] : slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const ImageMeta mt = meta[img];
+    const int n = mt.n, ld = mt.ld;
+    cx<T>* sites = arena + mt.site_off;
+    int* bd = reinterpret_cast<int*>(smem_raw + Lay::off_bd);
+    const double* px = pixels + mt.pixel_off;
+    // |0...0> then the encoding R_Y(pi x); every bond is 1
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) bd[k] = 1;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        cx<T>* s = sites + (size_t)k * (2 * ld * ld);
+        double sn, cs;
+        sincos(0.5 * M_PI * px[k], &sn, &cs);
+        s[0] = mk<T>(T(cs), T(0));
+        s[ld] = mk<T>(T(sn), T(0));
+    }
+    __syncthreads();
+    const int L = mt.L < WAVE_LAYERS ? mt.L : WAVE_LAYERS;
+    const int supersteps = (L > 0 && n > 1) ? (n - 1) + 2 * (L - 1) : 0;
+    for (int t = 0; t < supersteps; ++t) {
+        const int k = t - 2 * warp;
+        bool ok = true;
+        if (warp < L && k >= 0 && k < n - 1) {
+            switch (warp) {
+                case 0: ok = wave_step<T, TQ, WaveDims<CHI, 0>::CL, WaveDims<CHI, 0>::CLR>(
+                            smem_raw + Lay::off_w0, bd, k, n, ld, sites, gates, gn, 0, lane, status); break;
+                case 1: ok = wave_step<T, TQ, WaveDims<CHI, 1>::CL, WaveDims<CHI, 1>::CLR>(
+                            smem_raw + Lay::off_w1, bd, k, n, ld, sites, gates, gn, 1, lane, status); break;
+                case 2: ok = wave_step<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>(
+                            smem_raw + Lay::off_w2, bd, k, n, ld, sites, gates, gn, 2, lane, status); break;
+                default: ok = wave_step<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>(
+                            smem_raw + Lay::off_w3, bd, k, n, ld, sites, gates, gn, 3, lane, status); break;
+            }
+        }
+        // global writes of this super-step become visible to the other warps here
+        if (__syncthreads_or(ok ? 0 : 1)) break;
+    }
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) bonds_out[mt.bond_off + k] = bd[k];
+    if (threadIdx.x == 0) discarded_out[img] = 0.0;
 }
 
 }  // namespace mpsano

@@ -42,11 +42,39 @@ mps_status launch_circuit_team(mps_batch* b, const double* pixels, int ansatz) {
     return MPS_OK;
 }
 
+// Layer-pipelined kernel (ladder ansatz, no truncation, at most WAVE_LAYERS layers):
+// one CTA of one warp per layer for each image, in descending-cost order.  Its
+// buffers only depend on min(CHI, 16) since a ladder bond is at most 2^layers.
+template <typename T, typename TQ, int CHI>
+mps_status launch_circuit_wave(mps_batch* b, const double* pixels) {
+    constexpr int CW = CHI < 16 ? CHI : 16;
+    using Lay = WaveLayout<T, TQ, CW>;
+    const size_t smem = Lay::bytes;
+    if (smem > (size_t)smem_optin_limit())
+        return fail(MPS_ERR_UNSUPPORTED, "layer-pipelined circuit kernel needs %zu B shared memory", smem);
+    auto kern = circuit_wave_kernel<T, TQ, CW>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int warps = std::max(1, std::min(b->L_max, WAVE_LAYERS));
+    timing_begin(b, KIND_CIRCUIT);
+    kern<<<b->B, 32 * warps, smem, b->stream>>>(b->meta_d, b->B, b->order_d, pixels,
+                                                reinterpret_cast<const cx<T>*>(b->gates), b->gate_n,
+                                                reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
+                                                b->discarded_d, b->status_d);
+    timing_end(b);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return MPS_OK;
+}
+
 // Wider teams are compiled only for the mixed path at bond bucket 16 without
 // truncation (the benchmark shape); measured on B300 they do not beat one warp per
 // image, so every other combination runs one warp per image.
 template <typename T, typename TQ, int CHI, bool TRUNC>
 mps_status launch_circuit(mps_batch* b, const double* pixels, int ansatz) {
+    if constexpr (!TRUNC) {
+        if (b->layer_pipeline && ansatz == MPS_ANSATZ_LADDER && b->L_max >= 1 && b->L_max <= WAVE_LAYERS)
+            return launch_circuit_wave<T, TQ, CHI>(b, pixels);
+    }
     if constexpr (CHI == 16 && !TRUNC && sizeof(T) == 4 && sizeof(TQ) == 4) {
         if (b->circuit_threads == 64) return launch_circuit_team<T, TQ, CHI, TRUNC, 64>(b, pixels, ansatz);
     }

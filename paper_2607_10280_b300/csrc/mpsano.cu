@@ -362,6 +362,12 @@ mps_status mps_set_launch_shape(mps_batch* b, int32_t images_per_cta, int32_t ci
     return MPS_OK;
 }
 
+mps_status mps_set_layer_pipeline(mps_batch* b, int32_t enable) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    b->layer_pipeline = enable != 0;
+    return MPS_OK;
+}
+
 mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circuit* circ) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
     if (!pixels) return fail(MPS_ERR_INVALID_ARG, "pixels is NULL");
@@ -413,6 +419,7 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         b->gates_bytes = gbytes;
     }
     b->gate_n = b->n_max;
+    b->L_max = L_max;
     const double* pr = circ->ansatz == MPS_ANSATZ_LADDER ? circ->params : nullptr;
     mps_status st = launch_gate_table(b, circ->ansatz, L_max, pr, circ->params_n, pixels);
     if (st != MPS_OK) return st;

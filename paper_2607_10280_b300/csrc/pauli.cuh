@@ -293,19 +293,18 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     if (lane == 0) norm_out[img] = R[0].re;
 }
 
-template <typename T, int CHI, int UW>
+template <typename T, int CHI, int UW, bool DIAG>
 __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
                                                     const int32_t* __restrict__ unit_image,
                                                     const cx<T>* __restrict__ arena,
                                                     const int32_t* __restrict__ bonds,
                                                     const cx<T>* __restrict__ renv, int64_t renv_stride,
-                                                    const T* __restrict__ norms, T* __restrict__ out,
-                                                    int diag_pairs) {
+                                                    const T* __restrict__ norms, T* __restrict__ out) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NTHR = 32 * UW;
-    const bool diag = diag_pairs != 0;
+    constexpr bool diag = DIAG;   // both diagonal pair sets as well (a separate instantiation)
     // one (image, column) unit per CTA, worked on by UW warps
     const int lane = threadIdx.x;
     const int unit = blockIdx.x;

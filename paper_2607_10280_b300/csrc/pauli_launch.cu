@@ -7,19 +7,20 @@
 namespace mpsano {
 namespace {
 
-template <typename T, int CHI, int UW>
-mps_status launch_pauli_uw(mps_batch* b, void* out, bool diag) {
+template <typename T, int CHI, int UW, bool DIAG>
+mps_status launch_pauli_uw(mps_batch* b, void* out) {
+    constexpr bool diag = DIAG;
     using Lay = PauliLayout<T, CHI>;
     const int limit = smem_optin_limit();
     const size_t smem = Lay::team_bytes(UW, diag);
     if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "Pauli kernel shared memory %zu B", smem);
-    auto pk = pauli_kernel<T, CHI, UW>;
+    auto pk = pauli_kernel<T, CHI, UW, DIAG>;
     CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     timing_begin(b, KIND_PAULI);
     pk<<<b->n_units, 32 * UW, smem, b->stream>>>(
         b->meta_d, b->n_units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
-        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out), diag ? 1 : 0);
+        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out));
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
@@ -41,10 +42,12 @@ mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
+    // the diagonal pair sets are compiled for 2-warp teams only
+    if (diag) return launch_pauli_uw<T, CHI, 2, true>(b, out);
     switch (b->pauli_warps) {
-        case 1: return launch_pauli_uw<T, CHI, 1>(b, out, diag);
-        case 4: return launch_pauli_uw<T, CHI, 4>(b, out, diag);
-        default: return launch_pauli_uw<T, CHI, 2>(b, out, diag);
+        case 1: return launch_pauli_uw<T, CHI, 1, false>(b, out);
+        case 4: return launch_pauli_uw<T, CHI, 4, false>(b, out);
+        default: return launch_pauli_uw<T, CHI, 2, false>(b, out);
     }
 }
 

@@ -49,13 +49,14 @@ def oracle_cache(x, p, L, chi, ansatz="ladder", params=None, backend="mps"):
     return st.pair_paulis(prs), st.min_gap
 
 
-def run_gpu(pixels_list, ps, L, chi, precision, ansatz="ladder", params=None, shape=None):
+def run_gpu(pixels_list, ps, L, chi, precision, ansatz="ladder", params=None, shape=None, pipeline=True):
     from paper_2607_10280_b300.api import Batch
     px = torch.tensor(np.concatenate([np.asarray(x) for x in pixels_list]), dtype=torch.float64, device="cuda")
     pr = None if params is None else torch.tensor(params, dtype=torch.float64, device="cuda").contiguous()
     b = Batch(np.asarray(ps, dtype=np.int32), chi, precision)
     if shape:
         b.set_launch_shape(*shape)
+    b.set_layer_pipeline(pipeline)
     b.apply_circuit(px, L, ansatz, pr)
     out = b.pauli_cache()
     b.sync()
@@ -288,3 +289,39 @@ def test_diagonal_pairs_vs_oracle(precision, ansatz, p, L, chi):
             continue
         ref = st.pair_paulis(prs)
         assert np.max(np.abs(blk - ref)) < tol_for(precision, st.min_gap), (st.min_gap, np.max(np.abs(blk - ref)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_orth64"])
+def test_layer_pipeline_equals_sequential_sweep(precision):
+    """The layer-pipelined circuit kernel (ladder, no truncation, L <= 4) runs every
+    two-qubit step on the same inputs as the sequential sweep: same bond dimensions
+    and Pauli caches equal to the last bit (the comparison allows 1e-12 / 2e-7 in
+    case the compiler contracts a multiply-add differently in the two kernels)."""
+    cases = [([7] * 6, 4, 16), ([5] * 5, 3, 8), ([4, 9, 6, 16, 5], 2, 16), ([6] * 4, 1, 2),
+             ([3, 2, 8, 7], [4, 0, 3, 2], 32)]
+    bound = 1e-12 if precision == "fp64" else 2e-7
+    for ci, (ps, L, chi) in enumerate(cases):
+        X = [synth.garment_pixels(1, p, seed=60 + 7 * ci + i)[0] for i, p in enumerate(ps)]
+        params = synth.circuit_params(int(np.max(L)), max(ps) ** 2, seed=70 + ci)
+        seq, b_seq, d_seq = run_gpu(X, ps, L, chi, precision, params=params, pipeline=False)
+        pip, b_pip, d_pip = run_gpu(X, ps, L, chi, precision, params=params, pipeline=True)
+        assert all(np.array_equal(u, v) for u, v in zip(b_seq, b_pip)), ci
+        assert np.all(d_pip == 0.0) and np.all(d_seq == 0.0)
+        for i in range(len(ps)):
+            err = np.max(np.abs(seq[i] - pip[i]))
+            assert err <= bound, (ci, i, err)
+    # the sample of the pipelined path also matches the oracle
+    ref, _ = oracle_cache(X[0], ps[0], int(L[0]), chi, params=params)
+    assert np.max(np.abs(pip[0] - ref)) < TOL[precision]
+
+
+def test_layer_pipeline_falls_back_when_a_step_truncates():
+    """chi < 2^L (a truncating pass): the sequential sweep runs whatever the switch."""
+    p, L, chi = 5, 3, 4
+    X = synth.garment_pixels(3, p, seed=91)
+    params = synth.circuit_params(L, p * p, seed=92)
+    a, ba, da = run_gpu(list(X), [p] * 3, L, chi, "mixed", params=params, pipeline=False)
+    b, bb, db = run_gpu(list(X), [p] * 3, L, chi, "mixed", params=params, pipeline=True)
+    assert all(np.array_equal(u, v) for u, v in zip(ba, bb)) and np.array_equal(da, db)
+    for i in range(3):
+        assert np.array_equal(a[i], b[i])
