@@ -27,6 +27,7 @@
 // 3*CHI rows of stride ZS = 2*CHI + 1.
 #pragma once
 #include "common.cuh"
+#include "linalg.cuh"
 
 namespace mpsano {
 
@@ -65,15 +66,16 @@ struct Tile {
 
 // out[m][n] = sum_{seg < NSEG} sum_{k < K} opA(Ab[ao(m) + seg*as_seg + k*as])
 //                                          * Bb[bo(n) + seg*bs_seg + k*bs]
-// for m < M, n < N, delivered through store(m, n, value).
-template <typename T, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, class AO, class BO, class ST>
+// for m < M, n < N, delivered through store(m, so(n), value); the column offsets
+// ao, bo and so are evaluated once per tile row / column.
+template <typename T, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, class AO, class BO, class SO, class ST>
 __device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as_seg,
                                           const cx<T>* Bb, BO bo, int bs, int bs_seg,
-                                          int M, int N, int K, ST store, int lane) {
+                                          int M, int N, int K, SO so, ST store, int lane) {
     const int tm = lane / NT, tn = lane % NT;
     for (int m0 = 0; m0 < M; m0 += MT * TM) {
         for (int n0 = 0; n0 < N; n0 += NT * TN) {
-            int aoff[TM], boff[TN];
+            int aoff[TM], boff[TN], soff[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) {
                 const int m = m0 + tm + MT * i;
@@ -83,6 +85,7 @@ __device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as
             for (int j = 0; j < TN; ++j) {
                 const int n = n0 + tn + NT * j;
                 boff[j] = bo(n < N ? n : N - 1);
+                soff[j] = so(n < N ? n : N - 1);
             }
             cx<T> acc[TM][TN];
 #pragma unroll
@@ -115,7 +118,7 @@ __device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as
 #pragma unroll
                 for (int j = 0; j < TN; ++j) {
                     const int n = n0 + tn + NT * j;
-                    if (m < M && n < N) store(m, n, acc[i][j]);
+                    if (m < M && n < N) store(m, soff[j], acc[i][j]);
                 }
             }
         }
@@ -134,7 +137,7 @@ __device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<
     team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false>(
         C, [Dr](int m) { return (m / Dr) * MAT + (m % Dr) * CS; }, 1, 0,
         A, [](int n) { return n * CS; }, 1, 0, NB * Dr, 2 * Dl, Dr,
-        [S](int m, int n, cx<T> v) { S[m * ZS + n] = v; }, lane);
+        [](int n) { return n; }, [S](int m, int sn, cx<T> v) { S[m * ZS + sn] = v; }, lane);
 }
 
 // Transfer of NB matrices through a site A (Dl x 2 x Dr), in place:
@@ -150,7 +153,8 @@ __device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int
     team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true>(
         A, [](int l) { return 2 * l * CS; }, 1, CS,
         S, [Dl, Dr](int n) { return (n / Dl) * Dr * ZS + 2 * (n % Dl); }, ZS, 1, Dl, NB * Dl, Dr,
-        [C, Dl](int l, int n, cx<T> v) { C[(n / Dl) * MAT + l * CS + (n % Dl)] = v; }, lane);
+        [Dl](int n) { return (n / Dl) * MAT + (n % Dl); },
+        [C](int l, int sn, cx<T> v) { C[l * CS + sn] = v; }, lane);
     team_sync();
 }
 
@@ -165,7 +169,7 @@ __device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, in
     auto off = [Dr](int m) { return (m / Dr) * CS + (m % Dr); };
     team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true>(
         A, off, 2 * CS, 0, A, off, 2 * CS, 0, 2 * Dr, 2 * Dr, Dl,
-        [F](int m, int n, cx<T> v) { F[m * ZS + n] = v; }, lane);
+        [](int n) { return n; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
 }
 
 // <E_a, Y> for a = X, Y, Z (from the blocks F_{ss'} in S) and Y in {C_X, C_Y, C_Z, R}:
@@ -182,8 +186,7 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
         T acc[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc[i] = T(0);
-        for (int o = lane; o < D * D; o += 32) {
-            const int r = o / D, rp = o % D;
+        team_for_2d<32>(D, D, lane, [&](int r, int rp) {
             const cx<T> f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
             const cx<T> f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
             cx<T> e[3];
@@ -201,7 +204,7 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
                     if (C || b == 3) acc[4 * a + b] += e[a].re * y[b].re - e[a].im * y[b].im;
-        }
+        });
 #pragma unroll
         for (int i = 0; i < 12; ++i) out[i] = warp_sum(acc[i]);
         if (NTHR > 32 && lane == 0)
@@ -231,31 +234,27 @@ __device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* R, c
     using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
     team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true>(
         A, [](int m) { return m * CS; }, 1, 0, S, [](int n) { return n; }, ZS, 0, 2 * Dl, 2 * Dl, Dr,
-        [G](int m, int n, cx<T> v) { G[m * ZS + n] = v; }, lane);
+        [](int n) { return n; }, [G](int m, int sn, cx<T> v) { G[m * ZS + sn] = v; }, lane);
     team_sync();
-    for (int o = lane; o < Dl * Dl; o += NTHR) {
-        const int l = o / Dl, lp = o % Dl;
+    team_for_2d<NTHR>(Dl, Dl, lane, [&](int l, int lp) {
         const cx<T> g00 = G[(2 * l) * ZS + 2 * lp], g01 = G[(2 * l) * ZS + 2 * lp + 1];
         const cx<T> g10 = G[(2 * l + 1) * ZS + 2 * lp], g11 = G[(2 * l + 1) * ZS + 2 * lp + 1];
         const cx<T> d = g10 - g01;
         C[l * CS + lp] = g01 + g10;
         C[MAT + l * CS + lp] = mk<T>(-d.im, d.re);
         C[2 * MAT + l * CS + lp] = g00 - g11;
-    }
+    });
     team_sync();
 }
 
 template <typename T, int CS, int NTHR = 32>
 __device__ __forceinline__ void load_site_p(cx<T>* dst, const cx<T>* src, int ld, int Dl, int Dr, int lane) {
-    for (int o = lane; o < 2 * Dl * Dr; o += NTHR) {
-        const int row = o / Dr, r = o % Dr;
-        dst[row * CS + r] = src[row * ld + r];
-    }
+    team_for_2d<NTHR>(2 * Dl, Dr, lane, [&](int row, int r) { dst[row * CS + r] = src[row * ld + r]; });
 }
 
 template <typename T, int CS, int NTHR = 32>
 __device__ __forceinline__ void load_mat(cx<T>* dst, const cx<T>* src, int ld, int D, int lane) {
-    for (int o = lane; o < D * D; o += NTHR) dst[(o / D) * CS + (o % D)] = src[(o / D) * ld + (o % D)];
+    team_for_2d<NTHR>(D, D, lane, [&](int r, int c) { dst[r * CS + c] = src[r * ld + c]; });
 }
 
 template <typename T, int CHI>
@@ -285,7 +284,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     for (int j = n - 1; j >= 0; --j) {
         const int Dl = bd[j], Dr = bd[j + 1];
         cx<T>* dst = rg + (size_t)j * CHI * CHI;
-        for (int o = lane; o < Dr * Dr; o += 32) dst[(o / Dr) * CHI + (o % Dr)] = R[(o / Dr) * CS + (o % Dr)];
+        team_for_2d<32>(Dr, Dr, lane, [&](int r, int c) { dst[r * CHI + c] = R[r * CS + c]; });
         load_site_p<T, CS>(A, sites + (size_t)j * 2 * ld * ld, ld, Dl, Dr, lane);
         __syncwarp();
         transfer<T, CHI, 1, 32>(R, A, S, Dl, Dr, lane);
@@ -294,7 +293,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
 }
 
 template <typename T, int CHI, int UW, bool DIAG>
-__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
+__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8) / (sizeof(T) == 8 ? 2 : 1)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
                                                     const int32_t* __restrict__ unit_image,
                                                     const cx<T>* __restrict__ arena,
                                                     const int32_t* __restrict__ bonds,
