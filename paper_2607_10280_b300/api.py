@@ -149,18 +149,22 @@ class Batch:
 
 
 def ano_features(pauli: torch.Tensor, m: int, abd: torch.Tensor, W: torch.Tensor = None,
-                 bias: torch.Tensor = None, stream=None):
+                 bias: torch.Tensor = None, stream=None, feats: torch.Tensor = None, out: torch.Tensor = None):
     """Features q (Eq. 5) and, if W is given, y = W q + b (Eq. 6).
 
     pauli: [n_images * m, 16] float32/float64; abd: float32 [m][16]; W: float32 [out][m].
+    feats / out: optional preallocated float32 [n_images][m] / [n_images][out] outputs.
     """
     n_images = pauli.shape[0] // m
-    feats = torch.empty((n_images, m), dtype=torch.float32, device=pauli.device)
-    out = None
+    if feats is None:
+        feats = torch.empty((n_images, m), dtype=torch.float32, device=pauli.device)
     out_dim = 0
     if W is not None:
         out_dim = W.shape[0]
-        out = torch.empty((n_images, out_dim), dtype=torch.float32, device=pauli.device)
+        if out is None:
+            out = torch.empty((n_images, out_dim), dtype=torch.float32, device=pauli.device)
+    else:
+        out = None
     check(lib().ano_features(_ptr(pauli), 1 if pauli.dtype == torch.float64 else 0, n_images, m,
                              _ptr(abd), _ptr(W) if W is not None else None,
                              _ptr(bias) if bias is not None else None, out_dim, _ptr(feats),
@@ -192,13 +196,18 @@ def extract(pixels, p, L: int, chi: int, precision: str = "mixed", ansatz: str =
 class Pipeline:
     """End-to-end path for a fixed batch layout: host pixels in, host results out.
 
-    Every run copies the pixels from (pinned) host memory to the device, runs the
+    Every step copies the pixels from (pinned) host memory to the device, runs the
     circuit, the Pauli cache, the ANO features and the linear layer, and copies the
     Pauli cache, the features and the reconstruction back to pinned host buffers.
-    All steps are enqueued on one stream; run() returns after the copies finish.
+    Copies run on a copy stream and the kernels on the compute stream, with `depth`
+    sets of device and host buffers, so that the copies of one step overlap the
+    kernels of the next: submit() enqueues a step and returns its slot, result(slot)
+    waits for that step's results.  A slot's host buffers stay valid until the slot
+    is submitted again (`depth` submits later).  run() is submit() then result().
     """
 
-    def __init__(self, p, chi, L, precision, params, abd, W=None, bias=None, ansatz="ladder", stream=None):
+    def __init__(self, p, chi, L, precision, params, abd, W=None, bias=None, ansatz="ladder", stream=None,
+                 depth: int = 2):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.batch = Batch(p, chi, precision, self.stream)
         self.L, self.ansatz = L, ansatz
@@ -209,26 +218,57 @@ class Pipeline:
         self.m = pair_count(int(p[0]))
         n_px = int(self.batch.pixel_offsets[-1])
         dev = torch.device("cuda", torch.cuda.current_device())
-        self.px_dev = torch.empty(n_px, dtype=torch.float64, device=dev)
+        self.copy_stream = torch.cuda.Stream(device=dev)
         dt = torch.float64 if precision == "fp64" else torch.float32
-        self.pauli_dev = torch.empty((int(self.batch.pair_offsets[-1]), 16), dtype=dt, device=dev)
         B = self.batch.n_images
-        self.pauli_host = torch.empty(self.pauli_dev.shape, dtype=dt).pin_memory()
-        self.feat_host = torch.empty((B, self.m), dtype=torch.float32).pin_memory()
-        self.out_host = None if W is None else torch.empty((B, W.shape[0]), dtype=torch.float32).pin_memory()
+        n_pairs = int(self.batch.pair_offsets[-1])
+        self.slots = []
+        for _ in range(max(1, depth)):
+            sl = {"px": torch.empty(n_px, dtype=torch.float64, device=dev),
+                  "pauli": torch.empty((n_pairs, 16), dtype=dt, device=dev),
+                  "feats": torch.empty((B, self.m), dtype=torch.float32, device=dev),
+                  "out": None if W is None else torch.empty((B, W.shape[0]), dtype=torch.float32, device=dev),
+                  "pauli_h": torch.empty((n_pairs, 16), dtype=dt).pin_memory(),
+                  "feats_h": torch.empty((B, self.m), dtype=torch.float32).pin_memory(),
+                  "out_h": None if W is None else torch.empty((B, W.shape[0]), dtype=torch.float32).pin_memory(),
+                  "ev_in": torch.cuda.Event(), "ev_comp": torch.cuda.Event(), "ev_out": torch.cuda.Event()}
+            self.slots.append(sl)
+        self._next = 0
         self.h2d_bytes = n_px * 8
-        self.d2h_bytes = (self.pauli_host.numel() * self.pauli_host.element_size() + self.feat_host.numel() * 4
-                          + (0 if self.out_host is None else self.out_host.numel() * 4))
+        sl = self.slots[0]
+        self.d2h_bytes = (sl["pauli_h"].numel() * sl["pauli_h"].element_size() + sl["feats_h"].numel() * 4
+                          + (0 if sl["out_h"] is None else sl["out_h"].numel() * 4))
+
+    def submit(self, host_pixels: torch.Tensor) -> int:
+        k = self._next
+        self._next = (k + 1) % len(self.slots)
+        sl = self.slots[k]
+        sl["ev_out"].synchronize()          # the previous results of this slot have been read back
+        cs = self.copy_stream
+        with torch.cuda.stream(cs):
+            cs.wait_event(sl["ev_comp"])     # the previous step of this slot no longer reads its pixels
+            sl["px"].copy_(host_pixels, non_blocking=True)
+            sl["ev_in"].record(cs)
+        with torch.cuda.stream(self.stream):
+            self.stream.wait_event(sl["ev_in"])
+            self.batch.apply_circuit(sl["px"], self.L, self.ansatz, self.params)
+            self.batch.pauli_cache(sl["pauli"])
+            ano_features(sl["pauli"], self.m, self.abd, self.W, self.bias, self.stream,
+                         feats=sl["feats"], out=sl["out"])
+            sl["ev_comp"].record(self.stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(sl["ev_comp"])
+            sl["pauli_h"].copy_(sl["pauli"], non_blocking=True)
+            sl["feats_h"].copy_(sl["feats"], non_blocking=True)
+            if sl["out"] is not None:
+                sl["out_h"].copy_(sl["out"], non_blocking=True)
+            sl["ev_out"].record(cs)
+        return k
+
+    def result(self, k: int):
+        sl = self.slots[k]
+        sl["ev_out"].synchronize()
+        return sl["pauli_h"], sl["feats_h"], sl["out_h"]
 
     def run(self, host_pixels: torch.Tensor):
-        with torch.cuda.stream(self.stream):
-            self.px_dev.copy_(host_pixels, non_blocking=True)
-            self.batch.apply_circuit(self.px_dev, self.L, self.ansatz, self.params)
-            self.batch.pauli_cache(self.pauli_dev)
-            feats, out = ano_features(self.pauli_dev, self.m, self.abd, self.W, self.bias, self.stream)
-            self.pauli_host.copy_(self.pauli_dev, non_blocking=True)
-            self.feat_host.copy_(feats, non_blocking=True)
-            if out is not None:
-                self.out_host.copy_(out, non_blocking=True)
-        self.stream.synchronize()
-        return self.pauli_host, self.feat_host, self.out_host
+        return self.result(self.submit(host_pixels))

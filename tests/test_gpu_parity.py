@@ -325,3 +325,30 @@ def test_layer_pipeline_falls_back_when_a_step_truncates():
     assert all(np.array_equal(u, v) for u, v in zip(ba, bb)) and np.array_equal(da, db)
     for i in range(3):
         assert np.array_equal(a[i], b[i])
+
+
+def test_pipeline_overlapped_steps_keep_their_results():
+    """Pipeline.submit/result with two buffer sets: steps whose copies overlap the next
+    step's kernels return exactly what each step gives when run alone."""
+    from paper_2607_10280_b300 import api
+    p, B, L, chi = 5, 16, 2, 4
+    m = api.pair_count(p)
+    params = torch.tensor(synth.circuit_params(L, p * p, seed=101), dtype=torch.float64, device="cuda")
+    abd = torch.tensor(synth.observable_params(m, seed=102), dtype=torch.float32, device="cuda")
+    W, b = synth.linear_params(40, m, seed=103)
+    W = torch.tensor(W, dtype=torch.float32, device="cuda")
+    b = torch.tensor(b, dtype=torch.float32, device="cuda")
+    pipe = api.Pipeline(np.full(B, p, np.int32), chi, L, "mixed", params, abd, W, b)
+    host = [torch.tensor(synth.garment_pixels(B, p, seed=110 + s).reshape(-1), dtype=torch.float64).pin_memory()
+            for s in range(3)]
+    alone = [[t.clone() for t in pipe.run(h)] for h in host]
+    k0 = pipe.submit(host[0])
+    k1 = pipe.submit(host[1])
+    r0 = [t.clone() for t in pipe.result(k0)]
+    k2 = pipe.submit(host[2])
+    r1 = [t.clone() for t in pipe.result(k1)]
+    r2 = [t.clone() for t in pipe.result(k2)]
+    for got, ref in zip((r0, r1, r2), alone):
+        for g, r in zip(got, ref):
+            assert torch.equal(g, r)
+    assert not torch.equal(r0[0], r1[0])
