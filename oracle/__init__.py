@@ -20,8 +20,11 @@ Modules, each a plain restatement of the paper:
 * ``ano``         Hermitian observables from (A, B, D), Pauli coefficients
                   c = 2^-2 Tr(H P) (Eq. 4), features (Eq. 5) and the linear
                   reconstruction layer (Eq. 6).
+* ``train``       training on cached Paulis (Sec. II.C-D): MSE term of Eq. 7,
+                  its gradients by the chain rule, and the two Adam optimizers.
 
-Pins: every function here is checked by ``tests/test_oracle_*.py`` against
+Pins: every function here is checked by ``tests/test_oracle_*.py`` and
+``tests/test_train_oracle.py`` against
 values fixed by the paper or by mathematics (closed forms, brute-force
 Kronecker products, Clifford conjugation, Schmidt truncation of the dense
 state, Pauli-basis completeness).  No function is "parity unpinned".
