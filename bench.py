@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-sample", type=int, default=8, help="images timed through the per-image FP64 path")
     ap.add_argument("--batch", type=int, default=BATCH, help="images per GPU (profiling of smaller cases)")
-    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "uneven", "large", "serve"],
+    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "uneven", "large", "serve", "train"],
                     help="headline (default): 7x7 L=4 chi=16; the others are the chi x L sweep, the uneven "
                          "batch, the 16x16 batch and the serving run")
     ap.add_argument("--requests", type=int, default=4000, help="serving run: number of requests")
@@ -550,6 +550,51 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_train(args):
+    """Training on cached Paulis (Sec. II.C-D): the Pauli cache of 1024 7x7 images
+    (L = 4, chi = 16) is computed once; then full-batch steps of the MSE term of Eq. 7
+    with two Adam optimizers train (A, B, D) and the linear layer 84 -> 784 towards
+    synthetic 28 x 28 targets.  Reports training steps/s, the step time against one
+    recomputation of the cache, and the loss curve."""
+    torch = _setup_torch()
+    from paper_2607_10280_b300 import api, synth
+    p, B, L, chi, O = 7, 1024, 4, 16, 784
+    m = api.pair_count(p)
+    X = synth.garment_pixels(B, p)
+    Y = torch.tensor(synth.garment_pixels(B, 28, seed=5), dtype=torch.float32, device="cuda")
+    params = torch.tensor(synth.circuit_params(L, p * p), dtype=torch.float64, device="cuda")
+    px = torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda")
+    b = api.Batch(np.full(B, p, np.int32), chi, "mixed")
+    pauli = torch.empty((B * m, 16), dtype=torch.float32, device="cuda")
+
+    def cache():
+        b.apply_circuit(px, L, "ladder", params)
+        b.pauli_cache(pauli)
+    cache()
+    torch.cuda.synchronize()
+    cache_ms = _time_events(torch, cache, 5)
+    abd = torch.tensor(synth.observable_params(m), dtype=torch.float32, device="cuda")
+    Wn, bn = synth.linear_params(O, m)
+    W = torch.tensor(Wn, dtype=torch.float32, device="cuda")
+    bias = torch.tensor(bn, dtype=torch.float32, device="cuda")
+    tr = api.Trainer(pauli, m, abd, W, bias, lr_abd=1e-2, lr_linear=1e-3)
+    first = tr.step(Y).item()
+    steps = max(10, args.steps)
+    losses = []
+    step_ms = _time_events(torch, lambda: losses.append(tr.step(Y)), steps)
+    losses = [first] + [x.item() for x in losses]
+    line = {"metric": "training steps/s on cached Paulis, 1024 7x7 images, ANO 84x16 + linear 84->784, "
+                      "MSE + two Adam optimizers",
+            "value": 1e3 / step_ms, "unit": "steps/s", "n_gpus": 1, "higher_is_better": True,
+            "images_per_s": B * 1e3 / step_ms, "ms_per_step": step_ms,
+            "pauli_cache_ms": cache_ms, "cache_over_step": cache_ms / step_ms,
+            "loss_first": losses[0], "loss_last": losses[-1], "steps_timed": steps,
+            "config": {"workload": "7x7 garment-like images, ladder L=4 chi=16 Pauli cache (once); "
+                                   "targets 28x28 garment-like (synthetic)", "images": B, "pairs": m,
+                       "out_dim": O}}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -557,4 +602,5 @@ if __name__ == "__main__":
     elif a.config == "headline":
         run_ours(a)
     else:
-        {"sweep": run_sweep, "uneven": run_uneven, "large": run_large, "serve": run_serve}[a.config](a)
+        {"sweep": run_sweep, "uneven": run_uneven, "large": run_large, "serve": run_serve,
+         "train": run_train}[a.config](a)

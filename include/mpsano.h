@@ -143,6 +143,50 @@ mps_status ano_features(const void* pauli, int32_t pauli_f64, int64_t n_images, 
  * makes ano_features use a plain FP32 CUDA-core GEMM instead. */
 mps_status ano_status(void);
 
+/* ---- Training on cached Pauli expectations (Sec. II.C-D) ----
+ * The Pauli cache depends on the image only, so it is computed once; a training
+ * step then updates the observable parameters (A, B, D) and the linear layer
+ * (W, b) from the cache alone.  The loss is the MSE term of Eq. 7,
+ *   L = mse_weight * mean_{i,o} (y_hat[i][o] - y[i][o])^2,  y_hat = W q + b,
+ * (the LPIPS term of Eq. 7 needs a pretrained network and is not part of this
+ * library), and two Adam optimizers (Kingma and Ba, with bias correction) update
+ * (A, B, D) and (W, b) with their own learning rates. */
+typedef struct {
+    float lr_abd;      /* learning rate of the (A, B, D) optimizer */
+    float lr_linear;   /* learning rate of the (W, b) optimizer */
+    float beta1;       /* first-moment decay, 0 <= beta1 < 1 (0.9) */
+    float beta2;       /* second-moment decay, 0 <= beta2 < 1 (0.999) */
+    float eps;         /* > 0, added to sqrt(v_hat) (1e-8) */
+    float mse_weight;  /* lambda_MSE of Eq. 7 */
+} ano_adam;
+
+/* Floats of device workspace that ano_train_step needs (-1 on bad sizes).  Layout,
+ * in floats: features [n_images][m] at 0, then d L / d y_hat [n_images][out_dim],
+ * d L / d q [n_images][m], the gradient [m*16 + out_dim*m + out_dim] of
+ * (abd, W, b) in that order, then FP64 scratch. */
+int64_t ano_train_workspace_floats(int64_t n_images, int32_t m, int32_t out_dim);
+
+/* One full-batch training step, asynchronous on `stream`:
+ *   pauli, pauli_f64   device Pauli cache [n_images*m][16] (FP32, or FP64 if pauli_f64)
+ *   abd                device [m][16] observable parameters, updated in place
+ *   W, bias            device [out_dim][m] and [out_dim], updated in place
+ *   targets            device [n_images][out_dim] ground truth y
+ *   adam_moments       device [2][m*16 + out_dim*m + out_dim] first then second
+ *                      moments of (abd, W, b); caller-owned, zero before step 1
+ *   step               Adam step number t >= 1 (bias correction 1 - beta^t)
+ *   hp                 host hyper-parameters
+ *   workspace          device, ano_train_workspace_floats() floats, 8-byte aligned
+ *   loss               device double: the loss at the parameters before the update
+ * The gradients are left in the workspace.  The three GEMMs (y_hat, d L / d q,
+ * d L / d W) run on the tcgen05 tensor cores (3-term TF32 split); batch reductions
+ * accumulate in FP64 in a fixed order, so a step is bit-reproducible.  Errors:
+ * MPS_ERR_INVALID_ARG for NULL pointers, non-positive sizes, step < 1, beta
+ * outside [0, 1), eps <= 0 or a misaligned workspace; a failed tensor-core wait is
+ * reported by ano_status. */
+mps_status ano_train_step(const void* pauli, int32_t pauli_f64, int64_t n_images, int32_t m, float* abd,
+                          float* W, float* bias, int32_t out_dim, const float* targets, float* adam_moments,
+                          int32_t step, const ano_adam* hp, float* workspace, double* loss, void* stream);
+
 /* ---- diagnostics and control ------------------------------------------------ */
 
 /* Wait for the batch's stream and return the first device-side error, if any. */

@@ -36,6 +36,11 @@ class mps_circuit(ctypes.Structure):
     ]
 
 
+class ano_adam(ctypes.Structure):
+    _fields_ = [("lr_abd", ctypes.c_float), ("lr_linear", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("mse_weight", ctypes.c_float)]
+
+
 _c = ctypes
 SIGNATURES = {
     "mps_create_batch": (_c.c_int, [_c.c_int32, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32), _c.c_int32,
@@ -49,6 +54,10 @@ SIGNATURES = {
                                 _c.c_void_p, _c.c_int32, _c.c_void_p, _c.c_void_p, _c.c_void_p]),
     "mps_sync": (_c.c_int, [_c.c_void_p]),
     "ano_status": (_c.c_int, []),
+    "ano_train_workspace_floats": (_c.c_int64, [_c.c_int64, _c.c_int32, _c.c_int32]),
+    "ano_train_step": (_c.c_int, [_c.c_void_p, _c.c_int32, _c.c_int64, _c.c_int32, _c.c_void_p, _c.c_void_p,
+                                  _c.c_void_p, _c.c_int32, _c.c_void_p, _c.c_void_p, _c.c_int32,
+                                  _c.POINTER(ano_adam), _c.c_void_p, _c.c_void_p, _c.c_void_p]),
     "mps_last_error": (_c.c_char_p, []),
     "mps_pair_count": (_c.c_int64, [_c.c_int32, _c.c_int32]),
     "mps_bond_dims": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_int32)]),

@@ -272,3 +272,78 @@ class Pipeline:
 
     def run(self, host_pixels: torch.Tensor):
         return self.result(self.submit(host_pixels))
+
+
+def save_pauli_cache(path: str, cache: torch.Tensor, meta: dict = None) -> None:
+    """Write a Pauli cache (any device, [M][16]) and its description to an .npz file.
+    The cache depends on the images only, so training can reload it instead of
+    simulating the circuits again (Sec. II.C)."""
+    meta = dict(meta or {})
+    np.savez(path, cache=cache.detach().cpu().numpy(), meta=np.array(repr(sorted(meta.items()))))
+
+
+def load_pauli_cache(path: str, device=None) -> torch.Tensor:
+    with np.load(path if str(path).endswith(".npz") else str(path) + ".npz") as z:
+        t = torch.from_numpy(z["cache"].copy())
+    return t.to(device) if device is not None else t
+
+
+class Trainer:
+    """Full-batch training of (A, B, D) and (W, b) on a cached Pauli cache
+    (Sec. II.C-D, MSE term of Eq. 7, two Adam optimizers), through ano_train_step.
+
+    pauli: device [n_images * m][16] (float32 or float64); abd [m][16], W [out][m] and
+    bias [out] are device float32 tensors trained in place.  step(targets) enqueues
+    one step on the stream and returns the device loss (float64 scalar tensor) at
+    the parameters before the update.
+    """
+
+    def __init__(self, pauli: torch.Tensor, m: int, abd: torch.Tensor, W: torch.Tensor, bias: torch.Tensor,
+                 lr_abd: float = 1e-2, lr_linear: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8, mse_weight: float = 1.0, stream=None):
+        for name, t in (("abd", abd), ("W", W), ("bias", bias)):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+        self.pauli, self.m = pauli, m
+        self.n_images = pauli.shape[0] // m
+        self.abd, self.W, self.bias = abd, W, bias
+        self.out_dim = W.shape[0]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.hp = _lib.ano_adam(lr_abd, lr_linear, beta1, beta2, eps, mse_weight)
+        n_par = m * 16 + self.out_dim * m + self.out_dim
+        self.moments = torch.zeros(2 * n_par, dtype=torch.float32, device=pauli.device)
+        n_ws = lib().ano_train_workspace_floats(self.n_images, m, self.out_dim)
+        if n_ws < 0:
+            raise ValueError("bad training sizes")
+        self.workspace = torch.zeros(int(n_ws), dtype=torch.float32, device=pauli.device)
+        self.loss = torch.zeros((), dtype=torch.float64, device=pauli.device)
+        self.t = 0
+
+    def step(self, targets: torch.Tensor) -> torch.Tensor:
+        assert targets.is_cuda and targets.dtype == torch.float32 and targets.is_contiguous()
+        assert targets.shape == (self.n_images, self.out_dim)
+        self.t += 1
+        check(lib().ano_train_step(_ptr(self.pauli), 1 if self.pauli.dtype == torch.float64 else 0,
+                                   self.n_images, self.m, _ptr(self.abd), _ptr(self.W), _ptr(self.bias),
+                                   self.out_dim, _ptr(targets), _ptr(self.moments), self.t,
+                                   ctypes.byref(self.hp), _ptr(self.workspace), _ptr(self.loss),
+                                   _stream_handle(self.stream)))
+        return self.loss
+
+    def gradients(self):
+        """Views of the last step's gradients (g_abd [m][16], g_W [out][m], g_b [out])."""
+        B, m, O = self.n_images, self.m, self.out_dim
+        g0 = 2 * B * m + B * O
+        g = self.workspace[g0:g0 + m * 16 + O * m + O]
+        return g[:m * 16].view(m, 16), g[m * 16:m * 16 + O * m].view(O, m), g[m * 16 + O * m:]
+
+    def state_dict(self) -> dict:
+        return {"abd": self.abd.clone(), "W": self.W.clone(), "bias": self.bias.clone(),
+                "moments": self.moments.clone(), "t": self.t}
+
+    def load_state_dict(self, sd: dict) -> None:
+        self.abd.copy_(sd["abd"])
+        self.W.copy_(sd["W"])
+        self.bias.copy_(sd["bias"])
+        self.moments.copy_(sd["moments"])
+        self.t = int(sd["t"])

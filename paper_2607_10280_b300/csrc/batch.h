@@ -70,6 +70,11 @@ void timing_begin(mps_batch* b, int kind);
 void timing_end(mps_batch* b);
 // Opt-in shared-memory limit per block on the current device.
 int smem_optin_limit();
+// Y(r, o) = sum_k X(r, k) W(o, k) + bias[o] on the tensor cores (strided operands,
+// see linear_tc_kernel); failures of its bounded waits surface through ano_status.
+mps_status launch_linear_tc(const float* X, int64_t xs_r, int64_t xs_k, int rows, int K, const float* W,
+                            int64_t ws_o, int64_t ws_k, const float* bias, int out_dim, float* Y,
+                            cudaStream_t s);
 
 mps_status launch_circuit_fp64_t0(mps_batch* b, int chi_tpl, const double* px, int ansatz);
 mps_status launch_circuit_fp64_t1(mps_batch* b, int chi_tpl, const double* px, int ansatz);

@@ -53,7 +53,7 @@ __global__ void ano_kernel(const TP* __restrict__ pauli, int64_t n_images, int m
 
 // Plain FP32 y = W q + b on CUDA cores, used when tensor-core tiles do not apply.
 // 16 x 16 output tile per block, K staged through shared memory.
-__global__ void linear_fp32_kernel(const float* __restrict__ X, int64_t rows, int K,
+static __global__ void linear_fp32_kernel(const float* __restrict__ X, int64_t rows, int K,
                                    const float* __restrict__ W, const float* __restrict__ bias,
                                    int out_dim, float* __restrict__ Y) {
     __shared__ float xs[16][17], ws[16][17];

@@ -1,6 +1,8 @@
 // Linear reconstruction layer y = W q + b (Eq. 6) on the tcgen05 tensor cores.
 //
-// Y[r][o] = sum_k X[r][k] W[o][k] + bias[o], FP32 in and out.  TF32 alone has an
+// Y[r][o] = sum_k X(r, k) W(o, k) + bias[o], FP32 in and out, with X(r, k) at
+// X[r * xs_r + k * xs_k] and W(o, k) at W[o * ws_o + k * ws_k] (so transposed
+// operands of the backward pass need no copy).  TF32 alone has an
 // 11-bit significand, so each operand is split as x = x_hi + x_lo with
 // x_hi = tf32(x), x_lo = tf32(x - x_hi), and three products x_hi w_hi + x_hi w_lo +
 // x_lo w_hi accumulate in FP32 (relative error near 2^-22 per term).
@@ -69,8 +71,9 @@ __device__ __forceinline__ bool tc_mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-__global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict__ X, int rows, int K,
-                                                        const float* __restrict__ W,
+__global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict__ X, int64_t xs_r, int64_t xs_k,
+                                                        int rows, int K, const float* __restrict__ W,
+                                                        int64_t ws_o, int64_t ws_k,
                                                         const float* __restrict__ bias, int out_dim,
                                                         float* __restrict__ Y, int* status) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -101,16 +104,26 @@ __global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict_
     int failed_parity = 0;
     const int chunks = (K + TC_KC - 1) / TC_KC;
     for (int ch = 0; ch < chunks && ok; ++ch) {
-        // stage the hi/lo panels of this K chunk (zero outside the matrices)
+        // stage the hi/lo panels of this K chunk (zero outside the matrices); consecutive
+        // threads walk the operand's unit-stride index so the loads coalesce
+        const bool x_kfast = xs_k == 1, w_kfast = ws_k == 1;
         for (int e = tid; e < TC_M * TC_KC; e += 128) {
-            const int row = e / TC_KC, k = e % TC_KC, kk = ch * TC_KC + k;
+            const int row = x_kfast ? e / TC_KC : e % TC_M, k = x_kfast ? e % TC_KC : e / TC_M;
+            const int kk = ch * TC_KC + k;
             const int off = tc_panel_offset(row, k);
-            float xa = 0.f, wb = 0.f;
-            if (r0 + row < rows && kk < K) xa = X[(size_t)(r0 + row) * K + kk];
-            if (o0 + row < out_dim && kk < K) wb = W[(size_t)(o0 + row) * K + kk];
-            const uint32_t xh = tf32_round(xa), wh = tf32_round(wb);
+            float xa = 0.f;
+            if (r0 + row < rows && kk < K) xa = X[(int64_t)(r0 + row) * xs_r + (int64_t)kk * xs_k];
+            const uint32_t xh = tf32_round(xa);
             *reinterpret_cast<uint32_t*>(a_hi + off) = xh;
             *reinterpret_cast<uint32_t*>(a_lo + off) = tf32_round(xa - __uint_as_float(xh));
+        }
+        for (int e = tid; e < TC_N * TC_KC; e += 128) {
+            const int row = w_kfast ? e / TC_KC : e % TC_N, k = w_kfast ? e % TC_KC : e / TC_N;
+            const int kk = ch * TC_KC + k;
+            const int off = tc_panel_offset(row, k);
+            float wb = 0.f;
+            if (o0 + row < out_dim && kk < K) wb = W[(int64_t)(o0 + row) * ws_o + (int64_t)kk * ws_k];
+            const uint32_t wh = tf32_round(wb);
             *reinterpret_cast<uint32_t*>(b_hi + off) = wh;
             *reinterpret_cast<uint32_t*>(b_lo + off) = tf32_round(wb - __uint_as_float(wh));
         }

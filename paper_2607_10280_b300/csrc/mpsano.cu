@@ -34,6 +34,26 @@ namespace mpsano {
 
 void count_launch() { g_launches.fetch_add(1); }
 
+mps_status launch_linear_tc(const float* X, int64_t xs_r, int64_t xs_k, int rows, int K, const float* W,
+                            int64_t ws_o, int64_t ws_k, const float* bias, int out_dim, float* Y,
+                            cudaStream_t s) {
+    static int attr_dev = -1;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (attr_dev != dev) {
+        CUDA_TRY(cudaFuncSetAttribute(linear_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TC_SMEM_BYTES));
+        attr_dev = dev;
+    }
+    int* st = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress((void**)&st, g_epilogue_status));
+    dim3 grid((out_dim + TC_N - 1) / TC_N, (unsigned)((rows + TC_M - 1) / TC_M));
+    linear_tc_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(X, xs_r, xs_k, rows, K, W, ws_o, ws_k, bias, out_dim, Y, st);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return MPS_OK;
+}
+
 namespace {
 cudaEvent_t pooled_event(mps_batch* b) {
     if (!b->event_pool.empty()) {
@@ -472,16 +492,7 @@ mps_status ano_features(const void* pauli, int32_t pauli_f64, int64_t n_images, 
             dim3 grid((out_dim + 15) / 16, (unsigned)((n_images + 15) / 16));
             linear_fp32_kernel<<<grid, 256, 0, s>>>(features, n_images, m, W, bias, out_dim, out);
         } else {
-            static bool attr_set = false;
-            if (!attr_set) {
-                CUDA_TRY(cudaFuncSetAttribute(linear_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)TC_SMEM_BYTES));
-                attr_set = true;
-            }
-            int* st = nullptr;
-            CUDA_TRY(cudaGetSymbolAddress((void**)&st, g_epilogue_status));
-            dim3 grid((out_dim + TC_N - 1) / TC_N, (unsigned)((n_images + TC_M - 1) / TC_M));
-            linear_tc_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(features, (int)n_images, m, W, bias, out_dim, out, st);
+            return launch_linear_tc(features, m, 1, (int)n_images, m, W, m, 1, bias, out_dim, out, s);
         }
         CUDA_TRY(cudaGetLastError());
         count_launch();

@@ -67,3 +67,22 @@ def test_pair_counts(lib):
         assert lib.mps_pair_count(p, 1) == 2 * p * (p - 1) + 2 * (p - 1) ** 2
     assert lib.mps_pair_count(7, 1) == 156       # Sec. II.C
     assert isinstance(lib.mps_launch_count(), int)
+
+
+def test_training_entry_validation(lib):
+    """ano_train_step rejects bad arguments on the host, before any device work."""
+    assert lib.ano_train_workspace_floats(0, 84, 784) == -1
+    n = lib.ano_train_workspace_floats(1024, 84, 784)
+    assert n >= 2 * 1024 * 84 + 1024 * 784 + 84 * 16 + 784 * 84 + 784
+    hp = _lib.ano_adam(1e-2, 1e-3, 0.9, 0.999, 1e-8, 1.0)
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
+    args = [fake, 0, 8, 4, fake, fake, fake, 10, fake, fake, 1, ctypes.byref(hp), fake, fake, None]
+    a = list(args); a[0] = None
+    assert lib.ano_train_step(*a) == 1
+    a = list(args); a[10] = 0                       # Adam steps count from 1
+    assert lib.ano_train_step(*a) == 1 and b"step" in lib.mps_last_error()
+    bad = _lib.ano_adam(1e-2, 1e-3, 1.0, 0.999, 1e-8, 1.0)
+    a = list(args); a[11] = ctypes.byref(bad)
+    assert lib.ano_train_step(*a) == 1
+    a = list(args); a[12] = ctypes.c_void_p(0x1004)  # workspace not 8-byte aligned
+    assert lib.ano_train_step(*a) == 1 and b"aligned" in lib.mps_last_error()
