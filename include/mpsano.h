@@ -68,6 +68,10 @@ typedef enum { MPS_ANSATZ_LADDER = 0, MPS_ANSATZ_PAPER = 1 } mps_ansatz;
  * both diagonals (2p(p-1) + 2(p-1)^2 pairs: 156 at p = 7). */
 typedef enum { MPS_PAIRS_HV = 0, MPS_PAIRS_HVD = 1 } mps_pair_set;
 
+/* Largest accepted bond cap, and largest bond dimension the kernels hold. */
+#define MPS_CHI_LIMIT 4096
+#define MPS_BOND_LIMIT 32
+
 typedef struct mps_batch mps_batch;
 
 typedef struct {
@@ -83,7 +87,10 @@ typedef struct {
 /* Create a batch of n_images independent MPS (Sec. II.B, Eq. 3).
  *   p        host [n_images], image sides, 2 <= p_i <= 16 (n_i = p_i^2 qubits)
  *   chi      host [n_images] bond caps, or NULL to use chi_all for every image
- *   chi_all  bond cap when chi == NULL, 1 <= chi <= 64
+ *   chi_all  bond cap when chi == NULL, 1 <= chi <= MPS_CHI_LIMIT.  Any chi is a cap:
+ *            bonds only grow to min(chi, 2 D_left, 2 D_right) (e.g. at most 2^L for
+ *            the ladder), and the kernels hold bonds up to MPS_BOND_LIMIT; a circuit
+ *            that would need more returns MPS_ERR_UNSUPPORTED from mps_apply_circuit
  *   prec     mps_precision
  *   stream   cudaStream_t (NULL = legacy default stream) used by every later call
  *   out      receives the handle

@@ -226,7 +226,7 @@ mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const
     for (int i = 0; i < n_images; ++i) {
         const int ci = chi ? chi[i] : chi_all;
         if (p[i] < 2 || p[i] > 16) return fail(MPS_ERR_INVALID_ARG, "p[%d] = %d outside 2..16", i, p[i]);
-        if (ci < 1 || ci > 64) return fail(MPS_ERR_INVALID_ARG, "chi[%d] = %d outside 1..64", i, ci);
+        if (ci < 1 || ci > MPS_CHI_LIMIT) return fail(MPS_ERR_INVALID_ARG, "chi[%d] = %d outside 1..%d", i, ci, MPS_CHI_LIMIT);
     }
     b->B = n_images;
     b->meta_h.assign(n_images, ImageMeta{});
@@ -238,10 +238,11 @@ mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const
         const int pi = p[i];
         const int ci = chi ? chi[i] : chi_all;
         const int n = pi * pi;
-        // largest bond any circuit can reach: min(chi, 2^floor(n/2))
+        // largest bond any circuit can reach: min(chi, 2^floor(n/2)), and at most the
+        // largest compiled bond bucket (a circuit that needs more is refused later)
         int cap = 1;
         while (cap < ci && cap < (1 << std::min(n / 2, 20))) cap <<= 1;
-        cap = std::min(cap, ci);
+        cap = std::min(std::min(cap, ci), MPS_BOND_LIMIT);
         int ld = 4;
         while (ld < cap) ld <<= 1;
         ImageMeta& m = b->meta_h[i];

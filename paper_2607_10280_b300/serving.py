@@ -34,7 +34,7 @@ def image_footprint(p: int, chi: int, precision: str = "mixed") -> int:
     cap = 1
     while cap < chi and cap < (1 << min(n // 2, 20)):
         cap <<= 1
-    cap = min(cap, chi)
+    cap = min(cap, chi, 32)          # the library pads sites to at most its largest bond bucket
     ld = 4
     while ld < cap:
         ld <<= 1

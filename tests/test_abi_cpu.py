@@ -55,6 +55,7 @@ def test_host_side_validation(lib):
     bad = (ctypes.c_int32 * 1)(17)
     assert lib.mps_create_batch(1, bad, None, 4, 1, None, ctypes.byref(out)) == 1
     assert lib.mps_create_batch(1, p, None, 0, 1, None, ctypes.byref(out)) == 1
+    assert lib.mps_create_batch(1, p, None, 4097, 1, None, ctypes.byref(out)) == 1   # above MPS_CHI_LIMIT
     assert lib.mps_create_batch(1, p, None, 4, 1, None, None) == 1
     assert lib.mps_destroy_batch(None) == 0
     assert lib.mps_sync(None) == 1

@@ -294,9 +294,10 @@ def test_diagonal_pairs_vs_oracle(precision, ansatz, p, L, chi):
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_orth64"])
 def test_layer_pipeline_equals_sequential_sweep(precision):
     """The layer-pipelined circuit kernel (ladder, no truncation, L <= 4) runs every
-    two-qubit step on the same inputs as the sequential sweep: same bond dimensions
-    and Pauli caches equal to the last bit (the comparison allows 1e-12 / 2e-7 in
-    case the compiler contracts a multiply-add differently in the two kernels)."""
+    two-qubit step on the same inputs and with the same operations as the sequential
+    sweep: same bond dimensions and Pauli caches equal to the last bit (the
+    comparison allows 1e-12 / 2e-7 in case the compiler fuses a multiply and an add
+    into one FMA in one kernel and not in the other)."""
     cases = [([7] * 6, 4, 16), ([5] * 5, 3, 8), ([4, 9, 6, 16, 5], 2, 16), ([6] * 4, 1, 2),
              ([3, 2, 8, 7], [4, 0, 3, 2], 32)]
     bound = 1e-12 if precision == "fp64" else 2e-7
@@ -352,3 +353,19 @@ def test_pipeline_overlapped_steps_keep_their_results():
         for g, r in zip(got, ref):
             assert torch.equal(g, r)
     assert not torch.equal(r0[0], r1[0])
+
+
+def test_bond_caps_above_the_exact_bond_change_nothing():
+    """Sec. III sweeps chi up to 2048 at 7x7: bonds never exceed 2^L there, so every cap
+    chi >= 2^L gives the same state (same bonds, same Pauli cache to the last bit)."""
+    p, L = 7, 3
+    X = list(synth.garment_pixels(4, p, seed=120))
+    params = synth.circuit_params(L, p * p, seed=121)
+    base, b0, _ = run_gpu(X, [p] * 4, L, 8, "mixed", params=params)
+    for chi in (9, 64, 2048):
+        got, bb, _ = run_gpu(X, [p] * 4, L, chi, "mixed", params=params)
+        assert all(np.array_equal(u, v) for u, v in zip(b0, bb))
+        for i in range(4):
+            assert np.array_equal(got[i], base[i]), chi
+    ref, _ = oracle_cache(X[0], p, L, 2048, params=params)
+    assert np.max(np.abs(base[0] - ref)) < TOL["mixed"]
