@@ -30,7 +30,10 @@ __device__ __forceinline__ T team_sum(T v, double* red, int tid) {
 // Calls f(row, col) for every row < R and col < C, spreading the pairs over the
 // NTHR threads without integer division: columns are padded to a power of two cp,
 // thread -> (col = tid % cp, first row = tid / cp).
-template <int NTHR, class F>
+// UNROLL: unroll factor of the row loop.  The circuit kernels keep 1 (their many
+// short loops otherwise overflow the instruction cache); load loops that wait on
+// global memory use 4.
+template <int NTHR, int UNROLL = 1, class F>
 __device__ __forceinline__ void team_for_2d(int R, int C, int tid, F f) {
     if (C <= 0 || R <= 0) return;
     const int cp = C <= 1 ? 1 : 1 << (32 - __clz(C - 1));
@@ -42,7 +45,7 @@ __device__ __forceinline__ void team_for_2d(int R, int C, int tid, F f) {
         const int col = tid & (cp - 1);
         const int rstep = NTHR >> shift;
         if (col < C) {
-#pragma unroll 4
+#pragma unroll UNROLL
             for (int row = tid >> shift; row < R; row += rstep) f(row, col);
         }
     }
@@ -94,7 +97,7 @@ __device__ __forceinline__ void apply_reflector(cx<T>* A, int ld, int M, int N, 
         if (active) {
             w = t * w;
             if (g == 0) a[j] = a[j] - w;
-#pragma unroll 4
+#pragma unroll 1
             for (int r = j + 1 + g; r < M; r += G) a[r] = a[r] - v[r] * w;
         }
     }

@@ -68,7 +68,10 @@ struct Tile {
 //                                          * Bb[bo(n) + seg*bs_seg + k*bs]
 // for m < M, n < N, delivered through store(m, so(n), value); the column offsets
 // ao, bo and so are evaluated once per tile row / column.
-template <typename T, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, class AO, class BO, class SO, class ST>
+// KU: unroll factor of the k loop (1 keeps the Pauli kernel's code small enough for
+// the instruction cache; the environment kernel, one warp per image, prefers 2).
+template <typename T, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, int KU, class AO, class BO, class SO,
+          class ST>
 __device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as_seg,
                                           const cx<T>* Bb, BO bo, int bs, int bs_seg,
                                           int M, int N, int K, SO so, ST store, int lane) {
@@ -96,7 +99,7 @@ __device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as
             for (int seg = 0; seg < NSEG; ++seg) {
                 const cx<T>* As = Ab + seg * as_seg;
                 const cx<T>* Bs = Bb + seg * bs_seg;
-#pragma unroll 2
+#pragma unroll KU
                 for (int k = 0; k < K; ++k) {
                     cx<T> a[TM], b[TN];
 #pragma unroll
@@ -129,12 +132,12 @@ __device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as
 // times the transposed site rows n = 2l + s < 2 Dl.
 __device__ __forceinline__ void team_sync() { __syncthreads(); }
 
-template <typename T, int CHI, int NB, int NTHR>
+template <typename T, int CHI, int NB, int NTHR, int KU = 1>
 __device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
     using Tl = Tile<T, NB * CHI, 2 * CHI, NTHR>;
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false>(
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
         C, [Dr](int m) { return (m / Dr) * MAT + (m % Dr) * CS; }, 1, 0,
         A, [](int n) { return n * CS; }, 1, 0, NB * Dr, 2 * Dl, Dr,
         [](int n) { return n; }, [S](int m, int sn, cx<T> v) { S[m * ZS + sn] = v; }, lane);
@@ -143,14 +146,14 @@ __device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<
 // Transfer of NB matrices through a site A (Dl x 2 x Dr), in place:
 //   C_b <- sum_s conj(A^s) C_b A^{sT}     (C_b: Dr x Dr in, Dl x Dl out)
 // with S[b*Dr + r][2l'+s] = (C_b A^{sT})[r][l'] as the intermediate.
-template <typename T, int CHI, int NB, int NTHR>
+template <typename T, int CHI, int NB, int NTHR, int KU = 1>
 __device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    times_site_t<T, CHI, NB, NTHR>(C, A, S, Dl, Dr, lane);
+    times_site_t<T, CHI, NB, NTHR, KU>(C, A, S, Dl, Dr, lane);
     team_sync();
     using Tl = Tile<T, CHI, NB * CHI, NTHR>;
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true>(
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
         A, [](int l) { return 2 * l * CS; }, 1, CS,
         S, [Dl, Dr](int n) { return (n / Dl) * Dr * ZS + 2 * (n % Dl); }, ZS, 1, Dl, NB * Dl, Dr,
         [Dl](int n) { return (n / Dl) * MAT + (n % Dl); },
@@ -167,7 +170,7 @@ __device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, in
     using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
     cx<T>* F = S + CHI * ZS;
     auto off = [Dr](int m) { return (m / Dr) * CS + (m % Dr); };
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true>(
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
         A, off, 2 * CS, 0, A, off, 2 * CS, 0, 2 * Dr, 2 * Dr, Dl,
         [](int n) { return n; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
 }
@@ -186,7 +189,7 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
         T acc[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc[i] = T(0);
-        team_for_2d<32>(D, D, lane, [&](int r, int rp) {
+        team_for_2d<32, 4>(D, D, lane, [&](int r, int rp) {
             const cx<T> f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
             const cx<T> f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
             cx<T> e[3];
@@ -232,11 +235,11 @@ __device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* R, c
     team_sync();
     cx<T>* G = S + CHI * ZS;
     using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true>(
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
         A, [](int m) { return m * CS; }, 1, 0, S, [](int n) { return n; }, ZS, 0, 2 * Dl, 2 * Dl, Dr,
         [](int n) { return n; }, [G](int m, int sn, cx<T> v) { G[m * ZS + sn] = v; }, lane);
     team_sync();
-    team_for_2d<NTHR>(Dl, Dl, lane, [&](int l, int lp) {
+    team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int l, int lp) {
         const cx<T> g00 = G[(2 * l) * ZS + 2 * lp], g01 = G[(2 * l) * ZS + 2 * lp + 1];
         const cx<T> g10 = G[(2 * l + 1) * ZS + 2 * lp], g11 = G[(2 * l + 1) * ZS + 2 * lp + 1];
         const cx<T> d = g10 - g01;
@@ -249,12 +252,12 @@ __device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* R, c
 
 template <typename T, int CS, int NTHR = 32>
 __device__ __forceinline__ void load_site_p(cx<T>* dst, const cx<T>* src, int ld, int Dl, int Dr, int lane) {
-    team_for_2d<NTHR>(2 * Dl, Dr, lane, [&](int row, int r) { dst[row * CS + r] = src[row * ld + r]; });
+    team_for_2d<NTHR, 4>(2 * Dl, Dr, lane, [&](int row, int r) { dst[row * CS + r] = src[row * ld + r]; });
 }
 
 template <typename T, int CS, int NTHR = 32>
 __device__ __forceinline__ void load_mat(cx<T>* dst, const cx<T>* src, int ld, int D, int lane) {
-    team_for_2d<NTHR>(D, D, lane, [&](int r, int c) { dst[r * CS + c] = src[r * ld + c]; });
+    team_for_2d<NTHR, 4>(D, D, lane, [&](int r, int c) { dst[r * CS + c] = src[r * ld + c]; });
 }
 
 template <typename T, int CHI>
@@ -284,10 +287,10 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     for (int j = n - 1; j >= 0; --j) {
         const int Dl = bd[j], Dr = bd[j + 1];
         cx<T>* dst = rg + (size_t)j * CHI * CHI;
-        team_for_2d<32>(Dr, Dr, lane, [&](int r, int c) { dst[r * CHI + c] = R[r * CS + c]; });
+        team_for_2d<32, 4>(Dr, Dr, lane, [&](int r, int c) { dst[r * CHI + c] = R[r * CS + c]; });
         load_site_p<T, CS>(A, sites + (size_t)j * 2 * ld * ld, ld, Dl, Dr, lane);
         __syncwarp();
-        transfer<T, CHI, 1, 32>(R, A, S, Dl, Dr, lane);
+        transfer<T, CHI, 1, 32, 2>(R, A, S, Dl, Dr, lane);
     }
     if (lane == 0) norm_out[img] = R[0].re;
 }
