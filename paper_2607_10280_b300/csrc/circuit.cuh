@@ -8,7 +8,12 @@
 //   * min(M, N) <= chi (nothing to truncate): exact split.  N <= M: Householder
 //     QR, A_k = Q, A_{k+1} = R.  M < N: A_k = I_M, A_{k+1} = theta.  The state is
 //     the one the SVD split would give, in another gauge of the new bond.
-//   * min(M, N) > chi: SVD truncation at the orthogonality centre.  Gram matrix of
+//   * Each CNOT at most doubles the Schmidt rank across its cut, so after c CNOTs
+//     the rank is at most 2^c and a split keeps at most cap = min(chi, 2^c).
+//     min(M, N) > cap = 2^c <= chi: theta has rank <= cap, and a Householder QR
+//     with column pivoting stopped after cap steps splits it exactly up to
+//     rounding, in any gauge (the paper ansatz's odd-bond sub-layer needs it).
+//   * min(M, N) > cap = chi < 2^c: SVD truncation at the orthogonality centre.  Gram matrix of
 //     the smaller side in FP64; cyclic Jacobi eigensolver (FP64 path: in FP64;
 //     mixed path: in FP32 on the rounded Gram, sigma^2 then taken as FP64 Rayleigh
 //     quotients, and solved again in FP64 when the gap at the cut is below 1e-3 of
@@ -47,7 +52,10 @@ struct CircuitLayout {
     static constexpr size_t off_th = (off_rb + sizeof(cx<T>) * CHI * CS + 15) & ~size_t(15);
     static constexpr size_t off_tau = off_th + sizeof(cx<TQ>) * THETA;
     static constexpr size_t off_bd = off_tau + sizeof(cx<TQ>) * K;
-    static constexpr size_t off_gram = (off_bd + sizeof(int) * (MAX_QUBITS + 1) + 15) & ~size_t(15);
+    static constexpr size_t off_cn = off_bd + sizeof(int) * (MAX_QUBITS + 1);   // CNOTs per cut
+    static constexpr size_t off_perm = off_cn + sizeof(int) * (MAX_QUBITS + 1);  // pivoted QR
+    static constexpr size_t off_cnorm = (off_perm + sizeof(int) * K + 15) & ~size_t(15);
+    static constexpr size_t off_gram = (off_cnorm + sizeof(TQ) * K + 15) & ~size_t(15);
     static constexpr size_t off_vec = off_gram + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_taud = off_vec + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_lam = off_taud + (TRUNC ? sizeof(cx<double>) * K : 0);
@@ -151,6 +159,9 @@ struct CircuitTeam {
     cx<TQ>* th;   // theta, column-major M x N, rows (l,s), columns (t,r)
     cx<TQ>* tau;
     int* bd;      // bd[k] = left bond of site k, k = 0..n
+    int* cn;      // cn[k] = CNOTs applied so far across the cut left of site k
+    int* perm;    // column order of a pivoted QR
+    TQ* cnorm;    // its column norms
     cx<double>* G;
     cx<double>* V;
     cx<double>* taud;
@@ -159,6 +170,7 @@ struct CircuitTeam {
     double* red;  // team reductions
     int* flag;    // team broadcast
     int lane, n, chi, ld;
+    int keep;     // singular values an SVD truncation keeps
     cx<T>* sites;        // this image's site 0 in the arena
     double discarded;
     int* status;
@@ -188,11 +200,17 @@ struct CircuitTeam {
     }
 
     // ---- split theta (M x N) into site k (written to global) and cur (new centre) ----
+    // cap: most singular values the split may keep, min(chi, 2^c) with c the CNOTs
+    // that have crossed this cut (each at most doubles the Schmidt rank).
+    // min(M, N) <= cap: exact QR / identity split.  Otherwise exact_cap (cap = 2^c
+    // <= chi, so theta has rank <= cap): rank-revealing split by pivoted QR, which
+    // drops only rounding noise.  Otherwise (cap = chi < 2^c) an SVD truncation to
+    // chi; the caller has moved the orthogonality centre here first.
     // Returns the new bond dimension.
-    __device__ int split(int k, int Dl, int Dr, bool allow_trunc) {
+    __device__ int split(int k, int Dl, int Dr, int cap, bool exact_cap) {
         const int M = 2 * Dl, N = 2 * Dr;
         const int mn = M < N ? M : N;
-        if (mn <= chi || !allow_trunc) {
+        if (mn <= cap) {
             if (N <= M) {
                 // Householder QR: A_k = Q (M x N), cur = R (N x N) reshaped (N, 2, Dr)
                 team_qr<NTHR>(th, LDM, M, N, tau, red, lane);
@@ -218,15 +236,36 @@ struct CircuitTeam {
             tsync<NTHR>();
             return M;
         }
+        if (exact_cap) return rank_split(k, M, N, Dr, cap);
         if constexpr (TRUNC) {
+            keep = cap;
             return svd_truncate(k, Dl, Dr);
         } else {
             raise_status(status, DEV_BAD_SHAPE);
-            return chi;
+            return cap;
         }
     }
 
-    // SVD truncation to chi of theta (M x N), min(M, N) > chi.
+    // Rank-revealing split of theta (M x N, rank <= cap < min(M, N)): pivoted QR
+    // stopped after cap reflectors, A_k = Q (M x cap), cur = R P^T (cap x N)
+    // reshaped (cap, 2, Dr).  The discarded rows of R are rounding noise.
+    __device__ int rank_split(int k, int M, int N, int Dr, int cap) {
+        team_qrcp<NTHR>(th, LDM, M, N, cap, tau, perm, cnorm, red, lane);
+        team_for_2d<NTHR>(cap, N, lane, [&](int i, int c) {
+            const int oc = perm[c];
+            const int t = oc >= Dr ? 1 : 0, r = oc - t * Dr;
+            const cx<TQ> v = (i <= c) ? th[c * LDM + i] : czero<TQ>();
+            cur[(2 * i + t) * CS + r] = cvt<T>(v);
+        });
+        tsync<NTHR>();
+        team_form_q<NTHR>(th, LDM, M, cap, tau, lane);
+        cx<T>* dst = site_ptr(k);
+        team_for_2d<NTHR>(M, cap, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
+        tsync<NTHR>();
+        return cap;
+    }
+
+    // SVD truncation of theta (M x N) to keep singular values, min(M, N) > keep.
     __device__ int svd_truncate(int k, int Dl, int Dr) {
         const int M = 2 * Dl, N = 2 * Dr;
         const bool left = M <= N;      // Gram of the row space (M x M) or column space (N x N)
@@ -290,8 +329,11 @@ struct CircuitTeam {
             // Near a tie at the cut the FP32 eigenvectors mix the kept and the dropped
             // directions at the FP32 rounding level; there the eigenproblem is solved
             // again in FP64 (G still holds the FP64 Gram, V is free for FP64 vectors).
-            const double gap = lam[ord[chi - 1]] - lam[ord[chi]];
-            if (gap < 1e-3 * lam[ord[0]]) {
+            // A tie between negligible eigenvalues (lambda_keep <= 1e-12 lambda_1)
+            // needs no redo: whichever of those directions is kept, the state moves
+            // by at most sqrt(2 lambda_keep / lambda_1) <= 1.5e-6 of its norm.
+            const double gap = lam[ord[keep - 1]] - lam[ord[keep]];
+            if (gap < 1e-3 * lam[ord[0]] && lam[ord[keep - 1]] > 1e-12 * lam[ord[0]]) {
                 if (lane < 32) warp_jacobi_eigh<double>(G, V, LDK, K, lane, 40);
                 tsync<NTHR>();
                 for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
@@ -305,13 +347,13 @@ struct CircuitTeam {
         for (int i = lane; i < K; i += NTHR) {
             const double w = lam[ord[i]] > 0.0 ? lam[ord[i]] : 0.0;
             tot += w;
-            if (i >= chi) drop += w;
+            if (i >= keep) drop += w;
         }
         tot = team_sum<NTHR>(tot, red, lane);
         drop = team_sum<NTHR>(drop, red, lane);
         if (tot > 0.0) discarded += drop / tot;
         tsync<NTHR>();
-        const int D = chi;
+        const int D = keep;
         // U_chi (M x D, FP64) into the Gram buffer
         cx<double>* U = G;
         auto vec = [&](int c, int r) -> cx<double> {
@@ -419,6 +461,9 @@ struct CircuitTeam {
     }
 };
 
+// Largest Schmidt rank after c CNOTs across a cut (operator Schmidt rank 2 each).
+__device__ __forceinline__ int rank_bound(int c) { return c >= 30 ? (1 << 30) : (1 << c); }
+
 // Pass description: bonds first..n-2; at bond k a CNOT if (k - first) % stride == 0
 // (ladder: stride 1), otherwise an exact centre move.  gates_on_load applies the
 // layer's one-qubit gates as the sites are loaded.  fresh: the state is the
@@ -429,7 +474,9 @@ __device__ bool run_pass(CircuitTeam<T, TQ, CHI, TRUNC, NTHR>& w, int first, int
     constexpr int CS = CircuitTeam<T, TQ, CHI, TRUNC, NTHR>::CS;
     const int n = w.n, lane = w.lane;
     int* bd = w.bd;
-    // does any step of this pass truncate?  (bond dimensions only; thread 0)
+    // does any step of this pass truncate lossily (keep chi < min(M, N) with chi
+    // below the rank bound 2^c of its cut)?  Bond dimensions only; thread 0.
+    int* cn = w.cn;
     if (lane == 0) {
         int trunc = 0;
         int dl = bd[first];
@@ -437,8 +484,10 @@ __device__ bool run_pass(CircuitTeam<T, TQ, CHI, TRUNC, NTHR>& w, int first, int
             if ((k - first) % stride == 0) {
                 const int m = 2 * dl, nn = 2 * bd[k + 2];
                 const int mn = m < nn ? m : nn;
-                if (mn > w.chi) trunc = 1;
-                dl = mn < w.chi ? mn : w.chi;
+                const int rb = rank_bound(cn[k + 1] + 1);
+                if (mn > w.chi && rb > w.chi) trunc = 1;
+                const int cap = rb < w.chi ? rb : w.chi;
+                dl = mn < cap ? mn : cap;
             } else {
                 const int m = 2 * dl;
                 dl = m < bd[k + 1] ? m : bd[k + 1];
@@ -477,8 +526,11 @@ __device__ bool run_pass(CircuitTeam<T, TQ, CHI, TRUNC, NTHR>& w, int first, int
         tsync<NTHR>();
         int nb;
         if ((k - first) % stride == 0) {
+            const int c = cn[k + 1] + 1;
+            const int rb = rank_bound(c);
             w.form_theta(Dl, Dm, Dr, true);
-            nb = w.split(k, Dl, Dr, trunc != 0);
+            nb = w.split(k, Dl, Dr, rb < w.chi ? rb : w.chi, rb <= w.chi);
+            if (lane == 0) cn[k + 1] = c;
         } else {
             nb = w.move_right(k, Dl, Dm, Dr);
         }
@@ -516,6 +568,9 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
     w.th = reinterpret_cast<cx<TQ>*>(base + Lay::off_th);
     w.tau = reinterpret_cast<cx<TQ>*>(base + Lay::off_tau);
     w.bd = reinterpret_cast<int*>(base + Lay::off_bd);
+    w.cn = reinterpret_cast<int*>(base + Lay::off_cn);
+    w.perm = reinterpret_cast<int*>(base + Lay::off_perm);
+    w.cnorm = reinterpret_cast<TQ*>(base + Lay::off_cnorm);
     w.G = reinterpret_cast<cx<double>*>(base + Lay::off_gram);
     w.V = reinterpret_cast<cx<double>*>(base + Lay::off_vec);
     w.taud = reinterpret_cast<cx<double>*>(base + Lay::off_taud);
@@ -543,7 +598,7 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
         const int n = mt.n;
 
         // |0...0> then the encoding R_Y(pi x) (ladder); every bond is 1
-        for (int k = lane; k <= n; k += NTHR) w.bd[k] = 1;
+        for (int k = lane; k <= n; k += NTHR) { w.bd[k] = 1; w.cn[k] = 0; }
         for (int k = lane; k < n; k += NTHR) {
             cx<T>* s = w.site_ptr(k);
             double sn = 0.0, cs = 1.0;
@@ -632,6 +687,9 @@ __device__ bool wave_step(unsigned char* buf, int* bd, int k, int n, int ld, cx<
     w.rb = nullptr; w.G = nullptr; w.V = nullptr; w.taud = nullptr; w.lam = nullptr; w.ord = nullptr;
     w.red = nullptr; w.flag = nullptr;
     w.bd = bd;
+    w.cn = nullptr;
+    w.perm = nullptr;
+    w.cnorm = nullptr;
     w.lane = lane;
     w.n = n;
     w.chi = CL;
@@ -657,7 +715,7 @@ __device__ bool wave_step(unsigned char* buf, int* bd, int k, int n, int ld, cx<
     load_site<T, CS, 32>(w.nxt, w.site_ptr(k + 1), ld, Dm, Dr, &g, lane);
     __syncwarp();
     w.form_theta(Dl, Dm, Dr, true);
-    w.split(k, Dl, Dr, false);
+    w.split(k, Dl, Dr, 1 << 30, true);   // exact: no ladder step exceeds its rank bound
     if (k == n - 2) {
         store_site<T, CS, 32>(w.site_ptr(n - 1), w.cur, ld, nb, Dr, lane);
     }

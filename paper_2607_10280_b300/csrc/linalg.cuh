@@ -103,42 +103,91 @@ __device__ __forceinline__ void apply_reflector(cx<T>* A, int ld, int M, int N, 
     }
 }
 
-// Householder QR of the M x N matrix A (LAPACK geqr2 convention, K = min(M, N)
-// reflectors H_j = I - tau_j v_j v_j^H, A = H_0 ... H_{K-1} R).  On return the
-// upper trapezoid holds R (real diagonal), the strict lower part the reflector
-// tails, tau[0..K) the scalars.  red: NTHR/32 doubles of scratch.
+// Householder step j of a QR: reflector for column j (rows j..M-1), applied to
+// columns j+1..N-1 (LAPACK geqr2 convention, H_j = I - tau_j v_j v_j^H, R[j][j]
+// real).  The reflector tail replaces A(j+1:M, j); tau[j] gets the scalar.
+template <int NTHR, typename T>
+__device__ __forceinline__ void householder_step(cx<T>* A, int ld, int M, int N, int j, cx<T>* tau, double* red,
+                                                 int tid) {
+    cx<T>* col = A + j * ld;
+    T s = T(0);
+    for (int r = j + 1 + tid; r < M; r += NTHR) s += norm2(col[r]);
+    s = team_sum<NTHR>(s, red, tid);
+    const cx<T> alpha = col[j];
+    const bool trivial = (s == T(0)) && (alpha.im == T(0));
+    cx<T> t = czero<T>();
+    T beta = alpha.re;
+    cx<T> scale = mk<T>(T(1), T(0));
+    if (!trivial) {
+        const T nrm = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + s);
+        beta = alpha.re >= T(0) ? -nrm : nrm;
+        t = mk<T>((beta - alpha.re) / beta, -alpha.im / beta);
+        const cx<T> d = mk<T>(alpha.re - beta, alpha.im);
+        const T dd = norm2(d);
+        scale = mk<T>(d.re / dd, -d.im / dd);
+    }
+    tsync<NTHR>();
+    if (!trivial) {
+        for (int r = j + 1 + tid; r < M; r += NTHR) col[r] = col[r] * scale;
+    }
+    if (tid == 0) {
+        col[j] = mk<T>(beta, T(0));
+        tau[j] = t;
+    }
+    tsync<NTHR>();
+    if (!trivial) apply_reflector<NTHR>(A, ld, M, N, j, conj(t), tid);
+    tsync<NTHR>();
+}
+
+// Householder QR of the M x N matrix A (K = min(M, N) reflectors,
+// A = H_0 ... H_{K-1} R).  On return the upper trapezoid holds R (real diagonal),
+// the strict lower part the reflector tails, tau[0..K) the scalars.  red: NTHR/32
+// doubles of scratch.
 template <int NTHR, typename T>
 __device__ void team_qr(cx<T>* A, int ld, int M, int N, cx<T>* tau, double* red, int tid) {
     const int K = M < N ? M : N;
-    for (int j = 0; j < K; ++j) {
-        cx<T>* col = A + j * ld;
-        T s = T(0);
-        for (int r = j + 1 + tid; r < M; r += NTHR) s += norm2(col[r]);
-        s = team_sum<NTHR>(s, red, tid);
-        const cx<T> alpha = col[j];
-        const bool trivial = (s == T(0)) && (alpha.im == T(0));
-        cx<T> t = czero<T>();
-        T beta = alpha.re;
-        cx<T> scale = mk<T>(T(1), T(0));
-        if (!trivial) {
-            const T nrm = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + s);
-            beta = alpha.re >= T(0) ? -nrm : nrm;
-            t = mk<T>((beta - alpha.re) / beta, -alpha.im / beta);
-            const cx<T> d = mk<T>(alpha.re - beta, alpha.im);
-            const T dd = norm2(d);
-            scale = mk<T>(d.re / dd, -d.im / dd);
+    for (int j = 0; j < K; ++j) householder_step<NTHR>(A, ld, M, N, j, tau, red, tid);
+}
+
+// Householder QR with column pivoting (Businger-Golub), stopped after `steps`
+// reflectors: A P = Q R with the largest remaining column moved to position j
+// before step j (ties: the lowest index).  perm[c] is the original index of
+// column c; cnorm: N scratch values.  For a matrix of rank <= steps the rows of R
+// below `steps` are rounding noise, so Q(:, 0:steps) and R(0:steps, :) P^T
+// reproduce A to the working precision (rank-revealing split).
+template <int NTHR, typename T>
+__device__ void team_qrcp(cx<T>* A, int ld, int M, int N, int steps, cx<T>* tau, int* perm, T* cnorm,
+                          double* red, int tid) {
+    for (int c = tid; c < N; c += NTHR) perm[c] = c;
+    tsync<NTHR>();
+    for (int j = 0; j < steps; ++j) {
+        for (int c = j + tid; c < N; c += NTHR) {
+            const cx<T>* a = A + c * ld;
+            T s = T(0);
+            for (int r = j; r < M; ++r) s += norm2(a[r]);
+            cnorm[c] = s;
         }
         tsync<NTHR>();
-        if (!trivial) {
-            for (int r = j + 1 + tid; r < M; r += NTHR) col[r] = col[r] * scale;
-        }
-        if (tid == 0) {
-            col[j] = mk<T>(beta, T(0));
-            tau[j] = t;
+        int p = j;
+        T best = cnorm[j];
+        for (int c = j + 1; c < N; ++c)
+            if (cnorm[c] > best) { best = cnorm[c]; p = c; }
+        if (p != j) {
+            cx<T>* a = A + j * ld;
+            cx<T>* b = A + p * ld;
+            for (int r = tid; r < M; r += NTHR) {
+                const cx<T> x = a[r];
+                a[r] = b[r];
+                b[r] = x;
+            }
+            if (tid == 0) {
+                const int x = perm[j];
+                perm[j] = perm[p];
+                perm[p] = x;
+            }
         }
         tsync<NTHR>();
-        if (!trivial) apply_reflector<NTHR>(A, ld, M, N, j, conj(t), tid);
-        tsync<NTHR>();
+        householder_step<NTHR>(A, ld, M, N, j, tau, red, tid);
     }
 }
 

@@ -122,38 +122,47 @@ namespace {
 // Bond dimensions reachable by one image, simulated on dimensions only with the
 // same rules as the circuit kernel.  Returns the largest bond; sets *trunc if any
 // two-qubit step must truncate.
-int dry_run_bonds(int n, int L, int chi, int ansatz, bool* trunc) {
-    std::vector<int> bd(n + 1, 1);
+// Host mirror of the circuit kernel's bond dimensions (run_pass): returns the largest
+// bond; *svd is set when some step truncates lossily (an SVD split to chi below the
+// rank bound 2^c of its cut).  Splits that only drop the rank beyond 2^c use the
+// pivoted QR, which every circuit kernel has.
+int dry_run_bonds(int n, int L, int chi, int ansatz, bool* svd) {
+    std::vector<int> bd(n + 1, 1), cn(n + 1, 0);
     int mx = 1;
     bool any = false;
+    auto rank_bound = [](int c) { return c >= 30 ? (1 << 30) : (1 << c); };
     auto pass = [&](int first, int stride) {
-        bool t = false;
+        bool lossy = false;
         int dl = bd[first];
         for (int k = first; k < n - 1; ++k) {
             if ((k - first) % stride == 0) {
                 const int m = 2 * dl, nn = 2 * bd[k + 2];
                 const int mn = std::min(m, nn);
-                if (mn > chi) t = true;
-                dl = std::min(mn, chi);
+                const int rb = rank_bound(cn[k + 1] + 1);
+                if (mn > chi && rb > chi) lossy = true;
+                dl = std::min(mn, std::min(chi, rb));
             } else {
                 dl = std::min(2 * dl, bd[k + 1]);
             }
         }
-        if (t) {  // centre moves right-to-left (LQ) before the pass
+        if (lossy) {  // centre moves right-to-left (LQ) before the pass
             for (int k = n - 1; k > first; --k) bd[k] = std::min(bd[k], 2 * bd[k + 1]);
         }
         for (int k = first; k < n - 1; ++k) {
             int nb;
             if ((k - first) % stride == 0) {
                 const int m = 2 * bd[k], nn = 2 * bd[k + 2];
-                nb = std::min(chi, std::min(m, nn));
+                const int c = cn[k + 1] + 1;
+                const int cap = std::min(chi, rank_bound(c));
+                if (std::min(m, nn) > cap && rank_bound(c) > chi) any = true;   // lossy: SVD kernels
+                nb = std::min(cap, std::min(m, nn));
+                cn[k + 1] = c;
             } else {
                 nb = std::min(2 * bd[k], bd[k + 1]);
             }
             bd[k + 1] = nb;
             mx = std::max(mx, nb);
         }
-        any = any || t;
     };
     for (int l = 0; l < L; ++l) {
         if (ansatz == MPS_ANSATZ_LADDER) {
@@ -163,7 +172,7 @@ int dry_run_bonds(int n, int L, int chi, int ansatz, bool* trunc) {
             if (n > 2) pass(1, 2);
         }
     }
-    *trunc = any;
+    *svd = any;
     return mx;
 }
 

@@ -370,3 +370,29 @@ def test_linear_layer_special_cases():
     b = np.ones(5)
     assert np.allclose(ano.linear(np.eye(5), q, b), q + 1)
     assert np.allclose(ano.linear(np.zeros((3, 5)), q, np.arange(3.0)), np.arange(3.0))
+
+
+@pytest.mark.parametrize("ansatz", ["ladder", "paper"])
+def test_schmidt_rank_at_most_two_to_the_cnots_across_the_cut(ansatz):
+    """A CNOT has operator Schmidt rank 2 and one-qubit gates have rank 1, so after c
+    CNOTs have crossed a cut the state's Schmidt rank there is at most 2^c.  Checked on
+    the dense state after every gate (3x3 and 4x4 images, L = 3 and 2): the GPU splits
+    keep at most min(chi, 2^c) values on this ground."""
+    from oracle import circuit as circ, statevector as sv
+    for p, L in ((3, 3), (4, 2)):
+        n = p * p
+        rng = np.random.default_rng(7)
+        x = rng.random(n)
+        params = rng.uniform(0, 2 * np.pi, size=(L, n, 2))
+        ops = circ.build_circuit(ansatz, x, L, params if ansatz == "ladder" else None)
+        psi = sv.zero_state(n)
+        crossed = np.zeros(n - 1, dtype=int)
+        for kind, k, M in ops:
+            if kind == "1q":
+                psi = sv.apply_1q(psi, k, M)
+                continue
+            psi = sv.apply_2q(psi, k, M)
+            crossed[k] += 1
+            for cut in range(n - 1):
+                s = sv.schmidt_values(psi, cut)
+                assert np.sum(s > 1e-10 * s[0]) <= 2 ** crossed[cut]
