@@ -38,6 +38,13 @@ struct mps_batch {
     int circuit_threads = 32;              // threads per image in the circuit kernel
     bool layer_pipeline = true;            // layer-pipelined kernel where it applies
     int L_max = 0;                         // most layers of any image in the last circuit
+    // images of the next circuit launch: run_order[0 .. run_count), and whether the
+    // layer-pipelined kernel runs them
+    const int32_t* run_order = nullptr;
+    int run_count = 0;
+    bool use_wave = false;
+    std::vector<int32_t> cost_order;       // all images by descending cost
+    std::vector<int32_t> order_h;          // the order last uploaded to order_d
     int32_t* order_d = nullptr;            // circuit work queue: images by descending cost
     int32_t* order_pinned = nullptr;       // staging of order_d
     int32_t* units_pinned = nullptr;       // staging of units_d

@@ -28,11 +28,11 @@ mps_status launch_circuit_team(mps_batch* b, const double* pixels, int ansatz) {
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHR * per_cta, smem));
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int needed = (b->B + per_cta - 1) / per_cta;
+    const int needed = (b->run_count + per_cta - 1) / per_cta;
     const int grid = std::max(1, std::min(needed, std::max(1, per_sm) * sms));
     CUDA_TRY(cudaMemsetAsync(b->queue_d, 0, sizeof(int), b->stream));
     timing_begin(b, KIND_CIRCUIT);
-    kern<<<grid, NTHR * per_cta, smem, b->stream>>>(b->meta_d, b->B, b->order_d, b->queue_d, pixels,
+    kern<<<grid, NTHR * per_cta, smem, b->stream>>>(b->meta_d, b->run_count, b->run_order, b->queue_d, pixels,
                                                    reinterpret_cast<const cx<T>*>(b->gates), b->gate_n, ansatz,
                                                    reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
                                                    b->discarded_d, b->status_d);
@@ -43,7 +43,7 @@ mps_status launch_circuit_team(mps_batch* b, const double* pixels, int ansatz) {
 }
 
 // Layer-pipelined kernel (ladder ansatz, no truncation, at most WAVE_LAYERS layers):
-// one CTA of one warp per layer for each image, in descending-cost order.  Its
+// one CTA of one warp per layer for each image of b->run_order[0 .. run_count).  Its
 // buffers only depend on min(CHI, 16) since a ladder bond is at most 2^layers.
 template <typename T, typename TQ, int CHI>
 mps_status launch_circuit_wave(mps_batch* b, const double* pixels) {
@@ -56,7 +56,7 @@ mps_status launch_circuit_wave(mps_batch* b, const double* pixels) {
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int warps = std::max(1, std::min(b->L_max, WAVE_LAYERS));
     timing_begin(b, KIND_CIRCUIT);
-    kern<<<b->B, 32 * warps, smem, b->stream>>>(b->meta_d, b->B, b->order_d, pixels,
+    kern<<<b->run_count, 32 * warps, smem, b->stream>>>(b->meta_d, b->run_count, b->run_order, pixels,
                                                 reinterpret_cast<const cx<T>*>(b->gates), b->gate_n,
                                                 reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
                                                 b->discarded_d, b->status_d);
@@ -72,8 +72,7 @@ mps_status launch_circuit_wave(mps_batch* b, const double* pixels) {
 template <typename T, typename TQ, int CHI, bool TRUNC>
 mps_status launch_circuit(mps_batch* b, const double* pixels, int ansatz) {
     if constexpr (!TRUNC) {
-        if (b->layer_pipeline && ansatz == MPS_ANSATZ_LADDER && b->L_max >= 1 && b->L_max <= WAVE_LAYERS)
-            return launch_circuit_wave<T, TQ, CHI>(b, pixels);
+        if (b->use_wave) return launch_circuit_wave<T, TQ, CHI>(b, pixels);
     }
     if constexpr (CHI == 16 && !TRUNC && sizeof(T) == 4 && sizeof(TQ) == 4) {
         if (b->circuit_threads == 64) return launch_circuit_team<T, TQ, CHI, TRUNC, 64>(b, pixels, ansatz);

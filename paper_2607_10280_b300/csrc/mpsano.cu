@@ -321,6 +321,8 @@ mps_status fit_and_upload(mps_batch* b) {
         const ImageMeta& mc = b->meta_h[c];
         return (int64_t)ma.n * ma.ld * ma.ld * ma.ld > (int64_t)mc.n * mc.ld * mc.ld * mc.ld;
     });
+    b->cost_order.assign(b->order_pinned, b->order_pinned + B);
+    b->order_h = b->cost_order;
     std::memcpy(b->units_pinned, b->units_h.data(), sizeof(int32_t) * b->units_h.size());
     std::memcpy(b->meta_pinned, b->meta_h.data(), sizeof(ImageMeta) * B);
     TRY_GROW(cudaMemsetAsync(b->status_d, 0, sizeof(int), b->stream));
@@ -415,10 +417,15 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         if (circ->params_n < b->n_max)
             return fail(MPS_ERR_INVALID_ARG, "params_n = %d < largest n = %d", circ->params_n, b->n_max);
     }
-    // bond dimensions, shared-memory bucket and truncation per image
-    int mx = 1;
-    bool trunc = false;
+    // bond dimensions, shared-memory bucket and truncation per image.  Images whose
+    // circuit the layer-pipelined kernel can run (ladder, nothing lossy, 1 <= L <= 4)
+    // go to it, the others to the sequential kernel, so that an image's kernel (and
+    // its result) depends on its own circuit only, not on the rest of the batch.
+    int mx = 1, mx_wave = 1, mx_seq = 1;
+    bool trunc_seq = false;
     bool changed = false;
+    std::vector<char> wave(b->B, 0);
+    int n_wave = 0;
     for (int i = 0; i < b->B; ++i) {
         ImageMeta& m = b->meta_h[i];
         const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
@@ -427,10 +434,29 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         const int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
         if (bi > m.ld) return fail(MPS_ERR_UNSUPPORTED, "image %d reaches bond %d > padding %d", i, bi, m.ld);
         mx = std::max(mx, bi);
-        trunc = trunc || t;
+        wave[i] = b->layer_pipeline && circ->ansatz == MPS_ANSATZ_LADDER && !t && L >= 1 && L <= WAVE_LAYERS;
+        if (wave[i]) {
+            ++n_wave;
+            mx_wave = std::max(mx_wave, bi);
+        } else {
+            mx_seq = std::max(mx_seq, bi);
+            trunc_seq = trunc_seq || t;
+        }
     }
     const int chi_tpl = chi_bucket(mx);
     if (chi_tpl < 0) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > 32 not supported", mx);
+    // work order: pipelined images first, each part by descending cost
+    std::vector<int32_t> order;
+    order.reserve(b->B);
+    for (int32_t i : b->cost_order) if (wave[i]) order.push_back(i);
+    for (int32_t i : b->cost_order) if (!wave[i]) order.push_back(i);
+    if (order != b->order_h) {
+        CUDA_TRY(cudaStreamSynchronize(b->stream));  // pinned staging may still be in flight
+        std::memcpy(b->order_pinned, order.data(), sizeof(int32_t) * b->B);
+        CUDA_TRY(cudaMemcpyAsync(b->order_d, b->order_pinned, sizeof(int32_t) * b->B, cudaMemcpyHostToDevice,
+                                 b->stream));
+        b->order_h = order;
+    }
     if (changed) {
         CUDA_TRY(cudaStreamSynchronize(b->stream));  // pinned staging may still be in flight
         std::memcpy(b->meta_pinned, b->meta_h.data(), sizeof(ImageMeta) * b->B);
@@ -453,12 +479,27 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     const double* pr = circ->ansatz == MPS_ANSATZ_LADDER ? circ->params : nullptr;
     mps_status st = launch_gate_table(b, circ->ansatz, L_max, pr, circ->params_n, pixels);
     if (st != MPS_OK) return st;
-    switch (b->prec) {
-        case MPS_FP64: st = launch_circuit_fp64(b, chi_tpl, trunc, pixels, circ->ansatz); break;
-        case MPS_MIXED: st = launch_circuit_mixed(b, chi_tpl, trunc, pixels, circ->ansatz); break;
-        default: st = launch_circuit_orth64(b, chi_tpl, trunc, pixels, circ->ansatz); break;
+    auto launch = [&](int bucket, bool trunc) {
+        switch (b->prec) {
+            case MPS_FP64: return launch_circuit_fp64(b, bucket, trunc, pixels, circ->ansatz);
+            case MPS_MIXED: return launch_circuit_mixed(b, bucket, trunc, pixels, circ->ansatz);
+            default: return launch_circuit_orth64(b, bucket, trunc, pixels, circ->ansatz);
+        }
+    };
+    if (n_wave > 0) {
+        b->use_wave = true;
+        b->run_order = b->order_d;
+        b->run_count = n_wave;
+        st = launch(chi_bucket(mx_wave), false);
+        if (st != MPS_OK) return st;
     }
-    if (st != MPS_OK) return st;
+    if (n_wave < b->B) {
+        b->use_wave = false;
+        b->run_order = b->order_d + n_wave;
+        b->run_count = b->B - n_wave;
+        st = launch(chi_bucket(mx_seq), trunc_seq);
+        if (st != MPS_OK) return st;
+    }
     b->chi_tpl = chi_tpl;
     b->circuit_done = true;
     return MPS_OK;

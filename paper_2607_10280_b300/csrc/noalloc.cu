@@ -171,6 +171,9 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
     b.gate_n = n;
     b.queue_d = reinterpret_cast<int*>(base + OFF_QUEUE);
     b.order_d = nullptr;   // equal sizes: images in index order
+    b.run_order = nullptr;
+    b.run_count = n_images;
+    b.use_wave = false;
 
     const int threads = 128;
     const int work = std::max(n_images * p, n_images);

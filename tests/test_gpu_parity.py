@@ -388,3 +388,23 @@ def test_paper_ansatz_exact_regime_rank_revealing_splits(precision):
         assert np.all(np.asarray(disc) == 0.0)          # nothing lossy
         for i in range(3):
             assert np.max(np.abs(got[i] - ref[i])) < TOL[precision], (chi, i)
+
+
+def test_mixed_batch_routes_each_image_by_its_own_circuit():
+    """A batch mixing images the layer-pipelined kernel can run (chi >= 2^L) with images
+    that truncate: every image gives the same bits as in a batch of its own."""
+    p = 6
+    X = list(synth.garment_pixels(6, p, seed=140))
+    params = synth.circuit_params(3, p * p, seed=141)
+    chis = np.array([8, 4, 16, 2, 8, 4], dtype=np.int32)       # L = 3: exact, lossy, ...
+    from paper_2607_10280_b300.api import Batch
+    px = torch.tensor(np.concatenate(X), dtype=torch.float64, device="cuda")
+    pr = torch.tensor(params, dtype=torch.float64, device="cuda")
+    b = Batch(np.full(6, p, np.int32), chis, "mixed")
+    b.apply_circuit(px, 3, "ladder", pr)
+    mixed = b.pauli_cache().cpu().numpy()
+    b.close()
+    m = 2 * p * (p - 1)
+    for i in range(6):
+        alone, _, _ = run_gpu([X[i]], [p], 3, int(chis[i]), "mixed", params=params)
+        assert np.array_equal(mixed[i * m:(i + 1) * m], alone[0]), i
