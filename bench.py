@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--config", default="headline", choices=["headline", "sweep", "uneven", "large", "serve", "train"],
                     help="headline (default): 7x7 L=4 chi=16; the others are the chi x L sweep, the uneven "
                          "batch, the 16x16 batch and the serving run")
-    ap.add_argument("--requests", type=int, default=4000, help="serving run: number of requests")
+    ap.add_argument("--requests", type=int, default=20000, help="serving run: number of requests (10 s at 2000/s)")
     return ap.parse_args()
 
 
