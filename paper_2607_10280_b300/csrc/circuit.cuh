@@ -55,7 +55,9 @@ struct CircuitLayout {
     static constexpr size_t off_cn = off_bd + sizeof(int) * (MAX_QUBITS + 1);   // CNOTs per cut
     static constexpr size_t off_perm = off_cn + sizeof(int) * (MAX_QUBITS + 1);  // pivoted QR
     static constexpr size_t off_cnorm = (off_perm + sizeof(int) * K + 15) & ~size_t(15);
-    static constexpr size_t off_gram = (off_cnorm + sizeof(TQ) * K + 15) & ~size_t(15);
+    static constexpr int WYK = CHI < 16 ? CHI : 16;                              // compact-WY Q up to K = 16
+    static constexpr size_t off_wy = (off_cnorm + sizeof(TQ) * K + 15) & ~size_t(15);
+    static constexpr size_t off_gram = (off_wy + sizeof(cx<TQ>) * 2 * WYK * (WYK + 1) + 15) & ~size_t(15);
     static constexpr size_t off_vec = off_gram + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_taud = off_vec + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_lam = off_taud + (TRUNC ? sizeof(cx<double>) * K : 0);
@@ -162,6 +164,8 @@ struct CircuitTeam {
     int* cn;      // cn[k] = CNOTs applied so far across the cut left of site k
     int* perm;    // column order of a pivoted QR
     TQ* cnorm;    // its column norms
+    cx<TQ>* wy;   // compact-WY scratch, 2 wyk (wyk + 1) elements
+    int wyk;      // largest K whose Q is formed in compact-WY form
     cx<double>* G;
     cx<double>* V;
     cx<double>* taud;
@@ -199,6 +203,19 @@ struct CircuitTeam {
         tsync<NTHR>();
     }
 
+    // The explicit Q (M x K) of the reflectors in th / tau, stored as site k.
+    __device__ void q_to_site(int k, int M, int K) {
+        cx<T>* dst = site_ptr(k);
+        if (K <= wyk) {
+            team_form_q_wy<NTHR>(th, LDM, M, K, tau, wy, lane,
+                                 [&](int r, int c, cx<TQ> v) { dst[r * ld + c] = cvt<T>(v); });
+        } else {
+            team_form_q<NTHR>(th, LDM, M, K, tau, lane);
+            team_for_2d<NTHR>(M, K, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
+        }
+        tsync<NTHR>();
+    }
+
     // ---- split theta (M x N) into site k (written to global) and cur (new centre) ----
     // cap: most singular values the split may keep, min(chi, 2^c) with c the CNOTs
     // that have crossed this cut (each at most doubles the Schmidt rank).
@@ -220,10 +237,7 @@ struct CircuitTeam {
                     cur[(2 * i + t) * CS + r] = cvt<T>(v);
                 });
                 tsync<NTHR>();
-                team_form_q<NTHR>(th, LDM, M, N, tau, lane);
-                cx<T>* dst = site_ptr(k);
-                team_for_2d<NTHR>(M, N, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
-                tsync<NTHR>();
+                q_to_site(k, M, N);
                 return N;
             }
             // M < N: A_k = I_M, cur = theta reshaped (M, 2, Dr)
@@ -258,10 +272,7 @@ struct CircuitTeam {
             cur[(2 * i + t) * CS + r] = cvt<T>(v);
         });
         tsync<NTHR>();
-        team_form_q<NTHR>(th, LDM, M, cap, tau, lane);
-        cx<T>* dst = site_ptr(k);
-        team_for_2d<NTHR>(M, cap, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
-        tsync<NTHR>();
+        q_to_site(k, M, cap);
         return cap;
     }
 
@@ -571,6 +582,8 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
     w.cn = reinterpret_cast<int*>(base + Lay::off_cn);
     w.perm = reinterpret_cast<int*>(base + Lay::off_perm);
     w.cnorm = reinterpret_cast<TQ*>(base + Lay::off_cnorm);
+    w.wy = reinterpret_cast<cx<TQ>*>(base + Lay::off_wy);
+    w.wyk = Lay::WYK;
     w.G = reinterpret_cast<cx<double>*>(base + Lay::off_gram);
     w.V = reinterpret_cast<cx<double>*>(base + Lay::off_vec);
     w.taud = reinterpret_cast<cx<double>*>(base + Lay::off_taud);
@@ -652,7 +665,8 @@ struct WaveBuf {
     static constexpr size_t off_nxt = off_cur + sizeof(cx<T>) * 2 * CL * CS;
     static constexpr size_t off_th = (off_nxt + sizeof(cx<T>) * 2 * CLR * CS + 15) & ~size_t(15);
     static constexpr size_t off_tau = off_th + sizeof(cx<TQ>) * 2 * CLR * LDM;
-    static constexpr size_t bytes = (off_tau + sizeof(cx<TQ>) * 2 * CLR + 15) & ~size_t(15);
+    static constexpr size_t off_wy = (off_tau + sizeof(cx<TQ>) * 2 * CLR + 15) & ~size_t(15);
+    static constexpr size_t bytes = (off_wy + sizeof(cx<TQ>) * 2 * CL * (CL + 1) + 15) & ~size_t(15);
 };
 
 template <int CHI, int J> struct WaveDims {
@@ -690,6 +704,8 @@ __device__ bool wave_step(unsigned char* buf, int* bd, int k, int n, int ld, cx<
     w.cn = nullptr;
     w.perm = nullptr;
     w.cnorm = nullptr;
+    w.wy = reinterpret_cast<cx<TQ>*>(buf + B::off_wy);
+    w.wyk = CL;   // a ladder split has K = 2 D_right <= CL
     w.lane = lane;
     w.n = n;
     w.chi = CL;

@@ -15,12 +15,19 @@ template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { cx<T> z; z
 template <typename T> __device__ __forceinline__ cx<T> czero() { return mk<T>(T(0), T(0)); }
 template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk<T>(a.re + b.re, a.im + b.im); }
 template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk<T>(a.re - b.re, a.im - b.im); }
+// Products that the compiler may not fuse into a neighbouring add: with every
+// multiply of the complex helpers either an explicit fma or one of these, each
+// kernel instantiation computes the same bits from the same inputs.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
-    return mk<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+    return mk<T>(fma(a.re, b.re, -mul_rn(a.im, b.im)), fma(a.re, b.im, mul_rn(a.im, b.re)));
 }
-template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk<T>(s * a.re, s * a.im); }
+template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) {
+    return mk<T>(mul_rn(s, a.re), mul_rn(s, a.im));
+}
 template <typename T> __device__ __forceinline__ cx<T> conj(cx<T> a) { return mk<T>(a.re, -a.im); }
-template <typename T> __device__ __forceinline__ T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+template <typename T> __device__ __forceinline__ T norm2(cx<T> a) { return fma(a.re, a.re, mul_rn(a.im, a.im)); }
 // acc += a * b
 template <typename T> __device__ __forceinline__ void cmac(cx<T>& acc, cx<T> a, cx<T> b) {
     acc.re = fma(a.re, b.re, acc.re); acc.re = fma(-a.im, b.im, acc.re);

@@ -206,7 +206,7 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
-                    if (C || b == 3) acc[4 * a + b] += e[a].re * y[b].re - e[a].im * y[b].im;
+                    if (C || b == 3) acc[4 * a + b] = fma(-e[a].im, y[b].im, fma(e[a].re, y[b].re, acc[4 * a + b]));
         });
 #pragma unroll
         for (int i = 0; i < 12; ++i) out[i] = warp_sum(acc[i]);
