@@ -55,9 +55,7 @@ struct CircuitLayout {
     static constexpr size_t off_cn = off_bd + sizeof(int) * (MAX_QUBITS + 1);   // CNOTs per cut
     static constexpr size_t off_perm = off_cn + sizeof(int) * (MAX_QUBITS + 1);  // pivoted QR
     static constexpr size_t off_cnorm = (off_perm + sizeof(int) * K + 15) & ~size_t(15);
-    static constexpr int WYK = CHI < 16 ? CHI : 16;                              // compact-WY Q up to K = 16
-    static constexpr size_t off_wy = (off_cnorm + sizeof(TQ) * K + 15) & ~size_t(15);
-    static constexpr size_t off_gram = (off_wy + sizeof(cx<TQ>) * 2 * WYK * (WYK + 1) + 15) & ~size_t(15);
+    static constexpr size_t off_gram = (off_cnorm + sizeof(TQ) * K + 15) & ~size_t(15);
     static constexpr size_t off_vec = off_gram + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_taud = off_vec + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_lam = off_taud + (TRUNC ? sizeof(cx<double>) * K : 0);
@@ -127,8 +125,8 @@ __device__ __forceinline__ void load_site(cx<T>* dst, const cx<T>* src, int ld, 
     team_for_2d<NTHR>(Dl, Dr, lane, [&](int l, int r) {
         const cx<T> a0 = src[(2 * l) * ld + r], a1 = src[(2 * l + 1) * ld + r];
         if (g) {
-            dst[(2 * l) * CS + r] = g->u00 * a0 + g->u01 * a1;
-            dst[(2 * l + 1) * CS + r] = g->u10 * a0 + g->u11 * a1;
+            dst[(2 * l) * CS + r] = cdot2(g->u00, a0, g->u01, a1);
+            dst[(2 * l + 1) * CS + r] = cdot2(g->u10, a0, g->u11, a1);
         } else {
             dst[(2 * l) * CS + r] = a0;
             dst[(2 * l + 1) * CS + r] = a1;
@@ -145,8 +143,8 @@ template <typename T, int CS, int NTHR>
 __device__ __forceinline__ void apply_gate_smem(cx<T>* site, int Dl, int Dr, const Gate1<T>& g, int lane) {
     team_for_2d<NTHR>(Dl, Dr, lane, [&](int l, int r) {
         const cx<T> a0 = site[(2 * l) * CS + r], a1 = site[(2 * l + 1) * CS + r];
-        site[(2 * l) * CS + r] = g.u00 * a0 + g.u01 * a1;
-        site[(2 * l + 1) * CS + r] = g.u10 * a0 + g.u11 * a1;
+        site[(2 * l) * CS + r] = cdot2(g.u00, a0, g.u01, a1);
+        site[(2 * l + 1) * CS + r] = cdot2(g.u10, a0, g.u11, a1);
     });
 }
 
@@ -164,8 +162,6 @@ struct CircuitTeam {
     int* cn;      // cn[k] = CNOTs applied so far across the cut left of site k
     int* perm;    // column order of a pivoted QR
     TQ* cnorm;    // its column norms
-    cx<TQ>* wy;   // compact-WY scratch, 2 wyk (wyk + 1) elements
-    int wyk;      // largest K whose Q is formed in compact-WY form
     cx<double>* G;
     cx<double>* V;
     cx<double>* taud;
@@ -206,13 +202,8 @@ struct CircuitTeam {
     // The explicit Q (M x K) of the reflectors in th / tau, stored as site k.
     __device__ void q_to_site(int k, int M, int K) {
         cx<T>* dst = site_ptr(k);
-        if (K <= wyk) {
-            team_form_q_wy<NTHR>(th, LDM, M, K, tau, wy, lane,
-                                 [&](int r, int c, cx<TQ> v) { dst[r * ld + c] = cvt<T>(v); });
-        } else {
-            team_form_q<NTHR>(th, LDM, M, K, tau, lane);
-            team_for_2d<NTHR>(M, K, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
-        }
+        team_form_q<NTHR>(th, LDM, M, K, tau, lane);
+        team_for_2d<NTHR>(M, K, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
         tsync<NTHR>();
     }
 
@@ -582,8 +573,6 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
     w.cn = reinterpret_cast<int*>(base + Lay::off_cn);
     w.perm = reinterpret_cast<int*>(base + Lay::off_perm);
     w.cnorm = reinterpret_cast<TQ*>(base + Lay::off_cnorm);
-    w.wy = reinterpret_cast<cx<TQ>*>(base + Lay::off_wy);
-    w.wyk = Lay::WYK;
     w.G = reinterpret_cast<cx<double>*>(base + Lay::off_gram);
     w.V = reinterpret_cast<cx<double>*>(base + Lay::off_vec);
     w.taud = reinterpret_cast<cx<double>*>(base + Lay::off_taud);
@@ -665,8 +654,7 @@ struct WaveBuf {
     static constexpr size_t off_nxt = off_cur + sizeof(cx<T>) * 2 * CL * CS;
     static constexpr size_t off_th = (off_nxt + sizeof(cx<T>) * 2 * CLR * CS + 15) & ~size_t(15);
     static constexpr size_t off_tau = off_th + sizeof(cx<TQ>) * 2 * CLR * LDM;
-    static constexpr size_t off_wy = (off_tau + sizeof(cx<TQ>) * 2 * CLR + 15) & ~size_t(15);
-    static constexpr size_t bytes = (off_wy + sizeof(cx<TQ>) * 2 * CL * (CL + 1) + 15) & ~size_t(15);
+    static constexpr size_t bytes = (off_tau + sizeof(cx<TQ>) * 2 * CLR + 15) & ~size_t(15);
 };
 
 template <int CHI, int J> struct WaveDims {
@@ -704,8 +692,6 @@ __device__ bool wave_step(unsigned char* buf, int* bd, int k, int n, int ld, cx<
     w.cn = nullptr;
     w.perm = nullptr;
     w.cnorm = nullptr;
-    w.wy = reinterpret_cast<cx<TQ>*>(buf + B::off_wy);
-    w.wyk = CL;   // a ladder split has K = 2 D_right <= CL
     w.lane = lane;
     w.n = n;
     w.chi = CL;

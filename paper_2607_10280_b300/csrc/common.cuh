@@ -38,6 +38,18 @@ template <typename T> __device__ __forceinline__ void cmac_cj(cx<T>& acc, cx<T> 
     acc.re = fma(a.re, b.re, acc.re); acc.re = fma(a.im, b.im, acc.re);
     acc.im = fma(a.re, b.im, acc.im); acc.im = fma(-a.im, b.re, acc.im);
 }
+// acc -= a * b
+template <typename T> __device__ __forceinline__ void cmsub(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.re = fma(-a.re, b.re, acc.re); acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(-a.re, b.im, acc.im); acc.im = fma(-a.im, b.re, acc.im);
+}
+// u0 * a0 + u1 * a1 as one fma chain
+template <typename T> __device__ __forceinline__ cx<T> cdot2(cx<T> u0, cx<T> a0, cx<T> u1, cx<T> a1) {
+    cx<T> acc = mk<T>(mul_rn(u0.re, a0.re), mul_rn(u0.re, a0.im));
+    acc.re = fma(-u0.im, a0.im, acc.re); acc.im = fma(u0.im, a0.re, acc.im);
+    cmac(acc, u1, a1);
+    return acc;
+}
 template <typename To, typename Ti> __device__ __forceinline__ cx<To> cvt(cx<Ti> a) {
     return mk<To>(To(a.re), To(a.im));
 }

@@ -98,7 +98,7 @@ __device__ __forceinline__ void apply_reflector(cx<T>* A, int ld, int M, int N, 
             w = t * w;
             if (g == 0) a[j] = a[j] - w;
 #pragma unroll 1
-            for (int r = j + 1 + g; r < M; r += G) a[r] = a[r] - v[r] * w;
+            for (int r = j + 1 + g; r < M; r += G) cmsub(a[r], v[r], w);
         }
     }
 }
@@ -209,56 +209,6 @@ __device__ void team_form_q(cx<T>* A, int ld, int M, int K, const cx<T>* tau, in
         }
         tsync<NTHR>();
     }
-}
-
-// The explicit Q = H_0 ... H_{K-1} [I_K; 0] (M x K) from the reflectors that team_qr
-// left in A (column-major, ld) and tau, through the compact WY form
-// H_0 ... H_{K-1} = I - V T V^H (Schreiber and Van Loan): T is upper triangular with
-// T[j][j] = tau_j and T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^H v_j), so
-// Q = [I_K; 0] - V Z with Z = T V_1^H (V_1 = the top K x K block of V).  A is read
-// only; Q(r, c) is handed to store(r, c, value).  W: 2 K (K + 1) complex scratch.
-// Same product as team_form_q, in K + 4 team barriers instead of 2 K.
-template <int NTHR, typename T, class ST>
-__device__ void team_form_q_wy(const cx<T>* A, int ld, int M, int K, const cx<T>* tau, cx<T>* W, int tid,
-                               ST store) {
-    const int KS = K + 1;
-    cx<T>* Y = W;             // Y[i][j] = v_i^H v_j (i < j); later Z
-    cx<T>* Tm = W + K * KS;   // T
-    team_for_2d<NTHR>(K, K, tid, [&](int i, int j) {
-        if (i >= j) return;
-        cx<T> acc = conj(A[i * ld + j]);               // row j: V[j][i] * V[j][j], V[j][j] = 1
-        for (int r = j + 1; r < M; ++r) cmac_cj(acc, A[i * ld + r], A[j * ld + r]);
-        Y[i * KS + j] = acc;
-    });
-    tsync<NTHR>();
-    for (int j = 0; j < K; ++j) {
-        for (int i = tid; i < j; i += NTHR) {
-            cx<T> acc = czero<T>();
-            for (int k = i; k < j; ++k) cmac(acc, Tm[i * KS + k], Y[k * KS + j]);
-            Tm[i * KS + j] = czero<T>() - tau[j] * acc;
-        }
-        if (tid == 0) Tm[j * KS + j] = tau[j];
-        tsync<NTHR>();
-    }
-    // Z[i][c] = sum_{k=i..c} T[i][k] conj(V[c][k]) (zero for i > c), over Y's storage
-    team_for_2d<NTHR>(K, K, tid, [&](int i, int c) {
-        cx<T> acc = czero<T>();
-        if (i <= c) {
-            for (int k = i; k < c; ++k) cmac(acc, Tm[i * KS + k], conj(A[k * ld + c]));
-            acc = acc + Tm[i * KS + c];
-        }
-        Y[i * KS + c] = acc;
-    });
-    tsync<NTHR>();
-    // Q[r][c] = delta_rc - sum_{i <= min(r, c)} V[r][i] Z[i][c]
-    team_for_2d<NTHR>(M, K, tid, [&](int r, int c) {
-        const int top = r < c ? r : c;
-        cx<T> acc = czero<T>();
-        for (int i = 0; i < top; ++i) cmac(acc, A[i * ld + r], Y[i * KS + c]);
-        if (top == r) acc = acc + Y[r * KS + c];        // V[r][r] = 1 (r <= c < K)
-        else cmac(acc, A[top * ld + r], Y[top * KS + c]);
-        store(r, c, mk<T>((r == c ? T(1) : T(0)) - acc.re, -acc.im));
-    });
 }
 
 // Cyclic parallel (round-robin) Jacobi eigensolver for the K x K Hermitian matrix G
