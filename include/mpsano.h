@@ -170,7 +170,8 @@ typedef struct {
 /* Floats of device workspace that ano_train_step needs (-1 on bad sizes).  Layout,
  * in floats: features [n_images][m] at 0, then d L / d y_hat [n_images][out_dim],
  * d L / d q [n_images][m], the gradient [m*16 + out_dim*m + out_dim] of
- * (abd, W, b) in that order, then FP64 scratch. */
+ * (abd, W, b) in that order, then FP64 scratch and the split-K partial tiles of
+ * the two backward GEMMs. */
 int64_t ano_train_workspace_floats(int64_t n_images, int32_t m, int32_t out_dim);
 
 /* One full-batch training step, asynchronous on `stream`:

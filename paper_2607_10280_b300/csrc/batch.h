@@ -79,9 +79,13 @@ void timing_end(mps_batch* b);
 int smem_optin_limit();
 // Y(r, o) = sum_k X(r, k) W(o, k) + bias[o] on the tensor cores (strided operands,
 // see linear_tc_kernel); failures of its bounded waits surface through ano_status.
+// With partial != NULL and k_split > 1, K is split over linear_tc_splits(K, k_split)
+// CTAs per tile whose partial tiles (planes of rows x out_dim floats in `partial`)
+// are then summed in a fixed order.
 mps_status launch_linear_tc(const float* X, int64_t xs_r, int64_t xs_k, int rows, int K, const float* W,
                             int64_t ws_o, int64_t ws_k, const float* bias, int out_dim, float* Y,
-                            cudaStream_t s);
+                            cudaStream_t s, int k_split = 1, float* partial = nullptr);
+int linear_tc_splits(int K, int k_split);
 
 mps_status launch_circuit_fp64_t0(mps_batch* b, int chi_tpl, const double* px, int ansatz);
 mps_status launch_circuit_fp64_t1(mps_batch* b, int chi_tpl, const double* px, int ansatz);

@@ -1,6 +1,7 @@
 // Linear reconstruction layer y = W q + b (Eq. 6) on the tcgen05 tensor cores.
 //
-// Y[r][o] = sum_k X(r, k) W(o, k) + bias[o], FP32 in and out, with X(r, k) at
+// Y[r][o] = sum_k X(r, k) W(o, k) + bias[o], FP32 in and out (optionally split over
+// K: plane z of Y gets the sum over K chunks [z cps, (z+1) cps)), with X(r, k) at
 // X[r * xs_r + k * xs_k] and W(o, k) at W[o * ws_o + k * ws_k] (so transposed
 // operands of the backward pass need no copy).  TF32 alone has an
 // 11-bit significand, so each operand is split as x = x_hi + x_lo with
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict_
                                                         int rows, int K, const float* __restrict__ W,
                                                         int64_t ws_o, int64_t ws_k,
                                                         const float* __restrict__ bias, int out_dim,
-                                                        float* __restrict__ Y, int* status) {
+                                                        float* __restrict__ Y, int chunks_per_split, int* status) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* a_hi = tc_smem;
     unsigned char* a_lo = a_hi + TC_PANEL;
@@ -100,10 +101,16 @@ __global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict_
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
+    // split K: CTA z of the grid's z dimension takes K chunks [z cps, (z+1) cps) and
+    // writes its partial sums to plane z of Y (rows x out_dim each)
+    const int chunks = (K + TC_KC - 1) / TC_KC;
+    const int ch0 = blockIdx.z * chunks_per_split;
+    const int ch1 = ch0 + chunks_per_split < chunks ? ch0 + chunks_per_split : chunks;
+    Y += (size_t)blockIdx.z * rows * out_dim;
     bool ok = true;
     int failed_parity = 0;
-    const int chunks = (K + TC_KC - 1) / TC_KC;
-    for (int ch = 0; ch < chunks && ok; ++ch) {
+    for (int ch = ch0; ch < ch1 && ok; ++ch) {
+        const int lc = ch - ch0;   // local chunk: mbarrier phase and accumulate flag
         // stage the hi/lo panels of this K chunk (zero outside the matrices); consecutive
         // threads walk the operand's unit-stride index so the loads coalesce
         const bool x_kfast = xs_k == 1, w_kfast = ws_k == 1;
@@ -135,7 +142,7 @@ __global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict_
                 const uint32_t koff = ks * 2 * TC_LBO;   // 8 TF32 = two core matrices along K
                 const uint64_t dah = tc_smem_desc(smem_u32(a_hi) + koff), dal = tc_smem_desc(smem_u32(a_lo) + koff);
                 const uint64_t dbh = tc_smem_desc(smem_u32(b_hi) + koff), dbl = tc_smem_desc(smem_u32(b_lo) + koff);
-                const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
+                const uint32_t acc0 = (lc > 0 || ks > 0) ? 1u : 0u;
                 // D (+)= A_lo B_hi, then + A_hi B_lo, then + A_hi B_hi
                 asm volatile(
                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -155,8 +162,8 @@ __global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict_
         }
         // every thread waits for the MMAs of this chunk before the panels are reused;
         // the outcome is made uniform over the CTA (the epilogue is warp-collective)
-        ok = __syncthreads_and(tc_mbar_wait(smem_u32(mbar), (uint32_t)(ch & 1)) ? 1 : 0) != 0;
-        failed_parity = ch & 1;
+        ok = __syncthreads_and(tc_mbar_wait(smem_u32(mbar), (uint32_t)(lc & 1)) ? 1 : 0) != 0;
+        failed_parity = lc & 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
     }
     if (!ok) {

@@ -34,9 +34,28 @@ namespace mpsano {
 
 void count_launch() { g_launches.fetch_add(1); }
 
+namespace {
+// Y[i] = sum_z P[z][i] (+ bias[i % out_dim]), planes summed in order z = 0, 1, ...
+__global__ void sum_planes_kernel(const float* __restrict__ P, int planes, int64_t n, int out_dim,
+                                  const float* __restrict__ bias, float* __restrict__ Y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = bias ? bias[i % out_dim] : 0.f;
+    for (int z = 0; z < planes; ++z) s += P[(int64_t)z * n + i];
+    Y[i] = s;
+}
+}  // namespace
+
+int linear_tc_splits(int K, int k_split) {
+    const int chunks = (K + TC_KC - 1) / TC_KC;
+    const int ks = std::max(1, std::min(k_split, chunks));
+    const int cps = (chunks + ks - 1) / ks;
+    return std::max(1, (chunks + cps - 1) / cps);
+}
+
 mps_status launch_linear_tc(const float* X, int64_t xs_r, int64_t xs_k, int rows, int K, const float* W,
                             int64_t ws_o, int64_t ws_k, const float* bias, int out_dim, float* Y,
-                            cudaStream_t s) {
+                            cudaStream_t s, int k_split, float* partial) {
     static int attr_dev = -1;
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -47,10 +66,22 @@ mps_status launch_linear_tc(const float* X, int64_t xs_r, int64_t xs_k, int rows
     }
     int* st = nullptr;
     CUDA_TRY(cudaGetSymbolAddress((void**)&st, g_epilogue_status));
-    dim3 grid((out_dim + TC_N - 1) / TC_N, (unsigned)((rows + TC_M - 1) / TC_M));
-    linear_tc_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(X, xs_r, xs_k, rows, K, W, ws_o, ws_k, bias, out_dim, Y, st);
+    const int chunks = (K + TC_KC - 1) / TC_KC;
+    const int ks = std::max(1, std::min(partial ? k_split : 1, chunks));
+    const int cps = (chunks + ks - 1) / ks;          // every plane gets >= 1 chunk
+    const int planes = (chunks + cps - 1) / cps;
+    dim3 grid((out_dim + TC_N - 1) / TC_N, (unsigned)((rows + TC_M - 1) / TC_M), (unsigned)planes);
+    linear_tc_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(X, xs_r, xs_k, rows, K, W, ws_o, ws_k,
+                                                      planes > 1 ? nullptr : bias, out_dim,
+                                                      planes > 1 ? partial : Y, std::max(cps, 1), st);
     CUDA_TRY(cudaGetLastError());
     count_launch();
+    if (planes > 1) {
+        const int64_t n = (int64_t)rows * out_dim;
+        sum_planes_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(partial, planes, n, out_dim, bias, Y);
+        CUDA_TRY(cudaGetLastError());
+        count_launch();
+    }
     return MPS_OK;
 }
 

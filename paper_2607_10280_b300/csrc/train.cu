@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "batch.h"
@@ -48,21 +49,32 @@ __global__ void __launch_bounds__(RED_THREADS) mse_grad_kernel(float* __restrict
     }
 }
 
+// one warp: lane l sums partials l, l + 32, ...; the lane sums combine in a fixed
+// butterfly order
 __global__ void loss_final_kernel(const double* __restrict__ partial, int n, double factor, double* __restrict__ loss) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += partial[i];
-        *loss = factor * s;
-    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += partial[i];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *loss = factor * s;
 }
 
-// g_b[o] = sum_i g_y[i][o]
-__global__ void bias_grad_kernel(const float* __restrict__ gy, int64_t B, int O, float* __restrict__ gb) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= O) return;
+// g_b[o] = sum_i g_y[i][o]: block of 32 x 8 threads per 32 outputs, 8 row slices
+// summed in FP64 and combined in a fixed order.
+__global__ void __launch_bounds__(256) bias_grad_kernel(const float* __restrict__ gy, int64_t B, int O,
+                                                        float* __restrict__ gb) {
+    __shared__ double part[8][33];
+    const int c = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const int o = blockIdx.x * 32 + c;
     double s = 0.0;
-    for (int64_t i = 0; i < B; ++i) s += gy[i * O + o];
-    gb[o] = (float)s;
+    if (o < O)
+        for (int64_t i = slice; i < B; i += 8) s += gy[i * O + o];
+    part[slice][c] = s;
+    __syncthreads();
+    if (slice == 0 && o < O) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += part[k][c];
+        gb[o] = (float)t;
+    }
 }
 
 // One block per pair q: g_c[q][alpha] = sum_i g_f[i][q] P[i][q][alpha] (16 partial
@@ -119,8 +131,10 @@ __global__ void adam_kernel(float* __restrict__ abd, float* __restrict__ W, floa
     *theta -= lr * (m / c1) / (sqrtf(v / c2) + eps);
 }
 
+constexpr int GEMM_SPLIT = 16;     // K splits of the two backward GEMMs (K = out_dim, n_images)
+
 struct TrainLayout {
-    int64_t feats, gy, gf, grads, partial, total;   // float offsets
+    int64_t feats, gy, gf, grads, partial, planes, total;   // float offsets
     int64_t n_abd, n_w, n_b;
 };
 
@@ -134,7 +148,8 @@ TrainLayout train_layout(int64_t B, int m, int O) {
     t.gf = t.gy + B * O;
     t.grads = t.gf + B * m;
     t.partial = (t.grads + t.n_abd + t.n_w + t.n_b + 1) & ~int64_t(1);   // 8-byte aligned doubles
-    t.total = t.partial + 2 * LOSS_BLOCKS;
+    t.planes = t.partial + 2 * LOSS_BLOCKS;                               // split-K partial tiles
+    t.total = t.planes + GEMM_SPLIT * std::max(B * m, (int64_t)O * m);
     return t;
 }
 
@@ -184,12 +199,12 @@ mps_status ano_train_step(const void* pauli, int32_t pauli_f64, int64_t n_images
     CUDA_TRY(cudaGetLastError());
     count_launch();
     // g_f[i][q] = sum_o g_y[i][o] W[o][q]      (X = g_y, "W"(q, o) = W[o][q])
-    st = launch_linear_tc(gy, O, 1, B, O, W, 1, m, nullptr, m, gf, s);
+    st = launch_linear_tc(gy, O, 1, B, O, W, 1, m, nullptr, m, gf, s, GEMM_SPLIT, workspace + t.planes);
     if (st != MPS_OK) return st;
     // g_W[o][q] = sum_i g_y[i][o] f[i][q]       (X(o, i) = g_y[i][o], "W"(q, i) = f[i][q])
-    st = launch_linear_tc(gy, 1, O, O, B, feats, 1, m, nullptr, m, g_w, s);
+    st = launch_linear_tc(gy, 1, O, O, B, feats, 1, m, nullptr, m, g_w, s, GEMM_SPLIT, workspace + t.planes);
     if (st != MPS_OK) return st;
-    bias_grad_kernel<<<(O + 127) / 128, 128, 0, s>>>(gy, n_images, O, g_b);
+    bias_grad_kernel<<<(O + 31) / 32, 256, 0, s>>>(gy, n_images, O, g_b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
     if (pauli_f64)
