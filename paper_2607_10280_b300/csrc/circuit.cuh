@@ -199,6 +199,18 @@ struct CircuitTeam {
         tsync<NTHR>();
     }
 
+    // Householder QR of theta (M x N, N <= M) in place; R (N x N) reshaped (N, 2, Dr)
+    // becomes the new centre; the reflectors and tau stay in th / tau.
+    __device__ void qr_to_cur(int M, int N, int Dr) {
+        team_qr<NTHR>(th, LDM, M, N, tau, red, lane);
+        team_for_2d<NTHR>(N, N, lane, [&](int i, int c) {
+            const int t = c >= Dr ? 1 : 0, r = c - t * Dr;
+            const cx<TQ> v = (i <= c) ? th[c * LDM + i] : czero<TQ>();
+            cur[(2 * i + t) * CS + r] = cvt<T>(v);
+        });
+        tsync<NTHR>();
+    }
+
     // The explicit Q (M x K) of the reflectors in th / tau, stored as site k.
     __device__ void q_to_site(int k, int M, int K) {
         cx<T>* dst = site_ptr(k);
@@ -221,13 +233,7 @@ struct CircuitTeam {
         if (mn <= cap) {
             if (N <= M) {
                 // Householder QR: A_k = Q (M x N), cur = R (N x N) reshaped (N, 2, Dr)
-                team_qr<NTHR>(th, LDM, M, N, tau, red, lane);
-                team_for_2d<NTHR>(N, N, lane, [&](int i, int c) {
-                    const int t = c >= Dr ? 1 : 0, r = c - t * Dr;
-                    const cx<TQ> v = (i <= c) ? th[c * LDM + i] : czero<TQ>();
-                    cur[(2 * i + t) * CS + r] = cvt<T>(v);
-                });
-                tsync<NTHR>();
+                qr_to_cur(M, N, Dr);
                 q_to_site(k, M, N);
                 return N;
             }
@@ -652,9 +658,14 @@ struct WaveBuf {
     static constexpr int CS = CL + 1, LDM = 2 * CL + 1;
     static constexpr size_t off_cur = 0;
     static constexpr size_t off_nxt = off_cur + sizeof(cx<T>) * 2 * CL * CS;
+    // two theta / reflector buffers and two tau buffers (alternating super-steps), and
+    // per buffer a record (k, M, N, Q pending)
+    static constexpr size_t TH_BYTES = (sizeof(cx<TQ>) * 2 * CLR * LDM + 15) & ~size_t(15);
+    static constexpr size_t TAU_BYTES = (sizeof(cx<TQ>) * 2 * CLR + 15) & ~size_t(15);
     static constexpr size_t off_th = (off_nxt + sizeof(cx<T>) * 2 * CLR * CS + 15) & ~size_t(15);
-    static constexpr size_t off_tau = off_th + sizeof(cx<TQ>) * 2 * CLR * LDM;
-    static constexpr size_t bytes = (off_tau + sizeof(cx<TQ>) * 2 * CLR + 15) & ~size_t(15);
+    static constexpr size_t off_tau = off_th + 2 * TH_BYTES;
+    static constexpr size_t off_rec = off_tau + 2 * TAU_BYTES;
+    static constexpr size_t bytes = off_rec + 8 * sizeof(int);
 };
 
 template <int CHI, int J> struct WaveDims {
@@ -677,15 +688,16 @@ struct WaveLayout {
 // One step (bond k) of layer `layer` for the warp that owns it.  Returns false
 // (after raising the status) when a bond exceeds the layer's buffers.
 template <typename T, typename TQ, int CL, int CLR>
-__device__ bool wave_step(unsigned char* buf, int* bd, int k, int n, int ld, cx<T>* sites,
-                          const cx<T>* gates, int gn, int layer, int lane, int* status) {
+__device__ bool wave_step(unsigned char* buf, int t, int* bd, int k, int n, int ld, cx<T>* sites,
+                          const cx<T>* gates, int gn, int layer, bool defer_q, int lane, int* status) {
     using B = WaveBuf<T, TQ, CL, CLR>;
     constexpr int CS = B::CS;
     CircuitTeam<T, TQ, CL, false, 32> w;
     w.cur = reinterpret_cast<cx<T>*>(buf + B::off_cur);
     w.nxt = reinterpret_cast<cx<T>*>(buf + B::off_nxt);
-    w.th = reinterpret_cast<cx<TQ>*>(buf + B::off_th);
-    w.tau = reinterpret_cast<cx<TQ>*>(buf + B::off_tau);
+    w.th = reinterpret_cast<cx<TQ>*>(buf + B::off_th + (t & 1) * B::TH_BYTES);
+    w.tau = reinterpret_cast<cx<TQ>*>(buf + B::off_tau + (t & 1) * B::TAU_BYTES);
+    int* rec = reinterpret_cast<int*>(buf + B::off_rec) + 4 * (t & 1);
     w.rb = nullptr; w.G = nullptr; w.V = nullptr; w.taud = nullptr; w.lam = nullptr; w.ord = nullptr;
     w.red = nullptr; w.flag = nullptr;
     w.bd = bd;
@@ -717,13 +729,36 @@ __device__ bool wave_step(unsigned char* buf, int* bd, int k, int n, int ld, cx<
     load_site<T, CS, 32>(w.nxt, w.site_ptr(k + 1), ld, Dm, Dr, &g, lane);
     __syncwarp();
     w.form_theta(Dl, Dm, Dr, true);
-    w.split(k, Dl, Dr, 1 << 30, true);   // exact: no ladder step exceeds its rank bound
+    if (defer_q && 2 * Dr <= 2 * Dl) {
+        // QR only; warp 0 forms this site's Q from the reflectors next super-step
+        w.qr_to_cur(2 * Dl, 2 * Dr, Dr);
+        if (lane == 0) { rec[0] = k; rec[1] = 2 * Dl; rec[2] = 2 * Dr; rec[3] = 1; }
+    } else {
+        w.split(k, Dl, Dr, 1 << 30, true);   // exact: no ladder step exceeds its rank bound
+    }
     if (k == n - 2) {
         store_site<T, CS, 32>(w.site_ptr(n - 1), w.cur, ld, nb, Dr, lane);
     }
     __syncwarp();
     if (lane == 0) bd[k + 1] = nb;
     return true;
+}
+
+// The Q factor a layer's warp left pending in reflector buffer `slot` (see
+// wave_step), formed and stored by warp 0.
+template <typename T, typename TQ, int CL, int CLR>
+__device__ void wave_deferred_q(unsigned char* buf, int slot, int ld, cx<T>* sites, int lane) {
+    using B = WaveBuf<T, TQ, CL, CLR>;
+    int* rec = reinterpret_cast<int*>(buf + B::off_rec) + 4 * slot;
+    if (!rec[3]) return;
+    CircuitTeam<T, TQ, CL, false, 32> w;
+    w.th = reinterpret_cast<cx<TQ>*>(buf + B::off_th + slot * B::TH_BYTES);
+    w.tau = reinterpret_cast<cx<TQ>*>(buf + B::off_tau + slot * B::TAU_BYTES);
+    w.lane = lane;
+    w.ld = ld;
+    w.sites = sites;
+    w.q_to_site(rec[0], rec[1], rec[2]);
+    if (lane == 0) rec[3] = 0;
 }
 
 template <typename T, typename TQ, int CHI>
@@ -752,22 +787,43 @@ __global__ void __launch_bounds__(32 * WAVE_LAYERS, 8) circuit_wave_kernel(
         s[0] = mk<T>(T(cs), T(0));
         s[ld] = mk<T>(T(sn), T(0));
     }
-    __syncthreads();
     const int L = mt.L < WAVE_LAYERS ? mt.L : WAVE_LAYERS;
-    const int supersteps = (L > 0 && n > 1) ? (n - 1) + 2 * (L - 1) : 0;
+    const int last = L - 1;
+    // the last layer's sites feed no later layer: its Q factors are formed by warp 0
+    // (the cheapest layer) one super-step later, off the last layer's critical path
+    const bool defer = L >= 2;
+    if (threadIdx.x < 8) {
+        reinterpret_cast<int*>(smem_raw + Lay::off_w0 + WaveBuf<T, TQ, WaveDims<CHI, 0>::CL, WaveDims<CHI, 0>::CLR>::off_rec)[threadIdx.x] = 0;
+        reinterpret_cast<int*>(smem_raw + Lay::off_w1 + WaveBuf<T, TQ, WaveDims<CHI, 1>::CL, WaveDims<CHI, 1>::CLR>::off_rec)[threadIdx.x] = 0;
+        reinterpret_cast<int*>(smem_raw + Lay::off_w2 + WaveBuf<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>::off_rec)[threadIdx.x] = 0;
+        reinterpret_cast<int*>(smem_raw + Lay::off_w3 + WaveBuf<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>::off_rec)[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int supersteps = (L > 0 && n > 1) ? (n - 1) + 2 * (L - 1) + (defer ? 1 : 0) : 0;
     for (int t = 0; t < supersteps; ++t) {
         const int k = t - 2 * warp;
         bool ok = true;
         if (warp < L && k >= 0 && k < n - 1) {
+            const bool dq = defer && warp == last;
             switch (warp) {
                 case 0: ok = wave_step<T, TQ, WaveDims<CHI, 0>::CL, WaveDims<CHI, 0>::CLR>(
-                            smem_raw + Lay::off_w0, bd, k, n, ld, sites, gates, gn, 0, lane, status); break;
+                            smem_raw + Lay::off_w0, t, bd, k, n, ld, sites, gates, gn, 0, dq, lane, status); break;
                 case 1: ok = wave_step<T, TQ, WaveDims<CHI, 1>::CL, WaveDims<CHI, 1>::CLR>(
-                            smem_raw + Lay::off_w1, bd, k, n, ld, sites, gates, gn, 1, lane, status); break;
+                            smem_raw + Lay::off_w1, t, bd, k, n, ld, sites, gates, gn, 1, dq, lane, status); break;
                 case 2: ok = wave_step<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>(
-                            smem_raw + Lay::off_w2, bd, k, n, ld, sites, gates, gn, 2, lane, status); break;
+                            smem_raw + Lay::off_w2, t, bd, k, n, ld, sites, gates, gn, 2, dq, lane, status); break;
                 default: ok = wave_step<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>(
-                            smem_raw + Lay::off_w3, bd, k, n, ld, sites, gates, gn, 3, lane, status); break;
+                            smem_raw + Lay::off_w3, t, bd, k, n, ld, sites, gates, gn, 3, dq, lane, status); break;
+            }
+        }
+        if (defer && warp == 0 && t >= 1) {
+            switch (last) {
+                case 1: wave_deferred_q<T, TQ, WaveDims<CHI, 1>::CL, WaveDims<CHI, 1>::CLR>(
+                            smem_raw + Lay::off_w1, (t - 1) & 1, ld, sites, lane); break;
+                case 2: wave_deferred_q<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>(
+                            smem_raw + Lay::off_w2, (t - 1) & 1, ld, sites, lane); break;
+                default: wave_deferred_q<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>(
+                            smem_raw + Lay::off_w3, (t - 1) & 1, ld, sites, lane); break;
             }
         }
         // global writes of this super-step become visible to the other warps here
