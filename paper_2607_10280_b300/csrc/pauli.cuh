@@ -9,7 +9,7 @@
 //
 //   pauli_kernel  one warp per (image, grid column c).  The warp walks column c
 //                 from the bottom row up.  At a column site j it
-//                   - closes the vertical pair (j, j+p) with the three closing
+//                   - closes the vertical pair (j, j+p) with the closing
 //                     matrices C_b carried up from site j+p,
 //                   - builds the closings of site j as a right site,
 //                       C_b^{(j)} = sum_{s,s'} P_b[s][s'] conj(A_j^s) R_j A_j^{s'T},
@@ -19,6 +19,11 @@
 //                 A left site i contributes E_a[r][r'] = sum_{l,s,s'} conj(A[l,s,r])
 //                 P_a[s][s'] A[l,s',r'] and <P_a (x) P_b> = <E_a, C_b> / <psi|psi>,
 //                 <P_a> = <E_a, R_i> / <psi|psi> (elementwise product summed).
+//                 The closings are Hermitian and the transfer is complex-linear
+//                 and keeps Hermiticity, so C_X and C_Y travel as the single
+//                 matrix M = C_X + i C_Y (= 2 G01: X + iY is twice the raising
+//                 operator), split back at a closing as C_X = (M + M^H)/2,
+//                 C_Y = (M - M^H)/(2i): two carried matrices instead of three.
 //
 // Every contraction is a small complex GEMM done by a team of UW warps (one
 // (image, column) unit per CTA) with a register tile of TM x TN outputs per thread;
@@ -37,11 +42,11 @@ struct PauliLayout {
     static constexpr int MAT = CHI * CS;
     static constexpr int ZS = 2 * CHI + 1;
     static constexpr int SROWS = 3 * CHI;
-    // A (2 MAT), R (1 MAT), C (3 MAT), S (3 CHI rows x ZS); with diagonal pairs also
-    // Cd (3 MAT, the carried closings one site further)
-    static constexpr int ELEMS = 6 * MAT + SROWS * ZS;
+    // A (2 MAT), R (1 MAT), C (2 MAT: M = C_X + i C_Y, C_Z), S (3 CHI rows x ZS);
+    // with diagonal pairs also Cd (2 MAT, the carried closings one site further)
+    static constexpr int ELEMS = 5 * MAT + SROWS * ZS;
     static constexpr size_t bytes = sizeof(cx<T>) * ELEMS;
-    static constexpr size_t elems(bool diag) { return ELEMS + (diag ? 3 * MAT : 0); }
+    static constexpr size_t elems(bool diag) { return ELEMS + (diag ? 2 * MAT : 0); }
     // plus the cross-warp reduction buffer of a UW-warp team
     static constexpr size_t team_bytes(int uw, bool diag = false) {
         return sizeof(cx<T>) * elems(diag) + sizeof(T) * 12 * uw;
@@ -176,7 +181,8 @@ __device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, in
 }
 
 // <E_a, Y> for a = X, Y, Z (from the blocks F_{ss'} in S) and Y in {C_X, C_Y, C_Z, R}:
-// out[4(a-1) + y].  C may be null (then only the R column is formed).  Warp 0 alone
+// out[4(a-1) + y], with C_X, C_Y unpacked from M = C[0] and C_Z = C[MAT].  C may be
+// null (then only the R column is formed).  Warp 0 alone
 // forms the sums, so the summation order (and every bit of the result) does not
 // depend on the team size; the other warps read the sums from red.
 template <typename T, int CHI, int NTHR>
@@ -199,8 +205,11 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
             cx<T> y[4];
             y[3] = R[r * CS + rp];
             if (C) {
-#pragma unroll
-                for (int b = 0; b < 3; ++b) y[b] = C[b * MAT + r * CS + rp];
+                const cx<T> m1 = C[r * CS + rp], m2 = conj(C[rp * CS + r]);
+                const cx<T> u = m1 + m2, v = m1 - m2;
+                y[0] = mk<T>(T(0.5) * u.re, T(0.5) * u.im);       // (M + M^H) / 2
+                y[1] = mk<T>(T(0.5) * v.im, T(-0.5) * v.re);      // (M - M^H) / (2i)
+                y[2] = C[MAT + r * CS + rp];
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -225,7 +234,8 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
 
 // Closings of a right site A (Dl x 2 x Dr) with right environment R:
 //   G[2l+s][2l'+s'] = sum_r conj(A[2l+s][r]) (R A^{s'T})[r][l'],
-//   C_X = G01 + G10, C_Y = i (G10 - G01), C_Z = G00 - G11  (Dl x Dl each, into C).
+//   C_X = G01 + G10, C_Y = i (G10 - G01), C_Z = G00 - G11  (Dl x Dl each); into C go
+//   M = C_X + i C_Y = 2 G01 and C_Z.
 template <typename T, int CHI, int NTHR>
 __device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* R, cx<T>* C, cx<T>* S,
                                                int Dl, int Dr, int lane) {
@@ -241,11 +251,9 @@ __device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* R, c
     team_sync();
     team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int l, int lp) {
         const cx<T> g00 = G[(2 * l) * ZS + 2 * lp], g01 = G[(2 * l) * ZS + 2 * lp + 1];
-        const cx<T> g10 = G[(2 * l + 1) * ZS + 2 * lp], g11 = G[(2 * l + 1) * ZS + 2 * lp + 1];
-        const cx<T> d = g10 - g01;
-        C[l * CS + lp] = g01 + g10;
-        C[MAT + l * CS + lp] = mk<T>(-d.im, d.re);
-        C[2 * MAT + l * CS + lp] = g00 - g11;
+        const cx<T> g11 = G[(2 * l + 1) * ZS + 2 * lp + 1];
+        C[l * CS + lp] = g01 + g01;
+        C[MAT + l * CS + lp] = g00 - g11;
     });
     team_sync();
 }
@@ -313,12 +321,12 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8) / (sizeof(T) == 8 ?
     if (unit >= n_units) return;
     const int img = unit_image[2 * unit], c = unit_image[2 * unit + 1];
     cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
-    T* red = reinterpret_cast<T*>(base + Lay::ELEMS + (diag ? 3 * MAT : 0));
+    T* red = reinterpret_cast<T*>(base + Lay::ELEMS + (diag ? 2 * MAT : 0));
     cx<T>* A = base;               // 2 MAT
     cx<T>* R = base + 2 * MAT;
-    cx<T>* C = base + 3 * MAT;     // 3 MAT: C_X, C_Y, C_Z
-    cx<T>* S = base + 6 * MAT;     // GEMM scratch
-    cx<T>* Cd = base + Lay::ELEMS; // 3 MAT (diagonal pairs only)
+    cx<T>* C = base + 3 * MAT;     // 2 MAT: M = C_X + i C_Y, C_Z
+    cx<T>* S = base + 5 * MAT;     // GEMM scratch
+    cx<T>* Cd = base + Lay::ELEMS; // 2 MAT (diagonal pairs only)
     const ImageMeta mt = meta[img];
     const int p = mt.p, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
@@ -361,9 +369,9 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8) / (sizeof(T) == 8 ?
         // diagonal (row, c-1)-(row+1, c): the closings carried from j+p, one site further
         const bool has_dd = diag && row < p - 1 && c >= 1;
         if (has_dd) {
-            for (int o = lane; o < 3 * MAT; o += NTHR) Cd[o] = C[o];
+            for (int o = lane; o < 2 * MAT; o += NTHR) Cd[o] = C[o];
             team_sync();
-            transfer<T, CHI, 3, NTHR>(Cd, A, S, Dl, Dr, lane);
+            transfer<T, CHI, 2, NTHR>(Cd, A, S, Dl, Dr, lane);
         }
         // closings of site j as a right site
         right_closings<T, CHI, NTHR>(A, R, C, S, Dl, Dr, lane);
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8) / (sizeof(T) == 8 ?
             team_sync();
         }
         if (row == 0) break;
-        // carry C_X, C_Y, C_Z through sites j-1 .. j-p+1
+        // carry M and C_Z through sites j-1 .. j-p+1
         for (int k = k0; k > j - p; --k) {
             const int Dlk = bd[k], Drk = bd[k + 1];
             if (k != k0) {
@@ -410,7 +418,7 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8) / (sizeof(T) == 8 ?
                 write_pair(base_da + (row - 1) * (p - 1) + c, single_k, single_j, dd);
                 team_sync();
             }
-            transfer<T, CHI, 3, NTHR>(C, A, S, Dlk, Drk, lane);
+            transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane);
         }
     }
 }

@@ -124,7 +124,8 @@ def pauli_flops(p: int, bonds) -> float:
             if row == 0:
                 break
             for k in range(k0, j - p, -1):
-                f += 3 * transfer(bonds[k], bonds[k + 1])
+                # two carried matrices: M = C_X + i C_Y and C_Z
+                f += 2 * transfer(bonds[k], bonds[k + 1])
     return f
 
 
