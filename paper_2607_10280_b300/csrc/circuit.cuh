@@ -55,7 +55,8 @@ struct CircuitLayout {
     static constexpr size_t off_cn = off_bd + sizeof(int) * (MAX_QUBITS + 1);   // CNOTs per cut
     static constexpr size_t off_perm = off_cn + sizeof(int) * (MAX_QUBITS + 1);  // pivoted QR
     static constexpr size_t off_cnorm = (off_perm + sizeof(int) * K + 15) & ~size_t(15);
-    static constexpr size_t off_gram = (off_cnorm + sizeof(TQ) * K + 15) & ~size_t(15);
+    static constexpr size_t off_cz = off_cnorm + sizeof(TQ) * K;                  // zero rows of cur
+    static constexpr size_t off_gram = (off_cz + sizeof(int) + 15) & ~size_t(15);
     static constexpr size_t off_vec = off_gram + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_taud = off_vec + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
     static constexpr size_t off_lam = off_taud + (TRUNC ? sizeof(cx<double>) * K : 0);
@@ -162,6 +163,12 @@ struct CircuitTeam {
     int* cn;      // cn[k] = CNOTs applied so far across the cut left of site k
     int* perm;    // column order of a pivoted QR
     TQ* cnorm;    // its column norms
+    // cur = R of a QR split is upper triangular, so its rows (l, s = 0) with l >= D_m
+    // of the next step are zero: *czp holds that D_m (NOZ: no known zero rows).  zr:
+    // rows (l, 0), l >= zr, left out of this step's theta (zr = Dl: none).
+    static constexpr int NOZ = 1 << 30;
+    int* czp;
+    int zr;
     cx<double>* G;
     cx<double>* V;
     cx<double>* taud;
@@ -178,9 +185,17 @@ struct CircuitTeam {
     __device__ cx<T>* site_ptr(int k) const { return sites + (size_t)k * (2 * ld * ld); }
 
     // ---- theta = cur(Dl x 2 x Dm) nxt(Dm x 2 x Dr), CNOT(control = left) folded in ----
-    __device__ void form_theta(int Dl, int Dm, int Dr, bool cnot) {
-        const int M = 2 * Dl, N = 2 * Dr;
-        team_for_2d<NTHR>(M, N, lane, [&](int row, int c) {
+    // theta = cur nxt with the structurally zero rows of cur left out when
+    // allow_compact: compact row q is (l, s) = (q / 2, q % 2) for q < 2 zr, then
+    // (zr + q - 2 zr, 1); the QR of the compact theta needs 2 Dr <= Dl + zr rows.
+    __device__ void form_theta(int Dl, int Dm, int Dr, bool cnot, bool allow_compact = false) {
+        const int N = 2 * Dr;
+        int z = *czp < Dl ? *czp : Dl;
+        if (!(allow_compact && z < Dl && N <= Dl + z)) z = Dl;
+        zr = z;
+        const int M = Dl + z;
+        team_for_2d<NTHR>(M, N, lane, [&](int q, int c) {
+            const int row = q < 2 * z ? q : 2 * (q - z) + 1;    // (l, s) -> 2 l + s
             const int s = row & 1;
             int t = c >= Dr ? 1 : 0;
             const int r = c - t * Dr;
@@ -194,9 +209,10 @@ struct CircuitTeam {
                 cmac(acc1, a[m + 1], b[2 * (m + 1) * CS]);
             }
             if (m < Dm) cmac(acc0, a[m], b[2 * m * CS]);
-            th[c * LDM + row] = cvt<TQ>(acc0 + acc1);
+            th[c * LDM + q] = cvt<TQ>(acc0 + acc1);
         });
         tsync<NTHR>();
+        if (lane == 0) *czp = NOZ;   // consumed; a QR split sets it again
     }
 
     // Householder QR of theta (M x N, N <= M) in place; R (N x N) reshaped (N, 2, Dr)
@@ -211,11 +227,17 @@ struct CircuitTeam {
         tsync<NTHR>();
     }
 
-    // The explicit Q (M x K) of the reflectors in th / tau, stored as site k.
-    __device__ void q_to_site(int k, int M, int K) {
+    // The explicit Q (M x K) of the reflectors in th / tau, stored as site k; with
+    // compaction (z < Dl) compact row q goes to row 2 l + s and the left-out rows
+    // (l, 0), l >= z, are zero.
+    __device__ void q_to_site(int k, int M, int K, int Dl, int z) {
         cx<T>* dst = site_ptr(k);
         team_form_q<NTHR>(th, LDM, M, K, tau, lane);
-        team_for_2d<NTHR>(M, K, lane, [&](int row, int c) { dst[row * ld + c] = cvt<T>(th[c * LDM + row]); });
+        team_for_2d<NTHR>(M, K, lane, [&](int q, int c) {
+            const int row = q < 2 * z ? q : 2 * (q - z) + 1;
+            dst[row * ld + c] = cvt<T>(th[c * LDM + q]);
+        });
+        team_for_2d<NTHR>(Dl - z, K, lane, [&](int i, int c) { dst[2 * (z + i) * ld + c] = czero<T>(); });
         tsync<NTHR>();
     }
 
@@ -233,8 +255,9 @@ struct CircuitTeam {
         if (mn <= cap) {
             if (N <= M) {
                 // Householder QR: A_k = Q (M x N), cur = R (N x N) reshaped (N, 2, Dr)
-                qr_to_cur(M, N, Dr);
-                q_to_site(k, M, N);
+                qr_to_cur(Dl + zr, N, Dr);
+                if (lane == 0) *czp = Dr;
+                q_to_site(k, Dl + zr, N, Dl, zr);
                 return N;
             }
             // M < N: A_k = I_M, cur = theta reshaped (M, 2, Dr)
@@ -269,7 +292,7 @@ struct CircuitTeam {
             cur[(2 * i + t) * CS + r] = cvt<T>(v);
         });
         tsync<NTHR>();
-        q_to_site(k, M, cap);
+        q_to_site(k, M, cap, M / 2, M / 2);
         return cap;
     }
 
@@ -413,6 +436,7 @@ struct CircuitTeam {
     // cur <- R * nxt.  Returns the new bond min(2 Dl, Dm).
     __device__ int move_right(int k, int Dl, int Dm, int Dr) {
         const int M = 2 * Dl, N = Dm;
+        if (lane == 0) *czp = NOZ;
         team_for_2d<NTHR>(M, N, lane, [&](int row, int c) { th[c * LDM + row] = cvt<TQ>(cur[row * CS + c]); });
         tsync<NTHR>();
         team_qr<NTHR>(th, LDM, M, N, tau, red, lane);
@@ -437,6 +461,7 @@ struct CircuitTeam {
     // site k = Q, cur <- site_{k-1} L.  Returns the new bond min(Dl, 2 Dr).
     __device__ int move_left(int k, int Dlm, int Dl, int Dr) {
         const int M = 2 * Dr, N = Dl;   // A^H is (2 Dr) x Dl
+        if (lane == 0) *czp = NOZ;
         team_for_2d<NTHR>(N, M, lane, [&](int l, int sr) {
             const int s = sr >= Dr ? 1 : 0, r = sr - s * Dr;
             th[l * LDM + sr] = conj(cvt<TQ>(cur[(2 * l + s) * CS + r]));
@@ -516,6 +541,7 @@ __device__ bool run_pass(CircuitTeam<T, TQ, CHI, TRUNC, NTHR>& w, int first, int
     } else {
         // the centre stays where it is; the pass starts from the stored site `first`
         load_site<T, CS, NTHR>(w.cur, w.site_ptr(first), w.ld, bd[first], bd[first + 1], nullptr, lane);
+        if (lane == 0) *w.czp = CircuitTeam<T, TQ, CHI, TRUNC, NTHR>::NOZ;
         tsync<NTHR>();
     }
     if (gates_on_load) {
@@ -536,8 +562,9 @@ __device__ bool run_pass(CircuitTeam<T, TQ, CHI, TRUNC, NTHR>& w, int first, int
         if ((k - first) % stride == 0) {
             const int c = cn[k + 1] + 1;
             const int rb = rank_bound(c);
-            w.form_theta(Dl, Dm, Dr, true);
-            nb = w.split(k, Dl, Dr, rb < w.chi ? rb : w.chi, rb <= w.chi);
+            const int cap = rb < w.chi ? rb : w.chi;
+            w.form_theta(Dl, Dm, Dr, true, 2 * Dr <= cap);
+            nb = w.split(k, Dl, Dr, cap, rb <= w.chi);
             if (lane == 0) cn[k + 1] = c;
         } else {
             nb = w.move_right(k, Dl, Dm, Dr);
@@ -579,6 +606,8 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
     w.cn = reinterpret_cast<int*>(base + Lay::off_cn);
     w.perm = reinterpret_cast<int*>(base + Lay::off_perm);
     w.cnorm = reinterpret_cast<TQ*>(base + Lay::off_cnorm);
+    w.czp = reinterpret_cast<int*>(base + Lay::off_cz);
+    w.zr = 0;
     w.G = reinterpret_cast<cx<double>*>(base + Lay::off_gram);
     w.V = reinterpret_cast<cx<double>*>(base + Lay::off_vec);
     w.taud = reinterpret_cast<cx<double>*>(base + Lay::off_taud);
@@ -664,8 +693,8 @@ struct WaveBuf {
     static constexpr size_t TAU_BYTES = (sizeof(cx<TQ>) * 2 * CLR + 15) & ~size_t(15);
     static constexpr size_t off_th = (off_nxt + sizeof(cx<T>) * 2 * CLR * CS + 15) & ~size_t(15);
     static constexpr size_t off_tau = off_th + 2 * TH_BYTES;
-    static constexpr size_t off_rec = off_tau + 2 * TAU_BYTES;
-    static constexpr size_t bytes = off_rec + 8 * sizeof(int);
+    static constexpr size_t off_rec = off_tau + 2 * TAU_BYTES;   // 2 x (k, M, N, pending, zr, Dl), then cz
+    static constexpr size_t bytes = off_rec + 13 * sizeof(int);
 };
 
 template <int CHI, int J> struct WaveDims {
@@ -697,13 +726,15 @@ __device__ bool wave_step(unsigned char* buf, int t, int* bd, int k, int n, int 
     w.nxt = reinterpret_cast<cx<T>*>(buf + B::off_nxt);
     w.th = reinterpret_cast<cx<TQ>*>(buf + B::off_th + (t & 1) * B::TH_BYTES);
     w.tau = reinterpret_cast<cx<TQ>*>(buf + B::off_tau + (t & 1) * B::TAU_BYTES);
-    int* rec = reinterpret_cast<int*>(buf + B::off_rec) + 4 * (t & 1);
+    int* rec = reinterpret_cast<int*>(buf + B::off_rec) + 6 * (t & 1);
     w.rb = nullptr; w.G = nullptr; w.V = nullptr; w.taud = nullptr; w.lam = nullptr; w.ord = nullptr;
     w.red = nullptr; w.flag = nullptr;
     w.bd = bd;
     w.cn = nullptr;
     w.perm = nullptr;
     w.cnorm = nullptr;
+    w.czp = reinterpret_cast<int*>(buf + B::off_rec) + 12;
+    w.zr = 0;
     w.lane = lane;
     w.n = n;
     w.chi = CL;
@@ -719,6 +750,7 @@ __device__ bool wave_step(unsigned char* buf, int t, int* bd, int k, int n, int 
     }
     if (k == 0) {
         // the pass starts from the stored site 0 with the layer's one-qubit gate
+        if (lane == 0) *w.czp = CircuitTeam<T, TQ, CL, false, 32>::NOZ;
         load_site<T, CS, 32>(w.cur, w.site_ptr(0), ld, Dl, Dm, nullptr, lane);
         __syncwarp();
         const Gate1<T> g = table_gate<T>(gates, gn, 0, layer, 0, 0);
@@ -728,11 +760,14 @@ __device__ bool wave_step(unsigned char* buf, int t, int* bd, int k, int n, int 
     const Gate1<T> g = table_gate<T>(gates, gn, 0, layer, 0, k + 1);
     load_site<T, CS, 32>(w.nxt, w.site_ptr(k + 1), ld, Dm, Dr, &g, lane);
     __syncwarp();
-    w.form_theta(Dl, Dm, Dr, true);
+    w.form_theta(Dl, Dm, Dr, true, true);
     if (defer_q && 2 * Dr <= 2 * Dl) {
         // QR only; warp 0 forms this site's Q from the reflectors next super-step
-        w.qr_to_cur(2 * Dl, 2 * Dr, Dr);
-        if (lane == 0) { rec[0] = k; rec[1] = 2 * Dl; rec[2] = 2 * Dr; rec[3] = 1; }
+        w.qr_to_cur(Dl + w.zr, 2 * Dr, Dr);
+        if (lane == 0) {
+            *w.czp = Dr;
+            rec[0] = k; rec[1] = Dl + w.zr; rec[2] = 2 * Dr; rec[3] = 1; rec[4] = w.zr; rec[5] = Dl;
+        }
     } else {
         w.split(k, Dl, Dr, 1 << 30, true);   // exact: no ladder step exceeds its rank bound
     }
@@ -749,7 +784,7 @@ __device__ bool wave_step(unsigned char* buf, int t, int* bd, int k, int n, int 
 template <typename T, typename TQ, int CL, int CLR>
 __device__ void wave_deferred_q(unsigned char* buf, int slot, int ld, cx<T>* sites, int lane) {
     using B = WaveBuf<T, TQ, CL, CLR>;
-    int* rec = reinterpret_cast<int*>(buf + B::off_rec) + 4 * slot;
+    int* rec = reinterpret_cast<int*>(buf + B::off_rec) + 6 * slot;
     if (!rec[3]) return;
     CircuitTeam<T, TQ, CL, false, 32> w;
     w.th = reinterpret_cast<cx<TQ>*>(buf + B::off_th + slot * B::TH_BYTES);
@@ -757,7 +792,7 @@ __device__ void wave_deferred_q(unsigned char* buf, int slot, int ld, cx<T>* sit
     w.lane = lane;
     w.ld = ld;
     w.sites = sites;
-    w.q_to_site(rec[0], rec[1], rec[2]);
+    w.q_to_site(rec[0], rec[1], rec[2], rec[5], rec[4]);
     if (lane == 0) rec[3] = 0;
 }
 
@@ -792,7 +827,7 @@ __global__ void __launch_bounds__(32 * WAVE_LAYERS, 8) circuit_wave_kernel(
     // the last layer's sites feed no later layer: its Q factors are formed by warp 0
     // (the cheapest layer) one super-step later, off the last layer's critical path
     const bool defer = L >= 2;
-    if (threadIdx.x < 8) {
+    if (threadIdx.x < 13) {
         reinterpret_cast<int*>(smem_raw + Lay::off_w0 + WaveBuf<T, TQ, WaveDims<CHI, 0>::CL, WaveDims<CHI, 0>::CLR>::off_rec)[threadIdx.x] = 0;
         reinterpret_cast<int*>(smem_raw + Lay::off_w1 + WaveBuf<T, TQ, WaveDims<CHI, 1>::CL, WaveDims<CHI, 1>::CLR>::off_rec)[threadIdx.x] = 0;
         reinterpret_cast<int*>(smem_raw + Lay::off_w2 + WaveBuf<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>::off_rec)[threadIdx.x] = 0;
