@@ -694,8 +694,15 @@ struct WaveBuf {
     static constexpr size_t off_th = (off_nxt + sizeof(cx<T>) * 2 * CLR * CS + 15) & ~size_t(15);
     static constexpr size_t off_tau = off_th + 2 * TH_BYTES;
     static constexpr size_t off_rec = off_tau + 2 * TAU_BYTES;   // 2 x (k, M, N, pending, zr, Dl), then cz
-    static constexpr size_t bytes = off_rec + 13 * sizeof(int);
+    static constexpr size_t bytes = (off_rec + 13 * sizeof(int) + 15) & ~size_t(15);   // next layer 16-aligned
 };
+
+template <int CHI, int J> struct WaveDims;
+template <typename T, typename TQ, int CL, int CLR>
+constexpr bool wave_buf_aligned() {
+    return WaveBuf<T, TQ, CL, CLR>::bytes % 16 == 0 && WaveBuf<T, TQ, CL, CLR>::off_th % 16 == 0 &&
+           WaveBuf<T, TQ, CL, CLR>::off_tau % 16 == 0 && WaveBuf<T, TQ, CL, CLR>::off_nxt % 16 == 0;
+}
 
 template <int CHI, int J> struct WaveDims {
     static constexpr int CL = (2 << J) < CHI ? (2 << J) : CHI;
@@ -712,6 +719,8 @@ struct WaveLayout {
     static constexpr size_t b3 = WaveBuf<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>::bytes;
     static constexpr size_t off_w1 = off_w0 + b0, off_w2 = off_w1 + b1, off_w3 = off_w2 + b2;
     static constexpr size_t bytes = off_w3 + b3;
+    static_assert(off_w0 % 16 == 0 && off_w1 % 16 == 0 && off_w2 % 16 == 0 && off_w3 % 16 == 0,
+                  "layer buffers must stay 16-byte aligned");
 };
 
 // One step (bond k) of layer `layer` for the warp that owns it.  Returns false
