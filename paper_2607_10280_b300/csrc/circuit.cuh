@@ -241,6 +241,27 @@ struct CircuitTeam {
         tsync<NTHR>();
     }
 
+    // Exact split (nothing dropped).  N <= M: Householder QR, A_k = Q (M x N),
+    // cur = R (N x N) reshaped (N, 2, Dr).  M < N: A_k = I_M, cur = theta reshaped
+    // (M, 2, Dr).  Returns the new bond dimension.
+    __device__ int split_exact(int k, int Dl, int Dr) {
+        const int M = 2 * Dl, N = 2 * Dr;
+        if (N <= M) {
+            qr_to_cur(Dl + zr, N, Dr);
+            if (lane == 0) *czp = Dr;
+            q_to_site(k, Dl + zr, N, Dl, zr);
+            return N;
+        }
+        cx<T>* dst = site_ptr(k);
+        team_for_2d<NTHR>(M, M, lane, [&](int row, int c) { dst[row * ld + c] = mk<T>(T(row == c ? 1 : 0), T(0)); });
+        team_for_2d<NTHR>(M, N, lane, [&](int i, int c) {
+            const int t = c >= Dr ? 1 : 0, r = c - t * Dr;
+            cur[(2 * i + t) * CS + r] = cvt<T>(th[c * LDM + i]);
+        });
+        tsync<NTHR>();
+        return M;
+    }
+
     // ---- split theta (M x N) into site k (written to global) and cur (new centre) ----
     // cap: most singular values the split may keep, min(chi, 2^c) with c the CNOTs
     // that have crossed this cut (each at most doubles the Schmidt rank).
@@ -252,24 +273,7 @@ struct CircuitTeam {
     __device__ int split(int k, int Dl, int Dr, int cap, bool exact_cap) {
         const int M = 2 * Dl, N = 2 * Dr;
         const int mn = M < N ? M : N;
-        if (mn <= cap) {
-            if (N <= M) {
-                // Householder QR: A_k = Q (M x N), cur = R (N x N) reshaped (N, 2, Dr)
-                qr_to_cur(Dl + zr, N, Dr);
-                if (lane == 0) *czp = Dr;
-                q_to_site(k, Dl + zr, N, Dl, zr);
-                return N;
-            }
-            // M < N: A_k = I_M, cur = theta reshaped (M, 2, Dr)
-            cx<T>* dst = site_ptr(k);
-            team_for_2d<NTHR>(M, M, lane, [&](int row, int c) { dst[row * ld + c] = mk<T>(T(row == c ? 1 : 0), T(0)); });
-            team_for_2d<NTHR>(M, N, lane, [&](int i, int c) {
-                const int t = c >= Dr ? 1 : 0, r = c - t * Dr;
-                cur[(2 * i + t) * CS + r] = cvt<T>(th[c * LDM + i]);
-            });
-            tsync<NTHR>();
-            return M;
-        }
+        if (mn <= cap) return split_exact(k, Dl, Dr);
         if (exact_cap) return rank_split(k, M, N, Dr, cap);
         if constexpr (TRUNC) {
             keep = cap;
@@ -778,7 +782,7 @@ __device__ bool wave_step(unsigned char* buf, int t, int* bd, int k, int n, int 
             rec[0] = k; rec[1] = Dl + w.zr; rec[2] = 2 * Dr; rec[3] = 1; rec[4] = w.zr; rec[5] = Dl;
         }
     } else {
-        w.split(k, Dl, Dr, 1 << 30, true);   // exact: no ladder step exceeds its rank bound
+        w.split_exact(k, Dl, Dr);   // no ladder step exceeds its rank bound
     }
     if (k == n - 2) {
         store_site<T, CS, 32>(w.site_ptr(n - 1), w.cur, ld, nb, Dr, lane);
