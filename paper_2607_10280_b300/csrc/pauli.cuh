@@ -268,6 +268,18 @@ __device__ __forceinline__ void load_mat(cx<T>* dst, const cx<T>* src, int ld, i
     team_for_2d<NTHR, 4>(D, D, lane, [&](int r, int c) { dst[r * CS + c] = src[r * ld + c]; });
 }
 
+// Asynchronous global -> shared copy of one complex element (cp.async, 8 or 16 B).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(cx<T>* dst, const cx<T>* src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if constexpr (sizeof(cx<T>) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <typename T, int CHI>
 __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ meta, int n_images,
                                                    const cx<T>* __restrict__ arena,
@@ -282,7 +294,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     const int img = blockIdx.x;
     if (img >= n_images) return;
     cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
-    cx<T>* A = base;
+    cx<T>* Abuf[2] = {base, base + 3 * MAT};   // site j in one, site j-1 arriving in the other
     cx<T>* R = base + 2 * MAT;
     cx<T>* S = base + 6 * MAT;
     const ImageMeta mt = meta[img];
@@ -290,15 +302,25 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     const int32_t* bd = bonds + mt.bond_off;
     const cx<T>* sites = arena + mt.site_off;
     cx<T>* rg = renv + (size_t)img * renv_stride;
+    // site j -> dstA with cp.async, so that its load overlaps the transfer through site j+1
+    auto prefetch = [&](int j, cx<T>* dstA) {
+        const int Dl = bd[j], Dr = bd[j + 1];
+        const cx<T>* src = sites + (size_t)j * 2 * ld * ld;
+        team_for_2d<32, 4>(2 * Dl, Dr, lane, [&](int row, int r) { cp_async_elem(dstA + row * CS + r, src + row * ld + r); });
+        cp_async_commit();
+    };
     if (lane == 0) R[0] = mk<T>(T(1), T(0));
-    __syncwarp();
+    if (n > 0) prefetch(n - 1, Abuf[0]);
+    int cb = 0;
     for (int j = n - 1; j >= 0; --j) {
         const int Dl = bd[j], Dr = bd[j + 1];
         cx<T>* dst = rg + (size_t)j * CHI * CHI;
         team_for_2d<32, 4>(Dr, Dr, lane, [&](int r, int c) { dst[r * CHI + c] = R[r * CS + c]; });
-        load_site_p<T, CS>(A, sites + (size_t)j * 2 * ld * ld, ld, Dl, Dr, lane);
+        cp_async_wait_all();
         __syncwarp();
-        transfer<T, CHI, 1, 32, 2>(R, A, S, Dl, Dr, lane);
+        if (j > 0) prefetch(j - 1, Abuf[cb ^ 1]);
+        transfer<T, CHI, 1, 32, 2>(R, Abuf[cb], S, Dl, Dr, lane);
+        cb ^= 1;
     }
     if (lane == 0) norm_out[img] = R[0].re;
 }
