@@ -15,9 +15,9 @@
 //     rounding, in any gauge (the paper ansatz's odd-bond sub-layer needs it).
 //   * min(M, N) > cap = chi < 2^c: SVD truncation at the orthogonality centre.  Gram matrix of
 //     the smaller side in FP64; cyclic Jacobi eigensolver (FP64 path: in FP64;
-//     mixed path: in FP32 on the rounded Gram, sigma^2 then taken as FP64 Rayleigh
-//     quotients, and solved again in FP64 when the gap at the cut is below 1e-3 of
-//     the largest); keep the chi largest, A_k = U_chi (re-orthogonalised by an FP64
+//     mixed path: in FP32 on the rounded Gram, the eigenvalues near the cut refined
+//     as FP64 Rayleigh quotients, and solved again in FP64 when the gap at the cut
+//     is below 1e-3 of the largest); keep the chi largest, A_k = U_chi (re-orthogonalised by an FP64
 //     Householder QR unless it came from an FP64 solve of the left Gram),
 //     A_{k+1} = U_chi^H theta rescaled to unit norm.
 //
@@ -322,8 +322,8 @@ struct CircuitTeam {
         tsync<NTHR>();
         // Eigen-decomposition of G.  FP64 path: Jacobi in FP64 in place (diag(G) = sigma^2,
         // V = eigenvectors).  Mixed path: Jacobi in FP32 on a rounded copy (in the V
-        // buffer), then sigma^2 as FP64 Rayleigh quotients v_i^H G v_i of the FP64 Gram,
-        // and the kept vectors re-orthogonalised in FP64 below.
+        // buffer), sigma^2 near the cut refined as FP64 Rayleigh quotients v_i^H G v_i of
+        // the FP64 Gram, and the kept vectors re-orthogonalised in FP64 below.
         cx<float>* G32 = reinterpret_cast<cx<float>*>(V);
         cx<float>* V32 = G32 + K * LDK;
         // rank the eigenvalues lam (descending, ties by index) into ord
@@ -348,19 +348,33 @@ struct CircuitTeam {
             tsync<NTHR>();
             if (lane < 32) warp_jacobi_eigh<float>(G32, V32, LDK, K, lane, 40);
             tsync<NTHR>();
-            // lam[i] = v_i^H G v_i in FP64 (Rayleigh quotients of the FP64 Gram)
-            for (int i = lane; i < K; i += NTHR) {
-                cx<double> acc = czero<double>();
-                const cx<float>* v = V32 + i * LDK;
-                for (int r = 0; r < K; ++r) {
-                    cx<double> gv = czero<double>();
-                    for (int c = 0; c < K; ++c) cmac(gv, G[c * LDK + r], cvt<double>(v[c]));
-                    cmac_cj(acc, cvt<double>(v[r]), gv);
-                }
-                lam[i] = acc.re;
-            }
+            // lambda from the FP32 Jacobi (absolute error ~ eps_32 lambda_1) ranks the
+            // vectors.  Only near the cut can that ranking or the tie test below need
+            // more: the vectors whose eigenvalue lies within 2e-3 lambda_1 of the cut get
+            // lambda = v^H G v in FP64 (Rayleigh quotients of the FP64 Gram, error
+            // ~ eps_32^2 lambda_1); elsewhere FP64 work on this part is 1/58 of FP32.
+            for (int i = lane; i < K; i += NTHR) lam[i] = (double)G32[i * LDK + i].re;
             tsync<NTHR>();
             rank_lam();
+            {
+                const double l1 = lam[ord[0]];
+                const double lc = 0.5 * (lam[ord[keep - 1]] + lam[ord[keep]]);
+                if (lam[ord[keep - 1]] - lam[ord[keep]] < 2e-3 * l1) {
+                    for (int i = lane; i < K; i += NTHR) {
+                        if (fabs(lam[i] - lc) > 2e-3 * l1) continue;
+                        cx<double> acc = czero<double>();
+                        const cx<float>* v = V32 + i * LDK;
+                        for (int r = 0; r < K; ++r) {
+                            cx<double> gv = czero<double>();
+                            for (int c = 0; c < K; ++c) cmac(gv, G[c * LDK + r], cvt<double>(v[c]));
+                            cmac_cj(acc, cvt<double>(v[r]), gv);
+                        }
+                        lam[i] = acc.re;
+                    }
+                    tsync<NTHR>();
+                    rank_lam();
+                }
+            }
             // Near a tie at the cut the FP32 eigenvectors mix the kept and the dropped
             // directions at the FP32 rounding level; there the eigenproblem is solved
             // again in FP64 (G still holds the FP64 Gram, V is free for FP64 vectors).
