@@ -89,10 +89,16 @@ def test_truncated_regime_vs_oracle_mps(precision, p, L, chi):
     params = synth.circuit_params(L, p * p, seed=101)
     got, _, disc = run_gpu(list(X), [p] * B, L, chi, precision, params=params)
     for i in range(B):
-        ref, gap = oracle_cache(X[i], p, L, chi, params=params)
+        st = o_mps.simulate(o_circ.build_circuit("ladder", X[i], L, params), p * p, chi)
+        ref, gap = st.pair_paulis(o_pairs.image_pairs(p)), st.min_gap
         if gap < 1e-6:
             continue
         assert np.max(np.abs(got[i] - ref)) < tol_for(precision, gap), (i, gap, np.max(np.abs(got[i] - ref)))
+        # the discarded weight summed over the steps (the truncation error's budget):
+        # eigenvalues from the FP32 Jacobi carry ~eps_32 lambda_1 each on the mixed path
+        ref_disc = float(np.sum(st.discarded))
+        bound = 1e-10 if precision == "fp64" else 1e-5 + 1e-4 * ref_disc
+        assert abs(disc[i] - ref_disc) <= bound, (i, disc[i], ref_disc)
     assert np.all(disc >= 0)
 
 
@@ -170,6 +176,47 @@ def test_headline_7x7_L4_chi16_sampled(precision):
         err = np.max(np.abs(got[i] - ref))
         assert err < TOL[precision], (i, err)
     assert np.max(disc) == 0.0   # chi = 2^L: nothing is truncated
+
+
+def test_headline_full_batch_sampled():
+    """The benchmark workload itself: 1024 garment-like 7x7 images (pixel seed 0),
+    L = 4, chi = 16, mixed, default launch shape (layer-pipelined circuit kernel,
+    64-thread Pauli teams); the first, a middle and the last image vs the oracle."""
+    p, L, chi, B = 7, 4, 16, 1024
+    X = synth.garment_pixels(B, p)
+    params = synth.circuit_params(L, p * p)
+    got, _, disc = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params)
+    for i in (0, 511, 1023):
+        ref, _ = oracle_cache(X[i], p, L, chi, params=params)
+        assert np.max(np.abs(got[i] - ref)) < TOL["mixed"], i
+    assert np.max(disc) == 0.0
+
+
+def test_truncated_full_batch_sampled_within_discarded_bound():
+    """Truncated regime at full size (1024 7x7 images, L = 4, chi = 4, mixed, as in the
+    chi x L sweep): sampled images vs the oracle at the same chi (gap-aware bound),
+    the reported discarded weight vs the oracle's, and the distance to the exact
+    result (oracle at chi = 2^L) within 2 sum_k sqrt(2 eps_k) <= 2 sqrt(2 T sum_k eps_k),
+    T = L (n - 1) two-qubit steps, with the GPU's own discarded weights."""
+    p, L, chi, B = 7, 4, 4, 1024
+    n = p * p
+    X = synth.garment_pixels(B, p)
+    params = synth.circuit_params(L, n)
+    got, _, disc = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params)
+    prs = o_pairs.image_pairs(p)
+    worst = 0.0
+    for i in (0, 511, 1023):
+        st = o_mps.simulate(o_circ.build_circuit("ladder", X[i], L, params), n, chi)
+        ref, gap = st.pair_paulis(prs), st.min_gap
+        if gap >= 1e-6:
+            assert np.max(np.abs(got[i] - ref)) < tol_for("mixed", gap), (i, gap)
+        ref_disc = float(np.sum(st.discarded))
+        assert abs(disc[i] - ref_disc) <= 1e-5 + 1e-4 * ref_disc, (i, disc[i], ref_disc)
+        exact, _ = oracle_cache(X[i], p, L, 2 ** L, params=params)
+        err = np.max(np.abs(got[i] - exact))
+        assert err <= 2.0 * np.sqrt(2.0 * L * (n - 1) * disc[i]) + 1e-5, (i, err, disc[i])
+        worst = max(worst, err)
+    assert worst > 1e-3   # the sampled images are truncated for real
 
 
 def test_large_16x16_and_uneven_mix():
