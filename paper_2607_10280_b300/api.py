@@ -199,9 +199,11 @@ class Pipeline:
     Every step copies the pixels from (pinned) host memory to the device, runs the
     circuit, the Pauli cache, the ANO features and the linear layer, and copies the
     Pauli cache, the features and the reconstruction back to pinned host buffers.
-    Copies run on a copy stream and the kernels on the compute stream, with `depth`
-    sets of device and host buffers, so that the copies of one step overlap the
-    kernels of the next: submit() enqueues a step and returns its slot, result(slot)
+    Uploads and downloads run on two copy streams of their own and the kernels on the
+    compute stream, with `depth` sets of device and host buffers, so that the copies
+    of one step overlap the kernels of the next (one copy stream for both would queue
+    the next step's upload behind this step's download, which waits for this step's
+    kernels, and stall the compute stream): submit() enqueues a step and returns its slot, result(slot)
     waits for that step's results.  A slot's host buffers stay valid until the slot
     is submitted again (`depth` submits later).  run() is submit() then result().
     """
@@ -218,7 +220,8 @@ class Pipeline:
         self.m = pair_count(int(p[0]))
         n_px = int(self.batch.pixel_offsets[-1])
         dev = torch.device("cuda", torch.cuda.current_device())
-        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.copy_stream = torch.cuda.Stream(device=dev)       # host -> device
+        self.d2h_stream = torch.cuda.Stream(device=dev)        # device -> host
         dt = torch.float64 if precision == "fp64" else torch.float32
         B = self.batch.n_images
         n_pairs = int(self.batch.pair_offsets[-1])
@@ -256,13 +259,14 @@ class Pipeline:
             ano_features(sl["pauli"], self.m, self.abd, self.W, self.bias, self.stream,
                          feats=sl["feats"], out=sl["out"])
             sl["ev_comp"].record(self.stream)
-        with torch.cuda.stream(cs):
-            cs.wait_event(sl["ev_comp"])
+        ds = self.d2h_stream
+        with torch.cuda.stream(ds):
+            ds.wait_event(sl["ev_comp"])
             sl["pauli_h"].copy_(sl["pauli"], non_blocking=True)
             sl["feats_h"].copy_(sl["feats"], non_blocking=True)
             if sl["out"] is not None:
                 sl["out_h"].copy_(sl["out"], non_blocking=True)
-            sl["ev_out"].record(cs)
+            sl["ev_out"].record(ds)
         return k
 
     def result(self, k: int):
