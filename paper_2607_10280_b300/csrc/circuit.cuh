@@ -722,9 +722,13 @@ constexpr bool wave_buf_aligned() {
            WaveBuf<T, TQ, CL, CLR>::off_tau % 16 == 0 && WaveBuf<T, TQ, CL, CLR>::off_nxt % 16 == 0;
 }
 
+// Layers 0..2 share one buffer shape, sized for layer 2, so that one compiled step
+// (one call site) serves all three and the kernel's code stays small for the
+// instruction cache; loops run to the actual bonds, so the arithmetic is the same.
 template <int CHI, int J> struct WaveDims {
-    static constexpr int CL = (2 << J) < CHI ? (2 << J) : CHI;
-    static constexpr int CLR = (1 << J) < CHI ? (1 << J) : CHI;
+    static constexpr int JJ = J < 2 ? 2 : J;
+    static constexpr int CL = (2 << JJ) < CHI ? (2 << JJ) : CHI;
+    static constexpr int CLR = (1 << JJ) < CHI ? (1 << JJ) : CHI;
 };
 
 template <typename T, typename TQ, int CHI>
@@ -736,6 +740,7 @@ struct WaveLayout {
     static constexpr size_t b2 = WaveBuf<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>::bytes;
     static constexpr size_t b3 = WaveBuf<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>::bytes;
     static constexpr size_t off_w1 = off_w0 + b0, off_w2 = off_w1 + b1, off_w3 = off_w2 + b2;
+    static_assert(b0 == b1 && b1 == b2, "layers 0..2 share one buffer shape (buffer j at off_w0 + j * b0)");
     static constexpr size_t bytes = off_w3 + b3;
     static_assert(off_w0 % 16 == 0 && off_w1 % 16 == 0 && off_w2 % 16 == 0 && off_w3 % 16 == 0,
                   "layer buffers must stay 16-byte aligned");
@@ -867,26 +872,20 @@ __global__ void __launch_bounds__(32 * WAVE_LAYERS, 8) circuit_wave_kernel(
         bool ok = true;
         if (warp < L && k >= 0 && k < n - 1) {
             const bool dq = defer && warp == last;
-            switch (warp) {
-                case 0: ok = wave_step<T, TQ, WaveDims<CHI, 0>::CL, WaveDims<CHI, 0>::CLR>(
-                            smem_raw + Lay::off_w0, t, bd, k, n, ld, sites, gates, gn, 0, dq, lane, status); break;
-                case 1: ok = wave_step<T, TQ, WaveDims<CHI, 1>::CL, WaveDims<CHI, 1>::CLR>(
-                            smem_raw + Lay::off_w1, t, bd, k, n, ld, sites, gates, gn, 1, dq, lane, status); break;
-                case 2: ok = wave_step<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>(
-                            smem_raw + Lay::off_w2, t, bd, k, n, ld, sites, gates, gn, 2, dq, lane, status); break;
-                default: ok = wave_step<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>(
-                            smem_raw + Lay::off_w3, t, bd, k, n, ld, sites, gates, gn, 3, dq, lane, status); break;
-            }
+            if (warp < 3)
+                ok = wave_step<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>(
+                    smem_raw + Lay::off_w0 + warp * Lay::b0, t, bd, k, n, ld, sites, gates, gn, warp, dq, lane, status);
+            else
+                ok = wave_step<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>(
+                    smem_raw + Lay::off_w3, t, bd, k, n, ld, sites, gates, gn, 3, dq, lane, status);
         }
         if (defer && warp == 0 && t >= 1) {
-            switch (last) {
-                case 1: wave_deferred_q<T, TQ, WaveDims<CHI, 1>::CL, WaveDims<CHI, 1>::CLR>(
-                            smem_raw + Lay::off_w1, (t - 1) & 1, ld, sites, lane); break;
-                case 2: wave_deferred_q<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>(
-                            smem_raw + Lay::off_w2, (t - 1) & 1, ld, sites, lane); break;
-                default: wave_deferred_q<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>(
-                            smem_raw + Lay::off_w3, (t - 1) & 1, ld, sites, lane); break;
-            }
+            if (last < 3)
+                wave_deferred_q<T, TQ, WaveDims<CHI, 2>::CL, WaveDims<CHI, 2>::CLR>(
+                    smem_raw + Lay::off_w0 + last * Lay::b0, (t - 1) & 1, ld, sites, lane);
+            else
+                wave_deferred_q<T, TQ, WaveDims<CHI, 3>::CL, WaveDims<CHI, 3>::CLR>(
+                    smem_raw + Lay::off_w3, (t - 1) & 1, ld, sites, lane);
         }
         // global writes of this super-step become visible to the other warps here
         if (__syncthreads_or(ok ? 0 : 1)) break;
