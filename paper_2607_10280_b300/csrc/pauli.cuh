@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
 }
 
 template <typename T, int CHI, int UW, bool DIAG>
-__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : 8) / (sizeof(T) == 8 ? 2 : 1)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
+__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16) ? 9 : 8) / (sizeof(T) == 8 ? 2 : 1)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
                                                     const int32_t* __restrict__ unit_image,
                                                     const cx<T>* __restrict__ arena,
                                                     const int32_t* __restrict__ bonds,
