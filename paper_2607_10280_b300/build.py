@@ -21,7 +21,7 @@ SOURCES = (["circuit_fp64_t1_c32.cu", "circuit_fp64_t1_c16.cu", "circuit_orth64_
             "pauli_launch.cu"]
            + [f"circuit_{p}_t{t}_c{c}.cu" for p in ("mixed", "fp64", "orth64") for t in (0, 1) for c in (4, 8, 16, 32)
               if not (t == 1 and p != "mixed" and c >= 16)]
-           + ["circuit_dispatch.cu", "mpsano.cu", "noalloc.cu", "train.cu"])
+           + ["circuit_dispatch.cu", "ladder_mpo.cu", "mpsano.cu", "noalloc.cu", "train.cu"])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

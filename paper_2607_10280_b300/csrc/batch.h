@@ -24,6 +24,9 @@ struct mps_batch {
     void* arena = nullptr;                 // sites
     void* renv = nullptr;                  // right environments
     int64_t renv_stride = 0;               // complex elements per image
+    void* lenv = nullptr;                  // left environments (operator-product ladder images), as renv
+    size_t cap_lenv = 0;
+    bool any_lenv = false;                 // some image of the last circuit is flagged META_LENV
     void* norms = nullptr;
     int32_t* bonds_d = nullptr;
     double* discarded_d = nullptr;
@@ -105,6 +108,10 @@ inline mps_status launch_circuit_orth64(mps_batch* b, int chi_tpl, bool trunc, c
 // Fill b->gates (allocated by the caller) with the one-qubit gate table of a circuit.
 mps_status launch_gate_table(mps_batch* b, int ansatz, int L_max, const double* params, int params_n,
                              const double* pixels);
+// Ladder circuits as operator products for b->run_order[0 .. run_count) (ladder_mpo.cu),
+// and the left environments of the images flagged META_LENV.
+mps_status launch_ladder_mpo(mps_batch* b, const double* pixels);
+mps_status launch_lenv(mps_batch* b);
 mps_status launch_pauli_fp64(mps_batch* b, void* out, bool diag = false);
 mps_status launch_pauli_mixed(mps_batch* b, void* out, bool diag = false);
 

@@ -72,7 +72,13 @@ struct ImageMeta {
     int64_t pixel_off;  // offset of the image's pixels in the packed pixel array
     int64_t pair_off;   // offset (in pairs) of the image's Pauli-cache block, horizontal + vertical
     int64_t pair_off_d; // the same with both diagonal pair sets
+    int32_t flags;      // META_LENV: the MPS is not left-canonical (see ladder_mpo.cu)
+    int32_t pad;
 };
+
+// ImageMeta::flags: the Pauli kernel contracts the left environments L_i (written by
+// lenv_kernel) instead of taking them as the identity.
+constexpr int32_t META_LENV = 1;
 
 // Device status word: first error wins.
 enum : int { DEV_OK = 0, DEV_BOND_OVERFLOW = 1, DEV_SMEM_OVERFLOW = 2, DEV_BAD_SHAPE = 3 };

@@ -230,6 +230,7 @@ void free_batch(mps_batch* b) {
     cudaFree(b->units_d);
     cudaFree(b->arena);
     cudaFree(b->renv);
+    cudaFree(b->lenv);
     cudaFree(b->norms);
     cudaFree(b->bonds_d);
     cudaFree(b->discarded_d);
@@ -455,32 +456,58 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     int mx = 1, mx_wave = 1, mx_seq = 1;
     bool trunc_seq = false;
     bool changed = false;
-    std::vector<char> wave(b->B, 0);
-    int n_wave = 0;
+    // A pipelined image whose 2^L fits its padding and its chi takes the operator-product
+    // path (ladder_mpo.cu: bond 2^L at every inner cut, not left-canonical, flagged
+    // META_LENV for the Pauli kernel).
+    std::vector<char> wave(b->B, 0), mpo(b->B, 0);
+    int n_wave = 0, n_mpo = 0;
     for (int i = 0; i < b->B; ++i) {
         ImageMeta& m = b->meta_h[i];
         const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
         if (m.L != L) { m.L = L; changed = true; }
         bool t = false;
-        const int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
+        int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
         if (bi > m.ld) return fail(MPS_ERR_UNSUPPORTED, "image %d reaches bond %d > padding %d", i, bi, m.ld);
+        const bool pipe = b->layer_pipeline && circ->ansatz == MPS_ANSATZ_LADDER && !t && L >= 1 && L <= WAVE_LAYERS;
+        mpo[i] = pipe && (1 << L) <= std::min(m.ld, m.chi) && (1 << L) <= 16;
+        const int32_t fl = mpo[i] ? META_LENV : 0;
+        if (m.flags != fl) { m.flags = fl; changed = true; }
+        if (mpo[i]) {
+            bi = 1 << L;
+            ++n_mpo;
+        }
         mx = std::max(mx, bi);
-        wave[i] = b->layer_pipeline && circ->ansatz == MPS_ANSATZ_LADDER && !t && L >= 1 && L <= WAVE_LAYERS;
+        wave[i] = pipe && !mpo[i];
         if (wave[i]) {
             ++n_wave;
             mx_wave = std::max(mx_wave, bi);
-        } else {
+        } else if (!mpo[i]) {
             mx_seq = std::max(mx_seq, bi);
             trunc_seq = trunc_seq || t;
         }
     }
     const int chi_tpl = chi_bucket(mx);
     if (chi_tpl < 0) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > 32 not supported", mx);
-    // work order: pipelined images first, each part by descending cost
+    // work order: operator-product images, pipelined images, the rest, each part by
+    // descending cost
     std::vector<int32_t> order;
     order.reserve(b->B);
+    for (int32_t i : b->cost_order) if (mpo[i]) order.push_back(i);
     for (int32_t i : b->cost_order) if (wave[i]) order.push_back(i);
-    for (int32_t i : b->cost_order) if (!wave[i]) order.push_back(i);
+    for (int32_t i : b->cost_order) if (!wave[i] && !mpo[i]) order.push_back(i);
+    if (n_mpo > 0) {
+        cudaError_t e;
+        if (b->cap_lenv < b->elem * b->renv_stride * b->B) {
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            cudaFree(b->lenv);
+            b->lenv = nullptr;
+            b->cap_lenv = 0;
+            e = cudaMalloc(&b->lenv, b->elem * b->renv_stride * b->B);
+            if (e != cudaSuccess) return fail(MPS_ERR_OOM, "left environments: %s", cudaGetErrorString(e));
+            b->cap_lenv = b->elem * b->renv_stride * b->B;
+        }
+    }
+    b->any_lenv = n_mpo > 0;
     if (order != b->order_h) {
         CUDA_TRY(cudaStreamSynchronize(b->stream));  // pinned staging may still be in flight
         std::memcpy(b->order_pinned, order.data(), sizeof(int32_t) * b->B);
@@ -517,17 +544,24 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
             default: return launch_circuit_orth64(b, bucket, trunc, pixels, circ->ansatz);
         }
     };
+    if (n_mpo > 0) {
+        b->use_wave = false;
+        b->run_order = b->order_d;
+        b->run_count = n_mpo;
+        st = launch_ladder_mpo(b, pixels);
+        if (st != MPS_OK) return st;
+    }
     if (n_wave > 0) {
         b->use_wave = true;
-        b->run_order = b->order_d;
+        b->run_order = b->order_d + n_mpo;
         b->run_count = n_wave;
         st = launch(chi_bucket(mx_wave), false);
         if (st != MPS_OK) return st;
     }
-    if (n_wave < b->B) {
+    if (n_mpo + n_wave < b->B) {
         b->use_wave = false;
-        b->run_order = b->order_d + n_wave;
-        b->run_count = b->B - n_wave;
+        b->run_order = b->order_d + n_mpo + n_wave;
+        b->run_count = b->B - n_mpo - n_wave;
         st = launch(chi_bucket(mx_seq), trunc_seq);
         if (st != MPS_OK) return st;
     }

@@ -74,6 +74,8 @@ __global__ void noalloc_setup_kernel(ImageMeta* meta, int32_t* units, double* di
         m.pixel_off = (int64_t)t * n;
         m.pair_off = (int64_t)t * 2 * p * (p - 1);
         m.pair_off_d = (int64_t)t * (2 * p * (p - 1) + 2 * (p - 1) * (p - 1));
+        m.flags = 0;
+        m.pad = 0;
         meta[t] = m;
         discarded[t] = 0.0;
     }

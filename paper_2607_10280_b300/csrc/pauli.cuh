@@ -1,7 +1,9 @@
 // Pauli-cache kernels (Sec. II.C, Eq. 5).
 //
-// The circuit kernel leaves every MPS left-canonical with the centre at site n-1,
-// so the environment of sites 0..i-1 is the identity.  Two kernels remain:
+// The circuit kernels leave every MPS left-canonical with the centre at site n-1,
+// so the environment of sites 0..i-1 is the identity; the operator-product ladder
+// path (ladder_mpo.cu) does not, and its images (META_LENV) bring left environments
+// L_i, contracted into E_a (left_blocks_env).  Two kernels remain:
 //
 //   renv_kernel   one warp per image: right environments R_j (contraction of sites
 //                 j+1..n-1 with their conjugates, bra index first) for j = n-1..0,
@@ -180,6 +182,33 @@ __device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, in
         [](int n) { return n; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
 }
 
+// The same blocks with a left environment L (Dl x Dl, row stride CHI, read from
+// global memory; NULL: the identity, left_blocks):
+// F[m][n] = sum_{l,l'} conj(A[2l+s_m][r_m]) L[l][l'] A[2l'+s_n][r_n], through
+// T[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r] in S rows 0 .. Dl.
+template <typename T, int CHI, int NTHR>
+__device__ __forceinline__ void left_blocks_env(const cx<T>* A, const cx<T>* Lg, cx<T>* S, int Dl, int Dr,
+                                                int lane) {
+    if (!Lg) {
+        left_blocks<T, CHI, NTHR>(A, S, Dl, Dr, lane);
+        return;
+    }
+    using Lay = PauliLayout<T, CHI>;
+    constexpr int CS = Lay::CS, ZS = Lay::ZS;
+    {
+        using Tl = Tile<T, CHI, 2 * CHI, NTHR>;
+        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+            Lg, [](int l) { return l * CHI; }, 1, 0, A, [Dr](int nn) { return (nn / Dr) * CS + (nn % Dr); }, 2 * CS, 0,
+            Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
+    }
+    team_sync();
+    cx<T>* F = S + CHI * ZS;
+    using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
+    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+        A, [Dr](int m) { return (m / Dr) * CS + (m % Dr); }, 2 * CS, 0, S, [](int nn) { return nn; }, ZS, 0,
+        2 * Dr, 2 * Dr, Dl, [](int nn) { return nn; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
+}
+
 // <E_a, Y> for a = X, Y, Z (from the blocks F_{ss'} in S) and Y in {C_X, C_Y, C_Z, R}:
 // out[4(a-1) + y], with C_X, C_Y unpacked from M = C[0] and C_Z = C[MAT].  C may be
 // null (then only the R column is formed).  Warp 0 alone
@@ -331,6 +360,7 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
                                                     const cx<T>* __restrict__ arena,
                                                     const int32_t* __restrict__ bonds,
                                                     const cx<T>* __restrict__ renv, int64_t renv_stride,
+                                                    const cx<T>* __restrict__ lenv,
                                                     const T* __restrict__ norms, T* __restrict__ out) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
@@ -354,6 +384,9 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
     const int32_t* bd = bonds + mt.bond_off;
     const cx<T>* sites = arena + mt.site_off;
     const cx<T>* rg = renv + (size_t)img * renv_stride;
+    // left environments (images whose MPS is not left-canonical), same layout as renv
+    const cx<T>* lgb = (lenv && (mt.flags & META_LENV)) ? lenv + (size_t)img * renv_stride : nullptr;
+    auto lenv_of = [lgb](int i) -> const cx<T>* { return lgb ? lgb + (size_t)i * CHI * CHI : nullptr; };
     const T inv_norm = T(1) / norms[img];
     T* outp = out + (size_t)(diag ? mt.pair_off_d : mt.pair_off) * 16;
     const int nh = p * (p - 1);                  // horizontal pairs come first, then vertical,
@@ -381,7 +414,7 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
         load_mat<T, CS, NTHR>(R, rg + (size_t)j * CHI * CHI, CHI, Dr, lane);
         team_sync();
         // site j as the left site: single-site terms and the vertical pair (j, j+p)
-        left_blocks<T, CHI, NTHR>(A, S, Dl, Dr, lane);
+        left_blocks_env<T, CHI, NTHR>(A, lenv_of(j), S, Dl, Dr, lane);
         team_sync();
         left_dots<T, CHI, NTHR>(S, row < p - 1 ? C : nullptr, R, Dr, d, red, lane);
         T single_j[3];
@@ -408,7 +441,7 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
         if (c > 0) {
             load_mat<T, CS, NTHR>(R, rg + (size_t)k0 * CHI * CHI, CHI, Dl, lane);
             team_sync();
-            left_blocks<T, CHI, NTHR>(A, S, Dl0, Dl, lane);
+            left_blocks_env<T, CHI, NTHR>(A, lenv_of(k0), S, Dl0, Dl, lane);
             team_sync();
             left_dots<T, CHI, NTHR>(S, C, R, Dl, d, red, lane);
             T single_k[3];
@@ -432,7 +465,7 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
                 // anti-diagonal (row-1, c+1)-(row, c): site k is the left site
                 load_mat<T, CS, NTHR>(R, rg + (size_t)k * CHI * CHI, CHI, Drk, lane);
                 team_sync();
-                left_blocks<T, CHI, NTHR>(A, S, Dlk, Drk, lane);
+                left_blocks_env<T, CHI, NTHR>(A, lenv_of(k), S, Dlk, Drk, lane);
                 team_sync();
                 left_dots<T, CHI, NTHR>(S, C, R, Drk, dd, red, lane);
                 T single_k[3];

@@ -20,6 +20,7 @@ mps_status launch_pauli_uw(mps_batch* b, void* out) {
     pk<<<b->n_units, 32 * UW, smem, b->stream>>>(
         b->meta_d, b->n_units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
+        reinterpret_cast<const cx<T>*>(b->any_lenv ? b->lenv : nullptr),
         reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out));
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
@@ -42,6 +43,10 @@ mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
+    if (b->any_lenv) {
+        const mps_status st = launch_lenv(b);
+        if (st != MPS_OK) return st;
+    }
     // the diagonal pair sets are compiled for 2-warp teams only
     if (diag) return launch_pauli_uw<T, CHI, 2, true>(b, out);
     switch (b->pauli_warps) {

@@ -155,12 +155,38 @@ def test_encoding_only_and_chi_one():
     assert np.all(disc > 0)
 
 
+def _ld(p, chi):
+    """Site padding of an image (the library's layout rule): the bond cap rounded up
+    to a power of two, at least 4."""
+    n = p * p
+    cap = 1
+    while cap < chi and cap < (1 << min(n // 2, 20)):
+        cap <<= 1
+    cap = min(cap, chi, 32)
+    ld = 4
+    while ld < cap:
+        ld <<= 1
+    return ld
+
+
+def _operator_product_path(p, L, chi):
+    """Whether the library runs a ladder image as an operator product (bond 2^L)."""
+    return 1 <= L <= 4 and (1 << L) <= min(_ld(p, chi), chi, 16)
+
+
 def test_ladder_bond_dimensions_7x7():
+    """Sequential sweep: canonical bonds min(chi, 2^L, 2^(k+1), 2^(n-k-1)); the
+    operator-product path (Sec. II.B as a CNOT-ladder product, no factorisation): 2^L
+    at every inner cut."""
     n, L, chi = 49, 3, 16
     X = synth.garment_pixels(2, 7, seed=40)
-    _, bonds, _ = run_gpu(list(X), [7, 7], L, chi, "mixed", params=synth.circuit_params(L, n))
+    params = synth.circuit_params(L, n)
+    _, bonds, _ = run_gpu(list(X), [7, 7], L, chi, "mixed", params=params, pipeline=False)
     expect = [1] + [min(chi, 2 ** L, 2 ** (k + 1), 2 ** (n - k - 1)) for k in range(n - 1)] + [1]
     assert bonds[0] == expect and bonds[1] == expect
+    _, bonds, _ = run_gpu(list(X), [7, 7], L, chi, "mixed", params=params, pipeline=True)
+    assert _operator_product_path(7, L, chi)
+    assert list(bonds[0]) == [1] + [2 ** L] * (n - 1) + [1] and list(bonds[1]) == list(bonds[0])
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
@@ -340,13 +366,13 @@ def test_diagonal_pairs_vs_oracle(precision, ansatz, p, L, chi):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_orth64"])
 def test_layer_pipeline_equals_sequential_sweep(precision):
-    """The layer-pipelined circuit kernel (ladder, no truncation, L <= 4) runs every
-    two-qubit step on the same inputs and with the same operations as the sequential
-    sweep: same bond dimensions, and Pauli caches equal to rounding (1e-12 FP64,
-    5e-6 mixed: the compiler may fuse a multiply and an add into one FMA in one
-    kernel and not in the other; in complex64 that moves a step by a few ulps,
-    which add up over the 255 steps per layer of a 16x16 image.  The FP64 bound
-    stays at 1e-12, so an ordering or synchronisation error would still show)."""
+    """The fast paths for ladder circuits without truncation (L <= 4) against the
+    sequential sweep: the layer-pipelined kernel runs every two-qubit step on the same
+    inputs with the same operations (same bonds); the operator-product path (2^L within
+    chi and the padding) builds the same state without factorisation, with bond 2^L at
+    every inner cut.  Pauli caches equal to rounding (1e-12 FP64, 5e-6 mixed: complex64
+    rounding of different but exact operation sequences, up to 255 steps per layer of
+    a 16x16 image); an ordering or synchronisation error would show in FP64."""
     cases = [([7] * 6, 4, 16), ([5] * 5, 3, 8), ([4, 9, 6, 16, 5], 2, 16), ([6] * 4, 1, 2),
              ([3, 2, 8, 7], [4, 0, 3, 2], 32)]
     bound = 1e-12 if precision == "fp64" else 5e-6
@@ -355,7 +381,12 @@ def test_layer_pipeline_equals_sequential_sweep(precision):
         params = synth.circuit_params(int(np.max(L)), max(ps) ** 2, seed=70 + ci)
         seq, b_seq, d_seq = run_gpu(X, ps, L, chi, precision, params=params, pipeline=False)
         pip, b_pip, d_pip = run_gpu(X, ps, L, chi, precision, params=params, pipeline=True)
-        assert all(np.array_equal(u, v) for u, v in zip(b_seq, b_pip)), ci
+        for i, p in enumerate(ps):
+            Li = int(np.atleast_1d(L)[i]) if np.ndim(L) else L
+            if _operator_product_path(p, Li, chi):
+                assert list(b_pip[i]) == [1] + [2 ** Li] * (p * p - 1) + [1], (ci, i)
+            else:
+                assert np.array_equal(b_seq[i], b_pip[i]), (ci, i)
         assert np.all(d_pip == 0.0) and np.all(d_seq == 0.0)
         for i in range(len(ps)):
             err = np.max(np.abs(seq[i] - pip[i]))
