@@ -246,7 +246,8 @@ mps_status mps_set_layer_pipeline(mps_batch* batch, int32_t enable);
 mps_status mps_set_timing(mps_batch* batch, int32_t enable);
 
 /* Sum of the recorded launch durations since the last call, per kernel kind
- * (0 circuit, 1 right environments, 2 Pauli cache): ms [3], launches [3].
+ * (0 circuit, 1 environments: right, and left for images whose ladder circuit ran
+ * as an operator product, 2 Pauli cache): ms [3], launches [3].
  * Synchronises the batch's stream, then clears the records. */
 mps_status mps_kernel_times(mps_batch* batch, double* ms, int64_t* launches);
 

@@ -137,8 +137,8 @@ class Batch:
 
     def kernel_times(self) -> dict:
         """{kind: (total ms, launches)} since the last call, from the library's events."""
-        ms = (ctypes.c_double * 3)()
-        cnt = (ctypes.c_int64 * 3)()
+        ms = (ctypes.c_double * len(_lib.KERNEL_KINDS))()
+        cnt = (ctypes.c_int64 * len(_lib.KERNEL_KINDS))()
         check(lib().mps_kernel_times(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.KERNEL_KINDS)}
 

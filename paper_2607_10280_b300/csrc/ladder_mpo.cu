@@ -18,12 +18,12 @@
 // The result is not left-canonical (a layer's operator keeps left orthonormality only
 // where the incoming parity is summed, not at site 0), so the Pauli kernel contracts
 // the left environments L_k = sum_s A_{k-1}^{s dagger} L_{k-1} A_{k-1}^s (L_0 = 1)
-// that lenv_kernel writes, marked per image by META_LENV.
+// that renv_kernel writes beside the right ones (lenv_image), for the images marked
+// META_LENV.
 #include <algorithm>
 
 #include "batch.h"
 #include "circuit.cuh"
-#include "pauli.cuh"
 
 namespace mpsano {
 namespace {
@@ -63,42 +63,44 @@ __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
             cur[0] = mk<T>(T(cs), T(0));
             cur[1] = mk<T>(T(sn), T(0));
         }
-        int Dl = 1, Dr = 1;
+        // every dimension is a power of two: indices by shifts and masks
+        int sl = 0, sr = 0;   // log2 Dl, log2 Dr
         for (int layer = 0; layer < L; ++layer) {
             __syncwarp();
             // the layer's one-qubit gate on the physical index
             const Gate1<T> g = table_gate<T>(gates, gn, 0, layer, img, k);
-            for (int e = lane; e < Dl * Dr; e += 32) {
-                const int l = e / Dr, r = e - l * Dr;
-                const cx<T> a0 = cur[(2 * l) * Dr + r], a1 = cur[(2 * l + 1) * Dr + r];
-                cur[(2 * l) * Dr + r] = cdot2(g.u00, a0, g.u01, a1);
-                cur[(2 * l + 1) * Dr + r] = cdot2(g.u10, a0, g.u11, a1);
+            for (int e = lane; e < (1 << (sl + sr)); e += 32) {
+                const int l = e >> sr, r = e & ((1 << sr) - 1);
+                const int i0 = ((2 * l) << sr) + r, i1 = i0 + (1 << sr);
+                const cx<T> a0 = cur[i0], a1 = cur[i1];
+                cur[i0] = cdot2(g.u00, a0, g.u01, a1);
+                cur[i1] = cdot2(g.u10, a0, g.u11, a1);
             }
             __syncwarp();
             // the layer's CNOT ladder: new bond index = old index + old dimension * parity
-            const int Dl2 = k == 0 ? Dl : 2 * Dl;
-            const int Dr2 = k == n - 1 ? Dr : 2 * Dr;
-            for (int e = lane; e < Dl2 * 2 * Dr2; e += 32) {
-                const int l2 = e / (2 * Dr2), rem = e - l2 * 2 * Dr2;
-                const int s = rem / Dr2, r2 = rem - s * Dr2;
-                const int a = l2 / Dl, l = l2 - a * Dl;       // a = 0 at site 0 (Dl2 = Dl)
+            const int sl2 = k == 0 ? sl : sl + 1;
+            const int sr2 = k == n - 1 ? sr : sr + 1;
+            for (int e = lane; e < (2 << (sl2 + sr2)); e += 32) {
+                const int l2 = e >> (sr2 + 1), s = (e >> sr2) & 1, r2 = e & ((1 << sr2) - 1);
+                const int a = l2 >> sl, l = l2 & ((1 << sl) - 1);   // a = 0 at site 0
                 cx<T> v;
                 if (k == n - 1) {
-                    v = cur[(2 * l + (a ^ s)) * Dr + r2];
+                    v = cur[((2 * l + (a ^ s)) << sr) + r2];
                 } else {
-                    const int b = r2 / Dr, r = r2 - b * Dr;
-                    v = s == b ? cur[(2 * l + (a ^ b)) * Dr + r] : czero<T>();
+                    const int b = r2 >> sr, r = r2 & ((1 << sr) - 1);
+                    v = s == b ? cur[((2 * l + (a ^ b)) << sr) + r] : czero<T>();
                 }
                 nxt[e] = v;
             }
             cx<T>* t = cur; cur = nxt; nxt = t;
-            Dl = Dl2;
-            Dr = Dr2;
+            sl = sl2;
+            sr = sr2;
         }
         __syncwarp();
+        const int Dl = 1 << sl;
         cx<T>* dst = sites + (size_t)k * 2 * ld * ld;
-        for (int e = lane; e < Dl * 2 * Dr; e += 32) {
-            const int row = e / Dr, r = e - row * Dr;
+        for (int e = lane; e < (2 << (sl + sr)); e += 32) {
+            const int row = e >> sr, r = e & ((1 << sr) - 1);
             dst[row * ld + r] = cur[e];
         }
         if (lane == 0) bonds_out[mt.bond_off + k] = Dl;
@@ -107,58 +109,6 @@ __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
     if (threadIdx.x == 0) {
         bonds_out[mt.bond_off + n] = 1;
         discarded_out[img] = 0.0;
-    }
-}
-
-// Left environments of the images flagged META_LENV (one warp per image; the others
-// return at once): L_0 = 1 and L_{k+1}[r][r'] = sum_{l,l',s} conj(A_k[l][s][r])
-// L_k[l][l'] A_k[l'][s][r'], stored like the right environments (L_k, D_k x D_k, at
-// k * CHI * CHI of the image's block; D_k = left bond of site k).
-template <typename T, int CHI>
-__global__ void __launch_bounds__(32) lenv_kernel(const ImageMeta* __restrict__ meta, int n_images,
-                                                   const cx<T>* __restrict__ arena,
-                                                   const int32_t* __restrict__ bonds,
-                                                   cx<T>* __restrict__ lenv, int64_t stride) {
-    using Lay = PauliLayout<T, CHI>;
-    constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x;
-    const int img = blockIdx.x;
-    if (img >= n_images) return;
-    const ImageMeta mt = meta[img];
-    if (!(mt.flags & META_LENV)) return;
-    cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
-    cx<T>* A = base;             // 2 MAT
-    cx<T>* Lm = base + 2 * MAT;  // MAT
-    cx<T>* S = base + 3 * MAT;   // CHI rows x ZS
-    const int n = mt.n, ld = mt.ld;
-    const int32_t* bd = bonds + mt.bond_off;
-    const cx<T>* sites = arena + mt.site_off;
-    cx<T>* lg = lenv + (size_t)img * stride;
-    if (lane == 0) Lm[0] = mk<T>(T(1), T(0));
-    __syncwarp();
-    for (int k = 0; k < n; ++k) {
-        const int Dl = bd[k], Dr = bd[k + 1];
-        cx<T>* dst = lg + (size_t)k * CHI * CHI;
-        team_for_2d<32, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
-        load_site_p<T, CS, 32>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
-        __syncwarp();
-        // S[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r]
-        {
-            using Tl = Tile<T, CHI, 2 * CHI, 32>;
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
-                Lm, [](int l) { return l * CS; }, 1, 0, A, [Dr](int nn) { return (nn / Dr) * CS + (nn % Dr); }, 2 * CS, 0,
-                Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
-        }
-        __syncwarp();
-        // L'[r][r'] = sum_{l,s} conj(A[2l+s][r]) S[l][s Dr + r']
-        {
-            using Tl = Tile<T, CHI, CHI, 32>;
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, 1>(
-                A, [](int r) { return r; }, 2 * CS, CS, S, [](int nn) { return nn; }, ZS, Dr, Dr, Dr, Dl,
-                [](int nn) { return nn; }, [Lm](int r, int sn, cx<T> v) { Lm[r * CS + sn] = v; }, lane);
-        }
-        __syncwarp();
     }
 }
 
@@ -178,41 +128,10 @@ mps_status launch_mpo_t(mps_batch* b, const double* pixels) {
     return MPS_OK;
 }
 
-template <typename T, int CHI>
-mps_status launch_lenv_t(mps_batch* b) {
-    using Lay = PauliLayout<T, CHI>;
-    const size_t smem = sizeof(cx<T>) * (3 * Lay::MAT + CHI * Lay::ZS);
-    if (smem > (size_t)smem_optin_limit()) return fail(MPS_ERR_UNSUPPORTED, "left environments: %zu B shared memory", smem);
-    auto k = lenv_kernel<T, CHI>;
-    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    timing_begin(b, KIND_RENV);
-    k<<<b->B, 32, smem, b->stream>>>(b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
-                                     reinterpret_cast<cx<T>*>(b->lenv), b->renv_stride);
-    timing_end(b);
-    CUDA_TRY(cudaGetLastError());
-    count_launch();
-    return MPS_OK;
-}
-
-template <typename T>
-mps_status launch_lenv_b(mps_batch* b) {
-    switch (b->chi_tpl) {
-        case 4: return launch_lenv_t<T, 4>(b);
-        case 8: return launch_lenv_t<T, 8>(b);
-        case 16: return launch_lenv_t<T, 16>(b);
-        case 32: return launch_lenv_t<T, 32>(b);
-    }
-    return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", b->chi_tpl);
-}
-
 }  // namespace
 
 mps_status launch_ladder_mpo(mps_batch* b, const double* pixels) {
     return b->prec == MPS_FP64 ? launch_mpo_t<double>(b, pixels) : launch_mpo_t<float>(b, pixels);
-}
-
-mps_status launch_lenv(mps_batch* b) {
-    return b->prec == MPS_FP64 ? launch_lenv_b<double>(b) : launch_lenv_b<float>(b);
 }
 
 }  // namespace mpsano

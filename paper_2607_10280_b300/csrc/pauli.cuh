@@ -49,6 +49,9 @@ struct PauliLayout {
     static constexpr int ELEMS = 5 * MAT + SROWS * ZS;
     static constexpr size_t bytes = sizeof(cx<T>) * ELEMS;
     static constexpr size_t elems(bool diag) { return ELEMS + (diag ? 2 * MAT : 0); }
+    // environment kernel: two site buffers, R, and CHI scratch rows (one transfer;
+    // the left-environment chain needs 3 MAT + CHI rows)
+    static constexpr size_t env_bytes = sizeof(cx<T>) * (5 * MAT + CHI * ZS);
     // plus the cross-warp reduction buffer of a UW-warp team
     static constexpr size_t team_bytes(int uw, bool diag = false) {
         return sizeof(cx<T>) * elems(diag) + sizeof(T) * 12 * uw;
@@ -309,23 +312,77 @@ __device__ __forceinline__ void cp_async_elem(cx<T>* dst, const cx<T>* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Left environments of one image (a warp): L_0 = 1 and L_{k+1}[r][r'] =
+// sum_{l,l',s} conj(A_k[l][s][r]) L_k[l][l'] A_k[l'][s][r'], stored like the right
+// environments (L_k, D_k x D_k, at k * CHI * CHI of the image's block).
+template <typename T, int CHI>
+__device__ __forceinline__ void lenv_image(const ImageMeta& mt, const cx<T>* __restrict__ arena,
+                                           const int32_t* __restrict__ bonds, cx<T>* lg, cx<T>* base,
+                                           int lane) {
+    using Lay = PauliLayout<T, CHI>;
+    constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
+    cx<T>* A = base;             // 2 MAT
+    cx<T>* Lm = base + 2 * MAT;  // MAT
+    cx<T>* S = base + 3 * MAT;   // CHI rows of ZS
+    const int n = mt.n, ld = mt.ld;
+    const int32_t* bd = bonds + mt.bond_off;
+    const cx<T>* sites = arena + mt.site_off;
+    if (lane == 0) Lm[0] = mk<T>(T(1), T(0));
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        const int Dl = bd[k], Dr = bd[k + 1];
+        cx<T>* dst = lg + (size_t)k * CHI * CHI;
+        team_for_2d<32, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
+        load_site_p<T, CS, 32>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
+        __syncwarp();
+        // S[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r]
+        {
+            using Tl = Tile<T, CHI, 2 * CHI, 32>;
+            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+                Lm, [](int l) { return l * CS; }, 1, 0, A, [Dr](int nn) { return (nn / Dr) * CS + (nn % Dr); }, 2 * CS, 0,
+                Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
+        }
+        __syncwarp();
+        // L'[r][r'] = sum_{l,s} conj(A[2l+s][r]) S[l][s Dr + r']
+        {
+            using Tl = Tile<T, CHI, CHI, 32>;
+            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, 1>(
+                A, [](int r) { return r; }, 2 * CS, CS, S, [](int nn) { return nn; }, ZS, Dr, Dr, Dr, Dl,
+                [](int nn) { return nn; }, [Lm](int r, int sn, cx<T> v) { Lm[r * CS + sn] = v; }, lane);
+        }
+        __syncwarp();
+    }
+}
+
+// CTA i < n_images: the right environments of image i; with lenv, CTA n_images + i:
+// the left environments of image i when it is flagged META_LENV (the two chains are
+// independent and latency-bound, so one launch runs them side by side).
 template <typename T, int CHI>
 __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ meta, int n_images,
                                                    const cx<T>* __restrict__ arena,
                                                    const int32_t* __restrict__ bonds,
                                                    cx<T>* __restrict__ renv, int64_t renv_stride,
+                                                   cx<T>* __restrict__ lenv,
                                                    T* __restrict__ norm_out) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // one warp per image and one image per CTA (block-wide syncs are warp syncs)
     const int lane = threadIdx.x;
+    if ((int)blockIdx.x >= n_images) {
+        const int li = blockIdx.x - n_images;
+        if (!lenv || li >= n_images) return;
+        const ImageMeta ml = meta[li];
+        if (ml.flags & META_LENV)
+            lenv_image<T, CHI>(ml, arena, bonds, lenv + (size_t)li * renv_stride,
+                               reinterpret_cast<cx<T>*>(smem_raw), lane);
+        return;
+    }
     const int img = blockIdx.x;
-    if (img >= n_images) return;
     cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
     cx<T>* Abuf[2] = {base, base + 3 * MAT};   // site j in one, site j-1 arriving in the other
     cx<T>* R = base + 2 * MAT;
-    cx<T>* S = base + 6 * MAT;
+    cx<T>* S = base + 5 * MAT;                 // CHI rows of ZS (env_bytes)
     const ImageMeta mt = meta[img];
     const int n = mt.n, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;

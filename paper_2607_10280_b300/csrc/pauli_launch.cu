@@ -32,21 +32,20 @@ template <typename T, int CHI>
 mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
     using Lay = PauliLayout<T, CHI>;
     const int limit = smem_optin_limit();
-    const size_t smem = Lay::bytes;
+    const size_t smem = Lay::env_bytes;
     if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "environment kernel shared memory %zu B", smem);
     auto rk = renv_kernel<T, CHI>;
     CUDA_TRY(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     timing_begin(b, KIND_RENV);
-    rk<<<b->B, 32, smem, b->stream>>>(
+    // right environments of every image; with operator-product images also their left
+    // environments, in the same launch (CTAs B .. 2B)
+    rk<<<b->any_lenv ? 2 * b->B : b->B, 32, smem, b->stream>>>(
         b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
-        reinterpret_cast<cx<T>*>(b->renv), b->renv_stride, reinterpret_cast<T*>(b->norms));
+        reinterpret_cast<cx<T>*>(b->renv), b->renv_stride,
+        reinterpret_cast<cx<T>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<T*>(b->norms));
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
-    if (b->any_lenv) {
-        const mps_status st = launch_lenv(b);
-        if (st != MPS_OK) return st;
-    }
     // the diagonal pair sets are compiled for 2-warp teams only
     if (diag) return launch_pauli_uw<T, CHI, 2, true>(b, out);
     switch (b->pauli_warps) {

@@ -16,6 +16,12 @@ circuit  per two-qubit step on theta = (2 Dl) x (2 Dr) with inner bond Dm:
 renv     per site                                 8 * (2 Dl Dr^2 + 2 Dl^2 Dr)
 pauli    per column unit: E_a and closings at its sites, the carried closing
          matrices through p - 1 sites per row     3 * 8 * (2 Dl Dr^2 + 2 Dl^2 Dr)
+
+Ladder circuits without truncation and 2^L <= min(chi, padding, 16) take the
+operator-product path (ladder_mpo.cu): bond 2^L at every inner cut, the circuit
+only applies one-qubit gates (32 Dl Dr per site and layer; the CNOT ladder copies
+entries), the environment launch adds left environments at the cost of the right
+ones, and each E_a of the Pauli kernel first forms L A (8 * 2 Dl^2 Dr).
 """
 from __future__ import annotations
 
@@ -99,9 +105,13 @@ def renv_flops(bonds) -> float:
     return sum(8.0 * (2 * bonds[j] * bonds[j + 1] ** 2 + 2 * bonds[j] ** 2 * bonds[j + 1]) for j in range(n))
 
 
-def pauli_flops(p: int, bonds) -> float:
-    """Flops of the Pauli kernel for one image (all p column units)."""
+def pauli_flops(p: int, bonds, lenv: bool = False) -> float:
+    """Flops of the Pauli kernel for one image (all p column units); lenv: the image
+    brings left environments (each E_a first forms L A)."""
     f = 0.0
+
+    def env_a(Dl, Dr):
+        return 8.0 * 2 * Dl * Dl * Dr if lenv else 0.0
 
     def transfer(Dl, Dr):  # C <- sum_s conj(A^s) C A^{sT}
         return 8.0 * (2 * Dl * Dr * Dr + 2 * Dl * Dl * Dr)
@@ -110,7 +120,7 @@ def pauli_flops(p: int, bonds) -> float:
         for row in range(p - 1, -1, -1):
             j = row * p + c
             Dl, Dr = bonds[j], bonds[j + 1]
-            f += 3 * 8.0 * Dr * Dr * 2 * Dl          # E_a
+            f += 3 * 8.0 * Dr * Dr * 2 * Dl + env_a(Dl, Dr)   # E_a
             f += 3 * 8.0 * Dr * Dr                   # <E_a, R>
             if row < p - 1:
                 f += 9 * 8.0 * Dr * Dr               # vertical closing
@@ -120,7 +130,7 @@ def pauli_flops(p: int, bonds) -> float:
             k0 = j - 1
             if c > 0:
                 D0 = bonds[k0]
-                f += 3 * 8.0 * Dl * Dl * 2 * D0 + 12 * 8.0 * Dl * Dl
+                f += 3 * 8.0 * Dl * Dl * 2 * D0 + 12 * 8.0 * Dl * Dl + env_a(D0, Dl)
             if row == 0:
                 break
             for k in range(k0, j - p, -1):
@@ -129,8 +139,37 @@ def pauli_flops(p: int, bonds) -> float:
     return f
 
 
+def padding(p: int, chi: int) -> int:
+    """Site padding of an image (the library's layout rule)."""
+    n = p * p
+    cap = 1
+    while cap < chi and cap < (1 << min(n // 2, 20)):
+        cap <<= 1
+    cap = min(cap, chi, 32)
+    ld = 4
+    while ld < cap:
+        ld <<= 1
+    return ld
+
+
+def operator_product_path(p: int, L: int, chi: int, ansatz: str = "ladder") -> bool:
+    """Whether the library runs the circuit as an operator product (ladder_mpo.cu)."""
+    return ansatz == "ladder" and 1 <= L <= 4 and (1 << L) <= min(padding(p, chi), chi, 16)
+
+
 def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder") -> dict:
     n = p * p
+    if operator_product_path(p, L, chi, ansatz):
+        D = 1 << L
+        bonds = [1] + [D] * (n - 1) + [1]
+        circ = 0.0
+        for k in range(n):
+            dl = dr = 1
+            for _ in range(L):
+                circ += 32.0 * dl * dr
+                dl = dl if k == 0 else 2 * dl
+                dr = dr if k == n - 1 else 2 * dr
+        # environments: right and left, in one launch
+        return {"circuit": circ, "renv": 2 * renv_flops(bonds), "pauli": pauli_flops(p, bonds, lenv=True)}
     _, bonds = circuit_schedule(n, L, chi, ansatz)
-    return {"circuit": circuit_flops(n, L, chi, ansatz), "renv": renv_flops(bonds),
-            "pauli": pauli_flops(p, bonds)}
+    return {"circuit": circuit_flops(n, L, chi, ansatz), "renv": renv_flops(bonds), "pauli": pauli_flops(p, bonds)}
