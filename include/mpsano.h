@@ -113,6 +113,11 @@ mps_status mps_destroy_batch(mps_batch* batch);
 /* Run the circuit on every image (Sec. II.B): reset to |0...0>, apply the gate list,
  * and after every two-qubit gate truncate the bond to chi at the orthogonality
  * centre (keep the largest min(chi, 2D_left, 2D_right) singular values, renormalise).
+ * A ladder circuit in which nothing is truncated, with 1 <= L <= 4 and 2^L within the
+ * image's chi and site padding, is built exactly without any factorisation (the CNOT
+ * ladder as a bond-2 operator, see mps_set_layer_pipeline): its MPS has bond 2^L at
+ * every inner cut and is not left-canonical; the Pauli cache then contracts left
+ * environments as well.  Same state, represented differently (mps_bond_dims).
  *   pixels  device, float64, packed [sum_i n_i] in image order, values in [0, 1]
  *   circ    host, see mps_circuit
  * Asynchronous. */
@@ -207,7 +212,8 @@ const char* mps_last_error(void);
 int64_t mps_pair_count(int32_t p, int32_t pair_set);
 
 /* Copy bond dimensions to the host: out [sum_i (n_i + 1)], image i's block holds
- * D_0 = 1, D_1, ..., D_{n_i} = 1 (D_k = left bond of site k).  Synchronous. */
+ * D_0 = 1, D_1, ..., D_{n_i} = 1 (D_k = left bond of site k; 2^L at every inner cut
+ * for an image built as an operator product, see mps_apply_circuit).  Synchronous. */
 mps_status mps_bond_dims(mps_batch* batch, int32_t* out);
 
 /* Copy per-image discarded weight sum_steps sum(dropped sigma^2)/sum(sigma^2) of
@@ -231,14 +237,19 @@ uint64_t mps_launch_count(void);
 mps_status mps_set_launch_shape(mps_batch* batch, int32_t images_per_cta, int32_t circuit_threads,
                                 int32_t pauli_threads);
 
-/* Layer pipelining of the circuit kernel (enable != 0: on, the default).  When the
- * ansatz is the ladder, no step of any image truncates (min(2 D_left, 2 D_right) <= chi
- * at every two-qubit gate) and no image has more than 4 layers, one warp per layer
- * works on each image and layer l applies its gate at bond k as soon as layer l-1
- * has finished bond k+1 (Sec. II.B's gate order is kept for every qubit).  Every
- * split is then exact, so the resulting MPS equals the one of the sequential sweep;
- * other circuits always run the sequential sweep.  Takes effect at the next
- * mps_apply_circuit. */
+/* Fast paths for ladder circuits (enable != 0: on, the default), chosen per image.
+ * An image whose ladder circuit truncates nowhere (min(2 D_left, 2 D_right) <= chi at
+ * every two-qubit gate) with 1 <= L <= 4:
+ *  - if 2^L <= min(chi, site padding, 16): operator product.  The ladder of CNOTs maps
+ *    |x_0 x_1 ...> to the prefix parities |x_0, x_0^x_1, ...>; as an operator its
+ *    bond carries the running parity, so each layer (one-qubit gates, then the
+ *    ladder) doubles every bond by copying entries, and every site tensor is built
+ *    on its own (exact, no factorisation; bond 2^L; not left-canonical);
+ *  - else: layer pipelining, one warp per layer; layer l applies its gate at bond k
+ *    as soon as layer l-1 has finished bond k+1 (Sec. II.B's gate order is kept for
+ *    every qubit), every split exact, the MPS equal to the sequential sweep's.
+ * Other circuits, and every circuit with enable = 0, run the sequential sweep.  Takes
+ * effect at the next mps_apply_circuit. */
 mps_status mps_set_layer_pipeline(mps_batch* batch, int32_t enable);
 
 /* Per-launch timing with CUDA events recorded on the batch's stream around each
