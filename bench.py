@@ -34,8 +34,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 PROFILED = {
     "pauli": ("profiles/pauli_kernel_7x7_L4_chi16_b1024.md",
               ("pauli.cuh", "pauli_launch.cu", "linalg.cuh", "common.cuh")),
-    "circuit": ("profiles/circuit_wave_kernel_7x7_L4_chi16_b1024.md",
-                ("circuit.cuh", "circuit_launch.cuh", "linalg.cuh", "common.cuh")),
+    "circuit": ("profiles/ladder_mpo_kernel_7x7_L4_chi16_b1024.md",
+                ("ladder_mpo.cu", "circuit.cuh", "common.cuh")),
     "renv": ("profiles/renv_kernel_7x7_L4_chi16_b1024.md",
              ("pauli.cuh", "pauli_launch.cu", "linalg.cuh", "common.cuh")),
 }
