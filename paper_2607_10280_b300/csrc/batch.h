@@ -108,8 +108,8 @@ inline mps_status launch_circuit_orth64(mps_batch* b, int chi_tpl, bool trunc, c
 // Fill b->gates (allocated by the caller) with the one-qubit gate table of a circuit.
 mps_status launch_gate_table(mps_batch* b, int ansatz, int L_max, const double* params, int params_n,
                              const double* pixels);
-// Ladder circuits as operator products for b->run_order[0 .. run_count) (ladder_mpo.cu).
-mps_status launch_ladder_mpo(mps_batch* b, const double* pixels);
+// Circuits as operator products for b->run_order[0 .. run_count) (ladder_mpo.cu).
+mps_status launch_ladder_mpo(mps_batch* b, const double* pixels, int ansatz);
 mps_status launch_pauli_fp64(mps_batch* b, void* out, bool diag = false);
 mps_status launch_pauli_mixed(mps_batch* b, void* out, bool diag = false);
 

@@ -1,5 +1,5 @@
-// Ladder circuit as an operator product (Sec. II.B, Eq. 3), and the left environments
-// it then needs.
+// Circuits as operator products (Sec. II.B, Eq. 3), and the left environments they
+// then need.
 //
 // The CNOT ladder CNOT(0->1), CNOT(1->2), ..., CNOT(n-2->n-1) applied in that order
 // maps the basis state |x_0 x_1 ... x_{n-1}> to |p_0 p_1 ... p_{n-1}> with the prefix
@@ -14,6 +14,15 @@
 // MPS with bond 2^L at every inner cut, site by site and without any factorisation:
 // ladder_mpo_kernel builds each site tensor independently.  No step truncates, so this
 // path is for circuits with 2^L <= chi; the state is exact up to rounding.
+//
+// The paper's brick-wall layer (CNOTs on the even bonds, then on the odd bonds) has
+// the same form: a CNOT is sum_c |c><c| (x) X^c, i.e. the projector P_c on the control
+// and X^c on the target joined by a bond index c, and every bond carries one CNOT per
+// layer.  Site k gets P_b from the CNOT on its right bond and X^a from the one on its
+// left bond, in the order the layer applies them: left first (P_b X^a: the whole
+// ladder, and the odd sites of the brick-wall), giving A[l][a xor b][r] at output bit
+// b, or right first (X^a P_b: the even sites of the brick-wall), giving A[l][b][r] at
+// output bit a xor b.
 //
 // The result is not left-canonical (a layer's operator keeps left orthonormality only
 // where the incoming parity is summed, not at site 0), so the Pauli kernel contracts
@@ -36,7 +45,7 @@ constexpr int MPO_WARPS = 4;
 template <typename T>
 __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
     const ImageMeta* __restrict__ meta, int n_images, const int32_t* __restrict__ order,
-    const double* __restrict__ pixels, const cx<T>* __restrict__ gates, int gn,
+    const double* __restrict__ pixels, const cx<T>* __restrict__ gates, int gn, int ansatz,
     cx<T>* __restrict__ arena, int32_t* __restrict__ bonds_out, double* __restrict__ discarded_out,
     int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -56,19 +65,22 @@ __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
     for (int k = warp; k < n; k += MPO_WARPS) {
         cx<T>* cur = buf + (size_t)warp * 2 * MPO_BUF;
         cx<T>* nxt = cur + MPO_BUF;
-        // encoding R_Y(pi x) on |0>
+        // ladder: the encoding R_Y(pi x) on |0>; paper: |0> (it encodes in every layer)
         if (lane == 0) {
-            double sn, cs;
-            sincos(0.5 * M_PI * px[k], &sn, &cs);
+            double sn = 0.0, cs = 1.0;
+            if (ansatz == 0) sincos(0.5 * M_PI * px[k], &sn, &cs);
             cur[0] = mk<T>(T(cs), T(0));
             cur[1] = mk<T>(T(sn), T(0));
         }
+        // the CNOT on the right bond acts before the one on the left bond (brick-wall,
+        // even site): X^a P_b; otherwise P_b X^a
+        const bool right_first = ansatz != 0 && (k & 1) == 0;
         // every dimension is a power of two: indices by shifts and masks
         int sl = 0, sr = 0;   // log2 Dl, log2 Dr
         for (int layer = 0; layer < L; ++layer) {
             __syncwarp();
             // the layer's one-qubit gate on the physical index
-            const Gate1<T> g = table_gate<T>(gates, gn, 0, layer, img, k);
+            const Gate1<T> g = table_gate<T>(gates, gn, ansatz, layer, img, k);
             for (int e = lane; e < (1 << (sl + sr)); e += 32) {
                 const int l = e >> sr, r = e & ((1 << sr) - 1);
                 const int i0 = ((2 * l) << sr) + r, i1 = i0 + (1 << sr);
@@ -77,7 +89,7 @@ __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
                 cur[i1] = cdot2(g.u10, a0, g.u11, a1);
             }
             __syncwarp();
-            // the layer's CNOT ladder: new bond index = old index + old dimension * parity
+            // the layer's CNOTs: new bond index = old index + old dimension * bond bit
             const int sl2 = k == 0 ? sl : sl + 1;
             const int sr2 = k == n - 1 ? sr : sr + 1;
             for (int e = lane; e < (2 << (sl2 + sr2)); e += 32) {
@@ -88,7 +100,8 @@ __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
                     v = cur[((2 * l + (a ^ s)) << sr) + r2];
                 } else {
                     const int b = r2 >> sr, r = r2 & ((1 << sr) - 1);
-                    v = s == b ? cur[((2 * l + (a ^ b)) << sr) + r] : czero<T>();
+                    if (right_first) v = s == (a ^ b) ? cur[((2 * l + b) << sr) + r] : czero<T>();
+                    else v = s == b ? cur[((2 * l + (a ^ b)) << sr) + r] : czero<T>();
                 }
                 nxt[e] = v;
             }
@@ -113,13 +126,13 @@ __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
 }
 
 template <typename T>
-mps_status launch_mpo_t(mps_batch* b, const double* pixels) {
+mps_status launch_mpo_t(mps_batch* b, const double* pixels, int ansatz) {
     auto k = ladder_mpo_kernel<T>;
     const size_t smem = sizeof(cx<T>) * 2 * MPO_BUF * MPO_WARPS;
     CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     timing_begin(b, KIND_CIRCUIT);
     k<<<b->run_count, 32 * MPO_WARPS, smem, b->stream>>>(b->meta_d, b->run_count, b->run_order, pixels,
-                                                      reinterpret_cast<const cx<T>*>(b->gates), b->gate_n,
+                                                      reinterpret_cast<const cx<T>*>(b->gates), b->gate_n, ansatz,
                                                       reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
                                                       b->discarded_d, b->status_d);
     timing_end(b);
@@ -130,8 +143,8 @@ mps_status launch_mpo_t(mps_batch* b, const double* pixels) {
 
 }  // namespace
 
-mps_status launch_ladder_mpo(mps_batch* b, const double* pixels) {
-    return b->prec == MPS_FP64 ? launch_mpo_t<double>(b, pixels) : launch_mpo_t<float>(b, pixels);
+mps_status launch_ladder_mpo(mps_batch* b, const double* pixels, int ansatz) {
+    return b->prec == MPS_FP64 ? launch_mpo_t<double>(b, pixels, ansatz) : launch_mpo_t<float>(b, pixels, ansatz);
 }
 
 }  // namespace mpsano

@@ -456,9 +456,9 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     int mx = 1, mx_wave = 1, mx_seq = 1;
     bool trunc_seq = false;
     bool changed = false;
-    // A pipelined image whose 2^L fits its padding and its chi takes the operator-product
-    // path (ladder_mpo.cu: bond 2^L at every inner cut, not left-canonical, flagged
-    // META_LENV for the Pauli kernel).
+    // An image whose circuit (either ansatz) truncates nowhere, with 1 <= L <= 4 and 2^L
+    // within its padding and chi, takes the operator-product path (ladder_mpo.cu: bond
+    // 2^L at every inner cut, not left-canonical, flagged META_LENV for the Pauli kernel).
     std::vector<char> wave(b->B, 0), mpo(b->B, 0);
     int n_wave = 0, n_mpo = 0;
     for (int i = 0; i < b->B; ++i) {
@@ -468,8 +468,9 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         bool t = false;
         int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
         if (bi > m.ld) return fail(MPS_ERR_UNSUPPORTED, "image %d reaches bond %d > padding %d", i, bi, m.ld);
-        const bool pipe = b->layer_pipeline && circ->ansatz == MPS_ANSATZ_LADDER && !t && L >= 1 && L <= WAVE_LAYERS;
-        mpo[i] = pipe && (1 << L) <= std::min(m.ld, m.chi) && (1 << L) <= 16;
+        const bool fast = b->layer_pipeline && !t && L >= 1 && L <= WAVE_LAYERS;   // nothing truncates
+        const bool pipe = fast && circ->ansatz == MPS_ANSATZ_LADDER;
+        mpo[i] = fast && (1 << L) <= std::min(m.ld, m.chi) && (1 << L) <= 16;
         const int32_t fl = mpo[i] ? META_LENV : 0;
         if (m.flags != fl) { m.flags = fl; changed = true; }
         if (mpo[i]) {
@@ -548,7 +549,7 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         b->use_wave = false;
         b->run_order = b->order_d;
         b->run_count = n_mpo;
-        st = launch_ladder_mpo(b, pixels);
+        st = launch_ladder_mpo(b, pixels, circ->ansatz);
         if (st != MPS_OK) return st;
     }
     if (n_wave > 0) {

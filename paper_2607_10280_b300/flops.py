@@ -17,7 +17,7 @@ renv     per site                                 8 * (2 Dl Dr^2 + 2 Dl^2 Dr)
 pauli    per column unit: E_a and closings at its sites, the carried closing
          matrices through p - 1 sites per row     3 * 8 * (2 Dl Dr^2 + 2 Dl^2 Dr)
 
-Ladder circuits without truncation and 2^L <= min(chi, padding, 16) take the
+Circuits without truncation and 2^L <= min(chi, padding, 16) take the
 operator-product path (ladder_mpo.cu): bond 2^L at every inner cut, the circuit
 only applies one-qubit gates (32 Dl Dr per site and layer; the CNOT ladder copies
 entries), the environment launch adds left environments at the cost of the right
@@ -153,8 +153,10 @@ def padding(p: int, chi: int) -> int:
 
 
 def operator_product_path(p: int, L: int, chi: int, ansatz: str = "ladder") -> bool:
-    """Whether the library runs the circuit as an operator product (ladder_mpo.cu)."""
-    return ansatz == "ladder" and 1 <= L <= 4 and (1 << L) <= min(padding(p, chi), chi, 16)
+    """Whether the library runs the circuit (either ansatz) as an operator product
+    (ladder_mpo.cu)."""
+    # 2^L <= chi: no cut ever needs more (each layer crosses a cut with one CNOT)
+    return 1 <= L <= 4 and (1 << L) <= min(padding(p, chi), chi, 16)
 
 
 def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder") -> dict:

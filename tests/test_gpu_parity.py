@@ -170,7 +170,7 @@ def _ld(p, chi):
 
 
 def _operator_product_path(p, L, chi):
-    """Whether the library runs a ladder image as an operator product (bond 2^L)."""
+    """Whether the library runs an image as an operator product (bond 2^L)."""
     return 1 <= L <= 4 and (1 << L) <= min(_ld(p, chi), chi, 16)
 
 
@@ -453,19 +453,24 @@ def test_bond_caps_above_the_exact_bond_change_nothing():
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_paper_ansatz_exact_regime_rank_revealing_splits(precision):
-    """Paper ansatz (Sec. II.B), 7x7, L = 3 at chi = 8 = 2^L and chi = 64: the odd-bond
-    sub-layer's theta has twice the rows and columns of its rank bound 2^c, and the
-    pivoted-QR split keeps exactly the rank (bonds <= 2^L) while the oracle keeps the
-    zero singular values.  Pauli caches match the exact oracle."""
+    """Paper ansatz (Sec. II.B), 7x7, L = 3 at chi = 8 = 2^L and chi = 64.  Sequential
+    sweep: the odd-bond sub-layer's theta has twice the rows and columns of its rank
+    bound 2^c, and the pivoted-QR split keeps exactly the rank (bonds <= 2^L) while the
+    oracle keeps the zero singular values.  Operator-product path (the brick-wall CNOTs
+    as bond-2 operators): bond 2^L at every inner cut.  Both match the exact oracle."""
     p, L = 7, 3
     X = list(synth.garment_pixels(3, p, seed=130))
     ref = [oracle_cache(X[i], p, L, 64, ansatz="paper")[0] for i in range(3)]
-    for chi in (8, 64):
-        got, bonds, disc = run_gpu(X, [p] * 3, L, chi, precision, ansatz="paper")
-        assert all(max(b) <= 2 ** L for b in bonds)
-        assert np.all(np.asarray(disc) == 0.0)          # nothing lossy
-        for i in range(3):
-            assert np.max(np.abs(got[i] - ref[i])) < TOL[precision], (chi, i)
+    for pipeline in (False, True):
+        for chi in (8, 64):
+            got, bonds, disc = run_gpu(X, [p] * 3, L, chi, precision, ansatz="paper", pipeline=pipeline)
+            if pipeline:
+                assert all(list(b) == [1] + [2 ** L] * (p * p - 1) + [1] for b in bonds)
+            else:
+                assert all(max(b) <= 2 ** L for b in bonds)
+            assert np.all(np.asarray(disc) == 0.0)          # nothing lossy
+            for i in range(3):
+                assert np.max(np.abs(got[i] - ref[i])) < TOL[precision], (pipeline, chi, i)
 
 
 def test_mixed_batch_routes_each_image_by_its_own_circuit():
