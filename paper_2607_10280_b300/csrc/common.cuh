@@ -79,6 +79,10 @@ struct ImageMeta {
 // ImageMeta::flags: the Pauli kernel contracts the left environments L_i (written by
 // lenv_kernel) instead of taking them as the identity.
 constexpr int32_t META_LENV = 1;
+// ImageMeta::flags: every site but the last is half-structured (A[2l+s][r] = 0 unless
+// r / (D_right / 2) == s: a ladder circuit built as an operator product), so the
+// contractions over a site's right index run over half of it (see times_site_t).
+constexpr int32_t META_HALF = 2;
 
 // Device status word: first error wins.
 enum : int { DEV_OK = 0, DEV_BOND_OVERFLOW = 1, DEV_SMEM_OVERFLOW = 2, DEV_BAD_SHAPE = 3 };

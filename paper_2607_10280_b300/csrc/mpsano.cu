@@ -471,7 +471,7 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         const bool fast = b->layer_pipeline && !t && L >= 1 && L <= WAVE_LAYERS;   // nothing truncates
         const bool pipe = fast && circ->ansatz == MPS_ANSATZ_LADDER;
         mpo[i] = fast && (1 << L) <= std::min(m.ld, m.chi) && (1 << L) <= 16;
-        const int32_t fl = mpo[i] ? META_LENV : 0;
+        const int32_t fl = mpo[i] ? (META_LENV | (circ->ansatz == MPS_ANSATZ_LADDER ? META_HALF : 0)) : 0;
         if (m.flags != fl) { m.flags = fl; changed = true; }
         if (mpo[i]) {
             bi = 1 << L;

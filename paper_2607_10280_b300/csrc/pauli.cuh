@@ -142,10 +142,27 @@ __device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as
 // times the transposed site rows n = 2l + s < 2 Dl.
 __device__ __forceinline__ void team_sync() { __syncthreads(); }
 
+// half: the site is "half-structured": A[2l+s][r] = 0 unless r lies in half s of the
+// right bond (s h <= r < (s+1) h, h = Dr/2), as every site but the last of a ladder
+// circuit built as an operator product (the last layer's parity bit is the top bit of
+// the right bond and equals the output bit).  The contractions over r then run over
+// that half only; the skipped terms are exact zeros, which leave an fma chain
+// unchanged, so the result is the same bit for bit at half the work.
 template <typename T, int CHI, int NB, int NTHR, int KU = 1>
-__device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane) {
+__device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane,
+                                             bool half = false) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
+    if (half) {
+        const int h = Dr >> 1;
+        using Tl = Tile<T, NB * CHI, CHI, NTHR>;
+        for (int s = 0; s < 2; ++s)   // the columns 2l'+s of one physical index
+            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
+                C, [Dr, s, h](int m) { return (m / Dr) * MAT + (m % Dr) * CS + s * h; }, 1, 0,
+                A, [s, h](int l) { return (2 * l + s) * CS + s * h; }, 1, 0, NB * Dr, Dl, h,
+                [s](int l) { return 2 * l + s; }, [S](int m, int sn, cx<T> v) { S[m * ZS + sn] = v; }, lane);
+        return;
+    }
     using Tl = Tile<T, NB * CHI, 2 * CHI, NTHR>;
     team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
         C, [Dr](int m) { return (m / Dr) * MAT + (m % Dr) * CS; }, 1, 0,
@@ -157,15 +174,19 @@ __device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<
 //   C_b <- sum_s conj(A^s) C_b A^{sT}     (C_b: Dr x Dr in, Dl x Dl out)
 // with S[b*Dr + r][2l'+s] = (C_b A^{sT})[r][l'] as the intermediate.
 template <typename T, int CHI, int NB, int NTHR, int KU = 1>
-__device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane) {
+__device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane,
+                                         bool half = false) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    times_site_t<T, CHI, NB, NTHR, KU>(C, A, S, Dl, Dr, lane);
+    times_site_t<T, CHI, NB, NTHR, KU>(C, A, S, Dl, Dr, lane, half);
     team_sync();
+    // segment s: r over half s of the right bond when the site is half-structured
+    const int K = half ? Dr >> 1 : Dr;
+    const int h = half ? Dr >> 1 : 0;
     using Tl = Tile<T, CHI, NB * CHI, NTHR>;
     team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
-        A, [](int l) { return 2 * l * CS; }, 1, CS,
-        S, [Dl, Dr](int n) { return (n / Dl) * Dr * ZS + 2 * (n % Dl); }, ZS, 1, Dl, NB * Dl, Dr,
+        A, [](int l) { return 2 * l * CS; }, 1, CS + h,
+        S, [Dl, Dr](int n) { return (n / Dl) * Dr * ZS + 2 * (n % Dl); }, ZS, 1 + h * ZS, Dl, NB * Dl, K,
         [Dl](int n) { return (n / Dl) * MAT + (n % Dl); },
         [C](int l, int sn, cx<T> v) { C[l * CS + sn] = v; }, lane);
     team_sync();
@@ -270,16 +291,27 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
 //   M = C_X + i C_Y = 2 G01 and C_Z.
 template <typename T, int CHI, int NTHR>
 __device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* R, cx<T>* C, cx<T>* S,
-                                               int Dl, int Dr, int lane) {
+                                               int Dl, int Dr, int lane, bool half = false) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    times_site_t<T, CHI, 1, NTHR>(R, A, S, Dl, Dr, lane);   // S[r][n] = (R A^T)[r][n]
+    times_site_t<T, CHI, 1, NTHR>(R, A, S, Dl, Dr, lane, half);   // S[r][n] = (R A^T)[r][n]
     team_sync();
     cx<T>* G = S + CHI * ZS;
-    using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
-        A, [](int m) { return m * CS; }, 1, 0, S, [](int n) { return n; }, ZS, 0, 2 * Dl, 2 * Dl, Dr,
-        [](int n) { return n; }, [G](int m, int sn, cx<T> v) { G[m * ZS + sn] = v; }, lane);
+    if (half) {
+        // rows 2l+s of G contract r over half s only (see times_site_t)
+        const int h = Dr >> 1;
+        using Tl = Tile<T, CHI, 2 * CHI, NTHR>;
+        for (int s = 0; s < 2; ++s)
+            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+                A, [s, h](int l) { return (2 * l + s) * CS + s * h; }, 1, 0, S + s * h * ZS, [](int n) { return n; },
+                ZS, 0, Dl, 2 * Dl, h, [](int n) { return n; },
+                [G, s](int l, int sn, cx<T> v) { G[(2 * l + s) * ZS + sn] = v; }, lane);
+    } else {
+        using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
+        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+            A, [](int m) { return m * CS; }, 1, 0, S, [](int n) { return n; }, ZS, 0, 2 * Dl, 2 * Dl, Dr,
+            [](int n) { return n; }, [G](int m, int sn, cx<T> v) { G[m * ZS + sn] = v; }, lane);
+    }
     team_sync();
     team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int l, int lp) {
         const cx<T> g00 = G[(2 * l) * ZS + 2 * lp], g01 = G[(2 * l) * ZS + 2 * lp + 1];
@@ -380,6 +412,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     }
     const int img = blockIdx.x;
     cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
+    const bool half_img = (meta[img].flags & META_HALF) != 0;
     cx<T>* Abuf[2] = {base, base + 3 * MAT};   // site j in one, site j-1 arriving in the other
     cx<T>* R = base + 2 * MAT;
     cx<T>* S = base + 5 * MAT;                 // CHI rows of ZS (env_bytes)
@@ -405,7 +438,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
         cp_async_wait_all();
         __syncwarp();
         if (j > 0) prefetch(j - 1, Abuf[cb ^ 1]);
-        transfer<T, CHI, 1, 32, 2>(R, Abuf[cb], S, Dl, Dr, lane);
+        transfer<T, CHI, 1, 32, 2>(R, Abuf[cb], S, Dl, Dr, lane, half_img && j < n - 1 && Dr >= 2);
         cb ^= 1;
     }
     if (lane == 0) norm_out[img] = R[0].re;
@@ -444,6 +477,9 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
     // left environments (images whose MPS is not left-canonical), same layout as renv
     const cx<T>* lgb = (lenv && (mt.flags & META_LENV)) ? lenv + (size_t)img * renv_stride : nullptr;
     auto lenv_of = [lgb](int i) -> const cx<T>* { return lgb ? lgb + (size_t)i * CHI * CHI : nullptr; };
+    // half-structured sites (META_HALF): every site but the last
+    const bool half_img = (mt.flags & META_HALF) != 0;
+    auto half_at = [half_img, &mt, bd](int i) { return half_img && i < mt.n - 1 && bd[i + 1] >= 2; };
     const T inv_norm = T(1) / norms[img];
     T* outp = out + (size_t)(diag ? mt.pair_off_d : mt.pair_off) * 16;
     const int nh = p * (p - 1);                  // horizontal pairs come first, then vertical,
@@ -483,10 +519,10 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
         if (has_dd) {
             for (int o = lane; o < 2 * MAT; o += NTHR) Cd[o] = C[o];
             team_sync();
-            transfer<T, CHI, 2, NTHR>(Cd, A, S, Dl, Dr, lane);
+            transfer<T, CHI, 2, NTHR>(Cd, A, S, Dl, Dr, lane, half_at(j));
         }
         // closings of site j as a right site
-        right_closings<T, CHI, NTHR>(A, R, C, S, Dl, Dr, lane);
+        right_closings<T, CHI, NTHR>(A, R, C, S, Dl, Dr, lane, half_at(j));
         T single_prev[3];
         for (int b = 0; b < 3; ++b) { single_prev[b] = single_up[b]; single_up[b] = single_j[b]; }
         if (c == 0 && row == 0) break;
@@ -530,7 +566,7 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
                 write_pair(base_da + (row - 1) * (p - 1) + c, single_k, single_j, dd);
                 team_sync();
             }
-            transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane);
+            transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane, half_at(k));
         }
     }
 }

@@ -21,7 +21,10 @@ Circuits without truncation and 2^L <= min(chi, padding, 16) take the
 operator-product path (ladder_mpo.cu): bond 2^L at every inner cut, the circuit
 only applies one-qubit gates (32 Dl Dr per site and layer; the CNOT ladder copies
 entries), the environment launch adds left environments at the cost of the right
-ones, and each E_a of the Pauli kernel first forms L A (8 * 2 Dl^2 Dr).
+ones, and each E_a of the Pauli kernel first forms L A (8 * 2 Dl^2 Dr).  For the
+ladder every site but the last is half-structured (A[2l+s][r] = 0 unless r is in
+half s of the right bond), and the transfers, right closings and right-environment
+steps contract half of it.
 """
 from __future__ import annotations
 
@@ -100,15 +103,23 @@ def circuit_flops(n: int, L: int, chi: int, ansatz: str = "ladder", jacobi_sweep
     return f
 
 
-def renv_flops(bonds) -> float:
+def renv_flops(bonds, half: bool = False) -> float:
+    """half: every site but the last is half-structured (its contractions over the
+    right index run over half of it, pauli.cuh times_site_t)."""
     n = len(bonds) - 1
-    return sum(8.0 * (2 * bonds[j] * bonds[j + 1] ** 2 + 2 * bonds[j] ** 2 * bonds[j + 1]) for j in range(n))
+    return sum(8.0 * (2 * bonds[j] * bonds[j + 1] ** 2 + 2 * bonds[j] ** 2 * bonds[j + 1])
+               * (0.5 if half and j < n - 1 else 1.0) for j in range(n))
 
 
-def pauli_flops(p: int, bonds, lenv: bool = False) -> float:
+def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
     """Flops of the Pauli kernel for one image (all p column units); lenv: the image
-    brings left environments (each E_a first forms L A)."""
+    brings left environments (each E_a first forms L A); half: every site but the last
+    is half-structured (transfers and right closings contract half the right index)."""
     f = 0.0
+    n = len(bonds) - 1
+
+    def hf(k):
+        return 0.5 if half and k < n - 1 else 1.0
 
     def env_a(Dl, Dr):
         return 8.0 * 2 * Dl * Dl * Dr if lenv else 0.0
@@ -124,7 +135,7 @@ def pauli_flops(p: int, bonds, lenv: bool = False) -> float:
             f += 3 * 8.0 * Dr * Dr                   # <E_a, R>
             if row < p - 1:
                 f += 9 * 8.0 * Dr * Dr               # vertical closing
-            f += 8.0 * (2 * Dl * Dr * Dr + 3 * Dl * Dl * Dr)   # right closings
+            f += 8.0 * (2 * Dl * Dr * Dr + 3 * Dl * Dl * Dr) * hf(j)   # right closings
             if c == 0 and row == 0:
                 break
             k0 = j - 1
@@ -135,7 +146,7 @@ def pauli_flops(p: int, bonds, lenv: bool = False) -> float:
                 break
             for k in range(k0, j - p, -1):
                 # two carried matrices: M = C_X + i C_Y and C_Z
-                f += 2 * transfer(bonds[k], bonds[k + 1])
+                f += 2 * transfer(bonds[k], bonds[k + 1]) * hf(k)
     return f
 
 
@@ -171,7 +182,9 @@ def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder") -> dict:
                 circ += 32.0 * dl * dr
                 dl = dl if k == 0 else 2 * dl
                 dr = dr if k == n - 1 else 2 * dr
-        # environments: right and left, in one launch
-        return {"circuit": circ, "renv": 2 * renv_flops(bonds), "pauli": pauli_flops(p, bonds, lenv=True)}
+        # environments: right (half-structured sites for the ladder) and left, in one launch
+        half = ansatz == "ladder"
+        return {"circuit": circ, "renv": renv_flops(bonds, half) + renv_flops(bonds),
+                "pauli": pauli_flops(p, bonds, lenv=True, half=half)}
     _, bonds = circuit_schedule(n, L, chi, ansatz)
     return {"circuit": circuit_flops(n, L, chi, ansatz), "renv": renv_flops(bonds), "pauli": pauli_flops(p, bonds)}
