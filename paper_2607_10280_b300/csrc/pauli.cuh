@@ -194,12 +194,24 @@ __device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int
 
 // F[m][n] = sum_l conj(A[2l+s_m][r_m]) A[2l+s_n][r_n], m = s_m*Dr + r_m, n = s_n*Dr + r_n:
 // the four physical blocks F_{ss'} of a left site, into S rows CHI .. CHI + 2 Dr.
+// half (a half-structured site, see times_site_t): F_ss'[r][r'] vanishes unless r is
+// in half s and r' in half s', so one Dr x Dr matrix F'[r][r'] = F_{s(r) s(r')}[r][r']
+// (s(r) = r >= Dr/2) holds every nonzero value, at a quarter of the work.
 template <typename T, int CHI, int NTHR>
-__device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane) {
+__device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane, bool half = false) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, ZS = Lay::ZS;
-    using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
     cx<T>* F = S + CHI * ZS;
+    if (half) {
+        const int h = Dr >> 1;
+        auto off = [h](int r) { return (r >= h ? CS : 0) + r; };
+        using Tl = Tile<T, CHI, CHI, NTHR>;
+        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+            A, off, 2 * CS, 0, A, off, 2 * CS, 0, Dr, Dr, Dl,
+            [](int n) { return n; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
+        return;
+    }
+    using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
     auto off = [Dr](int m) { return (m / Dr) * CS + (m % Dr); };
     team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
         A, off, 2 * CS, 0, A, off, 2 * CS, 0, 2 * Dr, 2 * Dr, Dl,
@@ -212,13 +224,30 @@ __device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, in
 // T[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r] in S rows 0 .. Dl.
 template <typename T, int CHI, int NTHR>
 __device__ __forceinline__ void left_blocks_env(const cx<T>* A, const cx<T>* Lg, cx<T>* S, int Dl, int Dr,
-                                                int lane) {
+                                                int lane, bool half = false) {
     if (!Lg) {
-        left_blocks<T, CHI, NTHR>(A, S, Dl, Dr, lane);
+        left_blocks<T, CHI, NTHR>(A, S, Dl, Dr, lane, half);
         return;
     }
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, ZS = Lay::ZS;
+    if (half) {   // compact F' as in left_blocks, through T'[l][r'] = sum_l' L[l][l'] A[2l'+s(r')][r']
+        const int h = Dr >> 1;
+        auto off = [h](int r) { return (r >= h ? CS : 0) + r; };
+        {
+            using Tl = Tile<T, CHI, CHI, NTHR>;
+            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+                Lg, [](int l) { return l * CHI; }, 1, 0, A, off, 2 * CS, 0, Dl, Dr, Dl,
+                [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
+        }
+        team_sync();
+        cx<T>* F = S + CHI * ZS;
+        using Tl = Tile<T, CHI, CHI, NTHR>;
+        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+            A, off, 2 * CS, 0, S, [](int nn) { return nn; }, ZS, 0, Dr, Dr, Dl,
+            [](int nn) { return nn; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
+        return;
+    }
     {
         using Tl = Tile<T, CHI, 2 * CHI, NTHR>;
         team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
@@ -240,21 +269,32 @@ __device__ __forceinline__ void left_blocks_env(const cx<T>* A, const cx<T>* Lg,
 // depend on the team size; the other warps read the sums from red.
 template <typename T, int CHI, int NTHR>
 __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const cx<T>* R, int D, T* out,
-                                          T* red, int lane) {
+                                          T* red, int lane, bool half = false) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
     const cx<T>* F = S + CHI * ZS;
+    const int h = D >> 1;
     if (lane < 32) {
         T acc[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc[i] = T(0);
         team_for_2d<32, 4>(D, D, lane, [&](int r, int rp) {
-            const cx<T> f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
-            const cx<T> f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
             cx<T> e[3];
-            e[0] = f01 + f10;                                     // X
-            e[1] = mk<T>(f01.im - f10.im, f10.re - f01.re);       // Y: i (F10 - F01)
-            e[2] = f00 - f11;                                     // Z
+            if (half) {
+                // compact F' (left_blocks): the one nonzero block at (r, r') is F_{s s'}
+                // with s = r >= h, s' = r' >= h; the same values as the full form
+                const cx<T> f = F[r * ZS + rp], z = czero<T>();
+                const int s0 = r >= h, s1 = rp >= h;
+                e[0] = s0 != s1 ? f : z;                                                   // X
+                e[1] = s0 == s1 ? z : (s0 ? mk<T>(-f.im, f.re) : mk<T>(f.im, -f.re));      // Y
+                e[2] = s0 != s1 ? z : (s0 ? mk<T>(-f.re, -f.im) : f);                      // Z
+            } else {
+                const cx<T> f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
+                const cx<T> f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
+                e[0] = f01 + f10;                                     // X
+                e[1] = mk<T>(f01.im - f10.im, f10.re - f01.re);       // Y: i (F10 - F01)
+                e[2] = f00 - f11;                                     // Z
+            }
             cx<T> y[4];
             y[3] = R[r * CS + rp];
             if (C) {
@@ -507,9 +547,9 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
         load_mat<T, CS, NTHR>(R, rg + (size_t)j * CHI * CHI, CHI, Dr, lane);
         team_sync();
         // site j as the left site: single-site terms and the vertical pair (j, j+p)
-        left_blocks_env<T, CHI, NTHR>(A, lenv_of(j), S, Dl, Dr, lane);
+        left_blocks_env<T, CHI, NTHR>(A, lenv_of(j), S, Dl, Dr, lane, half_at(j));
         team_sync();
-        left_dots<T, CHI, NTHR>(S, row < p - 1 ? C : nullptr, R, Dr, d, red, lane);
+        left_dots<T, CHI, NTHR>(S, row < p - 1 ? C : nullptr, R, Dr, d, red, lane, half_at(j));
         T single_j[3];
         for (int a = 0; a < 3; ++a) single_j[a] = d[4 * a + 3] * inv_norm;
         if (row < p - 1) write_pair(nh + j, single_j, single_up, d);
@@ -534,14 +574,14 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
         if (c > 0) {
             load_mat<T, CS, NTHR>(R, rg + (size_t)k0 * CHI * CHI, CHI, Dl, lane);
             team_sync();
-            left_blocks_env<T, CHI, NTHR>(A, lenv_of(k0), S, Dl0, Dl, lane);
+            left_blocks_env<T, CHI, NTHR>(A, lenv_of(k0), S, Dl0, Dl, lane, half_at(k0));
             team_sync();
-            left_dots<T, CHI, NTHR>(S, C, R, Dl, d, red, lane);
+            left_dots<T, CHI, NTHR>(S, C, R, Dl, d, red, lane, half_at(k0));
             T single_k[3];
             for (int a = 0; a < 3; ++a) single_k[a] = d[4 * a + 3] * inv_norm;
             write_pair(row * (p - 1) + (c - 1), single_k, single_j, d);
             if (has_dd) {
-                left_dots<T, CHI, NTHR>(S, Cd, R, Dl, dd, red, lane);
+                left_dots<T, CHI, NTHR>(S, Cd, R, Dl, dd, red, lane, half_at(k0));
                 write_pair(base_dd + row * (p - 1) + (c - 1), single_k, single_prev, dd);
             }
             team_sync();
@@ -558,9 +598,9 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
                 // anti-diagonal (row-1, c+1)-(row, c): site k is the left site
                 load_mat<T, CS, NTHR>(R, rg + (size_t)k * CHI * CHI, CHI, Drk, lane);
                 team_sync();
-                left_blocks_env<T, CHI, NTHR>(A, lenv_of(k), S, Dlk, Drk, lane);
+                left_blocks_env<T, CHI, NTHR>(A, lenv_of(k), S, Dlk, Drk, lane, half_at(k));
                 team_sync();
-                left_dots<T, CHI, NTHR>(S, C, R, Drk, dd, red, lane);
+                left_dots<T, CHI, NTHR>(S, C, R, Drk, dd, red, lane, half_at(k));
                 T single_k[3];
                 for (int a = 0; a < 3; ++a) single_k[a] = dd[4 * a + 3] * inv_norm;
                 write_pair(base_da + (row - 1) * (p - 1) + c, single_k, single_j, dd);

@@ -121,6 +121,9 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
     def hf(k):
         return 0.5 if half and k < n - 1 else 1.0
 
+    def hq(k):   # E_a of a half-structured site: one compact Dr x Dr block product
+        return 0.25 if half and k < n - 1 else 1.0
+
     def env_a(Dl, Dr):
         return 8.0 * 2 * Dl * Dl * Dr if lenv else 0.0
 
@@ -131,7 +134,7 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
         for row in range(p - 1, -1, -1):
             j = row * p + c
             Dl, Dr = bonds[j], bonds[j + 1]
-            f += 3 * 8.0 * Dr * Dr * 2 * Dl + env_a(Dl, Dr)   # E_a
+            f += (3 * 8.0 * Dr * Dr * 2 * Dl + env_a(Dl, Dr)) * hq(j)   # E_a
             f += 3 * 8.0 * Dr * Dr                   # <E_a, R>
             if row < p - 1:
                 f += 9 * 8.0 * Dr * Dr               # vertical closing
@@ -141,7 +144,7 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
             k0 = j - 1
             if c > 0:
                 D0 = bonds[k0]
-                f += 3 * 8.0 * Dl * Dl * 2 * D0 + 12 * 8.0 * Dl * Dl + env_a(D0, Dl)
+                f += (3 * 8.0 * Dl * Dl * 2 * D0 + env_a(D0, Dl)) * hq(k0) + 12 * 8.0 * Dl * Dl
             if row == 0:
                 break
             for k in range(k0, j - p, -1):
