@@ -401,12 +401,35 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt, const cx<T>* __r
     const cx<T>* sites = arena + mt.site_off;
     if (lane == 0) Lm[0] = mk<T>(T(1), T(0));
     __syncwarp();
+    const bool half_img = (mt.flags & META_HALF) != 0;
     for (int k = 0; k < n; ++k) {
         const int Dl = bd[k], Dr = bd[k + 1];
         cx<T>* dst = lg + (size_t)k * CHI * CHI;
         team_for_2d<32, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
         load_site_p<T, CS, 32>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
         __syncwarp();
+        if (half_img && k < n - 1 && Dr >= 2) {
+            // half-structured site: L A is needed only at (s, r) with r in half s
+            // (T'[l][r] = sum_l' L[l][l'] A[2l'+s(r)][r]), and L_{k+1} is block diagonal
+            // over the two halves (zero between them, as the full form gives)
+            const int h = Dr >> 1;
+            auto off = [h](int r) { return (r >= h ? CS : 0) + r; };
+            {
+                using Tl = Tile<T, CHI, CHI, 32>;
+                team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+                    Lm, [](int l) { return l * CS; }, 1, 0, A, off, 2 * CS, 0, Dl, Dr, Dl,
+                    [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
+            }
+            __syncwarp();
+            {
+                using Tl = Tile<T, CHI, CHI, 32>;
+                team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+                    A, off, 2 * CS, 0, S, [](int nn) { return nn; }, ZS, 0, Dr, Dr, Dl, [](int nn) { return nn; },
+                    [Lm, h](int r, int sn, cx<T> v) { Lm[r * CS + sn] = (r >= h) == (sn >= h) ? v : czero<T>(); }, lane);
+            }
+            __syncwarp();
+            continue;
+        }
         // S[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r]
         {
             using Tl = Tile<T, CHI, 2 * CHI, 32>;

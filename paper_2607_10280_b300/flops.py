@@ -187,7 +187,7 @@ def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder") -> dict:
                 dr = dr if k == n - 1 else 2 * dr
         # environments: right (half-structured sites for the ladder) and left, in one launch
         half = ansatz == "ladder"
-        return {"circuit": circ, "renv": renv_flops(bonds, half) + renv_flops(bonds),
+        return {"circuit": circ, "renv": 2 * renv_flops(bonds, half),
                 "pauli": pauli_flops(p, bonds, lenv=True, half=half)}
     _, bonds = circuit_schedule(n, L, chi, ansatz)
     return {"circuit": circuit_flops(n, L, chi, ansatz), "renv": renv_flops(bonds), "pauli": pauli_flops(p, bonds)}
