@@ -178,7 +178,24 @@ __device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int
                                          bool half = false) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    times_site_t<T, CHI, NB, NTHR, KU>(C, A, S, Dl, Dr, lane, half);
+    if (half) {
+        // A^s touches half s of the right bond only, so the transfer reads only the two
+        // diagonal blocks of C_b: S[b Dr + s h + i][2l'+s] = sum_{k<h} C_b[s h + i][s h + k]
+        // A[2l'+s][s h + k], i < h (the rows the second product reads)
+        const int h = Dr >> 1;
+        using Tl = Tile<T, NB * CHI / 2, CHI, NTHR>;
+        for (int s = 0; s < 2; ++s)
+            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
+                C, [s, h](int m) { const int b = m / h, i = m - b * h; return b * MAT + (s * h + i) * CS + s * h; }, 1, 0,
+                A, [s, h](int l) { return (2 * l + s) * CS + s * h; }, 1, 0, NB * h, Dl, h,
+                [s](int l) { return 2 * l + s; },
+                [S, s, h, Dr](int m, int sn, cx<T> v) {
+                    const int b = m / h, i = m - b * h;
+                    S[(b * Dr + s * h + i) * ZS + sn] = v;
+                }, lane);
+    } else {
+        times_site_t<T, CHI, NB, NTHR, KU>(C, A, S, Dl, Dr, lane);
+    }
     team_sync();
     // segment s: r over half s of the right bond when the site is half-structured
     const int K = half ? Dr >> 1 : Dr;
