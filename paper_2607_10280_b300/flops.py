@@ -193,7 +193,10 @@ def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder") -> dict:
                 dr = dr if k == n - 1 else 2 * dr
         # environments: right (half-structured sites for the ladder) and left, in one launch
         half = ansatz == "ladder"
-        return {"circuit": circ, "renv": 2 * renv_flops(bonds, half),
+        # left chain: L A on the needed half, block-diagonal result (half the dense work)
+        lenv = sum(8.0 * (2 * bonds[j] ** 2 * bonds[j + 1] + 2 * bonds[j] * bonds[j + 1] ** 2)
+                   * (0.5 if half and j < n - 1 else 1.0) for j in range(n))
+        return {"circuit": circ, "renv": renv_flops(bonds, half) + lenv,
                 "pauli": pauli_flops(p, bonds, lenv=True, half=half)}
     _, bonds = circuit_schedule(n, L, chi, ansatz)
     return {"circuit": circuit_flops(n, L, chi, ansatz), "renv": renv_flops(bonds), "pauli": pauli_flops(p, bonds)}
