@@ -317,18 +317,20 @@ def run_ours(args):
     e2e_steps = max(3, args.steps // 2)
     # every step: pinned host pixels -> device, the whole path, results -> pinned host
     # memory, read on the host; a step's copies overlap the next step's kernels
-    t0 = time.perf_counter()
-    prev = None
-    for _ in range(e2e_steps):
-        k = pipe.submit(host_px)
-        if prev is not None:
-            res = pipe.result(prev)
-        prev = k
-    res = pipe.result(prev)
-    torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
+    with ClockSampler(clock_path.replace(".csv", "_e2e.csv")) as clk_e2e:
+        t0 = time.perf_counter()
+        prev = None
+        for _ in range(e2e_steps):
+            k = pipe.submit(host_px)
+            if prev is not None:
+                res = pipe.result(prev)
+            prev = k
+        res = pipe.result(prev)
+        torch.cuda.synchronize()
+        e2e_dt = time.perf_counter() - t0
     e2e = {"value": world * BATCH * e2e_steps / e2e_dt, "unit": "images/s",
-           "h2d_bytes_per_step": pipe.h2d_bytes, "d2h_bytes_per_step": pipe.d2h_bytes}
+           "h2d_bytes_per_step": pipe.h2d_bytes, "d2h_bytes_per_step": pipe.d2h_bytes,
+           "steps": e2e_steps, "clocks": clk_e2e.summary(local)}
 
     # ---------------- the plain per-image FP64 GPU path on a sample of the same images
     ns = args.fp64_sample
