@@ -38,6 +38,11 @@
 
 namespace mpsano {
 
+// Smallest right bond at which a half-structured site's split contractions (one
+// product per physical index, see times_site_t) beat the dense ones: below it the
+// two products of depth D/2 cost more in launch overhead than they save.
+constexpr int HALF_SPLIT_MIN = 8;
+
 template <typename T, int CHI>
 struct PauliLayout {
     static constexpr int CS = CHI + 1;
@@ -518,7 +523,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
         cp_async_wait_all();
         __syncwarp();
         if (j > 0) prefetch(j - 1, Abuf[cb ^ 1]);
-        transfer<T, CHI, 1, 32, 2>(R, Abuf[cb], S, Dl, Dr, lane, half_img && j < n - 1 && Dr >= 2);
+        transfer<T, CHI, 1, 32, 2>(R, Abuf[cb], S, Dl, Dr, lane, half_img && j < n - 1 && Dr >= HALF_SPLIT_MIN);
         cb ^= 1;
     }
     if (lane == 0) norm_out[img] = R[0].re;
@@ -557,9 +562,12 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
     // left environments (images whose MPS is not left-canonical), same layout as renv
     const cx<T>* lgb = (lenv && (mt.flags & META_LENV)) ? lenv + (size_t)img * renv_stride : nullptr;
     auto lenv_of = [lgb](int i) -> const cx<T>* { return lgb ? lgb + (size_t)i * CHI * CHI : nullptr; };
-    // half-structured sites (META_HALF): every site but the last
+    // half-structured sites (META_HALF): every site but the last.  half_at: the compact
+    // left blocks (one product either way); half_tr: the contractions that split into
+    // one product per physical index, from bond HALF_SPLIT_MIN on
     const bool half_img = (mt.flags & META_HALF) != 0;
     auto half_at = [half_img, &mt, bd](int i) { return half_img && i < mt.n - 1 && bd[i + 1] >= 2; };
+    auto half_tr = [half_img, &mt, bd](int i) { return half_img && i < mt.n - 1 && bd[i + 1] >= HALF_SPLIT_MIN; };
     const T inv_norm = T(1) / norms[img];
     T* outp = out + (size_t)(diag ? mt.pair_off_d : mt.pair_off) * 16;
     const int nh = p * (p - 1);                  // horizontal pairs come first, then vertical,
@@ -599,10 +607,10 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
         if (has_dd) {
             for (int o = lane; o < 2 * MAT; o += NTHR) Cd[o] = C[o];
             team_sync();
-            transfer<T, CHI, 2, NTHR>(Cd, A, S, Dl, Dr, lane, half_at(j));
+            transfer<T, CHI, 2, NTHR>(Cd, A, S, Dl, Dr, lane, half_tr(j));
         }
         // closings of site j as a right site
-        right_closings<T, CHI, NTHR>(A, R, C, S, Dl, Dr, lane, half_at(j));
+        right_closings<T, CHI, NTHR>(A, R, C, S, Dl, Dr, lane, half_tr(j));
         T single_prev[3];
         for (int b = 0; b < 3; ++b) { single_prev[b] = single_up[b]; single_up[b] = single_j[b]; }
         if (c == 0 && row == 0) break;
@@ -646,7 +654,7 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
                 write_pair(base_da + (row - 1) * (p - 1) + c, single_k, single_j, dd);
                 team_sync();
             }
-            transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane, half_at(k));
+            transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane, half_tr(k));
         }
     }
 }

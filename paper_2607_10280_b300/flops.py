@@ -103,11 +103,15 @@ def circuit_flops(n: int, L: int, chi: int, ansatz: str = "ladder", jacobi_sweep
     return f
 
 
+HALF_SPLIT_MIN = 8   # pauli.cuh: split contractions of half-structured sites from this bond on
+
+
 def renv_flops(bonds, half: bool = False) -> float:
     """half: every site but the last is half-structured (its contractions over the
-    right index run over half of it, pauli.cuh times_site_t)."""
+    right index run over half of it from bond HALF_SPLIT_MIN on, pauli.cuh times_site_t)."""
     n = len(bonds) - 1
-    return sum(_transfer(bonds[j], bonds[j + 1], half and j < n - 1) for j in range(n))
+    return sum(_transfer(bonds[j], bonds[j + 1], half and j < n - 1 and bonds[j + 1] >= HALF_SPLIT_MIN)
+               for j in range(n))
 
 
 def _transfer(Dl: int, Dr: int, half: bool = False) -> float:
@@ -125,7 +129,7 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
     n = len(bonds) - 1
 
     def hf(k):
-        return 0.5 if half and k < n - 1 else 1.0
+        return 0.5 if half and k < n - 1 and bonds[k + 1] >= HALF_SPLIT_MIN else 1.0
 
     def hq(k):   # E_a of a half-structured site: one compact Dr x Dr block product
         return 0.25 if half and k < n - 1 else 1.0
@@ -134,7 +138,7 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
         return 8.0 * 2 * Dl * Dl * Dr if lenv else 0.0
 
     def transfer(Dl, Dr, k):  # C <- sum_s conj(A^s) C A^{sT} through site k
-        return _transfer(Dl, Dr, half and k < n - 1)
+        return _transfer(Dl, Dr, half and k < n - 1 and Dr >= HALF_SPLIT_MIN)
 
     for c in range(p):
         for row in range(p - 1, -1, -1):
