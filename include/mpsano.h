@@ -252,6 +252,15 @@ mps_status mps_set_launch_shape(mps_batch* batch, int32_t images_per_cta, int32_
  * effect at the next mps_apply_circuit. */
 mps_status mps_set_layer_pipeline(mps_batch* batch, int32_t enable);
 
+/* Half-structured sites (enable != 0: on, the default).  A ladder circuit built as an
+ * operator product leaves every site but the last with A[l][s][r] = 0 unless r lies
+ * in half s of the right bond (the last layer's parity bit is the top bit of the
+ * right index and equals the output bit); the environment and Pauli kernels then
+ * contract over that half only.  The skipped terms are exact zeros, so results are
+ * bit-identical with enable = 0 (the dense contractions), which exists to check
+ * exactly that.  Takes effect at the next mps_apply_circuit. */
+mps_status mps_set_half_structure(mps_batch* batch, int32_t enable);
+
 /* Per-launch timing with CUDA events recorded on the batch's stream around each
  * kernel the batch launches (enable != 0 turns it on; off by default). */
 mps_status mps_set_timing(mps_batch* batch, int32_t enable);

@@ -132,6 +132,11 @@ class Batch:
         """Layer-pipelined circuit kernel where it applies (ladder, no truncation, L <= 4)."""
         check(lib().mps_set_layer_pipeline(self._h, 1 if enable else 0))
 
+    def set_half_structure(self, enable: bool = True):
+        """Contractions over half of the right bond at half-structured sites (ladder
+        circuits built as operator products); results are bit-identical either way."""
+        check(lib().mps_set_half_structure(self._h, 1 if enable else 0))
+
     def set_timing(self, enable: bool = True):
         check(lib().mps_set_timing(self._h, 1 if enable else 0))
 

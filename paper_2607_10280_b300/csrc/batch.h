@@ -40,6 +40,7 @@ struct mps_batch {
     bool gates_owned = true;               // false when gates points into static scratch
     int circuit_threads = 32;              // threads per image in the circuit kernel
     bool layer_pipeline = true;            // layer-pipelined kernel where it applies
+    bool half_structure = true;            // exploit half-structured sites (META_HALF)
     int L_max = 0;                         // most layers of any image in the last circuit
     // images of the next circuit launch: run_order[0 .. run_count), and whether the
     // layer-pipelined kernel runs them

@@ -432,6 +432,12 @@ mps_status mps_set_layer_pipeline(mps_batch* b, int32_t enable) {
     return MPS_OK;
 }
 
+mps_status mps_set_half_structure(mps_batch* b, int32_t enable) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    b->half_structure = enable != 0;
+    return MPS_OK;
+}
+
 mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circuit* circ) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
     if (!pixels) return fail(MPS_ERR_INVALID_ARG, "pixels is NULL");
@@ -471,7 +477,8 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         const bool fast = b->layer_pipeline && !t && L >= 1 && L <= WAVE_LAYERS;   // nothing truncates
         const bool pipe = fast && circ->ansatz == MPS_ANSATZ_LADDER;
         mpo[i] = fast && (1 << L) <= std::min(m.ld, m.chi) && (1 << L) <= 16;
-        const int32_t fl = mpo[i] ? (META_LENV | (circ->ansatz == MPS_ANSATZ_LADDER ? META_HALF : 0)) : 0;
+        const int32_t fl =
+            mpo[i] ? (META_LENV | (circ->ansatz == MPS_ANSATZ_LADDER && b->half_structure ? META_HALF : 0)) : 0;
         if (m.flags != fl) { m.flags = fl; changed = true; }
         if (mpo[i]) {
             bi = 1 << L;

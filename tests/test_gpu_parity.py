@@ -396,6 +396,32 @@ def test_layer_pipeline_equals_sequential_sweep(precision):
     assert np.max(np.abs(pip[0] - ref)) < TOL[precision]
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_half_structured_contractions_are_bit_identical(precision):
+    """Ladder circuits built as operator products: every site but the last vanishes
+    outside half s of its right bond, and the environment and Pauli kernels contract
+    over that half only.  The skipped terms are exact zeros, so the Pauli caches (H+V
+    and with diagonals) equal the dense contractions bit for bit, at L = 4 (bond 16,
+    split products) and L = 2 (bond 4, compact left blocks only)."""
+    from paper_2607_10280_b300.api import Batch
+    for p, L, chi in ((7, 4, 16), (5, 2, 8)):
+        X = synth.garment_pixels(3, p, seed=150 + L)
+        params = torch.tensor(synth.circuit_params(L, p * p, seed=151), dtype=torch.float64, device="cuda")
+        px = torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda")
+        caches = []
+        for half in (True, False):
+            b = Batch(np.full(3, p, np.int32), chi, precision)
+            b.set_half_structure(half)
+            b.apply_circuit(px, L, "ladder", params)
+            hv, hvd = b.pauli_cache(), b.pauli_cache(pair_set="hvd")
+            b.sync()
+            caches.append((hv.cpu().numpy(), hvd.cpu().numpy()))
+            b.close()
+        assert np.array_equal(caches[0][0], caches[1][0]) and np.array_equal(caches[0][1], caches[1][1]), (p, L)
+        ref, _ = oracle_cache(X[0], p, L, chi, params=params.cpu().numpy())
+        assert np.max(np.abs(caches[0][0][:len(ref)] - ref)) < TOL[precision]
+
+
 def test_layer_pipeline_falls_back_when_a_step_truncates():
     """chi < 2^L (a truncating pass): the sequential sweep runs whatever the switch."""
     p, L, chi = 5, 3, 4
