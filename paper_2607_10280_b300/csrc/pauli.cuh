@@ -178,9 +178,12 @@ __device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<
 // Transfer of NB matrices through a site A (Dl x 2 x Dr), in place:
 //   C_b <- sum_s conj(A^s) C_b A^{sT}     (C_b: Dr x Dr in, Dl x Dl out)
 // with S[b*Dr + r][2l'+s] = (C_b A^{sT})[r][l'] as the intermediate.
+// diag_out: only the two diagonal blocks of the result are needed (its next use is a
+// transfer through a half-structured site, which reads nothing else), so the second
+// product forms those blocks alone; the rest of C_b is left as it was.
 template <typename T, int CHI, int NB, int NTHR, int KU = 1>
 __device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane,
-                                         bool half = false) {
+                                         bool half = false, bool diag_out = false) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
     if (half) {
@@ -205,12 +208,24 @@ __device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int
     // segment s: r over half s of the right bond when the site is half-structured
     const int K = half ? Dr >> 1 : Dr;
     const int h = half ? Dr >> 1 : 0;
-    using Tl = Tile<T, CHI, NB * CHI, NTHR>;
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
-        A, [](int l) { return 2 * l * CS; }, 1, CS + h,
-        S, [Dl, Dr](int n) { return (n / Dl) * Dr * ZS + 2 * (n % Dl); }, ZS, 1 + h * ZS, Dl, NB * Dl, K,
-        [Dl](int n) { return (n / Dl) * MAT + (n % Dl); },
-        [C](int l, int sn, cx<T> v) { C[l * CS + sn] = v; }, lane);
+    if (diag_out) {
+        const int g = Dl >> 1;
+        using Tl = Tile<T, CHI / 2, NB * CHI / 2, NTHR>;
+        for (int q = 0; q < 2; ++q)   // rows and columns l, l' in half q of the left bond
+            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
+                A, [q, g](int i) { return 2 * (q * g + i) * CS; }, 1, CS + h,
+                S, [Dr, q, g](int nn) { const int b = nn / g, i = nn - b * g; return b * Dr * ZS + 2 * (q * g + i); },
+                ZS, 1 + h * ZS, g, NB * g, K,
+                [q, g](int nn) { const int b = nn / g, i = nn - b * g; return b * MAT + q * g + i; },
+                [C, q, g](int i, int sn, cx<T> v) { C[(q * g + i) * CS + sn] = v; }, lane);
+    } else {
+        using Tl = Tile<T, CHI, NB * CHI, NTHR>;
+        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
+            A, [](int l) { return 2 * l * CS; }, 1, CS + h,
+            S, [Dl, Dr](int n) { return (n / Dl) * Dr * ZS + 2 * (n % Dl); }, ZS, 1 + h * ZS, Dl, NB * Dl, K,
+            [Dl](int n) { return (n / Dl) * MAT + (n % Dl); },
+            [C](int l, int sn, cx<T> v) { C[l * CS + sn] = v; }, lane);
+    }
     team_sync();
 }
 
@@ -654,7 +669,10 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
                 write_pair(base_da + (row - 1) * (p - 1) + c, single_k, single_j, dd);
                 team_sync();
             }
-            transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane, half_tr(k));
+            // the last transfer brings the closings to site j - p, where they close in full;
+            // before it, their next use is the transfer through site k - 1 (H+V pairs)
+            const bool dout = !diag && k > j - p + 1 && half_tr(k - 1);
+            transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane, half_tr(k), dout);
         }
     }
 }

@@ -114,11 +114,13 @@ def renv_flops(bonds, half: bool = False) -> float:
                for j in range(n))
 
 
-def _transfer(Dl: int, Dr: int, half: bool = False) -> float:
+def _transfer(Dl: int, Dr: int, half: bool = False, diag_out: bool = False) -> float:
     """One matrix through a site: C A^T (Dr x 2Dl x Dr) then sum_s conj(A^s) (C A^T)^s
     (Dl x Dl x 2Dr); on a half-structured site only the diagonal blocks of C enter the
-    first product (a quarter) and half of the right index the second (a half)."""
-    return 8.0 * (2 * Dl * Dr * Dr * (0.25 if half else 1.0) + 2 * Dl * Dl * Dr * (0.5 if half else 1.0))
+    first product (a quarter) and half of the right index the second (a half);
+    diag_out: only the diagonal blocks of the result are formed (half the second)."""
+    return 8.0 * (2 * Dl * Dr * Dr * (0.25 if half else 1.0)
+                  + 2 * Dl * Dl * Dr * (0.5 if half else 1.0) * (0.5 if diag_out else 1.0))
 
 
 def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
@@ -137,8 +139,9 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
     def env_a(Dl, Dr):
         return 8.0 * 2 * Dl * Dl * Dr if lenv else 0.0
 
-    def transfer(Dl, Dr, k):  # C <- sum_s conj(A^s) C A^{sT} through site k
-        return _transfer(Dl, Dr, half and k < n - 1 and Dr >= HALF_SPLIT_MIN)
+    def transfer(Dl, Dr, k, last):  # C <- sum_s conj(A^s) C A^{sT} through site k
+        dout = half and not last and bonds[k] >= HALF_SPLIT_MIN   # next: through site k - 1
+        return _transfer(Dl, Dr, half and k < n - 1 and Dr >= HALF_SPLIT_MIN, dout)
 
     for c in range(p):
         for row in range(p - 1, -1, -1):
@@ -159,7 +162,7 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
                 break
             for k in range(k0, j - p, -1):
                 # two carried matrices: M = C_X + i C_Y and C_Z
-                f += 2 * transfer(bonds[k], bonds[k + 1], k)
+                f += 2 * transfer(bonds[k], bonds[k + 1], k, k == j - p + 1)
     return f
 
 
