@@ -312,9 +312,12 @@ def run_ours(args):
     pipe = api.Pipeline(np.full(BATCH, P, np.int32), CHI, L, "mixed", params, abd, W, bias, stream=stream)
     pipe.batch.set_launch_shape(shape["images_per_cta"], shape["circuit_threads"], shape["pauli_threads"])
     host_px = torch.tensor(X.reshape(-1), dtype=torch.float64).pin_memory()
-    pipe.run(host_px)
+    # untimed warm-up of every buffer slot of the pipeline (W steps, at least two rounds
+    # of the slots), as for the device-timed loop
+    for _ in range(max(args.warmup, 2 * len(pipe.slots))):
+        pipe.run(host_px)
     torch.cuda.synchronize()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, args.steps)
     # every step: pinned host pixels -> device, the whole path, results -> pinned host
     # memory, read on the host; a step's copies overlap the next step's kernels
     with ClockSampler(clock_path.replace(".csv", "_e2e.csv")) as clk_e2e:
