@@ -268,7 +268,9 @@ def run_ours(args):
     batch.kernel_times()
     n0 = api.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clock_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_rank{rank}.csv")
+    # raw clock samples (the JSON line carries their summary)
+    import tempfile
+    clock_path = os.path.join(os.environ.get("BENCH_OUT_DIR", tempfile.gettempdir()), f"bench_clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clock_path), exist_ok=True)
     if world > 1:
         torch.distributed.barrier()
