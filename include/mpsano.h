@@ -43,7 +43,7 @@ typedef enum {
     MPS_ERR_OOM = 2,          /* device allocation failed */
     MPS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
     MPS_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
-    MPS_ERR_UNSUPPORTED = 5,  /* valid request outside what this build supports */
+    MPS_ERR_UNSUPPORTED = 5,  /* valid request outside what the library supports */
     MPS_ERR_NOT_READY = 6,    /* e.g. Pauli cache requested before a circuit ran */
     MPS_ERR_DEVICE = 7        /* a device-side check failed (see mps_last_error) */
 } mps_status;
