@@ -186,7 +186,8 @@ def operator_product_path(p: int, L: int, chi: int, ansatz: str = "ladder") -> b
     return 1 <= L <= 4 and (1 << L) <= min(padding(p, chi), chi, 16)
 
 
-def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder") -> dict:
+def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder", dense: bool = False) -> dict:
+    """dense: count the operator-product path's contractions without the half-structure."""
     n = p * p
     if operator_product_path(p, L, chi, ansatz):
         D = 1 << L
@@ -199,7 +200,7 @@ def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder") -> dict:
                 dl = dl if k == 0 else 2 * dl
                 dr = dr if k == n - 1 else 2 * dr
         # environments: right (half-structured sites for the ladder) and left, in one launch
-        half = ansatz == "ladder"
+        half = ansatz == "ladder" and not dense
         # left chain: L A on the needed half, block-diagonal result (half the dense work)
         lenv = sum(8.0 * (2 * bonds[j] ** 2 * bonds[j + 1] + 2 * bonds[j] * bonds[j + 1] ** 2)
                    * (0.5 if half and j < n - 1 else 1.0) for j in range(n))
