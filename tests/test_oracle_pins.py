@@ -375,6 +375,69 @@ def test_first_near_exact_bond_dimension_7x7(ansatz):
 
 # ----------------------------------------------------------- invariants ----
 
+def _operator_product_sites(ansatz, x, L, params):
+    """Site tensors [Dl][2][Dr] of a circuit whose CNOT layers act as operators, from
+    the decomposition CNOT = sum_c P_c (x) X^c: every layer applies its one-qubit gates,
+    then each site gets, for its left and right bond bits (a, b), the physical operator
+    P_b X^a (left CNOT first: the ladder, odd sites of the brick-wall) or X^a P_b
+    (right CNOT first: even sites of the brick-wall), placed at bond indices
+    (l + Dl a, r + Dr b).  Written here from that derivation alone."""
+    n = len(x)
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    P = [np.diag([1.0, 0.0]).astype(complex), np.diag([0.0, 1.0]).astype(complex)]
+    sites = []
+    for k in range(n):
+        t = np.zeros((1, 2, 1), dtype=complex)
+        if ansatz == "ladder":
+            t[0, :, 0] = expm_ry(np.pi * x[k]) @ np.array([1.0, 0.0])
+        else:
+            t[0, 0, 0] = 1.0
+        for layer in range(L):
+            if ansatz == "ladder":
+                G = expm_rz(params[layer][k][1]) @ expm_ry(params[layer][k][0])
+            else:
+                G = expm_ry(2 * np.pi * x[k] - np.pi) @ ((P_X + P_Z) / np.sqrt(2))
+            t = np.einsum("st,ltr->lsr", G, t)
+            Dl, _, Dr = t.shape
+            has_l, has_r = k > 0, k < n - 1
+            u = np.zeros((2 * Dl if has_l else Dl, 2, 2 * Dr if has_r else Dr), dtype=complex)
+            right_first = ansatz == "paper" and k % 2 == 0
+            for a in range(2 if has_l else 1):
+                for b in range(2 if has_r else 1):
+                    Xa = np.linalg.matrix_power(X, a) if has_l else np.eye(2)
+                    Pb = P[b] if has_r else np.eye(2)
+                    O = Xa @ Pb if right_first else Pb @ Xa
+                    u[a * Dl:(a + 1) * Dl, :, b * Dr:(b + 1) * Dr] = np.einsum("st,ltr->lsr", O, t)
+            t = u
+        sites.append(t)
+    return sites
+
+
+@pytest.mark.parametrize("ansatz,p,L", [("ladder", 3, 3), ("ladder", 4, 2), ("paper", 3, 3), ("paper", 4, 2)])
+def test_cnot_layers_as_bond_two_operators(ansatz, p, L):
+    """The construction behind the GPU's operator-product path (Sec. II.B as operator
+    products): contracting the site tensors gives the dense statevector of the circuit,
+    every inner bond is 2^L, and the sites that path treats as half-structured (all but
+    the last for the ladder) vanish outside half s of their right bond."""
+    n = p * p
+    x = synth.garment_pixels(1, p, seed=160 + L)[0]
+    params = synth.circuit_params(L, n, seed=161) if ansatz == "ladder" else None
+    sites = _operator_product_sites(ansatz, x, L, params)
+    psi = sites[0][0]
+    for t in sites[1:]:
+        psi = np.einsum("...a,asb->...sb", psi, t)
+    psi = psi.reshape(-1)
+    ref = sv.run(n, circuit.build_circuit(ansatz, x, L, params)).reshape(-1)
+    assert np.max(np.abs(psi - ref)) < 1e-12
+    assert [t.shape[2] for t in sites[:-1]] == [2 ** L] * (n - 1)
+    for k, t in enumerate(sites[:-1]):
+        if ansatz == "paper" and k % 2 == 0 and k > 0:
+            continue   # even brick-wall sites: output bit a xor b, not half-structured
+        h = t.shape[2] // 2
+        for s in range(2):
+            assert np.all(t[:, s, (1 - s) * h:(2 - s) * h] == 0), (k, s)
+
+
 def test_state_invariants_truncated():
     p, L, chi = 4, 3, 3
     n = p * p
