@@ -103,7 +103,10 @@ mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* c
 /* Give an existing batch a new list of images (same precision and stream), reusing
  * its device memory when the new layout fits and growing it otherwise.  Waits for
  * the batch's queued work first.  Arguments as in mps_create_batch.  A circuit must
- * be applied again before mps_pauli_cache. */
+ * be applied again before mps_pauli_cache.  Refused arguments (MPS_ERR_INVALID_ARG)
+ * leave the batch unchanged; a reshape that fails later (MPS_ERR_OOM, MPS_ERR_CUDA)
+ * leaves it allocated but unusable: mps_apply_circuit, mps_bond_dims and
+ * mps_discarded_weight return MPS_ERR_NOT_READY until a reshape succeeds. */
 mps_status mps_reshape_batch(mps_batch* batch, int32_t n_images, const int32_t* p, const int32_t* chi,
                              int32_t chi_all);
 
@@ -120,7 +123,10 @@ mps_status mps_destroy_batch(mps_batch* batch);
  * environments as well.  Same state, represented differently (mps_bond_dims).
  *   pixels  device, float64, packed [sum_i n_i] in image order, values in [0, 1]
  *   circ    host, see mps_circuit
- * Asynchronous. */
+ * Asynchronous.  A call that fails after its argument checks (MPS_ERR_UNSUPPORTED for
+ * a circuit whose bond exceeds the image's padding, MPS_ERR_OOM, MPS_ERR_CUDA) leaves
+ * no circuit on the batch: mps_pauli_cache returns MPS_ERR_NOT_READY until a call
+ * succeeds. */
 mps_status mps_apply_circuit(mps_batch* batch, const double* pixels, const mps_circuit* circ);
 
 /* Pauli cache (Sec. II.C, Eq. 5): for every image-local pair and every alpha,

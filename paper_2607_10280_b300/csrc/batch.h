@@ -34,6 +34,8 @@ struct mps_batch {
     int64_t total_pairs_hv = 0, total_pairs_hvd = 0;
     int64_t total_bonds = 0;
     bool circuit_done = false;
+    bool layout_ok = false;                // device buffers match the host layout
+    bool meta_dirty = false;               // meta_h changed since its last upload
     void* gates = nullptr;                 // one-qubit gate table of the last circuit
     size_t gates_bytes = 0;
     int gate_n = 0;                        // qubit stride of the gate table

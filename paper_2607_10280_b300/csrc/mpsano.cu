@@ -364,7 +364,8 @@ mps_status fit_and_upload(mps_batch* b) {
                              cudaMemcpyHostToDevice, b->stream));
     TRY_GROW(cudaMemcpyAsync(b->meta_d, b->meta_pinned, sizeof(ImageMeta) * B, cudaMemcpyHostToDevice, b->stream));
 #undef TRY_GROW
-    b->circuit_done = false;
+    b->meta_dirty = false;
+    b->layout_ok = true;
     return MPS_OK;
 }
 
@@ -400,8 +401,14 @@ mps_status mps_reshape_batch(mps_batch* b, int32_t n_images, const int32_t* p, c
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
     // the previous layout's work and its pinned staging must be finished before reuse
     CUDA_TRY(cudaStreamSynchronize(b->stream));
+    // layout_images checks every argument before it changes the batch, so refused
+    // arguments leave the batch as it was.  Once the host layout has changed, nothing
+    // may launch on the batch until the device buffers match it: a reshape that fails
+    // in fit_and_upload (out of memory) leaves layout_ok false until one succeeds.
     mps_status st = layout_images(b, n_images, p, chi, chi_all);
     if (st != MPS_OK) return st;
+    b->circuit_done = false;
+    b->layout_ok = false;
     return fit_and_upload(b);
 }
 
@@ -415,12 +422,13 @@ mps_status mps_destroy_batch(mps_batch* b) {
 mps_status mps_set_launch_shape(mps_batch* b, int32_t images_per_cta, int32_t circuit_threads,
                                 int32_t pauli_threads) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    // all three checked before any is applied: a refused call changes nothing
     if (circuit_threads != 0 && circuit_threads != 32 && circuit_threads != 64 && circuit_threads != 128)
         return fail(MPS_ERR_INVALID_ARG, "circuit_threads %d (32, 64 or 128)", circuit_threads);
-    if (circuit_threads) b->circuit_threads = circuit_threads;
     if (images_per_cta < 0 || images_per_cta > 8) return fail(MPS_ERR_INVALID_ARG, "images_per_cta %d", images_per_cta);
     if (pauli_threads != 0 && pauli_threads != 32 && pauli_threads != 64 && pauli_threads != 128)
         return fail(MPS_ERR_INVALID_ARG, "pauli_threads %d (32, 64 or 128)", pauli_threads);
+    if (circuit_threads) b->circuit_threads = circuit_threads;
     if (images_per_cta) b->images_per_cta = images_per_cta;
     if (pauli_threads) b->pauli_warps = pauli_threads / 32;
     return MPS_OK;
@@ -444,6 +452,7 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     if (!circ) return fail(MPS_ERR_INVALID_ARG, "circuit is NULL");
     if (circ->ansatz != MPS_ANSATZ_LADDER && circ->ansatz != MPS_ANSATZ_PAPER)
         return fail(MPS_ERR_INVALID_ARG, "unknown ansatz %d", circ->ansatz);
+    if (!b->layout_ok) return fail(MPS_ERR_NOT_READY, "the batch's last reshape failed");
     int L_max = 0;
     for (int i = 0; i < b->B; ++i) {
         const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
@@ -455,13 +464,15 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         if (circ->params_n < b->n_max)
             return fail(MPS_ERR_INVALID_ARG, "params_n = %d < largest n = %d", circ->params_n, b->n_max);
     }
+    // arguments checked: a call that fails from here on leaves no circuit for
+    // mps_pauli_cache to read
+    b->circuit_done = false;
     // bond dimensions, shared-memory bucket and truncation per image.  Images whose
     // circuit the layer-pipelined kernel can run (ladder, nothing lossy, 1 <= L <= 4)
     // go to it, the others to the sequential kernel, so that an image's kernel (and
     // its result) depends on its own circuit only, not on the rest of the batch.
     int mx = 1, mx_wave = 1, mx_seq = 1;
     bool trunc_seq = false;
-    bool changed = false;
     // An image whose circuit (either ansatz) truncates nowhere, with 1 <= L <= 4 and 2^L
     // within its padding and chi, takes the operator-product path (ladder_mpo.cu: bond
     // 2^L at every inner cut, not left-canonical, flagged META_LENV for the Pauli kernel).
@@ -470,7 +481,7 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     for (int i = 0; i < b->B; ++i) {
         ImageMeta& m = b->meta_h[i];
         const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
-        if (m.L != L) { m.L = L; changed = true; }
+        if (m.L != L) { m.L = L; b->meta_dirty = true; }
         bool t = false;
         int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
         if (bi > m.ld) return fail(MPS_ERR_UNSUPPORTED, "image %d reaches bond %d > padding %d", i, bi, m.ld);
@@ -479,7 +490,7 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         mpo[i] = fast && (1 << L) <= std::min(m.ld, m.chi) && (1 << L) <= 16;
         const int32_t fl =
             mpo[i] ? (META_LENV | (circ->ansatz == MPS_ANSATZ_LADDER && b->half_structure ? META_HALF : 0)) : 0;
-        if (m.flags != fl) { m.flags = fl; changed = true; }
+        if (m.flags != fl) { m.flags = fl; b->meta_dirty = true; }
         if (mpo[i]) {
             bi = 1 << L;
             ++n_mpo;
@@ -523,11 +534,14 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
                                  b->stream));
         b->order_h = order;
     }
-    if (changed) {
+    // uploaded whenever meta_h differs from the device copy, also when an earlier
+    // call changed meta_h and then failed before its upload
+    if (b->meta_dirty) {
         CUDA_TRY(cudaStreamSynchronize(b->stream));  // pinned staging may still be in flight
         std::memcpy(b->meta_pinned, b->meta_h.data(), sizeof(ImageMeta) * b->B);
         CUDA_TRY(cudaMemcpyAsync(b->meta_d, b->meta_pinned, sizeof(ImageMeta) * b->B,
                                  cudaMemcpyHostToDevice, b->stream));
+        b->meta_dirty = false;
     }
     // one-qubit gate table (FP64 math, rounded to the state type)
     const int rows = circ->ansatz == MPS_ANSATZ_LADDER ? L_max : b->B;
@@ -650,6 +664,7 @@ mps_status mps_sync(mps_batch* b) {
 
 mps_status mps_bond_dims(mps_batch* b, int32_t* out) {
     if (!b || !out) return fail(MPS_ERR_INVALID_ARG, "batch and out must be non-NULL");
+    if (!b->layout_ok) return fail(MPS_ERR_NOT_READY, "the batch's last reshape failed");
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     CUDA_TRY(cudaMemcpy(out, b->bonds_d, sizeof(int32_t) * b->total_bonds, cudaMemcpyDeviceToHost));
     return MPS_OK;
@@ -679,6 +694,7 @@ mps_status mps_kernel_times(mps_batch* b, double* ms, int64_t* launches) {
 
 mps_status mps_discarded_weight(mps_batch* b, double* out) {
     if (!b || !out) return fail(MPS_ERR_INVALID_ARG, "batch and out must be non-NULL");
+    if (!b->layout_ok) return fail(MPS_ERR_NOT_READY, "the batch's last reshape failed");
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     CUDA_TRY(cudaMemcpy(out, b->discarded_d, sizeof(double) * b->B, cudaMemcpyDeviceToHost));
     return MPS_OK;

@@ -517,3 +517,44 @@ def test_mixed_batch_routes_each_image_by_its_own_circuit():
     for i in range(6):
         alone, _, _ = run_gpu([X[i]], [p], 3, int(chis[i]), "mixed", params=params)
         assert np.array_equal(mixed[i * m:(i + 1) * m], alone[0]), i
+
+
+def test_failed_calls_leave_no_stale_state():
+    """Error paths of the batch handle: a circuit refused after its argument checks
+    (a bond above the image's padding) leaves no circuit for the Pauli cache to read;
+    the next good circuit gives the oracle's values; refused reshape arguments leave
+    the batch and its circuit as they were; a reshape asks for a new circuit."""
+    from paper_2607_10280_b300._lib import MpsError
+    from paper_2607_10280_b300.api import Batch
+    p, chi = 4, 64          # padding 32 (the largest compiled bond)
+    X = synth.garment_pixels(2, p, seed=31)
+    params = synth.circuit_params(6, p * p, seed=32)
+    px = torch.tensor(np.concatenate(X), dtype=torch.float64, device="cuda")
+    pr = torch.tensor(params, dtype=torch.float64, device="cuda").contiguous()
+    b = Batch(np.array([p, p], dtype=np.int32), chi, "mixed")
+    b.apply_circuit(px, [2, 2], "ladder", pr)
+    first = b.pauli_cache().clone()
+    with pytest.raises(MpsError) as e:
+        b.apply_circuit(px, [3, 6], "ladder", pr)      # bond 64 > padding 32 at image 1
+    assert e.value.status == 5
+    with pytest.raises(MpsError) as e:
+        b.pauli_cache()
+    assert e.value.status == 6
+    b.apply_circuit(px, [2, 2], "ladder", pr)
+    again = b.pauli_cache()
+    b.sync()
+    assert torch.equal(first, again)
+    res = again.double().cpu().numpy()
+    for i in range(2):
+        ref, _ = oracle_cache(X[i], p, 2, chi, params=params)
+        got = res[b.pair_offsets[i]:b.pair_offsets[i + 1]]
+        assert np.max(np.abs(got - ref)) < TOL["mixed"]
+    with pytest.raises(MpsError) as e:
+        b.reshape([1], chi)                           # p = 1 refused: nothing changes
+    assert e.value.status == 1
+    assert torch.equal(b.pauli_cache(), first)
+    b.reshape([3], chi)
+    with pytest.raises(MpsError) as e:
+        b.pauli_cache()
+    assert e.value.status == 6
+    b.close()
