@@ -140,7 +140,8 @@ mps_status mps_pauli_cache(mps_batch* batch, int32_t pair_set, void* out, int64_
 
 /* ANO features and linear reconstruction (Sec. II.A, II.C; Eq. 1, 4, 5, 6) for a batch
  * of images that share one pair layout of m pairs.
- *   pauli        device [n_images][m][16], float32 (pauli_f64 = 0) or float64 (= 1)
+ *   pauli        device [n_images][m][16], float32 (pauli_f64 = 0) or float64 (= 1);
+ *                1 <= n_images <= 2^31 - 1, m >= 1 (MPS_ERR_INVALID_ARG otherwise)
  *   abd          device float32 [m][16]: A[6] real off-diagonal, B[6] imaginary
  *                off-diagonal of H_q for (k,l) = (0,1),(0,2),(0,3),(1,2),(1,3),(2,3),
  *                D[4] diagonal; c_{q,alpha} = Tr(H_q P_alpha)/4 (Eq. 4)

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -612,6 +613,7 @@ mps_status ano_features(const void* pauli, int32_t pauli_f64, int64_t n_images, 
                         void* stream) {
     if (!pauli || !abd || !features) return fail(MPS_ERR_INVALID_ARG, "pauli, abd and features must be non-NULL");
     if (n_images <= 0 || m <= 0) return fail(MPS_ERR_INVALID_ARG, "n_images and m must be positive");
+    if (n_images > INT32_MAX) return fail(MPS_ERR_INVALID_ARG, "n_images %lld above 2^31 - 1", (long long)n_images);
     if (W && (!out || out_dim <= 0)) return fail(MPS_ERR_INVALID_ARG, "linear layer needs out and out_dim > 0");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int64_t tot = n_images * (int64_t)m;

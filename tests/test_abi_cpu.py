@@ -60,6 +60,10 @@ def test_host_side_validation(lib):
     assert lib.mps_destroy_batch(None) == 0
     assert lib.mps_sync(None) == 1
     assert lib.ano_features(None, 0, 1, 1, None, None, None, 0, None, None, None) == 1
+    # refused before any launch: the (host) buffers are never read
+    buf = (ctypes.c_float * 16)()
+    assert lib.ano_features(buf, 0, 1 << 31, 1, buf, None, None, 0, buf, None, None) == 1
+    assert b"2^31" in lib.mps_last_error()
 
 
 def test_pair_counts(lib):
