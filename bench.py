@@ -97,9 +97,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-sample", type=int, default=8, help="images timed through the per-image FP64 path")
     ap.add_argument("--batch", type=int, default=BATCH, help="images per GPU (profiling of smaller cases)")
-    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "uneven", "large", "serve", "train"],
+    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "uneven", "large", "serve", "train", "diag"],
                     help="headline (default): 7x7 L=4 chi=16; the others are the chi x L sweep, the uneven "
-                         "batch, the 16x16 batch and the serving run")
+                         "batch, the 16x16 batch, the serving run, training on cached Paulis and the "
+                         "156-pair layout with diagonals")
     ap.add_argument("--requests", type=int, default=20000, help="serving run: number of requests (10 s at 2000/s)")
     return ap.parse_args()
 
@@ -380,6 +381,54 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ other configurations
+def run_diag(args):
+    """The paper's full 7x7 pair layout: horizontal, vertical and both diagonal
+    neighbours (156 pairs), 1024 images, L = 4, chi = 16, mixed precision, then ANO
+    (156 x 16) and a linear layer 156 -> 784; beside it the same batch with the 84
+    H+V pairs.  The site tensors (205 MB) exceed L2, so timed steps read HBM."""
+    torch = _setup_torch()
+    from oracle import pipeline as opipe
+    from paper_2607_10280_b300 import api, synth
+    p, B, L, chi = 7, 1024, 4, 16
+    X = synth.garment_pixels(B, p)
+    params_np = synth.circuit_params(L, p * p)
+    params = torch.tensor(params_np, dtype=torch.float64, device="cuda")
+    px = torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda")
+    sample = [0, B // 2, B - 1]
+    rows = {}
+    for pair_set, diagonals in (("hvd", True), ("hv", False)):
+        m = api.pair_count(p, pair_set)
+        abd = torch.tensor(synth.observable_params(m), dtype=torch.float32, device="cuda")
+        W = torch.tensor(np.random.default_rng(3).standard_normal((p * p * 16, m)) / np.sqrt(m),
+                         dtype=torch.float32, device="cuda")
+        bias = torch.zeros(p * p * 16, dtype=torch.float32, device="cuda")
+        b = api.Batch(np.full(B, p, np.int32), chi, "mixed")
+        pauli = torch.empty((B * m, 16), dtype=torch.float32, device="cuda")
+
+        def step():
+            b.apply_circuit(px, L, "ladder", params)
+            b.pauli_cache(pauli, pair_set)
+            return api.ano_features(pauli, m, abd, W, bias)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        ms = _time_events(torch, step, max(10, args.steps))
+        got = pauli.double().cpu().numpy().reshape(B, m, 16)
+        err = max(float(np.max(np.abs(got[i] - opipe.pauli_cache(X[i], p, L, chi, "ladder", params_np,
+                                                                   diagonals=diagonals))))
+                  for i in sample)
+        rows[pair_set] = {"pairs": m, "ms_per_step": ms, "images_per_s": B / (ms / 1e3),
+                          "max_err_vs_oracle_sampled": err}
+        b.close()
+        print(json.dumps({pair_set: rows[pair_set]}), file=sys.stderr, flush=True)
+    line = {"metric": "images/s, 7x7 L=4 chi=16 batch 1024, 156 H+V+diagonal pairs + ANO + linear 156->784",
+            "value": rows["hvd"]["images_per_s"], "unit": "images/s", "n_gpus": 1,
+            "config": {"workload": "7x7 garment-like, ladder ansatz, L=4, chi=16, mixed; pair sets hvd (156) and hv (84)",
+                       "images": B, "l2": "site tensors 205 MB > L2"},
+            "table": rows}
+    print(json.dumps(line), flush=True)
+
+
 def _setup_torch():
     import torch
     rank, world, local = dist_env()
@@ -670,4 +719,4 @@ if __name__ == "__main__":
         run_ours(a)
     else:
         {"sweep": run_sweep, "uneven": run_uneven, "large": run_large, "serve": run_serve,
-         "train": run_train}[a.config](a)
+         "train": run_train, "diag": run_diag}[a.config](a)
