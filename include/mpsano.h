@@ -90,7 +90,12 @@ typedef struct {
  *   chi_all  bond cap when chi == NULL, 1 <= chi <= MPS_CHI_LIMIT.  Any chi is a cap:
  *            bonds only grow to min(chi, 2 D_left, 2 D_right) (e.g. at most 2^L for
  *            the ladder), and the kernels hold bonds up to MPS_BOND_LIMIT; a circuit
- *            that would need more returns MPS_ERR_UNSUPPORTED from mps_apply_circuit
+ *            that would need more returns MPS_ERR_UNSUPPORTED from mps_apply_circuit.
+ *            So does a circuit that truncates at a bond above 16 under MPS_FP64 or
+ *            MPS_MIXED_ORTH64: the FP64 factorisation workspace for bond 32 (about
+ *            290 KB and 248 KB per image) exceeds the shared memory of a block;
+ *            MPS_MIXED truncates up to bond 32, and every precision builds bond 32
+ *            where nothing is truncated.
  *   prec     mps_precision
  *   stream   cudaStream_t (NULL = legacy default stream) used by every later call
  *   out      receives the handle

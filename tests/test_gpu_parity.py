@@ -558,3 +558,34 @@ def test_failed_calls_leave_no_stale_state():
         b.pauli_cache()
     assert e.value.status == 6
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("L", [5, 6])
+def test_largest_bond_bucket_32(precision, L):
+    """Bonds at the largest compiled size, 32, on 5x5 images: L = 5 reaches it
+    exactly (2^L), L = 6 truncates a bond of 64 to chi = 32 at the middle cuts.  The
+    FP64 truncation workspace at bond 32 exceeds a block's shared memory, so that
+    case is refused on the host (MPS_ERR_UNSUPPORTED) before any launch."""
+    p, chi, B = 5, 32, 2
+    n = p * p
+    X = synth.garment_pixels(B, p, seed=70 + L)
+    params = synth.circuit_params(L, n, seed=71)
+    if precision == "fp64" and L == 6:
+        from paper_2607_10280_b300._lib import MpsError
+        with pytest.raises(MpsError) as e:
+            run_gpu(list(X), [p] * B, L, chi, precision, params=params)
+        assert e.value.status == 5 and "shared memory" in str(e.value)
+        return
+    got, bonds, disc = run_gpu(list(X), [p] * B, L, chi, precision, params=params)
+    expect = [1] + [min(chi, 2 ** L, 2 ** (k + 1), 2 ** (n - k - 1)) for k in range(n - 1)] + [1]
+    for i in range(B):
+        assert list(bonds[i]) == expect
+        st = o_mps.simulate(o_circ.build_circuit("ladder", X[i], L, params), n, chi)
+        ref, gap = st.pair_paulis(o_pairs.image_pairs(p)), st.min_gap
+        if gap < 1e-6:
+            continue
+        assert np.max(np.abs(got[i] - ref)) < tol_for(precision, gap), (i, gap, np.max(np.abs(got[i] - ref)))
+        if L == 5:
+            assert float(np.sum(st.discarded)) < 1e-20
+    assert max(expect) == 32
