@@ -50,11 +50,23 @@ typedef enum {
 
 /* Arithmetic of the path.
  *   MPS_FP64         complex128 everywhere (the plain FP64 path).
- *   MPS_MIXED        complex64 site tensors, gates, QR splits and environments;
- *                    FP64 for the Gram matrix, the eigen/singular values and the
- *                    re-orthogonalisation inside every step that truncates.
- *   MPS_MIXED_ORTH64 as MPS_MIXED, and every QR/LQ factorisation also in FP64. */
-typedef enum { MPS_FP64 = 0, MPS_MIXED = 1, MPS_MIXED_ORTH64 = 2 } mps_precision;
+ *   MPS_MIXED        complex64 wherever no singular value is discarded: gates, exact
+ *                    QR splits, operator products, environments and Pauli
+ *                    contractions.  An image whose circuit truncates lossily (keeps
+ *                    chi < rank at some cut) runs its whole circuit on a complex128
+ *                    state -- sequential truncation amplifies the rounding of a
+ *                    complex64 state far beyond 1e-5 (measured up to 4e-3 at chi = 2,
+ *                    7x7, L = 4) -- and the final MPS is rounded to complex64 for the
+ *                    environment and Pauli kernels.  Every Pauli entry then stays
+ *                    within 1e-5 of the FP64 result.
+ *   MPS_MIXED_ORTH64 as MPS_MIXED, and the QR/LQ factorisations of the complex64
+ *                    circuits also in FP64.
+ *   MPS_MIXED_FAST   complex64 state also through lossy truncations (FP64 only for
+ *                    the Gram matrix, the eigenvalues near the cut and the
+ *                    re-orthogonalisation of the kept vectors): faster, but its error
+ *                    in the truncated regime is NOT bounded by 1e-5; kept to measure
+ *                    what the FP64 state of MPS_MIXED costs. */
+typedef enum { MPS_FP64 = 0, MPS_MIXED = 1, MPS_MIXED_ORTH64 = 2, MPS_MIXED_FAST = 3 } mps_precision;
 
 /* Circuit family.
  *   MPS_ANSATZ_LADDER  R_Y(pi x_k) once, then L x [R_Y(alpha_{l,k}) then R_Z(beta_{l,k})
@@ -91,11 +103,6 @@ typedef struct {
  *            bonds only grow to min(chi, 2 D_left, 2 D_right) (e.g. at most 2^L for
  *            the ladder), and the kernels hold bonds up to MPS_BOND_LIMIT; a circuit
  *            that would need more returns MPS_ERR_UNSUPPORTED from mps_apply_circuit.
- *            So does a circuit that truncates at a bond above 16 under MPS_FP64 or
- *            MPS_MIXED_ORTH64: the FP64 factorisation workspace for bond 32 (about
- *            290 KB and 248 KB per image) exceeds the shared memory of a block;
- *            MPS_MIXED truncates up to bond 32, and every precision builds bond 32
- *            where nothing is truncated.
  *   prec     mps_precision
  *   stream   cudaStream_t (NULL = legacy default stream) used by every later call
  *   out      receives the handle
@@ -294,31 +301,38 @@ mps_status mps_kernel_times(mps_batch* batch, double* ms, int64_t* launches);
  *   - latency-bound serving loops, where cudaMalloc/cudaFree can synchronise the
  *     device and stall every stream.
  * It computes the same Pauli cache as mps_create_batch + mps_apply_circuit +
- * mps_pauli_cache for n_images images of one size, MPS_MIXED precision, the
- * ladder ansatz and the horizontal + vertical pair set, using the same kernels.
- * All working memory (site tensors, environments, bond dimensions, per-image
- * records) lives in one fixed array inside this library's device memory (about
- * 18.5 MiB, held on every GPU that loads the library until the process exits).
+ * mps_pauli_cache for n_images images of one size, MPS_MIXED precision (a circuit
+ * that truncates lossily runs on a complex128 state, as there), the ladder ansatz
+ * and the horizontal + vertical pair set, using the same kernels.  All working
+ * memory (site tensors, their complex128 copies for a truncating circuit,
+ * environments, bond dimensions, per-image records, the status word) lives in one
+ * fixed array inside this library's device memory (about 44 MiB, held on every GPU
+ * that loads the library until the process exits).
  *   n_images  1..64
  *   p, chi, L image side 2..16, bond cap 1..32, layers >= 0
  *   pixels    device float64 [n_images][p*p], values in [0, 1]
  *   params    device float64 [>= L][params_n][2] angles, params_n >= p*p (may be NULL if L == 0)
  *   out       device float32 [n_images][2p(p-1)][16], caller-owned
+ *   status    device int32, caller-owned, or NULL: receives, in stream order after the
+ *             Pauli cache, the first device-side error of this call (0 = none; 1 = a
+ *             bond exceeded the padding the host sized, 3 = a step the kernel does not
+ *             support), which the kernels record instead of writing out of bounds
  *   stream    cudaStream_t
  * Limits: with ld the smallest power of two >= 4 that holds the largest bond the
  * circuit reaches, n_images * p^2 * 2 * ld^2 * 8 bytes <= 12 MiB of site storage and
  * n_images * p^2 * ld^2 * 8 bytes <= 6 MiB of environments (e.g. up to 62 images of
- * 7x7 at chi = 16, L = 4).  Larger requests return MPS_ERR_INVALID_ARG with a message.
+ * 7x7 at chi = 16, L = 4), and L * p^2 <= 16384.  Larger requests return
+ * MPS_ERR_INVALID_ARG with a message.
  * No cudaMalloc, cudaFree or other allocating routine is called.  The first call on a
  * device looks up the array's device address with that device current; make that
  * first call before any stream capture.  Every call reuses the same array and
- * overwrites the previous call's contents (per-call state is cleared at its start),
- * so calls that overlap on the GPU -- on different streams or from different
- * threads -- race and corrupt each other: keep them on one stream.  Device-side
- * checks are not reported by this call.  Asynchronous on stream. */
+ * overwrites the previous call's contents (per-call state, the status word included,
+ * is cleared at its start), so calls that overlap on the GPU -- on different streams
+ * or from different threads -- race and corrupt each other: keep them on one stream.
+ * Asynchronous on stream. */
 mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32_t chi, int32_t L,
                                    const double* pixels, const double* params, int32_t params_n,
-                                   float* out, void* stream);
+                                   float* out, int32_t* status, void* stream);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,7 @@ MPS_OK = 0
 STATUS_NAMES = {0: "MPS_OK", 1: "MPS_ERR_INVALID_ARG", 2: "MPS_ERR_OOM", 3: "MPS_ERR_CUDA",
                 4: "MPS_ERR_TIMEOUT", 5: "MPS_ERR_UNSUPPORTED", 6: "MPS_ERR_NOT_READY",
                 7: "MPS_ERR_DEVICE"}
-PRECISION = {"fp64": 0, "mixed": 1, "mixed_orth64": 2}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_orth64": 2, "mixed_fast": 3}
 ANSATZ = {"ladder": 0, "paper": 1}
 PAIR_SET = {"hv": 0, "hvd": 1}
 
@@ -69,7 +69,7 @@ SIGNATURES = {
     "mps_set_half_structure": (_c.c_int, [_c.c_void_p, _c.c_int32]),
     "mps_kernel_times": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64)]),
     "mps_pauli_cache_noalloc": (_c.c_int, [_c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32, _c.c_void_p,
-                                           _c.c_void_p, _c.c_int32, _c.c_void_p, _c.c_void_p]),
+                                           _c.c_void_p, _c.c_int32, _c.c_void_p, _c.c_void_p, _c.c_void_p]),
 }
 KERNEL_KINDS = ("circuit", "renv", "pauli")
 

@@ -38,6 +38,14 @@ struct mps_batch {
     bool meta_dirty = false;               // meta_h changed since its last upload
     void* gates = nullptr;                 // one-qubit gate table of the last circuit
     size_t gates_bytes = 0;
+    // complex128 state of the images whose circuit truncates lossily under the mixed
+    // precisions (their chain runs in FP64 and is rounded into `arena` at its end), and
+    // the FP64 gate table that chain reads
+    void* arena64 = nullptr;
+    size_t cap_arena64 = 0;
+    void* gates64 = nullptr;
+    size_t gates64_bytes = 0;
+    int n_chain64 = 0;                     // images of the last circuit that took the FP64 chain
     int gate_n = 0;                        // qubit stride of the gate table
     bool gates_owned = true;               // false when gates points into static scratch
     int circuit_threads = 32;              // threads per image in the circuit kernel
@@ -108,9 +116,20 @@ mps_status launch_circuit_orth64_t1(mps_batch* b, int chi_tpl, const double* px,
 inline mps_status launch_circuit_orth64(mps_batch* b, int chi_tpl, bool trunc, const double* px, int ansatz) {
     return trunc ? launch_circuit_orth64_t1(b, chi_tpl, px, ansatz) : launch_circuit_orth64_t0(b, chi_tpl, px, ansatz);
 }
-// Fill b->gates (allocated by the caller) with the one-qubit gate table of a circuit.
+// Fill `dst` (allocated by the caller; complex128 entries if f64, else complex64) with
+// the one-qubit gate table of a circuit.
 mps_status launch_gate_table(mps_batch* b, int ansatz, int L_max, const double* params, int params_n,
-                             const double* pixels);
+                             const double* pixels, bool f64, void* dst);
+// Host mirror of the circuit kernels' bond rules for one image: returns the largest
+// bond; *svd is set when some step truncates lossily (an SVD split to chi below the
+// rank bound 2^c of its cut).
+int dry_run_bonds(int n, int L, int chi, int ansatz, bool* svd);
+// Smallest compiled bond bucket (4, 8, 16, 32) holding bond mx, or -1.
+int chi_bucket(int mx);
+// Rounds the complex128 sites that an FP64 chain wrote to src64 into b->arena
+// (complex64, same offsets) for the images b->run_order[0 .. run_count) (run_order
+// NULL: images 0 .. run_count-1).
+mps_status launch_round_sites(mps_batch* b, const void* src64);
 // Circuits as operator products for b->run_order[0 .. run_count) (ladder_mpo.cu).
 mps_status launch_ladder_mpo(mps_batch* b, const double* pixels, int ansatz);
 mps_status launch_pauli_fp64(mps_batch* b, void* out, bool diag = false);

@@ -38,6 +38,12 @@ namespace mpsano {
 constexpr int MAX_QUBITS = 256;  // p <= 16
 
 // Per-warp shared-memory layout.  CHI bounds every bond the images reach.
+// With TRUNC the site buffers (cur, nxt, rb) share one region with the FP64 Gram
+// matrix and eigenvectors (G, V) of the SVD truncation: theta is formed from cur and
+// nxt before G is written, rb serves only the exact centre moves, and the new centre
+// is written to cur (inside G) only after the last read of U (held in G), from V.
+// That keeps the FP64 workspace of a bond-32 truncation (about 205 KB) within the
+// shared memory of one block.
 template <typename T, typename TQ, int CHI, bool TRUNC>
 struct CircuitLayout {
     static constexpr int CS = CHI + 1;              // row stride of a site: element (l,s,r) at (2l+s)*CS + r
@@ -46,24 +52,29 @@ struct CircuitLayout {
     static constexpr int THETA = 2 * CHI * LDM;
     static constexpr int K = 2 * CHI;               // largest Gram matrix
     static constexpr int LDK = K + 1;
+    static constexpr size_t SITES_BYTES = sizeof(cx<T>) * (2 * SITE + CHI * CS);
+    static constexpr size_t GV_BYTES = TRUNC ? 2 * sizeof(cx<double>) * K * LDK : 0;
+    static constexpr size_t REGION = ((SITES_BYTES > GV_BYTES ? SITES_BYTES : GV_BYTES) + 15) & ~size_t(15);
     static constexpr size_t off_cur = 0;
     static constexpr size_t off_nxt = off_cur + sizeof(cx<T>) * SITE;
     static constexpr size_t off_rb = off_nxt + sizeof(cx<T>) * SITE;
-    static constexpr size_t off_th = (off_rb + sizeof(cx<T>) * CHI * CS + 15) & ~size_t(15);
+    static constexpr size_t off_gram = 0;
+    static constexpr size_t off_vec = off_gram + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
+    static constexpr size_t off_th = REGION;
     static constexpr size_t off_tau = off_th + sizeof(cx<TQ>) * THETA;
     static constexpr size_t off_bd = off_tau + sizeof(cx<TQ>) * K;
     static constexpr size_t off_cn = off_bd + sizeof(int) * (MAX_QUBITS + 1);   // CNOTs per cut
     static constexpr size_t off_perm = off_cn + sizeof(int) * (MAX_QUBITS + 1);  // pivoted QR
     static constexpr size_t off_cnorm = (off_perm + sizeof(int) * K + 15) & ~size_t(15);
     static constexpr size_t off_cz = off_cnorm + sizeof(TQ) * K;                  // zero rows of cur
-    static constexpr size_t off_gram = (off_cz + sizeof(int) + 15) & ~size_t(15);
-    static constexpr size_t off_vec = off_gram + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
-    static constexpr size_t off_taud = off_vec + (TRUNC ? sizeof(cx<double>) * K * LDK : 0);
+    static constexpr size_t off_taud = (off_cz + sizeof(int) + 15) & ~size_t(15);
     static constexpr size_t off_lam = off_taud + (TRUNC ? sizeof(cx<double>) * K : 0);
     static constexpr size_t off_ord = off_lam + (TRUNC ? sizeof(double) * K : 0);
     static constexpr size_t off_red = (off_ord + (TRUNC ? sizeof(int) * K : 0) + 15) & ~size_t(15);
     static constexpr size_t off_flag = off_red + sizeof(double) * 4;   // team reductions (<= 128 threads)
     static constexpr size_t bytes = (off_flag + sizeof(int) + 15) & ~size_t(15);
+    // the new centre (in cur) is written from V, so the two must not overlap
+    static_assert(!TRUNC || off_cur + sizeof(cx<T>) * SITE <= off_vec, "cur must lie within the Gram buffer");
 };
 
 // The 2x2 one-qubit gate applied to site k at the start of a layer.

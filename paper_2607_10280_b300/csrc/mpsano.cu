@@ -107,17 +107,17 @@ void timing_begin(mps_batch* b, int kind) {
 }
 
 mps_status launch_gate_table(mps_batch* b, int ansatz, int L_max, const double* params, int params_n,
-                             const double* pixels) {
+                             const double* pixels, bool f64, void* dst) {
     const int rows = ansatz == MPS_ANSATZ_LADDER ? L_max : b->B;
     const int total = rows * b->gate_n;
     if (total <= 0) return MPS_OK;
     const int threads = 128;
-    if (b->prec == MPS_FP64)
+    if (f64)
         gate_table_kernel<double><<<(total + threads - 1) / threads, threads, 0, b->stream>>>(
-            ansatz, rows, b->gate_n, params, params_n, b->meta_d, pixels, static_cast<cx<double>*>(b->gates));
+            ansatz, rows, b->gate_n, params, params_n, b->meta_d, pixels, static_cast<cx<double>*>(dst));
     else
         gate_table_kernel<float><<<(total + threads - 1) / threads, threads, 0, b->stream>>>(
-            ansatz, rows, b->gate_n, params, params_n, b->meta_d, pixels, static_cast<cx<float>*>(b->gates));
+            ansatz, rows, b->gate_n, params, params_n, b->meta_d, pixels, static_cast<cx<float>*>(dst));
     CUDA_TRY(cudaGetLastError());
     count_launch();
     return MPS_OK;
@@ -147,13 +147,6 @@ int smem_optin_limit() {
     return v > 0 ? v : 48 * 1024;
 }
 
-}  // namespace mpsano
-
-namespace {
-
-// Bond dimensions reachable by one image, simulated on dimensions only with the
-// same rules as the circuit kernel.  Returns the largest bond; sets *trunc if any
-// two-qubit step must truncate.
 // Host mirror of the circuit kernel's bond dimensions (run_pass): returns the largest
 // bond; *svd is set when some step truncates lossily (an SVD split to chi below the
 // rank bound 2^c of its cut).  Splits that only drop the rank beyond 2^c use the
@@ -214,9 +207,42 @@ int chi_bucket(int mx) {
     return -1;
 }
 
+namespace {
+// Rounds the complex128 sites of the images order[0 .. count) (order NULL: images
+// 0 .. count-1), written by the FP64 chain into src, to complex64 in dst at the same
+// offsets, over the bonds the chain wrote.  One CTA per image.
+__global__ void round_sites_kernel(const ImageMeta* __restrict__ meta, const int32_t* __restrict__ order, int count,
+                                   const int32_t* __restrict__ bonds, const cx<double>* __restrict__ src,
+                                   cx<float>* __restrict__ dst) {
+    if ((int)blockIdx.x >= count) return;
+    const ImageMeta m = meta[order ? order[blockIdx.x] : (int)blockIdx.x];
+    const int32_t* bd = bonds + m.bond_off;
+    const int ld = m.ld;
+    for (int k = 0; k < m.n; ++k) {
+        const int Dl = bd[k], Dr = bd[k + 1];
+        const size_t off = (size_t)m.site_off + (size_t)k * 2 * ld * ld;
+        for (int e = threadIdx.x; e < 2 * Dl * Dr; e += blockDim.x) {
+            const int row = e / Dr, r = e - row * Dr;
+            const cx<double> v = src[off + (size_t)row * ld + r];
+            dst[off + (size_t)row * ld + r] = mk<float>((float)v.re, (float)v.im);
+        }
+    }
+}
 }  // namespace
 
+mps_status launch_round_sites(mps_batch* b, const void* src64) {
+    if (b->run_count <= 0) return MPS_OK;
+    timing_begin(b, KIND_CIRCUIT);
+    round_sites_kernel<<<b->run_count, 256, 0, b->stream>>>(b->meta_d, b->run_order, b->run_count, b->bonds_d,
+                                                            static_cast<const cx<double>*>(src64),
+                                                            static_cast<cx<float>*>(b->arena));
+    timing_end(b);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return MPS_OK;
+}
 
+}  // namespace mpsano
 
 namespace {
 
@@ -238,6 +264,8 @@ void free_batch(mps_batch* b) {
     cudaFree(b->status_d);
     cudaFree(b->queue_d);
     cudaFree(b->order_d);
+    cudaFree(b->arena64);
+    cudaFree(b->gates64);
     if (b->gates_owned) cudaFree(b->gates);
     delete b;
 }
@@ -378,7 +406,7 @@ mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* c
                             int32_t prec, void* stream, mps_batch** out) {
     if (!out) return fail(MPS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (prec != MPS_FP64 && prec != MPS_MIXED && prec != MPS_MIXED_ORTH64)
+    if (prec != MPS_FP64 && prec != MPS_MIXED && prec != MPS_MIXED_ORTH64 && prec != MPS_MIXED_FAST)
         return fail(MPS_ERR_INVALID_ARG, "unknown precision %d", prec);
     mps_batch* b = new (std::nothrow) mps_batch();
     if (!b) return fail(MPS_ERR_OOM, "host allocation failed");
@@ -468,17 +496,23 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     // arguments checked: a call that fails from here on leaves no circuit for
     // mps_pauli_cache to read
     b->circuit_done = false;
-    // bond dimensions, shared-memory bucket and truncation per image.  Images whose
-    // circuit the layer-pipelined kernel can run (ladder, nothing lossy, 1 <= L <= 4)
-    // go to it, the others to the sequential kernel, so that an image's kernel (and
-    // its result) depends on its own circuit only, not on the rest of the batch.
-    int mx = 1, mx_wave = 1, mx_seq = 1;
+    // bond dimensions, shared-memory bucket and truncation per image.  Each image's
+    // kernel (and so its result) depends on its own circuit only, not on the rest of
+    // the batch:
+    //  - a circuit (either ansatz) that truncates nowhere, with 1 <= L <= 4 and 2^L within
+    //    the image's padding and chi: operator product (ladder_mpo.cu: bond 2^L at every
+    //    inner cut, not left-canonical, flagged META_LENV for the Pauli kernel);
+    //  - other ladder circuits that truncate nowhere with 1 <= L <= 4: layer-pipelined
+    //    kernel;
+    //  - a circuit that truncates lossily under MPS_MIXED or MPS_MIXED_ORTH64: the
+    //    sequential kernel on a complex128 state (sequential truncation amplifies the
+    //    rounding of a complex64 state far beyond 1e-5), rounded to complex64 at the end;
+    //  - everything else: the sequential kernel in the batch's own precision.
+    int mx = 1, mx_wave = 1, mx_seq = 1, mx_64 = 1;
     bool trunc_seq = false;
-    // An image whose circuit (either ansatz) truncates nowhere, with 1 <= L <= 4 and 2^L
-    // within its padding and chi, takes the operator-product path (ladder_mpo.cu: bond
-    // 2^L at every inner cut, not left-canonical, flagged META_LENV for the Pauli kernel).
-    std::vector<char> wave(b->B, 0), mpo(b->B, 0);
-    int n_wave = 0, n_mpo = 0;
+    const bool chain64_on = b->prec == MPS_MIXED || b->prec == MPS_MIXED_ORTH64;
+    std::vector<char> wave(b->B, 0), mpo(b->B, 0), c64(b->B, 0);
+    int n_wave = 0, n_mpo = 0, n_64 = 0;
     for (int i = 0; i < b->B; ++i) {
         ImageMeta& m = b->meta_h[i];
         const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
@@ -498,9 +532,13 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         }
         mx = std::max(mx, bi);
         wave[i] = pipe && !mpo[i];
+        c64[i] = !mpo[i] && !wave[i] && t && chain64_on;
         if (wave[i]) {
             ++n_wave;
             mx_wave = std::max(mx_wave, bi);
+        } else if (c64[i]) {
+            ++n_64;
+            mx_64 = std::max(mx_64, bi);
         } else if (!mpo[i]) {
             mx_seq = std::max(mx_seq, bi);
             trunc_seq = trunc_seq || t;
@@ -508,13 +546,14 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     }
     const int chi_tpl = chi_bucket(mx);
     if (chi_tpl < 0) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > 32 not supported", mx);
-    // work order: operator-product images, pipelined images, the rest, each part by
-    // descending cost
+    // work order: operator-product images, pipelined images, the rest in the batch's
+    // precision, then the FP64 chains, each part by descending cost
     std::vector<int32_t> order;
     order.reserve(b->B);
     for (int32_t i : b->cost_order) if (mpo[i]) order.push_back(i);
     for (int32_t i : b->cost_order) if (wave[i]) order.push_back(i);
-    for (int32_t i : b->cost_order) if (!wave[i] && !mpo[i]) order.push_back(i);
+    for (int32_t i : b->cost_order) if (!wave[i] && !mpo[i] && !c64[i]) order.push_back(i);
+    for (int32_t i : b->cost_order) if (c64[i]) order.push_back(i);
     if (n_mpo > 0) {
         cudaError_t e;
         if (b->cap_lenv < b->elem * b->renv_stride * b->B) {
@@ -544,7 +583,8 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
                                  cudaMemcpyHostToDevice, b->stream));
         b->meta_dirty = false;
     }
-    // one-qubit gate table (FP64 math, rounded to the state type)
+    // one-qubit gate table (FP64 math, rounded to the state type); a second one in FP64
+    // for the FP64 chains
     const int rows = circ->ansatz == MPS_ANSATZ_LADDER ? L_max : b->B;
     const size_t gbytes = (size_t)std::max(rows, 1) * b->n_max * 4 * b->elem;
     if (gbytes > b->gates_bytes) {
@@ -555,15 +595,43 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         CUDA_TRY(cudaMalloc(&b->gates, gbytes));
         b->gates_bytes = gbytes;
     }
+    if (n_64 > 0) {
+        const size_t g64 = (size_t)std::max(rows, 1) * b->n_max * 4 * sizeof(cx<double>);
+        const size_t a64 = sizeof(cx<double>) * b->need_sites;
+        if (g64 > b->gates64_bytes || a64 > b->cap_arena64) {
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            if (g64 > b->gates64_bytes) {
+                cudaFree(b->gates64);
+                b->gates64 = nullptr;
+                b->gates64_bytes = 0;
+                CUDA_TRY(cudaMalloc(&b->gates64, g64));
+                b->gates64_bytes = g64;
+            }
+            if (a64 > b->cap_arena64) {
+                cudaFree(b->arena64);
+                b->arena64 = nullptr;
+                b->cap_arena64 = 0;
+                CUDA_TRY(cudaMalloc(&b->arena64, a64));
+                b->cap_arena64 = a64;
+            }
+        }
+    }
     b->gate_n = b->n_max;
     b->L_max = L_max;
+    b->n_chain64 = n_64;
     const double* pr = circ->ansatz == MPS_ANSATZ_LADDER ? circ->params : nullptr;
-    mps_status st = launch_gate_table(b, circ->ansatz, L_max, pr, circ->params_n, pixels);
+    mps_status st = launch_gate_table(b, circ->ansatz, L_max, pr, circ->params_n, pixels, b->prec == MPS_FP64,
+                                      b->gates);
     if (st != MPS_OK) return st;
+    if (n_64 > 0) {
+        st = launch_gate_table(b, circ->ansatz, L_max, pr, circ->params_n, pixels, true, b->gates64);
+        if (st != MPS_OK) return st;
+    }
     auto launch = [&](int bucket, bool trunc) {
         switch (b->prec) {
             case MPS_FP64: return launch_circuit_fp64(b, bucket, trunc, pixels, circ->ansatz);
-            case MPS_MIXED: return launch_circuit_mixed(b, bucket, trunc, pixels, circ->ansatz);
+            case MPS_MIXED:
+            case MPS_MIXED_FAST: return launch_circuit_mixed(b, bucket, trunc, pixels, circ->ansatz);
             default: return launch_circuit_orth64(b, bucket, trunc, pixels, circ->ansatz);
         }
     };
@@ -581,11 +649,29 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         st = launch(chi_bucket(mx_wave), false);
         if (st != MPS_OK) return st;
     }
-    if (n_mpo + n_wave < b->B) {
+    const int n_seq = b->B - n_mpo - n_wave - n_64;
+    if (n_seq > 0) {
         b->use_wave = false;
         b->run_order = b->order_d + n_mpo + n_wave;
-        b->run_count = b->B - n_mpo - n_wave;
+        b->run_count = n_seq;
         st = launch(chi_bucket(mx_seq), trunc_seq);
+        if (st != MPS_OK) return st;
+    }
+    if (n_64 > 0) {
+        // the FP64 chain runs on the complex128 arena and gate table, then its sites are
+        // rounded into the batch's complex64 arena
+        b->use_wave = false;
+        b->run_order = b->order_d + (b->B - n_64);
+        b->run_count = n_64;
+        void* arena = b->arena;
+        void* gates = b->gates;
+        b->arena = b->arena64;
+        b->gates = b->gates64;
+        st = launch_circuit_fp64(b, chi_bucket(mx_64), true, pixels, circ->ansatz);
+        b->arena = arena;
+        b->gates = gates;
+        if (st != MPS_OK) return st;
+        st = launch_round_sites(b, b->arena64);
         if (st != MPS_OK) return st;
     }
     b->chi_tpl = chi_tpl;

@@ -16,9 +16,13 @@ namespace {
 
 constexpr int NA_MAX_IMAGES = 64;
 constexpr int NA_MAX_DEVICES = 64;
-constexpr size_t NA_ARENA_BYTES = size_t(12) << 20;   // site tensors
+constexpr size_t NA_ARENA_BYTES = size_t(12) << 20;   // site tensors (complex64)
 constexpr size_t NA_RENV_BYTES = size_t(6) << 20;     // right environments
-constexpr size_t NA_GATE_BYTES = size_t(512) << 10;   // one-qubit gate table
+constexpr size_t NA_GATE_BYTES = size_t(512) << 10;   // one-qubit gate table (complex64)
+// complex128 state and gate table of a circuit that truncates lossily (the FP64 chain
+// of the mixed precision), twice the complex64 sizes
+constexpr size_t NA_ARENA64_BYTES = 2 * NA_ARENA_BYTES;
+constexpr size_t NA_GATE64_BYTES = 2 * NA_GATE_BYTES;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t OFF_META = 0;
@@ -31,11 +35,13 @@ constexpr size_t OFF_QUEUE = align256(OFF_STATUS + sizeof(int));
 constexpr size_t OFF_ARENA = align256(OFF_QUEUE + sizeof(int));
 constexpr size_t OFF_RENV = align256(OFF_ARENA + NA_ARENA_BYTES);
 constexpr size_t OFF_GATES = align256(OFF_RENV + NA_RENV_BYTES);
-constexpr size_t NA_TOTAL = align256(OFF_GATES + NA_GATE_BYTES);
+constexpr size_t OFF_ARENA64 = align256(OFF_GATES + NA_GATE_BYTES);
+constexpr size_t OFF_GATES64 = align256(OFF_ARENA64 + NA_ARENA64_BYTES);
+constexpr size_t NA_TOTAL = align256(OFF_GATES64 + NA_GATE64_BYTES);
 
 }  // namespace
 
-// The scratch array.  Every GPU that loads this library holds it (about 18.5 MiB)
+// The scratch array.  Every GPU that loads this library holds it (about 44 MiB)
 // until the process exits.  Host code must not use its name as an address: the
 // device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_TOTAL];
@@ -86,38 +92,17 @@ __global__ void noalloc_setup_kernel(ImageMeta* meta, int32_t* units, double* di
     if (t == 0) *status = 0;
 }
 
-// Bond dimensions of the ladder circuit (dimension rules of the circuit kernel),
-// on a stack array: returns the largest bond and whether any step truncates.
-int ladder_bonds(int n, int L, int chi, bool* trunc) {
-    int bd[257];
-    for (int k = 0; k <= n; ++k) bd[k] = 1;
-    int mx = 1;
-    bool any = false;
-    for (int layer = 0; layer < L; ++layer) {
-        bool t = false;
-        int dl = bd[0];
-        for (int k = 0; k < n - 1; ++k) {
-            const int mn = std::min(2 * dl, 2 * bd[k + 2]);
-            if (mn > chi) t = true;
-            dl = std::min(mn, chi);
-        }
-        if (t && layer > 0)
-            for (int k = n - 1; k > 0; --k) bd[k] = std::min(bd[k], 2 * bd[k + 1]);
-        for (int k = 0; k < n - 1; ++k) {
-            bd[k + 1] = std::min(chi, std::min(2 * bd[k], 2 * bd[k + 2]));
-            mx = std::max(mx, bd[k + 1]);
-        }
-        any = any || t;
-    }
-    *trunc = any;
-    return mx;
+// The device status word of the call (first device-side error, 0 if none) into the
+// caller's int.
+__global__ void noalloc_status_kernel(const int* __restrict__ status, int32_t* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = *status;
 }
 
 }  // namespace
 
 extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32_t chi, int32_t L,
                                               const double* pixels, const double* params, int32_t params_n,
-                                              float* out, void* stream) {
+                                              float* out, int32_t* status, void* stream) {
     if (n_images < 1 || n_images > NA_MAX_IMAGES)
         return fail(MPS_ERR_INVALID_ARG, "n_images = %d outside 1..%d for the no-allocation entry point",
                     n_images, NA_MAX_IMAGES);
@@ -128,13 +113,15 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
     const int n = p * p;
     if (L > 0 && (!params || params_n < n))
         return fail(MPS_ERR_INVALID_ARG, "params must be non-NULL with params_n >= %d", n);
+    // bond dimensions from the library's one host mirror of the circuit kernels' rules;
+    // the kernels check every bond they write against the padding ld and report a
+    // violation through the status word
     bool trunc = false;
-    const int mx = ladder_bonds(n, L, chi, &trunc);
+    const int mx = dry_run_bonds(n, L, chi, MPS_ANSATZ_LADDER, &trunc);
+    const int chi_tpl = chi_bucket(mx);
+    if (chi_tpl < 0) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > 32", mx);
     int ld = 4;
     while (ld < mx) ld <<= 1;
-    int chi_tpl = 4;
-    while (chi_tpl < mx) chi_tpl <<= 1;
-    if (chi_tpl > 32) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > 32", mx);
     const size_t arena = (size_t)n_images * n * 2 * ld * ld * sizeof(cx<float>);
     const size_t renv = (size_t)n_images * n * ld * ld * sizeof(cx<float>);
     const size_t gate_bytes = (size_t)(L > 0 ? L : 1) * n * 4 * sizeof(cx<float>);
@@ -183,10 +170,31 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
         b.meta_d, b.units_d, b.discarded_d, b.status_d, n_images, p, chi, L, ld);
     CUDA_TRY(cudaGetLastError());
     count_launch();
-    st = launch_gate_table(&b, MPS_ANSATZ_LADDER, L, params, params_n, pixels);
-    if (st != MPS_OK) return st;
-    st = launch_circuit_mixed(&b, chi_tpl, trunc, pixels, MPS_ANSATZ_LADDER);
-    if (st != MPS_OK) return st;
+    if (trunc) {
+        // lossy truncation: the circuit runs on a complex128 state (the mixed
+        // precision's FP64 chain) in the scratch's FP64 region, then its sites are
+        // rounded into the complex64 arena for the environment and Pauli kernels
+        b.gates = base + OFF_GATES64;
+        b.gates_bytes = NA_GATE64_BYTES;
+        b.arena = base + OFF_ARENA64;
+        st = launch_gate_table(&b, MPS_ANSATZ_LADDER, L, params, params_n, pixels, true, b.gates);
+        if (st != MPS_OK) return st;
+        st = launch_circuit_fp64(&b, chi_tpl, true, pixels, MPS_ANSATZ_LADDER);
+        if (st != MPS_OK) return st;
+        b.arena = base + OFF_ARENA;
+        st = launch_round_sites(&b, base + OFF_ARENA64);
+        if (st != MPS_OK) return st;
+    } else {
+        st = launch_gate_table(&b, MPS_ANSATZ_LADDER, L, params, params_n, pixels, false, b.gates);
+        if (st != MPS_OK) return st;
+        st = launch_circuit_mixed(&b, chi_tpl, false, pixels, MPS_ANSATZ_LADDER);
+        if (st != MPS_OK) return st;
+    }
     b.chi_tpl = chi_tpl;
-    return launch_pauli_mixed(&b, out);
+    st = launch_pauli_mixed(&b, out);
+    if (st != MPS_OK || !status) return st;
+    noalloc_status_kernel<<<1, 32, 0, b.stream>>>(b.status_d, status);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return MPS_OK;
 }

@@ -69,6 +69,6 @@ def test_results_do_not_depend_on_the_mix():
         ref, st = o_pipe.pauli_cache(pix[i], p, L, chi, "ladder", params_np, return_state=True)
         if st.min_gap < 1e-6:
             continue                      # near-tie at a truncation cut: no unique answer
-        assert np.max(np.abs(reqs[i].pauli - ref)) < max(1e-5, 5e-8 / st.min_gap)   # complex64 state
+        assert np.max(np.abs(reqs[i].pauli - ref)) < 1e-5
         checked += 1
     assert checked >= 2
