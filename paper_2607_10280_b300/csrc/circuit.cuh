@@ -72,7 +72,11 @@ struct CircuitLayout {
     static constexpr size_t off_ord = off_lam + (TRUNC ? sizeof(double) * K : 0);
     static constexpr size_t off_red = (off_ord + (TRUNC ? sizeof(int) * K : 0) + 15) & ~size_t(15);
     static constexpr size_t off_flag = off_red + sizeof(double) * 4;   // team reductions (<= 128 threads)
-    static constexpr size_t bytes = (off_flag + sizeof(int) + 15) & ~size_t(15);
+    // FP64 truncation up to bond 16: the eigen-decomposition starts from FP32 Jacobi
+    // vectors, made orthonormal in FP64 in the buffer W (see svd_truncate)
+    static constexpr bool REFINE = TRUNC && sizeof(TQ) == 8 && CHI <= 16;
+    static constexpr size_t off_w = (off_flag + sizeof(int) + 15) & ~size_t(15);
+    static constexpr size_t bytes = (off_w + (REFINE ? sizeof(cx<double>) * K * LDK : 0) + 15) & ~size_t(15);
     // the new centre (in cur) is written from V, so the two must not overlap
     static_assert(!TRUNC || off_cur + sizeof(cx<T>) * SITE <= off_vec, "cur must lie within the Gram buffer");
 };
@@ -182,6 +186,7 @@ struct CircuitTeam {
     int zr;
     cx<double>* G;
     cx<double>* V;
+    cx<double>* W;   // FP64 eigenvector basis of the refined eigen-decomposition (Lay::REFINE)
     cx<double>* taud;
     double* lam;
     int* ord;
@@ -348,8 +353,74 @@ struct CircuitTeam {
             tsync<NTHR>();
         };
         bool fp64_vectors = sizeof(TQ) == 8;
+        const cx<double>* Vd = V;   // FP64 eigenvectors (columns), when fp64_vectors
         if constexpr (sizeof(TQ) == 8) {
-            if (lane < 32) warp_jacobi_eigh<double>(G, V, LDK, K, lane, 40);
+            if constexpr (Lay::REFINE) {
+                // The same FP64 eigen-decomposition as a Jacobi solve from scratch, at a
+                // fraction of its FP64 work: FP32 Jacobi on the rounded Gram gives
+                // vectors accurate to ~eps_32; they are made orthonormal in FP64 (Cholesky
+                // QR: their Gram matrix is I + O(eps_32), so R is perfectly conditioned),
+                // G becomes W^H G W in FP64, and FP64 Jacobi started from W (v_given)
+                // only has to remove off-diagonal entries of size ~eps_32 lambda_1 (two
+                // rotating sweeps instead of six to eight; clusters of eigenvalues below
+                // FP32 resolution are resolved by the same sweeps).
+                team_for_2d<NTHR>(K, K, lane, [&](int c, int r) { G32[c * LDK + r] = cvt<float>(G[c * LDK + r]); });
+                tsync<NTHR>();
+                if (lane < 32) warp_jacobi_eigh<float>(G32, V32, LDK, K, lane, 40);
+                tsync<NTHR>();
+                team_for_2d<NTHR>(K, K, lane, [&](int c, int r) { W[c * LDK + r] = cvt<double>(V32[c * LDK + r]); });
+                tsync<NTHR>();
+                // C = W^H W (upper triangle, column-major in the V buffer), then C = R^H R
+                cx<double>* C = V;
+                team_for_2d<NTHR>(K, K, lane, [&](int j, int i) {
+                    if (i > j) return;
+                    cx<double> acc = czero<double>();
+                    for (int r = 0; r < K; ++r) cmac_cj(acc, W[i * LDK + r], W[j * LDK + r]);
+                    C[j * LDK + i] = acc;
+                });
+                tsync<NTHR>();
+                for (int k = 0; k < K; ++k) {
+                    const double d = sqrt(C[k * LDK + k].re);
+                    const double inv = 1.0 / d;
+                    tsync<NTHR>();
+                    for (int j = k + lane; j < K; j += NTHR)
+                        C[j * LDK + k] = j == k ? mk<double>(d, 0.0) : inv * C[j * LDK + k];
+                    if (lane == 0) taud[k] = mk<double>(inv, 0.0);
+                    tsync<NTHR>();
+                    team_for_2d<NTHR>(K - 1 - k, K - 1 - k, lane, [&](int jj, int ii) {
+                        const int i = k + 1 + ii, j = k + 1 + jj;
+                        if (i <= j) cmsub(C[j * LDK + i], conj(C[i * LDK + k]), C[j * LDK + k]);
+                    });
+                    tsync<NTHR>();
+                }
+                // W <- W R^{-1}, row by row (forward substitution over the columns)
+                for (int r = lane; r < K; r += NTHR) {
+                    for (int c = 0; c < K; ++c) {
+                        cx<double> acc = W[c * LDK + r];
+                        for (int m = 0; m < c; ++m) cmsub(acc, W[m * LDK + r], C[c * LDK + m]);
+                        W[c * LDK + r] = taud[c].re * acc;
+                    }
+                }
+                tsync<NTHR>();
+                // G <- W^H (G W), through T = G W in the V buffer
+                cx<double>* Tm = V;
+                team_for_2d<NTHR>(K, K, lane, [&](int c, int r) {
+                    cx<double> acc = czero<double>();
+                    for (int m = 0; m < K; ++m) cmac(acc, G[m * LDK + r], W[c * LDK + m]);
+                    Tm[c * LDK + r] = acc;
+                });
+                tsync<NTHR>();
+                team_for_2d<NTHR>(K, K, lane, [&](int j, int i) {
+                    cx<double> acc = czero<double>();
+                    for (int r = 0; r < K; ++r) cmac_cj(acc, W[i * LDK + r], Tm[j * LDK + r]);
+                    G[j * LDK + i] = acc;
+                });
+                tsync<NTHR>();
+                if (lane < 32) warp_jacobi_eigh<double>(G, W, LDK, K, lane, 40, true);
+                Vd = W;
+            } else {
+                if (lane < 32) warp_jacobi_eigh<double>(G, V, LDK, K, lane, 40);
+            }
             tsync<NTHR>();
             for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
             tsync<NTHR>();
@@ -417,7 +488,7 @@ struct CircuitTeam {
         // U_chi (M x D, FP64) into the Gram buffer
         cx<double>* U = G;
         auto vec = [&](int c, int r) -> cx<double> {
-            if (fp64_vectors) return V[ord[c] * LDK + r];
+            if (fp64_vectors) return Vd[ord[c] * LDK + r];
             return cvt<double>(V32[ord[c] * LDK + r]);
         };
         if (left) {
@@ -639,6 +710,7 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
     w.zr = 0;
     w.G = reinterpret_cast<cx<double>*>(base + Lay::off_gram);
     w.V = reinterpret_cast<cx<double>*>(base + Lay::off_vec);
+    w.W = Lay::REFINE ? reinterpret_cast<cx<double>*>(base + Lay::off_w) : nullptr;
     w.taud = reinterpret_cast<cx<double>*>(base + Lay::off_taud);
     w.lam = reinterpret_cast<double*>(base + Lay::off_lam);
     w.ord = reinterpret_cast<int*>(base + Lay::off_ord);
@@ -667,10 +739,10 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
         for (int k = lane; k <= n; k += NTHR) { w.bd[k] = 1; w.cn[k] = 0; }
         for (int k = lane; k < n; k += NTHR) {
             cx<T>* s = w.site_ptr(k);
-            double sn = 0.0, cs = 1.0;
-            if (ansatz == 0) sincos(0.5 * M_PI * px[k], &sn, &cs);
-            s[0] = mk<T>(T(cs), T(0));
-            s[w.ld] = mk<T>(T(sn), T(0));
+            T sn = T(0), cs = T(1);
+            if (ansatz == 0) encode_amplitudes(px[k], &sn, &cs);
+            s[0] = mk<T>(cs, T(0));
+            s[w.ld] = mk<T>(sn, T(0));
         }
         tsync<NTHR>();
         bool ok = true;
@@ -770,7 +842,7 @@ __device__ bool wave_step(unsigned char* buf, int t, int* bd, int k, int n, int 
     w.th = reinterpret_cast<cx<TQ>*>(buf + B::off_th + (t & 1) * B::TH_BYTES);
     w.tau = reinterpret_cast<cx<TQ>*>(buf + B::off_tau + (t & 1) * B::TAU_BYTES);
     int* rec = reinterpret_cast<int*>(buf + B::off_rec) + 6 * (t & 1);
-    w.rb = nullptr; w.G = nullptr; w.V = nullptr; w.taud = nullptr; w.lam = nullptr; w.ord = nullptr;
+    w.rb = nullptr; w.G = nullptr; w.V = nullptr; w.W = nullptr; w.taud = nullptr; w.lam = nullptr; w.ord = nullptr;
     w.red = nullptr; w.flag = nullptr;
     w.bd = bd;
     w.cn = nullptr;
@@ -860,10 +932,10 @@ __global__ void __launch_bounds__(32 * WAVE_LAYERS, 8) circuit_wave_kernel(
     for (int k = threadIdx.x; k <= n; k += blockDim.x) bd[k] = 1;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         cx<T>* s = sites + (size_t)k * (2 * ld * ld);
-        double sn, cs;
-        sincos(0.5 * M_PI * px[k], &sn, &cs);
-        s[0] = mk<T>(T(cs), T(0));
-        s[ld] = mk<T>(T(sn), T(0));
+        T sn, cs;
+        encode_amplitudes(px[k], &sn, &cs);
+        s[0] = mk<T>(cs, T(0));
+        s[ld] = mk<T>(sn, T(0));
     }
     const int L = mt.L < WAVE_LAYERS ? mt.L : WAVE_LAYERS;
     const int last = L - 1;

@@ -54,6 +54,13 @@ template <typename To, typename Ti> __device__ __forceinline__ cx<To> cvt(cx<Ti>
     return mk<To>(To(a.re), To(a.im));
 }
 
+// The encoding R_Y(pi x)|0> = (cos(pi x / 2), sin(pi x / 2)) (Sec. II.B) in the state's
+// own precision: sincospi of x / 2 in FP32 for a complex64 state (the pixel rounds to
+// float, so the amplitudes carry ~1e-7, the rounding level of that state), in FP64
+// for a complex128 one.
+__device__ __forceinline__ void encode_amplitudes(double x, float* s, float* c) { sincospif((float)(0.5 * x), s, c); }
+__device__ __forceinline__ void encode_amplitudes(double x, double* s, double* c) { sincospi(0.5 * x, s, c); }
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
         cx<T>* nxt = cur + MPO_BUF;
         // ladder: the encoding R_Y(pi x) on |0>; paper: |0> (it encodes in every layer)
         if (lane == 0) {
-            double sn = 0.0, cs = 1.0;
-            if (ansatz == 0) sincos(0.5 * M_PI * px[k], &sn, &cs);
-            cur[0] = mk<T>(T(cs), T(0));
-            cur[1] = mk<T>(T(sn), T(0));
+            T sn = T(0), cs = T(1);
+            if (ansatz == 0) encode_amplitudes(px[k], &sn, &cs);
+            cur[0] = mk<T>(cs, T(0));
+            cur[1] = mk<T>(sn, T(0));
         }
         // the CNOT on the right bond acts before the one on the left bond (brick-wall,
         // even site): X^a P_b; otherwise P_b X^a

@@ -217,10 +217,13 @@ __device__ void team_form_q(cx<T>* A, int ld, int M, int K, const cx<T>* tau, in
 // G_in = V diag(lambda) V^H.  A round rotates K/2 disjoint index pairs; each pair
 // is owned by a group of LP = 32 / (K/2) lanes (a power of two) that split the
 // rows (column phase) and the columns (row phase) of the update.  Returns the sweeps.
+// With v_given the columns of V already hold an orthonormal starting basis (G then
+// being the matrix in that basis), and the rotations accumulate onto it.
 template <typename T>
-__device__ int warp_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int lane, int max_sweeps) {
-    for (int c = 0; c < K; ++c)
-        for (int r = lane; r < K; r += 32) V[c * ld + r] = mk<T>(r == c ? T(1) : T(0), T(0));
+__device__ int warp_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int lane, int max_sweeps, bool v_given = false) {
+    if (!v_given)
+        for (int c = 0; c < K; ++c)
+            for (int r = lane; r < K; r += 32) V[c * ld + r] = mk<T>(r == c ? T(1) : T(0), T(0));
     T tr = T(0);
     for (int r = lane; r < K; r += 32) tr += fabs(G[r * ld + r].re);
     tr = warp_sum(tr);

@@ -79,28 +79,81 @@ def circuit_schedule(n: int, L: int, chi: int, ansatz: str = "ladder") -> tuple:
     return tuple(steps), tuple(bd)
 
 
-def circuit_flops(n: int, L: int, chi: int, ansatz: str = "ladder", jacobi_sweeps: int = 6) -> float:
+def _jacobi_flops(K: int, sweeps: float) -> float:
+    """Cyclic Jacobi on a K x K Hermitian matrix: per rotation two columns of G and of
+    V and two rows of G (6 K complex rotation updates, 8 real flops each)."""
+    return sweeps * (K * (K - 1) / 2) * 48.0 * K
+
+
+def circuit_flops_by_pipe(n: int, L: int, chi: int, ansatz: str = "ladder", chain: str = "c64",
+                          jacobi_sweeps: float = 6.0, refine_sweeps: float = 2.0) -> dict:
+    """Flops of the sequential circuit kernel per image, split by the pipe that runs
+    them: {"fp32": ..., "fp64": ...}.
+
+    chain "c64": complex64 state (MPS_MIXED_FAST, and the exact-regime sequential
+    kernel of MPS_MIXED): gates, theta, QR/LQ in FP32; inside a truncation the Gram
+    matrix, U (re-orthogonalised by an FP64 QR) and U^H theta in FP64, the Jacobi
+    eigensolver in FP32.
+    chain "fp64": complex128 state (a truncating chain of MPS_MIXED, and MPS_FP64):
+    everything in FP64 except, up to bond 16, the FP32 Jacobi that starts the
+    eigen-decomposition, which then costs an FP64 Cholesky QR of the K x K vectors
+    (4 K^3), the transform W^H G W (16 K^3) and `refine_sweeps` rotating FP64 sweeps."""
     steps, _ = circuit_schedule(n, L, chi, ansatz)
-    f = 0.0
+    f32 = f64 = 0.0
+    state64 = chain == "fp64"
     for kind, Dl, Dm, Dr, nb in steps:
         if kind == "gate":
             M, N = 2 * Dl, 2 * Dr
-            f += 32.0 * Dm * Dr + 8.0 * M * N * Dm
+            g = 32.0 * Dm * Dr + 8.0 * M * N * Dm
             if min(M, N) <= chi:
                 if N <= M:
-                    f += _qr_flops(M, N)
+                    g += _qr_flops(M, N)
+                if state64:
+                    f64 += g
+                else:
+                    f32 += g
             else:
                 K = min(M, N)
-                f += 4.0 * K * K * max(M, N) + jacobi_sweeps * (K * (K - 1) / 2) * 48.0 * K
-                f += 8.0 * chi * M * N
-                if M > N:
-                    f += 8.0 * M * chi * N + _qr_flops(M, chi)
+                gram = 4.0 * K * K * max(M, N)
+                uht = 8.0 * chi * M * N
+                right = 8.0 * M * chi * N + _qr_flops(M, chi) if M > N else 0.0
+                if state64:
+                    f64 += g + gram + uht + right
+                    if K <= 32:   # bond <= 16: FP32 Jacobi, then the FP64 refinement
+                        f32 += _jacobi_flops(K, jacobi_sweeps)
+                        f64 += 4.0 * K ** 3 + 16.0 * K ** 3 + _jacobi_flops(K, refine_sweeps)
+                    else:
+                        f64 += _jacobi_flops(K, jacobi_sweeps)
+                else:
+                    f32 += g + _jacobi_flops(K, jacobi_sweeps)
+                    f64 += gram + uht + right + (0.0 if M > N else _qr_flops(M, chi))
         elif kind == "move":
             M, N = 2 * Dl, Dm
-            f += _qr_flops(M, N) + 8.0 * nb * Dm * 2 * Dr
+            g = _qr_flops(M, N) + 8.0 * nb * Dm * 2 * Dr
+            if state64:
+                f64 += g
+            else:
+                f32 += g
         else:  # lq of site (Dl x 2 Dr) and site_{k-1} * L
-            f += _qr_flops(2 * Dr, Dm) + 8.0 * 2 * Dl * Dm * nb
-    return f
+            g = _qr_flops(2 * Dr, Dm) + 8.0 * 2 * Dl * Dm * nb
+            if state64:
+                f64 += g
+            else:
+                f32 += g
+    return {"fp32": f32, "fp64": f64}
+
+
+def circuit_flops(n: int, L: int, chi: int, ansatz: str = "ladder", jacobi_sweeps: int = 6) -> float:
+    """All flops of the complex64-state sequential circuit kernel per image."""
+    d = circuit_flops_by_pipe(n, L, chi, ansatz, "c64", jacobi_sweeps)
+    return d["fp32"] + d["fp64"]
+
+
+def lossy(p: int, L: int, chi: int) -> bool:
+    """Whether a ladder circuit truncates lossily (its exact bond min(2^L, 2^floor(n/2))
+    exceeds chi), so that MPS_MIXED runs it on a complex128 state."""
+    n = p * p
+    return min(1 << min(L, 30), 1 << min(n // 2, 30)) > chi
 
 
 HALF_SPLIT_MIN = 8   # pauli.cuh: split contractions of half-structured sites from this bond on
