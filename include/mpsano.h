@@ -122,6 +122,15 @@ mps_status mps_create_batch(int32_t n_images, const int32_t* p, const int32_t* c
 mps_status mps_reshape_batch(mps_batch* batch, int32_t n_images, const int32_t* p, const int32_t* chi,
                              int32_t chi_all);
 
+/* Allocate now, for the batch's current layout, every device buffer that a later
+ * mps_apply_circuit may need: the left environments of operator-product images, and
+ * under MPS_MIXED / MPS_MIXED_ORTH64 the complex128 sites of truncating chains, plus
+ * gate tables for up to max(L_max, n_images) rows.  Afterwards mps_apply_circuit with
+ * at most L_max layers, on this layout or a smaller one set by mps_reshape_batch,
+ * allocates nothing (a serving loop then never stalls on cudaMalloc).  Waits for the
+ * batch's stream if it grows a buffer.  MPS_ERR_OOM if an allocation fails. */
+mps_status mps_reserve(mps_batch* batch, int32_t L_max);
+
 /* Release a batch (stream-ordered: waits for its queued work first). NULL is a no-op. */
 mps_status mps_destroy_batch(mps_batch* batch);
 

@@ -46,6 +46,7 @@ SIGNATURES = {
     "mps_create_batch": (_c.c_int, [_c.c_int32, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32), _c.c_int32,
                                     _c.c_int32, _c.c_void_p, _c.POINTER(_c.c_void_p)]),
     "mps_destroy_batch": (_c.c_int, [_c.c_void_p]),
+    "mps_reserve": (_c.c_int, [_c.c_void_p, _c.c_int32]),
     "mps_reshape_batch": (_c.c_int, [_c.c_void_p, _c.c_int32, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32),
                                      _c.c_int32]),
     "mps_apply_circuit": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.POINTER(mps_circuit)]),

@@ -62,6 +62,11 @@ class Batch:
         self.pixel_offsets = np.concatenate([[0], np.cumsum(self.n)])
         self.pair_offsets = np.concatenate([[0], np.cumsum([pair_count(int(q)) for q in p])])
 
+    def reserve(self, L_max: int):
+        """Allocate every buffer a circuit of up to L_max layers may need on this layout
+        (or a smaller one), so that later calls allocate nothing."""
+        check(lib().mps_reserve(self._h, int(L_max)))
+
     # -- lifetime ------------------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

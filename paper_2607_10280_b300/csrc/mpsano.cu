@@ -398,6 +398,52 @@ mps_status fit_and_upload(mps_batch* b) {
     return MPS_OK;
 }
 
+// Left environments for every image of the current layout (operator-product images).
+mps_status ensure_lenv(mps_batch* b) {
+    const size_t need = b->elem * b->renv_stride * b->B;
+    if (b->cap_lenv >= need && b->lenv) return MPS_OK;
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    cudaFree(b->lenv);
+    b->lenv = nullptr;
+    b->cap_lenv = 0;
+    const cudaError_t e = cudaMalloc(&b->lenv, need);
+    if (e != cudaSuccess) return fail(MPS_ERR_OOM, "left environments: %s", cudaGetErrorString(e));
+    b->cap_lenv = need;
+    return MPS_OK;
+}
+
+// Gate table for `rows` rows (layers of the ladder, images of the paper ansatz) and,
+// with chain64, the FP64 chain's complex128 arena and gate table.
+mps_status ensure_gates(mps_batch* b, int rows, bool chain64) {
+    const size_t gbytes = (size_t)std::max(rows, 1) * b->n_max * 4 * b->elem;
+    const size_t g64 = chain64 ? (size_t)std::max(rows, 1) * b->n_max * 4 * sizeof(cx<double>) : 0;
+    const size_t a64 = chain64 ? sizeof(cx<double>) * b->need_sites : 0;
+    if (gbytes <= b->gates_bytes && g64 <= b->gates64_bytes && a64 <= b->cap_arena64) return MPS_OK;
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (gbytes > b->gates_bytes) {
+        cudaFree(b->gates);
+        b->gates = nullptr;
+        b->gates_bytes = 0;
+        CUDA_TRY(cudaMalloc(&b->gates, gbytes));
+        b->gates_bytes = gbytes;
+    }
+    if (g64 > b->gates64_bytes) {
+        cudaFree(b->gates64);
+        b->gates64 = nullptr;
+        b->gates64_bytes = 0;
+        CUDA_TRY(cudaMalloc(&b->gates64, g64));
+        b->gates64_bytes = g64;
+    }
+    if (a64 > b->cap_arena64) {
+        cudaFree(b->arena64);
+        b->arena64 = nullptr;
+        b->cap_arena64 = 0;
+        CUDA_TRY(cudaMalloc(&b->arena64, a64));
+        b->cap_arena64 = a64;
+    }
+    return MPS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -446,6 +492,16 @@ mps_status mps_destroy_batch(mps_batch* b) {
     cudaStreamSynchronize(b->stream);
     free_batch(b);
     return MPS_OK;
+}
+
+mps_status mps_reserve(mps_batch* b, int32_t L_max) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    if (L_max < 0 || L_max > 64) return fail(MPS_ERR_INVALID_ARG, "L_max = %d outside 0..64", L_max);
+    if (!b->layout_ok) return fail(MPS_ERR_NOT_READY, "the batch's last reshape failed");
+    mps_status st = ensure_lenv(b);
+    if (st != MPS_OK) return st;
+    const bool chain64 = b->prec == MPS_MIXED || b->prec == MPS_MIXED_ORTH64;
+    return ensure_gates(b, std::max(L_max, b->B), chain64);
 }
 
 mps_status mps_set_launch_shape(mps_batch* b, int32_t images_per_cta, int32_t circuit_threads,
@@ -555,16 +611,8 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     for (int32_t i : b->cost_order) if (!wave[i] && !mpo[i] && !c64[i]) order.push_back(i);
     for (int32_t i : b->cost_order) if (c64[i]) order.push_back(i);
     if (n_mpo > 0) {
-        cudaError_t e;
-        if (b->cap_lenv < b->elem * b->renv_stride * b->B) {
-            CUDA_TRY(cudaStreamSynchronize(b->stream));
-            cudaFree(b->lenv);
-            b->lenv = nullptr;
-            b->cap_lenv = 0;
-            e = cudaMalloc(&b->lenv, b->elem * b->renv_stride * b->B);
-            if (e != cudaSuccess) return fail(MPS_ERR_OOM, "left environments: %s", cudaGetErrorString(e));
-            b->cap_lenv = b->elem * b->renv_stride * b->B;
-        }
+        const mps_status se = ensure_lenv(b);
+        if (se != MPS_OK) return se;
     }
     b->any_lenv = n_mpo > 0;
     if (order != b->order_h) {
@@ -586,35 +634,9 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     // one-qubit gate table (FP64 math, rounded to the state type); a second one in FP64
     // for the FP64 chains
     const int rows = circ->ansatz == MPS_ANSATZ_LADDER ? L_max : b->B;
-    const size_t gbytes = (size_t)std::max(rows, 1) * b->n_max * 4 * b->elem;
-    if (gbytes > b->gates_bytes) {
-        CUDA_TRY(cudaStreamSynchronize(b->stream));
-        cudaFree(b->gates);
-        b->gates = nullptr;
-        b->gates_bytes = 0;
-        CUDA_TRY(cudaMalloc(&b->gates, gbytes));
-        b->gates_bytes = gbytes;
-    }
-    if (n_64 > 0) {
-        const size_t g64 = (size_t)std::max(rows, 1) * b->n_max * 4 * sizeof(cx<double>);
-        const size_t a64 = sizeof(cx<double>) * b->need_sites;
-        if (g64 > b->gates64_bytes || a64 > b->cap_arena64) {
-            CUDA_TRY(cudaStreamSynchronize(b->stream));
-            if (g64 > b->gates64_bytes) {
-                cudaFree(b->gates64);
-                b->gates64 = nullptr;
-                b->gates64_bytes = 0;
-                CUDA_TRY(cudaMalloc(&b->gates64, g64));
-                b->gates64_bytes = g64;
-            }
-            if (a64 > b->cap_arena64) {
-                cudaFree(b->arena64);
-                b->arena64 = nullptr;
-                b->cap_arena64 = 0;
-                CUDA_TRY(cudaMalloc(&b->arena64, a64));
-                b->cap_arena64 = a64;
-            }
-        }
+    {
+        const mps_status se = ensure_gates(b, rows, n_64 > 0);
+        if (se != MPS_OK) return se;
     }
     b->gate_n = b->n_max;
     b->L_max = L_max;

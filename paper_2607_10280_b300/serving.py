@@ -2,15 +2,22 @@
 
 Requests of mixed size p, depth L and bond cap chi arrive at any time.  The
 server keeps `slots` execution slots, each with its own CUDA stream, a reusable
-MPS batch (``Batch.reshape`` reuses its device memory) and pinned staging
+MPS batch (``Batch.reshape`` reuses its device memory; ``Batch.reserve`` sizes
+every lazily allocated buffer up front, so no wave allocates) and pinned staging
 buffers.  Whenever a slot is free and requests are waiting, it forms a wave from
 the waiting requests in arrival order, admitting each while the wave's device
-footprint (site tensors + environments, about n * ld^2 * 3 complex values per
-image) fits the slot's share of the memory budget, and launches the wave:
-pixels host->device, circuit, Pauli cache, ANO features and linear layer for
-images that have an epilogue registered for their size, results device->host.
-Waves on different slots overlap on the GPU; a request that arrives while
-others run is admitted as soon as a slot frees, without waiting for the rest.
+footprint (site tensors, environments and, for a truncating circuit under the
+mixed precision, its complex128 chain) fits the slot's share of the memory
+budget, and launches the wave: pixels host->device, circuit, Pauli cache, ANO
+features and linear layer for images that have an epilogue registered for their
+size, results device->host.  Waves on different slots overlap on the GPU; a
+request that arrives while others run is admitted as soon as a slot frees,
+without waiting for the rest.
+
+A request whose circuit truncates lossily runs a long sequential chain on a
+complex128 state (its latency grows with p^2 L); `long_slots` of the slots serve
+only such requests, the others only the rest, so a short request never waits
+behind a truncating chain.
 
 Each image's arithmetic is independent of the other images in its wave, so a
 request's result does not depend on the mix it was served in.
@@ -26,20 +33,29 @@ import numpy as np
 import torch
 
 from .api import Batch, ano_features, pair_count
+from .flops import lossy, operator_product_path, padding
 
 
-def image_footprint(p: int, chi: int, precision: str = "mixed") -> int:
-    """Device bytes one image holds in a batch (sites + environments)."""
+def image_footprint(p: int, chi: int, precision: str = "mixed", L: int = None) -> int:
+    """Device bytes one image holds in a batch: site tensors (2 ld^2 complex values per
+    qubit) and right environments (ld^2).  With its depth L known, also the left
+    environments of an image built as an operator product (ld^2 per qubit) and, under
+    the mixed precisions, the complex128 sites of a truncating chain (2 ld^2 at 16 B)."""
     n = p * p
-    cap = 1
-    while cap < chi and cap < (1 << min(n // 2, 20)):
-        cap <<= 1
-    cap = min(cap, chi, 32)          # the library pads sites to at most its largest bond bucket
-    ld = 4
-    while ld < cap:
-        ld <<= 1
+    ld = padding(p, chi)
     elem = 16 if precision == "fp64" else 8
-    return n * 3 * ld * ld * elem
+    b = n * 3 * ld * ld * elem
+    if L is not None:
+        if operator_product_path(p, L, chi):
+            b += n * ld * ld * elem
+        if precision in ("mixed", "mixed_orth64") and lossy(p, L, chi):
+            b += n * 2 * ld * ld * 16
+    return b
+
+
+def request_class(r) -> str:
+    """Latency class of a request: its (p, L, chi)."""
+    return f"p{r.p}_L{r.L}_chi{r.chi}"
 
 
 def form_wave(pending, max_images: int, room: int, footprint) -> tuple:
@@ -68,6 +84,7 @@ class Request:
     pauli: np.ndarray = None
     features: np.ndarray = None
     output: np.ndarray = None
+    lane: str = ""          # "long" (truncating chain) or "short": the slots that served it
     event: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -76,12 +93,16 @@ class Request:
 
 
 class _Slot:
-    def __init__(self, idx, precision, max_images, max_p, max_chi, max_pairs, epi_m, epi_out, launch_shape):
+    def __init__(self, idx, precision, max_images, max_p, max_chi, max_pairs, epi_m, epi_out, launch_shape,
+                 max_L, long_lane=False):
         self.idx = idx
+        self.long_lane = long_lane          # serves only requests that run a truncating chain
         self.stream = torch.cuda.Stream()
         self.precision = precision
-        # sized once for the largest wave, then re-laid-out per wave without allocation
+        # sized once for the largest wave, every lazily allocated buffer included, then
+        # re-laid-out per wave without allocation
         self.batch = Batch(np.full(max_images, max_p, np.int32), max_chi, precision, self.stream)
+        self.batch.reserve(max_L)
         if launch_shape:
             self.batch.set_launch_shape(*launch_shape)
         max_pixels = max_images * max_p * max_p
@@ -94,7 +115,8 @@ class _Slot:
         self.epi_m = max(1, epi_m)
         self.feat_host = torch.empty(max_epi_images * self.epi_m, dtype=torch.float32).pin_memory()
         self.out_host = torch.empty(max_epi_images * max(1, epi_out), dtype=torch.float32).pin_memory()
-        self.done = torch.cuda.Event()
+        self.started = torch.cuda.Event(enable_timing=True)
+        self.done = torch.cuda.Event(enable_timing=True)
         self.wave = None
         self.footprint = 0
 
@@ -109,7 +131,7 @@ class Server:
 
     def __init__(self, params: torch.Tensor, epilogue: dict = None, slots: int = 4,
                  max_images_per_wave: int = 64, budget_bytes: int = 2 << 30, precision: str = "mixed",
-                 launch_shape=None, max_p: int = 16, max_chi: int = 32):
+                 launch_shape=None, max_p: int = 16, max_chi: int = 32, long_slots: int = None):
         self.params = params
         self.epilogue = epilogue or {}
         self.precision = precision
@@ -120,10 +142,18 @@ class Server:
         self.max_p, self.max_chi = max_p, max_chi
         epi_out = max((W.shape[0] for (_, W, _) in self.epilogue.values()), default=1)
         epi_m = max((pair_count(p) for p in self.epilogue), default=1)
+        # slots reserved for truncating chains (only the mixed precisions route them
+        # differently; one slot serves everything)
+        if long_slots is None:
+            long_slots = 1 if slots >= 2 else 0
+        self.long_slots = max(0, min(long_slots, slots - 1))
         self.slots = [_Slot(i, precision, max_images_per_wave, max_p, max_chi,
-                            max_images_per_wave * pair_count(max_p), epi_m, epi_out, launch_shape)
+                            max_images_per_wave * pair_count(max_p), epi_m, epi_out, launch_shape,
+                            params.shape[0], long_lane=i >= slots - self.long_slots)
                       for i in range(slots)]
-        self.pending = collections.deque()
+        self.pending = collections.deque()        # requests for the short lane
+        self.pending_long = collections.deque()   # requests that run a truncating chain
+        self.wave_log = []                        # (slot, images, long lane, device ms) per wave
         self.lock = threading.Lock()
         self.inflight_bytes = 0
         self.completed = []
@@ -140,14 +170,20 @@ class Server:
             raise ValueError("request exceeds the server's parameter table")
         if req.p > self.max_p or req.chi > self.max_chi:
             raise ValueError("request exceeds the server's largest image size or bond cap")
-        if image_footprint(req.p, req.chi, self.precision) > self.slot_budget:
+        if image_footprint(req.p, req.chi, self.precision, req.L) > self.slot_budget:
             raise ValueError("request does not fit a slot's memory budget")
         with self.lock:
             req.id = self._next_id
             self._next_id += 1
             req.t_submit = time.perf_counter()
-            self.pending.append(req)
+            self._queue_of(req).append(req)
         return req
+
+    def _is_long(self, req) -> bool:
+        return self.long_slots > 0 and self.precision in ("mixed", "mixed_orth64") and lossy(req.p, req.L, req.chi)
+
+    def _queue_of(self, req):
+        return self.pending_long if self._is_long(req) else self.pending
 
     def start(self):
         self._stop = False
@@ -158,7 +194,7 @@ class Server:
         if drain:
             while True:
                 with self.lock:
-                    busy = self.pending or any(s.wave for s in self.slots)
+                    busy = self.pending or self.pending_long or any(s.wave for s in self.slots)
                 if not busy:
                     break
                 time.sleep(0.0005)
@@ -183,18 +219,18 @@ class Server:
                 progressed = True
         for s in self.slots:
             if s.wave is None:
-                wave = self._admit()
+                wave = self._admit(self.pending_long if s.long_lane else self.pending)
                 if not wave:
-                    break
+                    continue
                 self._launch(s, wave)
                 progressed = True
         return progressed
 
-    def _admit(self):
+    def _admit(self, queue):
         with self.lock:
             room = min(self.slot_budget, self.budget - self.inflight_bytes)
-            wave, foot = form_wave(self.pending, self.max_images, room,
-                                   lambda r: image_footprint(r.p, r.chi, self.precision))
+            wave, foot = form_wave(queue, self.max_images, room,
+                                   lambda r: image_footprint(r.p, r.chi, self.precision, r.L))
             if wave:
                 self.inflight_bytes += foot
                 self.max_inflight_bytes = max(self.max_inflight_bytes, self.inflight_bytes)
@@ -205,10 +241,13 @@ class Server:
         # images with an epilogue first, grouped by size, so that each group's Pauli
         # blocks are contiguous
         wave.sort(key=lambda r: (0 if r.p in self.epilogue else 1, r.p))
+        for r in wave:
+            r.lane = "long" if s.long_lane else "short"
         ps = np.array([r.p for r in wave], np.int32)
         chis = np.array([r.chi for r in wave], np.int32)
         Ls = np.array([r.L for r in wave], np.int32)
         with torch.cuda.stream(s.stream):
+            s.started.record(s.stream)
             s.batch.reshape(ps, chis)
             offs = s.batch.pixel_offsets
             for i, r in enumerate(wave):
@@ -254,6 +293,7 @@ class Server:
         for r in wave:
             r.t_done = now
             r.event.set()
+        self.wave_log.append((s.idx, len(wave), s.long_lane, s.started.elapsed_time(s.done)))
         with self.lock:
             self.inflight_bytes -= s.footprint
             self.completed.extend(wave)
@@ -265,3 +305,11 @@ def latency_report(reqs) -> dict:
     lat = np.array([r.latency_s for r in reqs]) * 1e3
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "requests": len(reqs)}
+
+
+def latency_by(reqs, key) -> dict:
+    """latency_report of the requests grouped by key(request)."""
+    groups = collections.defaultdict(list)
+    for r in reqs:
+        groups[key(r)].append(r)
+    return {k: latency_report(v) for k, v in sorted(groups.items())}

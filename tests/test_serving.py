@@ -23,6 +23,12 @@ def test_admission_policy_respects_count_and_bytes():
     assert image_footprint(7, 16) == 49 * 3 * 16 * 16 * 8
     assert image_footprint(2, 64) == 4 * 3 * 4 * 4 * 8         # bond limited by 2^(n/2) = 4
     assert image_footprint(7, 16, "fp64") == 2 * image_footprint(7, 16)
+    # with the depth: left environments of an operator-product image (L = 4, chi = 16),
+    # the complex128 chain of a truncating one (L = 4, chi = 8), neither at L = 3, chi = 8
+    assert image_footprint(7, 16, "mixed", 4) == 49 * 4 * 16 * 16 * 8
+    assert image_footprint(7, 8, "mixed", 4) == 49 * 3 * 8 * 8 * 8 + 49 * 2 * 8 * 8 * 16
+    assert image_footprint(7, 8, "mixed", 3) == 49 * 4 * 8 * 8 * 8
+    assert image_footprint(7, 8, "fp64", 4) == 49 * 3 * 8 * 8 * 16
 
 
 @pytest.mark.gpu
@@ -52,6 +58,12 @@ def test_results_do_not_depend_on_the_mix():
         assert r.event.wait(120)
     srv.stop()
     assert srv.waves > 1 and srv.max_inflight_bytes <= budget
+    # requests that run a truncating (complex128) chain were served by the long lane only
+    from paper_2607_10280_b300.flops import lossy
+    assert any(lossy(r.p, r.L, r.chi) for r in reqs) and any(not lossy(r.p, r.L, r.chi) for r in reqs)
+    for r in reqs:
+        assert r.lane == ("long" if lossy(r.p, r.L, r.chi) else "short"), (r.p, r.L, r.chi, r.lane)
+    assert all(ms > 0 for (_, _, _, ms) in srv.wave_log)
     # every request again, alone in its own wave
     alone = Server(params, epi, slots=1, max_images_per_wave=1, max_p=8, max_chi=8)
     alone.start()
