@@ -97,8 +97,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-sample", type=int, default=8, help="images timed through the per-image FP64 path")
     ap.add_argument("--batch", type=int, default=BATCH, help="images per GPU (profiling of smaller cases)")
-    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "trunc", "uneven", "large", "serve",
-                                                            "train", "diag"],
+    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "trunc", "large_chi", "uneven",
+                                                            "large", "serve", "train", "diag"],
                     help="headline (default): 7x7 L=4 chi=16; the others are the chi x L sweep, the uneven "
                          "batch, the 16x16 batch, the serving run, training on cached Paulis and the "
                          "156-pair layout with diagonals")
@@ -604,6 +604,58 @@ def run_trunc(args):
     print(json.dumps(line), flush=True)
 
 
+def run_large_chi(args):
+    """The large-chi end of the paper's sweep (Sec. III): 64 garment-like 7x7 images at
+    L = 5, 6, 7 with chi in {16, 32, 64, 128}.  Bonds above 32 run the kernels with their
+    workspaces in global memory; at L = 7, chi = 64 the cut from 128 to 64 binds.  Per row:
+    images/s (mixed and FP64), the discarded weight, and the MAE and max error (Eq. 7) of
+    the mixed path against the FP64 path at chi = 2^L (exact)."""
+    torch = _setup_torch()
+    from paper_2607_10280_b300 import api, synth
+    p, B = 7, min(args.batch, 64)
+    m = api.pair_count(p)
+    X = synth.garment_pixels(B, p)
+    px = torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda")
+    rows = []
+    for Lr in (5, 6, 7):
+        params = torch.tensor(synth.circuit_params(Lr, p * p), dtype=torch.float64, device="cuda")
+        exact = None
+        res = {}
+        for chi in (128, 64, 32, 16):
+            r = {"L": Lr, "chi": chi}
+            for prec in ("fp64", "mixed"):
+                b = api.Batch(np.full(B, p, np.int32), chi, prec)
+                out = torch.empty((B * m, 16), dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+
+                def step():
+                    b.apply_circuit(px, Lr, "ladder", params)
+                    b.pauli_cache(out)
+                step()
+                torch.cuda.synchronize()
+                ms = _time_events(torch, step, 2)
+                r[f"images_per_s_{prec}"] = B / (ms / 1e3)
+                got = out.double().cpu().numpy().reshape(B, m, 16)
+                if prec == "fp64":
+                    r["discarded_weight_mean"] = float(np.mean(b.discarded_weight()))
+                    r["max_bond"] = int(max(max(x) for x in b.bond_dims()))
+                    if chi == 128:
+                        exact = got
+                res[prec] = got
+                b.close()
+            e = np.abs(res["mixed"] - exact)
+            r["mae_mixed_vs_exact"] = float(e.mean())
+            r["max_mixed_vs_exact"] = float(e.max())
+            r["max_mixed_vs_fp64_same_chi"] = float(np.max(np.abs(res["mixed"] - res["fp64"])))
+            rows.append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+    line = {"metric": "large-chi sweep at 7x7: images/s and error vs exact (chi = 2^L), L = 5..7, chi = 16..128",
+            "value": rows[-1]["images_per_s_mixed"], "unit": "images/s", "n_gpus": 1,
+            "config": {"workload": "7x7 garment-like, ladder ansatz, L in 5..7, chi in {16,32,64,128}", "images": B,
+                       "exact_reference": "the FP64 path at chi = 128 (= 2^L for L = 7, exact below)"},
+            "table": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_uneven(args):
     """512 images with p ~ U{4..16}, chi = 16, L in {1, 2}: the batched pipeline (persistent,
     cost-ordered circuit kernel; autotuned launch shape) replayed as one CUDA graph, vs a
@@ -884,5 +936,5 @@ if __name__ == "__main__":
     elif a.config == "headline":
         run_ours(a)
     else:
-        {"sweep": run_sweep, "trunc": run_trunc, "uneven": run_uneven, "large": run_large, "serve": run_serve,
+        {"sweep": run_sweep, "trunc": run_trunc, "large_chi": run_large_chi, "uneven": run_uneven, "large": run_large, "serve": run_serve,
          "train": run_train, "diag": run_diag}[a.config](a)

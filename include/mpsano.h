@@ -80,9 +80,13 @@ typedef enum { MPS_ANSATZ_LADDER = 0, MPS_ANSATZ_PAPER = 1 } mps_ansatz;
  * both diagonals (2p(p-1) + 2(p-1)^2 pairs: 156 at p = 7). */
 typedef enum { MPS_PAIRS_HV = 0, MPS_PAIRS_HVD = 1 } mps_pair_set;
 
-/* Largest accepted bond cap, and largest bond dimension the kernels hold. */
+/* Largest accepted bond cap, and largest bond dimension the kernels hold.  Bonds up
+ * to 32 run with their workspaces in shared memory; bonds of 64 and 128 run the same
+ * kernels with one 256-thread (circuit) or 128-thread (Pauli cache) team per image and
+ * the workspaces in global memory, allocated by the library (slower; the paper's
+ * large-chi sweep). */
 #define MPS_CHI_LIMIT 4096
-#define MPS_BOND_LIMIT 32
+#define MPS_BOND_LIMIT 128
 
 typedef struct mps_batch mps_batch;
 
@@ -103,6 +107,10 @@ typedef struct {
  *            bonds only grow to min(chi, 2 D_left, 2 D_right) (e.g. at most 2^L for
  *            the ladder), and the kernels hold bonds up to MPS_BOND_LIMIT; a circuit
  *            that would need more returns MPS_ERR_UNSUPPORTED from mps_apply_circuit.
+ *            Sites are padded for bonds up to min(chi, 2^floor(n/2), 32); a circuit that
+ *            needs a larger bond lays the batch out again with a larger padding in
+ *            mps_apply_circuit (that call waits for the stream and may allocate).  The
+ *            pair set with diagonals is built for bonds up to 32.
  *   prec     mps_precision
  *   stream   cudaStream_t (NULL = legacy default stream) used by every later call
  *   out      receives the handle

@@ -16,6 +16,7 @@ struct mps_batch {
     int n_max = 0;
     size_t elem = 8;                       // bytes per complex element of the state
     std::vector<mpsano::ImageMeta> meta_h;
+    std::vector<int32_t> p_h, chi_h;       // the layout's image sides and bond caps
     std::vector<int32_t> units_h;          // (image, column) pairs of the Pauli kernel
     int n_units = 0;                       // = units_h.size() / 2 when units_h is used
     mpsano::ImageMeta* meta_d = nullptr;
@@ -46,6 +47,10 @@ struct mps_batch {
     void* gates64 = nullptr;
     size_t gates64_bytes = 0;
     int n_chain64 = 0;                     // images of the last circuit that took the FP64 chain
+    // global-memory workspace of the kernels for bonds above 32 (their per-team buffers
+    // exceed a block's shared memory)
+    void* gws = nullptr;
+    size_t cap_gws = 0;
     int gate_n = 0;                        // qubit stride of the gate table
     bool gates_owned = true;               // false when gates points into static scratch
     int circuit_threads = 32;              // threads per image in the circuit kernel
@@ -133,6 +138,10 @@ mps_status launch_round_sites(mps_batch* b, const void* src64);
 // Circuits as operator products for b->run_order[0 .. run_count) (ladder_mpo.cu).
 mps_status launch_ladder_mpo(mps_batch* b, const double* pixels, int ansatz);
 mps_status launch_pauli_fp64(mps_batch* b, void* out, bool diag = false);
+// Environments and Pauli cache at bond buckets 64 and 128 (workspace in global memory).
+mps_status launch_pauli_large(mps_batch* b, void* out, bool diag, bool f64);
+// Global-memory workspace of at least `bytes` for the kernels of bonds above 32.
+mps_status ensure_gws(mps_batch* b, size_t bytes);
 mps_status launch_pauli_mixed(mps_batch* b, void* out, bool diag = false);
 
 }  // namespace mpsano

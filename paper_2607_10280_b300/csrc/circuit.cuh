@@ -71,10 +71,11 @@ struct CircuitLayout {
     static constexpr size_t off_lam = off_taud + (TRUNC ? sizeof(cx<double>) * K : 0);
     static constexpr size_t off_ord = off_lam + (TRUNC ? sizeof(double) * K : 0);
     static constexpr size_t off_red = (off_ord + (TRUNC ? sizeof(int) * K : 0) + 15) & ~size_t(15);
-    static constexpr size_t off_flag = off_red + sizeof(double) * 4;   // team reductions (<= 128 threads)
-    // FP64 truncation up to bond 16: the eigen-decomposition starts from FP32 Jacobi
-    // vectors, made orthonormal in FP64 in the buffer W (see svd_truncate)
-    static constexpr bool REFINE = TRUNC && sizeof(TQ) == 8 && CHI <= 16;
+    static constexpr size_t off_flag = off_red + sizeof(double) * 8;   // team reductions (<= 256 threads)
+    // FP64 truncation (up to bond 16 in shared memory, above 32 in global memory): the
+    // eigen-decomposition starts from FP32 Jacobi vectors, made orthonormal in FP64 in the
+    // buffer W (see svd_truncate); bond 32 has no room for W
+    static constexpr bool REFINE = TRUNC && sizeof(TQ) == 8 && (CHI <= 16 || CHI > 32);
     static constexpr size_t off_w = (off_flag + sizeof(int) + 15) & ~size_t(15);
     static constexpr size_t bytes = (off_w + (REFINE ? sizeof(cx<double>) * K * LDK : 0) + 15) & ~size_t(15);
     // the new centre (in cur) is written from V, so the two must not overlap
@@ -366,7 +367,7 @@ struct CircuitTeam {
                 // FP32 resolution are resolved by the same sweeps).
                 team_for_2d<NTHR>(K, K, lane, [&](int c, int r) { G32[c * LDK + r] = cvt<float>(G[c * LDK + r]); });
                 tsync<NTHR>();
-                if (lane < 32) warp_jacobi_eigh<float>(G32, V32, LDK, K, lane, 40);
+                team_jacobi_eigh<NTHR, float>(G32, V32, LDK, K, lane, 40, red);
                 tsync<NTHR>();
                 team_for_2d<NTHR>(K, K, lane, [&](int c, int r) { W[c * LDK + r] = cvt<double>(V32[c * LDK + r]); });
                 tsync<NTHR>();
@@ -416,10 +417,10 @@ struct CircuitTeam {
                     G[j * LDK + i] = acc;
                 });
                 tsync<NTHR>();
-                if (lane < 32) warp_jacobi_eigh<double>(G, W, LDK, K, lane, 40, true);
+                team_jacobi_eigh<NTHR, double>(G, W, LDK, K, lane, 40, red, true);
                 Vd = W;
             } else {
-                if (lane < 32) warp_jacobi_eigh<double>(G, V, LDK, K, lane, 40);
+                team_jacobi_eigh<NTHR, double>(G, V, LDK, K, lane, 40, red);
             }
             tsync<NTHR>();
             for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
@@ -428,7 +429,7 @@ struct CircuitTeam {
         } else {
             team_for_2d<NTHR>(K, K, lane, [&](int c, int r) { G32[c * LDK + r] = cvt<float>(G[c * LDK + r]); });
             tsync<NTHR>();
-            if (lane < 32) warp_jacobi_eigh<float>(G32, V32, LDK, K, lane, 40);
+            team_jacobi_eigh<NTHR, float>(G32, V32, LDK, K, lane, 40, red);
             tsync<NTHR>();
             // lambda from the FP32 Jacobi (absolute error ~ eps_32 lambda_1) ranks the
             // vectors.  Only near the cut can that ranking or the tie test below need
@@ -465,7 +466,7 @@ struct CircuitTeam {
             // by at most sqrt(2 lambda_keep / lambda_1) <= 1.5e-6 of its norm.
             const double gap = lam[ord[keep - 1]] - lam[ord[keep]];
             if (gap < 1e-3 * lam[ord[0]] && lam[ord[keep - 1]] > 1e-12 * lam[ord[0]]) {
-                if (lane < 32) warp_jacobi_eigh<double>(G, V, LDK, K, lane, 40);
+                team_jacobi_eigh<NTHR, double>(G, V, LDK, K, lane, 40, red);
                 tsync<NTHR>();
                 for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
                 tsync<NTHR>();
@@ -691,11 +692,15 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
     const ImageMeta* __restrict__ meta, int n_images, const int32_t* __restrict__ order, int* queue,
     const double* __restrict__ pixels, const cx<T>* __restrict__ gates, int gn, int ansatz,
     cx<T>* __restrict__ arena, int32_t* __restrict__ bonds_out,
-    double* __restrict__ discarded_out, int* status) {
+    double* __restrict__ discarded_out, int* status, unsigned char* __restrict__ gws) {
     using Lay = CircuitLayout<T, TQ, CHI, TRUNC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int team = threadIdx.x / NTHR, lane = threadIdx.x % NTHR;
-    unsigned char* base = smem_raw + (size_t)team * Lay::bytes;
+    // per-team workspace: shared memory, or (gws != NULL: bonds above 32, whose
+    // workspace exceeds a block's shared memory) a slice of global memory that the host
+    // sized as gridDim.x * blockDim.x / NTHR teams
+    unsigned char* base = (gws ? gws + (size_t)blockIdx.x * (blockDim.x / NTHR) * Lay::bytes : smem_raw)
+                          + (size_t)team * Lay::bytes;
     CircuitTeam<T, TQ, CHI, TRUNC, NTHR> w;
     w.cur = reinterpret_cast<cx<T>*>(base + Lay::off_cur);
     w.nxt = reinterpret_cast<cx<T>*>(base + Lay::off_nxt);

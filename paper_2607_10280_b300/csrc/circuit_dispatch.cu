@@ -18,6 +18,14 @@ mps_status launch_circuit_mixed_t1_c4(mps_batch* b, const double* px, int ansatz
 mps_status launch_circuit_mixed_t1_c8(mps_batch* b, const double* px, int ansatz);
 mps_status launch_circuit_mixed_t1_c16(mps_batch* b, const double* px, int ansatz);
 mps_status launch_circuit_mixed_t1_c32(mps_batch* b, const double* px, int ansatz);
+mps_status launch_circuit_fp64_t0_c64(mps_batch* b, const double* px, int ansatz);
+mps_status launch_circuit_fp64_t0_c128(mps_batch* b, const double* px, int ansatz);
+mps_status launch_circuit_fp64_t1_c64(mps_batch* b, const double* px, int ansatz);
+mps_status launch_circuit_fp64_t1_c128(mps_batch* b, const double* px, int ansatz);
+mps_status launch_circuit_mixed_t0_c64(mps_batch* b, const double* px, int ansatz);
+mps_status launch_circuit_mixed_t0_c128(mps_batch* b, const double* px, int ansatz);
+mps_status launch_circuit_mixed_t1_c64(mps_batch* b, const double* px, int ansatz);
+mps_status launch_circuit_mixed_t1_c128(mps_batch* b, const double* px, int ansatz);
 mps_status launch_circuit_orth64_t0_c4(mps_batch* b, const double* px, int ansatz);
 mps_status launch_circuit_orth64_t0_c8(mps_batch* b, const double* px, int ansatz);
 mps_status launch_circuit_orth64_t0_c16(mps_batch* b, const double* px, int ansatz);
@@ -33,6 +41,8 @@ mps_status launch_circuit_fp64_t0(mps_batch* b, int chi_tpl, const double* px, i
         case 8: return launch_circuit_fp64_t0_c8(b, px, ansatz);
         case 16: return launch_circuit_fp64_t0_c16(b, px, ansatz);
         case 32: return launch_circuit_fp64_t0_c32(b, px, ansatz);
+        case 64: return launch_circuit_fp64_t0_c64(b, px, ansatz);
+        case 128: return launch_circuit_fp64_t0_c128(b, px, ansatz);
     }
     return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", chi_tpl);
 }
@@ -43,6 +53,8 @@ mps_status launch_circuit_fp64_t1(mps_batch* b, int chi_tpl, const double* px, i
         case 8: return launch_circuit_fp64_t1_c8(b, px, ansatz);
         case 16: return launch_circuit_fp64_t1_c16(b, px, ansatz);
         case 32: return launch_circuit_fp64_t1_c32(b, px, ansatz);
+        case 64: return launch_circuit_fp64_t1_c64(b, px, ansatz);
+        case 128: return launch_circuit_fp64_t1_c128(b, px, ansatz);
     }
     return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", chi_tpl);
 }
@@ -53,6 +65,8 @@ mps_status launch_circuit_mixed_t0(mps_batch* b, int chi_tpl, const double* px, 
         case 8: return launch_circuit_mixed_t0_c8(b, px, ansatz);
         case 16: return launch_circuit_mixed_t0_c16(b, px, ansatz);
         case 32: return launch_circuit_mixed_t0_c32(b, px, ansatz);
+        case 64: return launch_circuit_mixed_t0_c64(b, px, ansatz);
+        case 128: return launch_circuit_mixed_t0_c128(b, px, ansatz);
     }
     return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", chi_tpl);
 }
@@ -63,6 +77,8 @@ mps_status launch_circuit_mixed_t1(mps_batch* b, int chi_tpl, const double* px, 
         case 8: return launch_circuit_mixed_t1_c8(b, px, ansatz);
         case 16: return launch_circuit_mixed_t1_c16(b, px, ansatz);
         case 32: return launch_circuit_mixed_t1_c32(b, px, ansatz);
+        case 64: return launch_circuit_mixed_t1_c64(b, px, ansatz);
+        case 128: return launch_circuit_mixed_t1_c128(b, px, ansatz);
     }
     return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", chi_tpl);
 }

@@ -12,6 +12,29 @@ template <typename T, typename TQ, int CHI, bool TRUNC, int NTHR>
 mps_status launch_circuit_team(mps_batch* b, const double* pixels, int ansatz) {
     using Lay = CircuitLayout<T, TQ, CHI, TRUNC>;
     const int limit = smem_optin_limit();
+    auto kern = circuit_kernel<T, TQ, CHI, TRUNC, NTHR>;
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if constexpr (NTHR > 32) {
+      if (Lay::bytes > (size_t)limit) {
+        // bonds above 32: the team's buffers live in global memory (a slice per CTA,
+        // one team per CTA), two CTAs per SM at most
+        const int grid = std::max(1, std::min(b->run_count, 2 * sms));
+        const mps_status st = ensure_gws(b, (size_t)grid * Lay::bytes);
+        if (st != MPS_OK) return st;
+        CUDA_TRY(cudaMemsetAsync(b->queue_d, 0, sizeof(int), b->stream));
+        timing_begin(b, KIND_CIRCUIT);
+        kern<<<grid, NTHR, 0, b->stream>>>(b->meta_d, b->run_count, b->run_order, b->queue_d, pixels,
+                                           reinterpret_cast<const cx<T>*>(b->gates), b->gate_n, ansatz,
+                                           reinterpret_cast<cx<T>*>(b->arena), b->bonds_d, b->discarded_d,
+                                           b->status_d, static_cast<unsigned char*>(b->gws));
+        timing_end(b);
+        CUDA_TRY(cudaGetLastError());
+        count_launch();
+        return MPS_OK;
+      }
+    }
     int per_cta = 1;   // images per CTA
     if (NTHR == 32) {
         per_cta = std::max(1, b->images_per_cta);
@@ -21,13 +44,10 @@ mps_status launch_circuit_team(mps_batch* b, const double* pixels, int ansatz) {
     if (smem > (size_t)limit)
         return fail(MPS_ERR_UNSUPPORTED, "circuit kernel needs %zu B shared memory per image (limit %d)",
                     Lay::bytes, limit);
-    auto kern = circuit_kernel<T, TQ, CHI, TRUNC, NTHR>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // persistent grid: as many CTAs as stay resident, capped by the work
-    int per_sm = 0, dev = 0, sms = 0;
+    int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHR * per_cta, smem));
-    CUDA_TRY(cudaGetDevice(&dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int needed = (b->run_count + per_cta - 1) / per_cta;
     const int grid = std::max(1, std::min(needed, std::max(1, per_sm) * sms));
     CUDA_TRY(cudaMemsetAsync(b->queue_d, 0, sizeof(int), b->stream));
@@ -35,7 +55,7 @@ mps_status launch_circuit_team(mps_batch* b, const double* pixels, int ansatz) {
     kern<<<grid, NTHR * per_cta, smem, b->stream>>>(b->meta_d, b->run_count, b->run_order, b->queue_d, pixels,
                                                    reinterpret_cast<const cx<T>*>(b->gates), b->gate_n, ansatz,
                                                    reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
-                                                   b->discarded_d, b->status_d);
+                                                   b->discarded_d, b->status_d, nullptr);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
@@ -71,6 +91,10 @@ mps_status launch_circuit_wave(mps_batch* b, const double* pixels) {
 // image, so every other combination runs one warp per image.
 template <typename T, typename TQ, int CHI, bool TRUNC>
 mps_status launch_circuit(mps_batch* b, const double* pixels, int ansatz) {
+    if constexpr (CHI > 32) {
+        // bonds above 32: one 256-thread team per image, workspace in global memory
+        return launch_circuit_team<T, TQ, CHI, TRUNC, 256>(b, pixels, ansatz);
+    } else {
     if constexpr (!TRUNC) {
         if (b->use_wave) return launch_circuit_wave<T, TQ, CHI>(b, pixels);
     }
@@ -78,6 +102,7 @@ mps_status launch_circuit(mps_batch* b, const double* pixels, int ansatz) {
         if (b->circuit_threads == 64) return launch_circuit_team<T, TQ, CHI, TRUNC, 64>(b, pixels, ansatz);
     }
     return launch_circuit_team<T, TQ, CHI, TRUNC, 32>(b, pixels, ansatz);
+    }
 }
 
 }  // namespace

@@ -1,0 +1,8 @@
+// Circuit kernel instantiation: state float, QR/LQ in float, with the SVD-truncation branch, bond bucket 128 (workspace in global memory).
+#include "circuit_launch.cuh"
+
+namespace mpsano {
+mps_status launch_circuit_mixed_t1_c128(mps_batch* b, const double* px, int ansatz) {
+    return launch_circuit<float, float, 128, true>(b, px, ansatz);
+}
+}  // namespace mpsano

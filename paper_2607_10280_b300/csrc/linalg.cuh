@@ -211,32 +211,46 @@ __device__ void team_form_q(cx<T>* A, int ld, int M, int K, const cx<T>* tau, in
     }
 }
 
-// Cyclic parallel (round-robin) Jacobi eigensolver for the K x K Hermitian matrix G
-// (column-major, ld), K <= 64, run by one warp in the arithmetic of T.  On return
-// diag(G) holds the eigenvalues and the columns of V (K x K, ld) the eigenvectors:
-// G_in = V diag(lambda) V^H.  A round rotates K/2 disjoint index pairs; each pair
-// is owned by a group of LP = 32 / (K/2) lanes (a power of two) that split the
-// rows (column phase) and the columns (row phase) of the update.  Returns the sweeps.
-// With v_given the columns of V already hold an orthonormal starting basis (G then
-// being the matrix in that basis), and the rotations accumulate onto it.
+// c a - f b for real c and complex f, as one fma chain per component.
 template <typename T>
-__device__ int warp_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int lane, int max_sweeps, bool v_given = false) {
+__device__ __forceinline__ cx<T> rot_minus(T c, cx<T> a, cx<T> f, cx<T> b) {
+    const T tr = fma(f.re, b.re, -mul_rn(f.im, b.im)), ti = fma(f.re, b.im, mul_rn(f.im, b.re));
+    return mk<T>(fma(c, a.re, -tr), fma(c, a.im, -ti));
+}
+// s a + g b for real s and complex g.
+template <typename T>
+__device__ __forceinline__ cx<T> rot_plus(T s, cx<T> a, cx<T> g, cx<T> b) {
+    const T tr = fma(g.re, b.re, -mul_rn(g.im, b.im)), ti = fma(g.re, b.im, mul_rn(g.im, b.re));
+    return mk<T>(fma(s, a.re, tr), fma(s, a.im, ti));
+}
+
+// Cyclic parallel (round-robin) Jacobi eigensolver for the K x K Hermitian matrix G
+// (column-major, ld), K <= 2 NTHR, run by a team of NTHR threads in the arithmetic of
+// T.  On return diag(G) holds the eigenvalues and the columns of V (K x K, ld) the
+// eigenvectors: G_in = V diag(lambda) V^H.  A round rotates K/2 disjoint index pairs;
+// each pair is owned by a group of LP threads (a power of two) that split the rows
+// (column phase) and the columns (row phase) of the update.  With v_given the columns
+// of V already hold an orthonormal starting basis (G being the matrix in that basis)
+// and the rotations accumulate onto it.  red: NTHR/32 doubles.  Returns the sweeps.
+template <int NTHR, typename T>
+__device__ int team_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int tid, int max_sweeps, double* red,
+                                bool v_given = false) {
     if (!v_given)
         for (int c = 0; c < K; ++c)
-            for (int r = lane; r < K; r += 32) V[c * ld + r] = mk<T>(r == c ? T(1) : T(0), T(0));
+            for (int r = tid; r < K; r += NTHR) V[c * ld + r] = mk<T>(r == c ? T(1) : T(0), T(0));
     T tr = T(0);
-    for (int r = lane; r < K; r += 32) tr += fabs(G[r * ld + r].re);
-    tr = warp_sum(tr);
+    for (int r = tid; r < K; r += NTHR) tr += fabs(G[r * ld + r].re);
+    tr = team_sum<NTHR>(tr, red, tid);
     // rotate while |G_pq| exceeds the rounding level of the pair's diagonal
     const T eps = sizeof(T) == 4 ? T(3e-7) : T(1e-15);
     const T abs_tol = (sizeof(T) == 4 ? T(3e-8) : T(1e-17)) * (tr > T(0) ? tr : T(1));
     const int Kp = (K + 1) & ~1;          // even number of slots; slot K (if K odd) is a dummy
     const int npairs = Kp / 2;
-    int LP = 1;                           // lanes per pair
-    while (LP * 2 * npairs <= 32) LP *= 2;
-    const int pair = lane / LP, sub = lane % LP;
+    int LP = 1;                           // threads per pair
+    while (LP * 2 * npairs <= NTHR) LP *= 2;
+    const int pair = tid / LP, sub = tid % LP;
     int sweep = 0;
-    __syncwarp();
+    tsync<NTHR>();
     for (; sweep < max_sweeps; ++sweep) {
         int rotated = 0;
         for (int round = 0; round < Kp - 1; ++round) {
@@ -267,39 +281,43 @@ __device__ int warp_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int lane, int
                 }
             }
             rotated |= rot;
-            __syncwarp();
+            const cx<T> se = mk<T>(s * e.re, s * e.im), ce = mk<T>(c * e.re, c * e.im);
+            tsync<NTHR>();
             // columns of G and V: G <- G J, V <- V J,
             // J(p,p) = c, J(p,q) = s, J(q,p) = -s e, J(q,q) = c e, e = e^{-i phi}
             if (rot) {
                 for (int r = sub; r < K; r += LP) {
                     const cx<T> gp = G[p * ld + r], gq = G[q * ld + r];
-                    G[p * ld + r] = c * gp - s * (e * gq);
-                    G[q * ld + r] = s * gp + c * (e * gq);
+                    G[p * ld + r] = rot_minus(c, gp, se, gq);
+                    G[q * ld + r] = rot_plus(s, gp, ce, gq);
                     const cx<T> vp = V[p * ld + r], vq = V[q * ld + r];
-                    V[p * ld + r] = c * vp - s * (e * vq);
-                    V[q * ld + r] = s * vp + c * (e * vq);
+                    V[p * ld + r] = rot_minus(c, vp, se, vq);
+                    V[q * ld + r] = rot_plus(s, vp, ce, vq);
                 }
             }
-            __syncwarp();
+            tsync<NTHR>();
             // rows of G: G <- J^H G
             if (rot) {
-                const cx<T> ec = conj(e);
+                const cx<T> sec = conj(se), cec = conj(ce);
                 for (int col = sub; col < K; col += LP) {
                     const cx<T> gp = G[col * ld + p], gq = G[col * ld + q];
-                    G[col * ld + p] = c * gp - s * (ec * gq);
-                    G[col * ld + q] = s * gp + c * (ec * gq);
+                    G[col * ld + p] = rot_minus(c, gp, sec, gq);
+                    G[col * ld + q] = rot_plus(s, gp, cec, gq);
                 }
             }
-            __syncwarp();
+            tsync<NTHR>();
             if (rot && sub == 0) {  // the 2x2 block is diagonal in exact arithmetic
                 G[q * ld + p] = czero<T>();
                 G[p * ld + q] = czero<T>();
                 G[p * ld + p].im = T(0);
                 G[q * ld + q].im = T(0);
             }
-            __syncwarp();
+            tsync<NTHR>();
         }
-        if (!__any_sync(0xffffffffu, rotated)) break;
+        int any;
+        if constexpr (NTHR == 32) any = __any_sync(0xffffffffu, rotated);
+        else any = __syncthreads_or(rotated);
+        if (!any) break;
     }
     return sweep;
 }

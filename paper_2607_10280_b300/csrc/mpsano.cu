@@ -202,9 +202,21 @@ int dry_run_bonds(int n, int L, int chi, int ansatz, bool* svd) {
 }
 
 int chi_bucket(int mx) {
-    for (int c : {4, 8, 16, 32})
+    for (int c : {4, 8, 16, 32, 64, 128})
         if (mx <= c) return c;
     return -1;
+}
+
+mps_status ensure_gws(mps_batch* b, size_t bytes) {
+    if (b->gws && b->cap_gws >= bytes) return MPS_OK;
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    cudaFree(b->gws);
+    b->gws = nullptr;
+    b->cap_gws = 0;
+    const cudaError_t e = cudaMalloc(&b->gws, bytes);
+    if (e != cudaSuccess) return fail(MPS_ERR_OOM, "kernel workspace of %zu B: %s", bytes, cudaGetErrorString(e));
+    b->cap_gws = bytes;
+    return MPS_OK;
 }
 
 namespace {
@@ -266,6 +278,7 @@ void free_batch(mps_batch* b) {
     cudaFree(b->order_d);
     cudaFree(b->arena64);
     cudaFree(b->gates64);
+    cudaFree(b->gws);
     if (b->gates_owned) cudaFree(b->gates);
     delete b;
 }
@@ -290,13 +303,24 @@ int64_t mps_pair_count(int32_t p, int32_t pair_set) {
 namespace {
 
 // Host-side layout of an image list: per-image records, Pauli work units and sizes.
-mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const int32_t* chi, int32_t chi_all) {
+// Site padding: a power of two >= 4 holding the largest bond the image can reach,
+// min(chi, 2^floor(n/2)), by default at most 32; ld_min (optional, per image) raises
+// it for a circuit that needs a larger bond (up to MPS_BOND_LIMIT).
+constexpr int LD_DEFAULT_CAP = 32;
+mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const int32_t* chi, int32_t chi_all,
+                         const int32_t* ld_min = nullptr) {
     if (n_images <= 0) return fail(MPS_ERR_INVALID_ARG, "n_images must be positive, got %d", n_images);
     if (!p) return fail(MPS_ERR_INVALID_ARG, "p is NULL");
     for (int i = 0; i < n_images; ++i) {
         const int ci = chi ? chi[i] : chi_all;
         if (p[i] < 2 || p[i] > 16) return fail(MPS_ERR_INVALID_ARG, "p[%d] = %d outside 2..16", i, p[i]);
         if (ci < 1 || ci > MPS_CHI_LIMIT) return fail(MPS_ERR_INVALID_ARG, "chi[%d] = %d outside 1..%d", i, ci, MPS_CHI_LIMIT);
+    }
+    if (p != b->p_h.data()) b->p_h.assign(p, p + n_images);
+    if (chi) {
+        if (chi != b->chi_h.data()) b->chi_h.assign(chi, chi + n_images);
+    } else {
+        b->chi_h.assign(n_images, chi_all);
     }
     b->B = n_images;
     b->meta_h.assign(n_images, ImageMeta{});
@@ -308,11 +332,12 @@ mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const
         const int pi = p[i];
         const int ci = chi ? chi[i] : chi_all;
         const int n = pi * pi;
-        // largest bond any circuit can reach: min(chi, 2^floor(n/2)), and at most the
-        // largest compiled bond bucket (a circuit that needs more is refused later)
+        // largest bond any circuit can reach: min(chi, 2^floor(n/2)), at most 32 unless
+        // a circuit asked for more (ld_min)
         int cap = 1;
         while (cap < ci && cap < (1 << std::min(n / 2, 20))) cap <<= 1;
-        cap = std::min(std::min(cap, ci), MPS_BOND_LIMIT);
+        cap = std::min(std::min(cap, ci), LD_DEFAULT_CAP);
+        if (ld_min) cap = std::max(cap, std::min(ld_min[i], MPS_BOND_LIMIT));
         int ld = 4;
         while (ld < cap) ld <<= 1;
         ImageMeta& m = b->meta_h[i];
@@ -564,6 +589,28 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     //    sequential kernel on a complex128 state (sequential truncation amplifies the
     //    rounding of a complex64 state far beyond 1e-5), rounded to complex64 at the end;
     //  - everything else: the sequential kernel in the batch's own precision.
+    // an image whose circuit needs a bond above its site padding (above 32) gets a
+    // larger padding: the batch is laid out again (its state is reset by this call anyway)
+    {
+        std::vector<int32_t> need(b->B, 0);
+        bool grow_ld = false;
+        for (int i = 0; i < b->B; ++i) {
+            const ImageMeta& m = b->meta_h[i];
+            const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
+            bool t = false;
+            const int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
+            need[i] = std::max(bi, m.ld);
+            if (bi > m.ld && bi <= MPS_BOND_LIMIT) grow_ld = true;
+        }
+        if (grow_ld) {
+            CUDA_TRY(cudaStreamSynchronize(b->stream));   // pinned staging may still be in flight
+            const std::vector<int32_t> p = b->p_h, chi = b->chi_h;
+            b->layout_ok = false;
+            mps_status st = layout_images(b, b->B, p.data(), chi.data(), 0, need.data());
+            if (st == MPS_OK) st = fit_and_upload(b);
+            if (st != MPS_OK) return st;
+        }
+    }
     int mx = 1, mx_wave = 1, mx_seq = 1, mx_64 = 1;
     bool trunc_seq = false;
     const bool chain64_on = b->prec == MPS_MIXED || b->prec == MPS_MIXED_ORTH64;
@@ -601,7 +648,7 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         }
     }
     const int chi_tpl = chi_bucket(mx);
-    if (chi_tpl < 0) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > 32 not supported", mx);
+    if (chi_tpl < 0) return fail(MPS_ERR_UNSUPPORTED, "bond dimension %d > %d not supported", mx, MPS_BOND_LIMIT);
     // work order: operator-product images, pipelined images, the rest in the batch's
     // precision, then the FP64 chains, each part by descending cost
     std::vector<int32_t> order;

@@ -53,12 +53,12 @@ struct PauliLayout {
     // with diagonal pairs also Cd (2 MAT, the carried closings one site further)
     static constexpr int ELEMS = 5 * MAT + SROWS * ZS;
     static constexpr size_t bytes = sizeof(cx<T>) * ELEMS;
-    static constexpr size_t elems(bool diag) { return ELEMS + (diag ? 2 * MAT : 0); }
+    __host__ __device__ static constexpr size_t elems(bool diag) { return ELEMS + (diag ? 2 * MAT : 0); }
     // environment kernel: two site buffers, R, and CHI scratch rows (one transfer;
     // the left-environment chain needs 3 MAT + CHI rows)
     static constexpr size_t env_bytes = sizeof(cx<T>) * (5 * MAT + CHI * ZS);
     // plus the cross-warp reduction buffer of a UW-warp team
-    static constexpr size_t team_bytes(int uw, bool diag = false) {
+    __host__ __device__ static constexpr size_t team_bytes(int uw, bool diag = false) {
         return sizeof(cx<T>) * elems(diag) + sizeof(T) * 12 * uw;
     }
 };
@@ -71,7 +71,8 @@ struct Tile {
     static constexpr int MT = (NTHR == 32) ? ((M_HINT >= 2 * N_HINT) ? 8 : 4)
                                            : ((M_HINT >= 2 * N_HINT) ? 16 : (M_HINT * 2 > N_HINT ? 8 : 4));
     static constexpr int NT = NTHR / MT;
-    static constexpr int CAP = sizeof(T) == 4 ? 48 : 24;
+    // register tile cap; products of bonds above 32 (hints above 64) take small tiles
+    static constexpr int CAP = (M_HINT > 64 || N_HINT > 64) ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 48 : 24);
     static constexpr int TM0 = (M_HINT + MT - 1) / MT;
     static constexpr int TM = TM0 < 1 ? 1 : (TM0 > CAP ? CAP : TM0);
     static constexpr int TN0 = (N_HINT + NT - 1) / NT;
@@ -489,16 +490,18 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt, const cx<T>* __r
 // CTA i < n_images: the right environments of image i; with lenv, CTA n_images + i:
 // the left environments of image i when it is flagged META_LENV (the two chains are
 // independent and latency-bound, so one launch runs them side by side).
-template <typename T, int CHI>
+// GMEM (bonds above 32): the workspace is a slice of global memory, env_bytes per CTA.
+template <typename T, int CHI, bool GMEM = false>
 __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ meta, int n_images,
                                                    const cx<T>* __restrict__ arena,
                                                    const int32_t* __restrict__ bonds,
                                                    cx<T>* __restrict__ renv, int64_t renv_stride,
                                                    cx<T>* __restrict__ lenv,
-                                                   T* __restrict__ norm_out) {
+                                                   T* __restrict__ norm_out, unsigned char* __restrict__ gws) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* raw = GMEM ? gws + (size_t)blockIdx.x * Lay::env_bytes : smem_raw;
     // one warp per image and one image per CTA (block-wide syncs are warp syncs)
     const int lane = threadIdx.x;
     if ((int)blockIdx.x >= n_images) {
@@ -507,11 +510,11 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
         const ImageMeta ml = meta[li];
         if (ml.flags & META_LENV)
             lenv_image<T, CHI>(ml, arena, bonds, lenv + (size_t)li * renv_stride,
-                               reinterpret_cast<cx<T>*>(smem_raw), lane);
+                               reinterpret_cast<cx<T>*>(raw), lane);
         return;
     }
     const int img = blockIdx.x;
-    cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
+    cx<T>* base = reinterpret_cast<cx<T>*>(raw);
     const bool half_img = (meta[img].flags & META_HALF) != 0;
     cx<T>* Abuf[2] = {base, base + 3 * MAT};   // site j in one, site j-1 arriving in the other
     cx<T>* R = base + 2 * MAT;
@@ -525,8 +528,12 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     auto prefetch = [&](int j, cx<T>* dstA) {
         const int Dl = bd[j], Dr = bd[j + 1];
         const cx<T>* src = sites + (size_t)j * 2 * ld * ld;
-        team_for_2d<32, 4>(2 * Dl, Dr, lane, [&](int row, int r) { cp_async_elem(dstA + row * CS + r, src + row * ld + r); });
-        cp_async_commit();
+        if constexpr (GMEM) {
+            team_for_2d<32, 4>(2 * Dl, Dr, lane, [&](int row, int r) { dstA[row * CS + r] = src[row * ld + r]; });
+        } else {
+            team_for_2d<32, 4>(2 * Dl, Dr, lane, [&](int row, int r) { cp_async_elem(dstA + row * CS + r, src + row * ld + r); });
+            cp_async_commit();
+        }
     };
     if (lane == 0) R[0] = mk<T>(T(1), T(0));
     if (n > 0) prefetch(n - 1, Abuf[0]);
@@ -535,7 +542,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
         const int Dl = bd[j], Dr = bd[j + 1];
         cx<T>* dst = rg + (size_t)j * CHI * CHI;
         team_for_2d<32, 4>(Dr, Dr, lane, [&](int r, int c) { dst[r * CHI + c] = R[r * CS + c]; });
-        cp_async_wait_all();
+        if constexpr (!GMEM) cp_async_wait_all();
         __syncwarp();
         if (j > 0) prefetch(j - 1, Abuf[cb ^ 1]);
         transfer<T, CHI, 1, 32, 2>(R, Abuf[cb], S, Dl, Dr, lane, half_img && j < n - 1 && Dr >= HALF_SPLIT_MIN);
@@ -544,23 +551,20 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     if (lane == 0) norm_out[img] = R[0].re;
 }
 
+// One (image, column) unit of the Pauli kernel, worked on by the CTA's UW warps with
+// its workspace at smem_raw.
 template <typename T, int CHI, int UW, bool DIAG>
-__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16) ? 9 : 8) / (sizeof(T) == 8 ? 2 : 1)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
-                                                    const int32_t* __restrict__ unit_image,
-                                                    const cx<T>* __restrict__ arena,
-                                                    const int32_t* __restrict__ bonds,
-                                                    const cx<T>* __restrict__ renv, int64_t renv_stride,
-                                                    const cx<T>* __restrict__ lenv,
-                                                    const T* __restrict__ norms, T* __restrict__ out) {
+__device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, const ImageMeta* __restrict__ meta,
+                                           const int32_t* __restrict__ unit_image,
+                                           const cx<T>* __restrict__ arena, const int32_t* __restrict__ bonds,
+                                           const cx<T>* __restrict__ renv, int64_t renv_stride,
+                                           const cx<T>* __restrict__ lenv, const T* __restrict__ norms,
+                                           T* __restrict__ out) {
     using Lay = PauliLayout<T, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NTHR = 32 * UW;
     constexpr bool diag = DIAG;   // both diagonal pair sets as well (a separate instantiation)
-    // one (image, column) unit per CTA, worked on by UW warps
     const int lane = threadIdx.x;
-    const int unit = blockIdx.x;
-    if (unit >= n_units) return;
     const int img = unit_image[2 * unit], c = unit_image[2 * unit + 1];
     cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
     T* red = reinterpret_cast<T*>(base + Lay::ELEMS + (diag ? 2 * MAT : 0));
@@ -674,6 +678,33 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
             const bool dout = !diag && k > j - p + 1 && half_tr(k - 1);
             transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane, half_tr(k), dout);
         }
+    }
+}
+
+
+// One (image, column) unit per CTA (GMEM: bonds above 32, workspace in global memory,
+// Lay::team_bytes per CTA, the CTAs stepping through the units).
+template <typename T, int CHI, int UW, bool DIAG, bool GMEM = false>
+__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16) ? 9 : 8) / (sizeof(T) == 8 ? 2 : 1)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
+                                                    const int32_t* __restrict__ unit_image,
+                                                    const cx<T>* __restrict__ arena,
+                                                    const int32_t* __restrict__ bonds,
+                                                    const cx<T>* __restrict__ renv, int64_t renv_stride,
+                                                    const cx<T>* __restrict__ lenv,
+                                                    const T* __restrict__ norms, T* __restrict__ out,
+                                                    unsigned char* __restrict__ gws) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (GMEM) {
+        constexpr size_t ws = (PauliLayout<T, CHI>::team_bytes(UW, DIAG) + 255) & ~size_t(255);
+        unsigned char* raw = gws + (size_t)blockIdx.x * ws;
+        for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+            pauli_unit<T, CHI, UW, DIAG>(unit, raw, meta, unit_image, arena, bonds, renv, renv_stride, lenv, norms, out);
+            __syncthreads();
+        }
+    } else {
+        if ((int)blockIdx.x >= n_units) return;
+        pauli_unit<T, CHI, UW, DIAG>(blockIdx.x, smem_raw, meta, unit_image, arena, bonds, renv, renv_stride, lenv,
+                                     norms, out);
     }
 }
 

@@ -21,7 +21,7 @@ mps_status launch_pauli_uw(mps_batch* b, void* out) {
         b->meta_d, b->n_units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
         reinterpret_cast<const cx<T>*>(b->any_lenv ? b->lenv : nullptr),
-        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out));
+        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out), nullptr);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
@@ -42,7 +42,7 @@ mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
     rk<<<b->any_lenv ? 2 * b->B : b->B, 32, smem, b->stream>>>(
         b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<cx<T>*>(b->renv), b->renv_stride,
-        reinterpret_cast<cx<T>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<T*>(b->norms));
+        reinterpret_cast<cx<T>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<T*>(b->norms), nullptr);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
@@ -62,6 +62,8 @@ mps_status dispatch_pauli(mps_batch* b, void* out, bool diag) {
         case 8: return launch_pauli<T, 8>(b, out, diag);
         case 16: return launch_pauli<T, 16>(b, out, diag);
         case 32: return launch_pauli<T, 32>(b, out, diag);
+        case 64:
+        case 128: return launch_pauli_large(b, out, diag, sizeof(T) == 8);
     }
     return fail(MPS_ERR_UNSUPPORTED, "bond dimension bucket %d not compiled", b->chi_tpl);
 }

@@ -514,21 +514,21 @@ def test_mixed_batch_routes_each_image_by_its_own_circuit():
 
 def test_failed_calls_leave_no_stale_state():
     """Error paths of the batch handle: a circuit refused after its argument checks
-    (a bond above the image's padding) leaves no circuit for the Pauli cache to read;
+    (a bond above the largest the kernels hold) leaves no circuit for the Pauli cache to read;
     the next good circuit gives the oracle's values; refused reshape arguments leave
     the batch and its circuit as they were; a reshape asks for a new circuit."""
     from paper_2607_10280_b300._lib import MpsError
     from paper_2607_10280_b300.api import Batch
-    p, chi = 4, 64          # padding 32 (the largest compiled bond)
+    p, chi = 5, 4096        # bond above the largest the kernels hold (128) at L = 8
     X = synth.garment_pixels(2, p, seed=31)
-    params = synth.circuit_params(6, p * p, seed=32)
+    params = synth.circuit_params(8, p * p, seed=32)
     px = torch.tensor(np.concatenate(X), dtype=torch.float64, device="cuda")
     pr = torch.tensor(params, dtype=torch.float64, device="cuda").contiguous()
     b = Batch(np.array([p, p], dtype=np.int32), chi, "mixed")
     b.apply_circuit(px, [2, 2], "ladder", pr)
     first = b.pauli_cache().clone()
     with pytest.raises(MpsError) as e:
-        b.apply_circuit(px, [3, 6], "ladder", pr)      # bond 64 > padding 32 at image 1
+        b.apply_circuit(px, [3, 8], "ladder", pr)      # bond 256 > 128 at image 1
     assert e.value.status == 5
     with pytest.raises(MpsError) as e:
         b.pauli_cache()
@@ -601,3 +601,56 @@ def test_truncated_full_batch_mixed_within_1e5_of_fp64(L, chi):
         ref = st.pair_paulis(o_pairs.image_pairs(p))
         assert np.max(np.abs(fp64[i] - ref)) < TOL["fp64"]
         assert np.max(np.abs(mixed[i] - ref)) < TOL["mixed"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("L,chi", [(6, 64), (7, 128)])
+def test_large_bonds_exact_vs_statevector(precision, L, chi):
+    """Bonds of 64 and 128 (the paper's large-chi sweep): 4x4 images (16 qubits) at
+    L = 6 and 7 reach bond 2^L at the middle cuts, held exactly at chi = 2^L; the
+    kernels run with their workspaces in global memory.  Against the dense
+    statevector."""
+    p, B = 4, 2
+    X = synth.garment_pixels(B, p, seed=80 + L)
+    params = synth.circuit_params(L, p * p, seed=81)
+    got, bonds, disc = run_gpu(list(X), [p] * B, L, chi, precision, params=params)
+    n = p * p
+    expect = [1] + [min(chi, 2 ** L, 2 ** (k + 1), 2 ** (n - k - 1)) for k in range(n - 1)] + [1]
+    assert max(expect) == chi
+    for i in range(B):
+        assert list(bonds[i]) == expect
+        ref, _ = oracle_cache(X[i], p, L, chi, params=params, backend="statevector")
+        assert np.max(np.abs(got[i] - ref)) < TOL[precision], (i, np.max(np.abs(got[i] - ref)))
+    assert np.max(disc) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bond_64_truncated_vs_oracle_mps(precision):
+    """A truncation at bond 64: 5x5 images (25 qubits), L = 7, chi = 64, where the
+    middle cuts would reach 128 (theta of 128 x 128, a 128 x 128 Gram matrix); both
+    precisions truncate on a complex128 state.  Against the oracle MPS at the same chi,
+    with the discarded weight."""
+    p, L, chi, B = 5, 7, 64, 1
+    X = synth.garment_pixels(B, p, seed=90)
+    params = synth.circuit_params(L, p * p, seed=91)
+    got, bonds, disc = run_gpu(list(X), [p] * B, L, chi, precision, params=params)
+    st = o_mps.simulate(o_circ.build_circuit("ladder", X[0], L, params), p * p, chi)
+    assert max(bonds[0]) == 64 and float(np.sum(st.discarded)) > 1e-8   # the cut binds
+    assert abs(disc[0] - float(np.sum(st.discarded))) <= 1e-10
+    if st.min_gap >= TIE_GAP:
+        ref = st.pair_paulis(o_pairs.image_pairs(p))
+        assert np.max(np.abs(got[0] - ref)) < TOL[precision], np.max(np.abs(got[0] - ref))
+
+
+def test_large_bonds_refuse_the_diagonal_pair_set():
+    from paper_2607_10280_b300._lib import MpsError
+    from paper_2607_10280_b300.api import Batch
+    p, L, chi = 4, 6, 64
+    X = synth.garment_pixels(1, p, seed=3)
+    b = Batch(np.array([p], np.int32), chi, "mixed")
+    b.apply_circuit(torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda"), L, "ladder",
+                    torch.tensor(synth.circuit_params(L, p * p), dtype=torch.float64, device="cuda"))
+    with pytest.raises(MpsError) as e:
+        b.pauli_cache(pair_set="hvd")
+    assert e.value.status == 5
+    b.close()
