@@ -97,8 +97,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-sample", type=int, default=8, help="images timed through the per-image FP64 path")
     ap.add_argument("--batch", type=int, default=BATCH, help="images per GPU (profiling of smaller cases)")
-    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "trunc", "large_chi", "uneven",
-                                                            "large", "serve", "train", "diag"],
+    ap.add_argument("--config", default="headline", choices=["headline", "sweep", "trunc", "large_chi", "paper",
+                                                            "uneven", "large", "serve", "train", "diag"],
                     help="headline (default): 7x7 L=4 chi=16; the others are the chi x L sweep, the uneven "
                          "batch, the 16x16 batch, the serving run, training on cached Paulis and the "
                          "156-pair layout with diagonals")
@@ -656,6 +656,57 @@ def run_large_chi(args):
     print(json.dumps(line), flush=True)
 
 
+def run_paper(args):
+    """The paper's own circuit (Sec. II.B, Eq. 2: H, R_Y(2 pi x - pi), staggered CNOTs, L
+    encoding-entangling layers) on 1024 garment-like 7x7 images at chi = 2^L (its first
+    near-exact point, Sec. III), circuit + Pauli cache for the 84 H+V pairs and the
+    paper's 156-pair layout with diagonals.  Its state is real: the mixed path runs the
+    real-element environment and Pauli kernels, shown beside the complex ones and the
+    FP64 path, with the max error against FP64 over all images."""
+    torch = _setup_torch()
+    from paper_2607_10280_b300 import api, synth
+    p, B = 7, min(args.batch, 1024)
+    X = synth.garment_pixels(B, p)
+    px = torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda")
+    rows = []
+    for pair_set in ("hv", "hvd"):
+        m = api.pair_count(p, pair_set)
+        for Lr in (1, 2, 3, 4):
+            chi = 1 << Lr
+            r = {"pairs": pair_set, "L": Lr, "chi": chi}
+            outs = {}
+            for name, prec, real in (("mixed_real", "mixed", True), ("mixed_complex", "mixed", False),
+                                     ("fp64", "fp64", False)):
+                b = api.Batch(np.full(B, p, np.int32), chi, prec)
+                b.set_real_arithmetic(real)
+                out = torch.empty((B * m, 16), dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+
+                def step():
+                    b.apply_circuit(px, Lr, "paper")
+                    b.pauli_cache(out, pair_set)
+                step()
+                torch.cuda.synchronize()
+                b.set_timing(True)
+                b.kernel_times()
+                steps = 10 if prec != "fp64" else 3
+                ms = _time_events(torch, step, steps)
+                kt = {k: v[0] / steps for k, v in b.kernel_times().items()}
+                b.close()
+                r[f"images_per_s_{name}"] = B / (ms / 1e3)
+                r[f"kernel_ms_{name}"] = kt
+                outs[name] = out.double().cpu().numpy()
+            r["max_err_mixed_real_vs_fp64"] = float(np.max(np.abs(outs["mixed_real"] - outs["fp64"])))
+            r["max_err_mixed_complex_vs_fp64"] = float(np.max(np.abs(outs["mixed_complex"] - outs["fp64"])))
+            rows.append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+    line = {"metric": "images/s, paper ansatz 7x7 batch 1024 at chi = 2^L (circuit + Pauli cache), real vs complex kernels",
+            "value": rows[3]["images_per_s_mixed_real"], "unit": "images/s", "n_gpus": 1,
+            "config": {"workload": "7x7 garment-like images, paper ansatz (H, R_Y(2 pi x - pi), staggered CNOTs), "
+                                   "L = 1..4, chi = 2^L; pair sets H+V (84) and H+V+diagonals (156)", "images": B},
+            "table": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_uneven(args):
     """512 images with p ~ U{4..16}, chi = 16, L in {1, 2}: the batched pipeline (persistent,
     cost-ordered circuit kernel; autotuned launch shape) replayed as one CUDA graph, vs a
@@ -936,5 +987,5 @@ if __name__ == "__main__":
     elif a.config == "headline":
         run_ours(a)
     else:
-        {"sweep": run_sweep, "trunc": run_trunc, "large_chi": run_large_chi, "uneven": run_uneven, "large": run_large, "serve": run_serve,
+        {"sweep": run_sweep, "trunc": run_trunc, "large_chi": run_large_chi, "paper": run_paper, "uneven": run_uneven, "large": run_large, "serve": run_serve,
          "train": run_train, "diag": run_diag}[a.config](a)

@@ -297,6 +297,14 @@ mps_status mps_set_layer_pipeline(mps_batch* batch, int32_t enable);
  * exactly that.  Takes effect at the next mps_apply_circuit. */
 mps_status mps_set_half_structure(mps_batch* batch, int32_t enable);
 
+/* Real-element environment and Pauli kernels for a real state (enable != 0: on, the
+ * default).  The paper ansatz's gates (H, R_Y(2 pi x - pi), CNOT) are real, so its state
+ * is real in every amplitude; under the mixed precisions the environment and Pauli
+ * kernels then contract real matrices (a quarter of the multiply-adds), and every Pauli
+ * with one Y is exactly zero.  enable = 0 runs the complex kernels (results agree to
+ * rounding).  Takes effect at the next mps_apply_circuit. */
+mps_status mps_set_real_arithmetic(mps_batch* batch, int32_t enable);
+
 /* Per-launch timing with CUDA events recorded on the batch's stream around each
  * kernel the batch launches (enable != 0 turns it on; off by default). */
 mps_status mps_set_timing(mps_batch* batch, int32_t enable);

@@ -142,6 +142,11 @@ class Batch:
         circuits built as operator products); results are bit-identical either way."""
         check(lib().mps_set_half_structure(self._h, 1 if enable else 0))
 
+    def set_real_arithmetic(self, enable: bool = True):
+        """Real-element environment and Pauli kernels for a real state (paper ansatz,
+        mixed precisions); results agree with the complex kernels to rounding."""
+        check(lib().mps_set_real_arithmetic(self._h, 1 if enable else 0))
+
     def set_timing(self, enable: bool = True):
         check(lib().mps_set_timing(self._h, 1 if enable else 0))
 

@@ -56,6 +56,8 @@ struct mps_batch {
     int circuit_threads = 32;              // threads per image in the circuit kernel
     bool layer_pipeline = true;            // layer-pipelined kernel where it applies
     bool half_structure = true;            // exploit half-structured sites (META_HALF)
+    bool real = false;                     // the last circuit's state is real (paper ansatz)
+    bool real_allowed = true;              // real-element kernels for real states (mps_set_real_arithmetic)
     int L_max = 0;                         // most layers of any image in the last circuit
     // images of the next circuit launch: run_order[0 .. run_count), and whether the
     // layer-pipelined kernel runs them
@@ -140,6 +142,8 @@ mps_status launch_ladder_mpo(mps_batch* b, const double* pixels, int ansatz);
 mps_status launch_pauli_fp64(mps_batch* b, void* out, bool diag = false);
 // Environments and Pauli cache at bond buckets 64 and 128 (workspace in global memory).
 mps_status launch_pauli_large(mps_batch* b, void* out, bool diag, bool f64);
+// Environments and Pauli cache of a real state (b->real), complex64 storage, bonds <= 32.
+mps_status launch_pauli_real(mps_batch* b, void* out, bool diag);
 // Global-memory workspace of at least `bytes` for the kernels of bonds above 32.
 mps_status ensure_gws(mps_batch* b, size_t bytes);
 mps_status launch_pauli_mixed(mps_batch* b, void* out, bool diag = false);

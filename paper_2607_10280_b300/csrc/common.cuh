@@ -61,6 +61,47 @@ template <typename To, typename Ti> __device__ __forceinline__ cx<To> cvt(cx<Ti>
 __device__ __forceinline__ void encode_amplitudes(double x, float* s, float* c) { sincospif((float)(0.5 * x), s, c); }
 __device__ __forceinline__ void encode_amplitudes(double x, double* s, double* c) { sincospi(0.5 * x, s, c); }
 
+// Element types of the contraction kernels: complex (cx<T>) or, for a state that is
+// real in every amplitude (the paper ansatz: H, R_Y and CNOT are real), the scalar
+// itself.  For a real element the complex helpers reduce to plain fma.
+template <typename E> struct elem_traits;
+template <typename T> struct elem_traits<cx<T>> {
+    using scalar = T;
+    static constexpr bool real = false;
+};
+template <> struct elem_traits<float> {
+    using scalar = float;
+    static constexpr bool real = true;
+};
+template <> struct elem_traits<double> {
+    using scalar = double;
+    static constexpr bool real = true;
+};
+template <typename E> __device__ __forceinline__ E ezero() {
+    if constexpr (elem_traits<E>::real) return E(0);
+    else return czero<typename elem_traits<E>::scalar>();
+}
+template <typename E> __device__ __forceinline__ E eone() {
+    using T = typename elem_traits<E>::scalar;
+    if constexpr (elem_traits<E>::real) return E(1);
+    else return mk<T>(T(1), T(0));
+}
+// the element of a complex value stored in global memory (its real part for a real element)
+template <typename E, typename T> __device__ __forceinline__ E to_elem(cx<T> v) {
+    if constexpr (elem_traits<E>::real) return E(v.re);
+    else return v;
+}
+template <typename E> __device__ __forceinline__ typename elem_traits<E>::scalar ereal(E v) {
+    if constexpr (elem_traits<E>::real) return v;
+    else return v.re;
+}
+__device__ __forceinline__ float conj(float a) { return a; }
+__device__ __forceinline__ double conj(double a) { return a; }
+__device__ __forceinline__ void cmac(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+__device__ __forceinline__ void cmac(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void cmac_cj(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+__device__ __forceinline__ void cmac_cj(double& acc, double a, double b) { acc = fma(a, b, acc); }
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -550,6 +550,12 @@ mps_status mps_set_layer_pipeline(mps_batch* b, int32_t enable) {
     return MPS_OK;
 }
 
+mps_status mps_set_real_arithmetic(mps_batch* b, int32_t enable) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    b->real_allowed = enable != 0;
+    return MPS_OK;
+}
+
 mps_status mps_set_half_structure(mps_batch* b, int32_t enable) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
     b->half_structure = enable != 0;
@@ -744,6 +750,9 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         if (st != MPS_OK) return st;
     }
     b->chi_tpl = chi_tpl;
+    // H, R_Y(2 pi x - pi) and CNOT are real: the paper ansatz's state is real in every
+    // amplitude (every kernel keeps its imaginary parts exactly zero)
+    b->real = b->real_allowed && circ->ansatz == MPS_ANSATZ_PAPER && b->prec != MPS_FP64;
     b->circuit_done = true;
     return MPS_OK;
 }

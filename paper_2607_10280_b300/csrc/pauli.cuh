@@ -33,6 +33,8 @@
 // broadcast.  D x D matrices use row stride CS = CHI + 1; the GEMM scratch S has
 // 3*CHI rows of stride ZS = 2*CHI + 1.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "linalg.cuh"
 
@@ -43,8 +45,9 @@ namespace mpsano {
 // two products of depth D/2 cost more in launch overhead than they save.
 constexpr int HALF_SPLIT_MIN = 8;
 
-template <typename T, int CHI>
+template <typename E, int CHI>
 struct PauliLayout {
+    using T = typename elem_traits<E>::scalar;
     static constexpr int CS = CHI + 1;
     static constexpr int MAT = CHI * CS;
     static constexpr int ZS = 2 * CHI + 1;
@@ -52,22 +55,23 @@ struct PauliLayout {
     // A (2 MAT), R (1 MAT), C (2 MAT: M = C_X + i C_Y, C_Z), S (3 CHI rows x ZS);
     // with diagonal pairs also Cd (2 MAT, the carried closings one site further)
     static constexpr int ELEMS = 5 * MAT + SROWS * ZS;
-    static constexpr size_t bytes = sizeof(cx<T>) * ELEMS;
+    static constexpr size_t bytes = sizeof(E) * ELEMS;
     __host__ __device__ static constexpr size_t elems(bool diag) { return ELEMS + (diag ? 2 * MAT : 0); }
     // environment kernel: two site buffers, R, and CHI scratch rows (one transfer;
     // the left-environment chain needs 3 MAT + CHI rows)
-    static constexpr size_t env_bytes = sizeof(cx<T>) * (5 * MAT + CHI * ZS);
+    static constexpr size_t env_bytes = sizeof(E) * (5 * MAT + CHI * ZS);
     // plus the cross-warp reduction buffer of a UW-warp team
     __host__ __device__ static constexpr size_t team_bytes(int uw, bool diag = false) {
-        return sizeof(cx<T>) * elems(diag) + sizeof(T) * 12 * uw;
+        return sizeof(E) * elems(diag) + sizeof(T) * 12 * uw;
     }
 };
 
 // Register-tile shape for an M x N output (compile-time bounds) computed by NTHR
 // threads: MT x NT threads, TM x TN complex accumulators per thread, at most 48
 // (float) or 24 (double).
-template <typename T, int M_HINT, int N_HINT, int NTHR = 32>
+template <typename E, int M_HINT, int N_HINT, int NTHR = 32>
 struct Tile {
+    using T = typename elem_traits<E>::scalar;
     static constexpr int MT = (NTHR == 32) ? ((M_HINT >= 2 * N_HINT) ? 8 : 4)
                                            : ((M_HINT >= 2 * N_HINT) ? 16 : (M_HINT * 2 > N_HINT ? 8 : 4));
     static constexpr int NT = NTHR / MT;
@@ -86,10 +90,10 @@ struct Tile {
 // ao, bo and so are evaluated once per tile row / column.
 // KU: unroll factor of the k loop (1 keeps the Pauli kernel's code small enough for
 // the instruction cache; the environment kernel, one warp per image, prefers 2).
-template <typename T, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, int KU, class AO, class BO, class SO,
+template <typename E, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, int KU, class AO, class BO, class SO,
           class ST>
-__device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as_seg,
-                                          const cx<T>* Bb, BO bo, int bs, int bs_seg,
+__device__ __forceinline__ void team_gemm(const E* Ab, AO ao, int as, int as_seg,
+                                          const E* Bb, BO bo, int bs, int bs_seg,
                                           int M, int N, int K, SO so, ST store, int lane) {
     const int tm = lane / NT, tn = lane % NT;
     for (int m0 = 0; m0 < M; m0 += MT * TM) {
@@ -106,18 +110,18 @@ __device__ __forceinline__ void team_gemm(const cx<T>* Ab, AO ao, int as, int as
                 boff[j] = bo(n < N ? n : N - 1);
                 soff[j] = so(n < N ? n : N - 1);
             }
-            cx<T> acc[TM][TN];
+            E acc[TM][TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = czero<T>();
+                for (int j = 0; j < TN; ++j) acc[i][j] = ezero<E>();
 #pragma unroll
             for (int seg = 0; seg < NSEG; ++seg) {
-                const cx<T>* As = Ab + seg * as_seg;
-                const cx<T>* Bs = Bb + seg * bs_seg;
+                const E* As = Ab + seg * as_seg;
+                const E* Bs = Bb + seg * bs_seg;
 #pragma unroll KU
                 for (int k = 0; k < K; ++k) {
-                    cx<T> a[TM], b[TN];
+                    E a[TM], b[TN];
 #pragma unroll
                     for (int i = 0; i < TM; ++i) a[i] = As[aoff[i] + k * as];
 #pragma unroll
@@ -154,26 +158,26 @@ __device__ __forceinline__ void team_sync() { __syncthreads(); }
 // the right bond and equals the output bit).  The contractions over r then run over
 // that half only; the skipped terms are exact zeros, which leave an fma chain
 // unchanged, so the result is the same bit for bit at half the work.
-template <typename T, int CHI, int NB, int NTHR, int KU = 1>
-__device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane,
+template <typename E, int CHI, int NB, int NTHR, int KU = 1>
+__device__ __forceinline__ void times_site_t(const E* C, const E* A, E* S, int Dl, int Dr, int lane,
                                              bool half = false) {
-    using Lay = PauliLayout<T, CHI>;
+    using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
     if (half) {
         const int h = Dr >> 1;
-        using Tl = Tile<T, NB * CHI, CHI, NTHR>;
+        using Tl = Tile<E, NB * CHI, CHI, NTHR>;
         for (int s = 0; s < 2; ++s)   // the columns 2l'+s of one physical index
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
+            team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
                 C, [Dr, s, h](int m) { return (m / Dr) * MAT + (m % Dr) * CS + s * h; }, 1, 0,
                 A, [s, h](int l) { return (2 * l + s) * CS + s * h; }, 1, 0, NB * Dr, Dl, h,
-                [s](int l) { return 2 * l + s; }, [S](int m, int sn, cx<T> v) { S[m * ZS + sn] = v; }, lane);
+                [s](int l) { return 2 * l + s; }, [S](int m, int sn, E v) { S[m * ZS + sn] = v; }, lane);
         return;
     }
-    using Tl = Tile<T, NB * CHI, 2 * CHI, NTHR>;
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
+    using Tl = Tile<E, NB * CHI, 2 * CHI, NTHR>;
+    team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
         C, [Dr](int m) { return (m / Dr) * MAT + (m % Dr) * CS; }, 1, 0,
         A, [](int n) { return n * CS; }, 1, 0, NB * Dr, 2 * Dl, Dr,
-        [](int n) { return n; }, [S](int m, int sn, cx<T> v) { S[m * ZS + sn] = v; }, lane);
+        [](int n) { return n; }, [S](int m, int sn, E v) { S[m * ZS + sn] = v; }, lane);
 }
 
 // Transfer of NB matrices through a site A (Dl x 2 x Dr), in place:
@@ -182,28 +186,28 @@ __device__ __forceinline__ void times_site_t(const cx<T>* C, const cx<T>* A, cx<
 // diag_out: only the two diagonal blocks of the result are needed (its next use is a
 // transfer through a half-structured site, which reads nothing else), so the second
 // product forms those blocks alone; the rest of C_b is left as it was.
-template <typename T, int CHI, int NB, int NTHR, int KU = 1>
-__device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane,
+template <typename E, int CHI, int NB, int NTHR, int KU = 1>
+__device__ __forceinline__ void transfer(E* C, const E* A, E* S, int Dl, int Dr, int lane,
                                          bool half = false, bool diag_out = false) {
-    using Lay = PauliLayout<T, CHI>;
+    using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
     if (half) {
         // A^s touches half s of the right bond only, so the transfer reads only the two
         // diagonal blocks of C_b: S[b Dr + s h + i][2l'+s] = sum_{k<h} C_b[s h + i][s h + k]
         // A[2l'+s][s h + k], i < h (the rows the second product reads)
         const int h = Dr >> 1;
-        using Tl = Tile<T, NB * CHI / 2, CHI, NTHR>;
+        using Tl = Tile<E, NB * CHI / 2, CHI, NTHR>;
         for (int s = 0; s < 2; ++s)
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
+            team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, KU>(
                 C, [s, h](int m) { const int b = m / h, i = m - b * h; return b * MAT + (s * h + i) * CS + s * h; }, 1, 0,
                 A, [s, h](int l) { return (2 * l + s) * CS + s * h; }, 1, 0, NB * h, Dl, h,
                 [s](int l) { return 2 * l + s; },
-                [S, s, h, Dr](int m, int sn, cx<T> v) {
+                [S, s, h, Dr](int m, int sn, E v) {
                     const int b = m / h, i = m - b * h;
                     S[(b * Dr + s * h + i) * ZS + sn] = v;
                 }, lane);
     } else {
-        times_site_t<T, CHI, NB, NTHR, KU>(C, A, S, Dl, Dr, lane);
+        times_site_t<E, CHI, NB, NTHR, KU>(C, A, S, Dl, Dr, lane);
     }
     team_sync();
     // segment s: r over half s of the right bond when the site is half-structured
@@ -211,21 +215,21 @@ __device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int
     const int h = half ? Dr >> 1 : 0;
     if (diag_out) {
         const int g = Dl >> 1;
-        using Tl = Tile<T, CHI / 2, NB * CHI / 2, NTHR>;
+        using Tl = Tile<E, CHI / 2, NB * CHI / 2, NTHR>;
         for (int q = 0; q < 2; ++q)   // rows and columns l, l' in half q of the left bond
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
+            team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
                 A, [q, g](int i) { return 2 * (q * g + i) * CS; }, 1, CS + h,
                 S, [Dr, q, g](int nn) { const int b = nn / g, i = nn - b * g; return b * Dr * ZS + 2 * (q * g + i); },
                 ZS, 1 + h * ZS, g, NB * g, K,
                 [q, g](int nn) { const int b = nn / g, i = nn - b * g; return b * MAT + q * g + i; },
-                [C, q, g](int i, int sn, cx<T> v) { C[(q * g + i) * CS + sn] = v; }, lane);
+                [C, q, g](int i, int sn, E v) { C[(q * g + i) * CS + sn] = v; }, lane);
     } else {
-        using Tl = Tile<T, CHI, NB * CHI, NTHR>;
-        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
+        using Tl = Tile<E, CHI, NB * CHI, NTHR>;
+        team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, KU>(
             A, [](int l) { return 2 * l * CS; }, 1, CS + h,
             S, [Dl, Dr](int n) { return (n / Dl) * Dr * ZS + 2 * (n % Dl); }, ZS, 1 + h * ZS, Dl, NB * Dl, K,
             [Dl](int n) { return (n / Dl) * MAT + (n % Dl); },
-            [C](int l, int sn, cx<T> v) { C[l * CS + sn] = v; }, lane);
+            [C](int l, int sn, E v) { C[l * CS + sn] = v; }, lane);
     }
     team_sync();
 }
@@ -235,69 +239,69 @@ __device__ __forceinline__ void transfer(cx<T>* C, const cx<T>* A, cx<T>* S, int
 // half (a half-structured site, see times_site_t): F_ss'[r][r'] vanishes unless r is
 // in half s and r' in half s', so one Dr x Dr matrix F'[r][r'] = F_{s(r) s(r')}[r][r']
 // (s(r) = r >= Dr/2) holds every nonzero value, at a quarter of the work.
-template <typename T, int CHI, int NTHR>
-__device__ __forceinline__ void left_blocks(const cx<T>* A, cx<T>* S, int Dl, int Dr, int lane, bool half = false) {
-    using Lay = PauliLayout<T, CHI>;
+template <typename E, int CHI, int NTHR>
+__device__ __forceinline__ void left_blocks(const E* A, E* S, int Dl, int Dr, int lane, bool half = false) {
+    using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, ZS = Lay::ZS;
-    cx<T>* F = S + CHI * ZS;
+    E* F = S + CHI * ZS;
     if (half) {
         const int h = Dr >> 1;
         auto off = [h](int r) { return (r >= h ? CS : 0) + r; };
-        using Tl = Tile<T, CHI, CHI, NTHR>;
-        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+        using Tl = Tile<E, CHI, CHI, NTHR>;
+        team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
             A, off, 2 * CS, 0, A, off, 2 * CS, 0, Dr, Dr, Dl,
-            [](int n) { return n; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
+            [](int n) { return n; }, [F](int m, int sn, E v) { F[m * ZS + sn] = v; }, lane);
         return;
     }
-    using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
+    using Tl = Tile<E, 2 * CHI, 2 * CHI, NTHR>;
     auto off = [Dr](int m) { return (m / Dr) * CS + (m % Dr); };
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+    team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
         A, off, 2 * CS, 0, A, off, 2 * CS, 0, 2 * Dr, 2 * Dr, Dl,
-        [](int n) { return n; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
+        [](int n) { return n; }, [F](int m, int sn, E v) { F[m * ZS + sn] = v; }, lane);
 }
 
 // The same blocks with a left environment L (Dl x Dl, row stride CHI, read from
 // global memory; NULL: the identity, left_blocks):
 // F[m][n] = sum_{l,l'} conj(A[2l+s_m][r_m]) L[l][l'] A[2l'+s_n][r_n], through
 // T[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r] in S rows 0 .. Dl.
-template <typename T, int CHI, int NTHR>
-__device__ __forceinline__ void left_blocks_env(const cx<T>* A, const cx<T>* Lg, cx<T>* S, int Dl, int Dr,
+template <typename E, int CHI, int NTHR>
+__device__ __forceinline__ void left_blocks_env(const E* A, const E* Lg, E* S, int Dl, int Dr,
                                                 int lane, bool half = false) {
     if (!Lg) {
-        left_blocks<T, CHI, NTHR>(A, S, Dl, Dr, lane, half);
+        left_blocks<E, CHI, NTHR>(A, S, Dl, Dr, lane, half);
         return;
     }
-    using Lay = PauliLayout<T, CHI>;
+    using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, ZS = Lay::ZS;
     if (half) {   // compact F' as in left_blocks, through T'[l][r'] = sum_l' L[l][l'] A[2l'+s(r')][r']
         const int h = Dr >> 1;
         auto off = [h](int r) { return (r >= h ? CS : 0) + r; };
         {
-            using Tl = Tile<T, CHI, CHI, NTHR>;
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+            using Tl = Tile<E, CHI, CHI, NTHR>;
+            team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
                 Lg, [](int l) { return l * CHI; }, 1, 0, A, off, 2 * CS, 0, Dl, Dr, Dl,
-                [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
+                [](int nn) { return nn; }, [S](int l, int sn, E v) { S[l * ZS + sn] = v; }, lane);
         }
         team_sync();
-        cx<T>* F = S + CHI * ZS;
-        using Tl = Tile<T, CHI, CHI, NTHR>;
-        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+        E* F = S + CHI * ZS;
+        using Tl = Tile<E, CHI, CHI, NTHR>;
+        team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
             A, off, 2 * CS, 0, S, [](int nn) { return nn; }, ZS, 0, Dr, Dr, Dl,
-            [](int nn) { return nn; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
+            [](int nn) { return nn; }, [F](int m, int sn, E v) { F[m * ZS + sn] = v; }, lane);
         return;
     }
     {
-        using Tl = Tile<T, CHI, 2 * CHI, NTHR>;
-        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+        using Tl = Tile<E, CHI, 2 * CHI, NTHR>;
+        team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
             Lg, [](int l) { return l * CHI; }, 1, 0, A, [Dr](int nn) { return (nn / Dr) * CS + (nn % Dr); }, 2 * CS, 0,
-            Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
+            Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, E v) { S[l * ZS + sn] = v; }, lane);
     }
     team_sync();
-    cx<T>* F = S + CHI * ZS;
-    using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
-    team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+    E* F = S + CHI * ZS;
+    using Tl = Tile<E, 2 * CHI, 2 * CHI, NTHR>;
+    team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
         A, [Dr](int m) { return (m / Dr) * CS + (m % Dr); }, 2 * CS, 0, S, [](int nn) { return nn; }, ZS, 0,
-        2 * Dr, 2 * Dr, Dl, [](int nn) { return nn; }, [F](int m, int sn, cx<T> v) { F[m * ZS + sn] = v; }, lane);
+        2 * Dr, 2 * Dr, Dl, [](int nn) { return nn; }, [F](int m, int sn, E v) { F[m * ZS + sn] = v; }, lane);
 }
 
 // <E_a, Y> for a = X, Y, Z (from the blocks F_{ss'} in S) and Y in {C_X, C_Y, C_Z, R}:
@@ -305,39 +309,61 @@ __device__ __forceinline__ void left_blocks_env(const cx<T>* A, const cx<T>* Lg,
 // null (then only the R column is formed).  Warp 0 alone
 // forms the sums, so the summation order (and every bit of the result) does not
 // depend on the team size; the other warps read the sums from red.
-template <typename T, int CHI, int NTHR>
-__device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const cx<T>* R, int D, T* out,
-                                          T* red, int lane, bool half = false) {
-    using Lay = PauliLayout<T, CHI>;
+template <typename E, int CHI, int NTHR>
+__device__ __forceinline__ void left_dots(const E* S, const E* C, const E* R, int D,
+                                          typename elem_traits<E>::scalar* out,
+                                          typename elem_traits<E>::scalar* red, int lane, bool half = false) {
+    using T = typename elem_traits<E>::scalar;
+    using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    const cx<T>* F = S + CHI * ZS;
+    const E* F = S + CHI * ZS;
     const int h = D >> 1;
     if (lane < 32) {
         T acc[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc[i] = T(0);
         team_for_2d<32, 4>(D, D, lane, [&](int r, int rp) {
-            cx<T> e[3];
+          if constexpr (elem_traits<E>::real) {
+            // a real state (no half-structured sites): E_X, E_Z, C_X, C_Z and R are real,
+            // E_Y = i (F10 - F01) and C_Y = -i (M - M^T) / 2 imaginary, so the entries with
+            // one Y vanish and <E_Y, C_Y> = sum (F10 - F01) (M - M^T) / 2
+            const E f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
+            const E f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
+            const E ex = f01 + f10, ey = f10 - f01, ez = f00 - f11;
+            const E rr = R[r * CS + rp];
+            acc[3] = fma(ex, rr, acc[3]);
+            acc[11] = fma(ez, rr, acc[11]);
+            if (C) {
+                const E m1 = C[r * CS + rp], m2 = C[rp * CS + r];
+                const E yx = T(0.5) * (m1 + m2), yy = T(0.5) * (m1 - m2), yz = C[MAT + r * CS + rp];
+                acc[0] = fma(ex, yx, acc[0]);
+                acc[2] = fma(ex, yz, acc[2]);
+                acc[5] = fma(ey, yy, acc[5]);
+                acc[8] = fma(ez, yx, acc[8]);
+                acc[10] = fma(ez, yz, acc[10]);
+            }
+          } else {
+            E e[3];
             if (half) {
                 // compact F' (left_blocks): the one nonzero block at (r, r') is F_{s s'}
                 // with s = r >= h, s' = r' >= h; the same values as the full form
-                const cx<T> f = F[r * ZS + rp], z = czero<T>();
+                const E f = F[r * ZS + rp], z = ezero<E>();
                 const int s0 = r >= h, s1 = rp >= h;
                 e[0] = s0 != s1 ? f : z;                                                   // X
                 e[1] = s0 == s1 ? z : (s0 ? mk<T>(-f.im, f.re) : mk<T>(f.im, -f.re));      // Y
                 e[2] = s0 != s1 ? z : (s0 ? mk<T>(-f.re, -f.im) : f);                      // Z
             } else {
-                const cx<T> f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
-                const cx<T> f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
+                const E f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
+                const E f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
                 e[0] = f01 + f10;                                     // X
                 e[1] = mk<T>(f01.im - f10.im, f10.re - f01.re);       // Y: i (F10 - F01)
                 e[2] = f00 - f11;                                     // Z
             }
-            cx<T> y[4];
+            E y[4];
             y[3] = R[r * CS + rp];
             if (C) {
-                const cx<T> m1 = C[r * CS + rp], m2 = conj(C[rp * CS + r]);
-                const cx<T> u = m1 + m2, v = m1 - m2;
+                const E m1 = C[r * CS + rp], m2 = conj(C[rp * CS + r]);
+                const E u = m1 + m2, v = m1 - m2;
                 y[0] = mk<T>(T(0.5) * u.re, T(0.5) * u.im);       // (M + M^H) / 2
                 y[1] = mk<T>(T(0.5) * v.im, T(-0.5) * v.re);      // (M - M^H) / (2i)
                 y[2] = C[MAT + r * CS + rp];
@@ -347,6 +373,7 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
                     if (C || b == 3) acc[4 * a + b] = fma(-e[a].im, y[b].im, fma(e[a].re, y[b].re, acc[4 * a + b]));
+          }
         });
 #pragma unroll
         for (int i = 0; i < 12; ++i) out[i] = warp_sum(acc[i]);
@@ -367,46 +394,47 @@ __device__ __forceinline__ void left_dots(const cx<T>* S, const cx<T>* C, const 
 //   G[2l+s][2l'+s'] = sum_r conj(A[2l+s][r]) (R A^{s'T})[r][l'],
 //   C_X = G01 + G10, C_Y = i (G10 - G01), C_Z = G00 - G11  (Dl x Dl each); into C go
 //   M = C_X + i C_Y = 2 G01 and C_Z.
-template <typename T, int CHI, int NTHR>
-__device__ __forceinline__ void right_closings(const cx<T>* A, const cx<T>* R, cx<T>* C, cx<T>* S,
+template <typename E, int CHI, int NTHR>
+__device__ __forceinline__ void right_closings(const E* A, const E* R, E* C, E* S,
                                                int Dl, int Dr, int lane, bool half = false) {
-    using Lay = PauliLayout<T, CHI>;
+    using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    times_site_t<T, CHI, 1, NTHR>(R, A, S, Dl, Dr, lane, half);   // S[r][n] = (R A^T)[r][n]
+    times_site_t<E, CHI, 1, NTHR>(R, A, S, Dl, Dr, lane, half);   // S[r][n] = (R A^T)[r][n]
     team_sync();
-    cx<T>* G = S + CHI * ZS;
+    E* G = S + CHI * ZS;
     if (half) {
         // rows 2l+s of G contract r over half s only (see times_site_t)
         const int h = Dr >> 1;
-        using Tl = Tile<T, CHI, 2 * CHI, NTHR>;
+        using Tl = Tile<E, CHI, 2 * CHI, NTHR>;
         for (int s = 0; s < 2; ++s)
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+            team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
                 A, [s, h](int l) { return (2 * l + s) * CS + s * h; }, 1, 0, S + s * h * ZS, [](int n) { return n; },
                 ZS, 0, Dl, 2 * Dl, h, [](int n) { return n; },
-                [G, s](int l, int sn, cx<T> v) { G[(2 * l + s) * ZS + sn] = v; }, lane);
+                [G, s](int l, int sn, E v) { G[(2 * l + s) * ZS + sn] = v; }, lane);
     } else {
-        using Tl = Tile<T, 2 * CHI, 2 * CHI, NTHR>;
-        team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+        using Tl = Tile<E, 2 * CHI, 2 * CHI, NTHR>;
+        team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
             A, [](int m) { return m * CS; }, 1, 0, S, [](int n) { return n; }, ZS, 0, 2 * Dl, 2 * Dl, Dr,
-            [](int n) { return n; }, [G](int m, int sn, cx<T> v) { G[m * ZS + sn] = v; }, lane);
+            [](int n) { return n; }, [G](int m, int sn, E v) { G[m * ZS + sn] = v; }, lane);
     }
     team_sync();
     team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int l, int lp) {
-        const cx<T> g00 = G[(2 * l) * ZS + 2 * lp], g01 = G[(2 * l) * ZS + 2 * lp + 1];
-        const cx<T> g11 = G[(2 * l + 1) * ZS + 2 * lp + 1];
+        const E g00 = G[(2 * l) * ZS + 2 * lp], g01 = G[(2 * l) * ZS + 2 * lp + 1];
+        const E g11 = G[(2 * l + 1) * ZS + 2 * lp + 1];
         C[l * CS + lp] = g01 + g01;
         C[MAT + l * CS + lp] = g00 - g11;
     });
     team_sync();
 }
 
-template <typename T, int CS, int NTHR = 32>
-__device__ __forceinline__ void load_site_p(cx<T>* dst, const cx<T>* src, int ld, int Dl, int Dr, int lane) {
-    team_for_2d<NTHR, 4>(2 * Dl, Dr, lane, [&](int row, int r) { dst[row * CS + r] = src[row * ld + r]; });
+template <typename E, int CS, int NTHR = 32>
+__device__ __forceinline__ void load_site_p(E* dst, const cx<typename elem_traits<E>::scalar>* src, int ld, int Dl,
+                                            int Dr, int lane) {
+    team_for_2d<NTHR, 4>(2 * Dl, Dr, lane, [&](int row, int r) { dst[row * CS + r] = to_elem<E>(src[row * ld + r]); });
 }
 
-template <typename T, int CS, int NTHR = 32>
-__device__ __forceinline__ void load_mat(cx<T>* dst, const cx<T>* src, int ld, int D, int lane) {
+template <typename E, int CS, int NTHR = 32>
+__device__ __forceinline__ void load_mat(E* dst, const E* src, int ld, int D, int lane) {
     team_for_2d<NTHR, 4>(D, D, lane, [&](int r, int c) { dst[r * CS + c] = src[r * ld + c]; });
 }
 
@@ -425,26 +453,27 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Left environments of one image (a warp): L_0 = 1 and L_{k+1}[r][r'] =
 // sum_{l,l',s} conj(A_k[l][s][r]) L_k[l][l'] A_k[l'][s][r'], stored like the right
 // environments (L_k, D_k x D_k, at k * CHI * CHI of the image's block).
-template <typename T, int CHI>
-__device__ __forceinline__ void lenv_image(const ImageMeta& mt, const cx<T>* __restrict__ arena,
-                                           const int32_t* __restrict__ bonds, cx<T>* lg, cx<T>* base,
+template <typename E, int CHI>
+__device__ __forceinline__ void lenv_image(const ImageMeta& mt,
+                                           const cx<typename elem_traits<E>::scalar>* __restrict__ arena,
+                                           const int32_t* __restrict__ bonds, E* lg, E* base,
                                            int lane) {
-    using Lay = PauliLayout<T, CHI>;
+    using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    cx<T>* A = base;             // 2 MAT
-    cx<T>* Lm = base + 2 * MAT;  // MAT
-    cx<T>* S = base + 3 * MAT;   // CHI rows of ZS
+    E* A = base;             // 2 MAT
+    E* Lm = base + 2 * MAT;  // MAT
+    E* S = base + 3 * MAT;   // CHI rows of ZS
     const int n = mt.n, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
-    const cx<T>* sites = arena + mt.site_off;
-    if (lane == 0) Lm[0] = mk<T>(T(1), T(0));
+    const cx<typename elem_traits<E>::scalar>* sites = arena + mt.site_off;
+    if (lane == 0) Lm[0] = eone<E>();
     __syncwarp();
     const bool half_img = (mt.flags & META_HALF) != 0;
     for (int k = 0; k < n; ++k) {
         const int Dl = bd[k], Dr = bd[k + 1];
-        cx<T>* dst = lg + (size_t)k * CHI * CHI;
+        E* dst = lg + (size_t)k * CHI * CHI;
         team_for_2d<32, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
-        load_site_p<T, CS, 32>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
+        load_site_p<E, CS, 32>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
         __syncwarp();
         if (half_img && k < n - 1 && Dr >= 2) {
             // half-structured site: L A is needed only at (s, r) with r in half s
@@ -453,35 +482,35 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt, const cx<T>* __r
             const int h = Dr >> 1;
             auto off = [h](int r) { return (r >= h ? CS : 0) + r; };
             {
-                using Tl = Tile<T, CHI, CHI, 32>;
-                team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+                using Tl = Tile<E, CHI, CHI, 32>;
+                team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
                     Lm, [](int l) { return l * CS; }, 1, 0, A, off, 2 * CS, 0, Dl, Dr, Dl,
-                    [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
+                    [](int nn) { return nn; }, [S](int l, int sn, E v) { S[l * ZS + sn] = v; }, lane);
             }
             __syncwarp();
             {
-                using Tl = Tile<T, CHI, CHI, 32>;
-                team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+                using Tl = Tile<E, CHI, CHI, 32>;
+                team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
                     A, off, 2 * CS, 0, S, [](int nn) { return nn; }, ZS, 0, Dr, Dr, Dl, [](int nn) { return nn; },
-                    [Lm, h](int r, int sn, cx<T> v) { Lm[r * CS + sn] = (r >= h) == (sn >= h) ? v : czero<T>(); }, lane);
+                    [Lm, h](int r, int sn, E v) { Lm[r * CS + sn] = (r >= h) == (sn >= h) ? v : ezero<E>(); }, lane);
             }
             __syncwarp();
             continue;
         }
         // S[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r]
         {
-            using Tl = Tile<T, CHI, 2 * CHI, 32>;
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+            using Tl = Tile<E, CHI, 2 * CHI, 32>;
+            team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
                 Lm, [](int l) { return l * CS; }, 1, 0, A, [Dr](int nn) { return (nn / Dr) * CS + (nn % Dr); }, 2 * CS, 0,
-                Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, cx<T> v) { S[l * ZS + sn] = v; }, lane);
+                Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, E v) { S[l * ZS + sn] = v; }, lane);
         }
         __syncwarp();
         // L'[r][r'] = sum_{l,s} conj(A[2l+s][r]) S[l][s Dr + r']
         {
-            using Tl = Tile<T, CHI, CHI, 32>;
-            team_gemm<T, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, 1>(
+            using Tl = Tile<E, CHI, CHI, 32>;
+            team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, 1>(
                 A, [](int r) { return r; }, 2 * CS, CS, S, [](int nn) { return nn; }, ZS, Dr, Dr, Dr, Dl,
-                [](int nn) { return nn; }, [Lm](int r, int sn, cx<T> v) { Lm[r * CS + sn] = v; }, lane);
+                [](int nn) { return nn; }, [Lm](int r, int sn, E v) { Lm[r * CS + sn] = v; }, lane);
         }
         __syncwarp();
     }
@@ -491,15 +520,20 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt, const cx<T>* __r
 // the left environments of image i when it is flagged META_LENV (the two chains are
 // independent and latency-bound, so one launch runs them side by side).
 // GMEM (bonds above 32): the workspace is a slice of global memory, env_bytes per CTA.
-template <typename T, int CHI, bool GMEM = false>
+// REAL: a real state (every amplitude real): real elements, environments stored as
+// reals in the same buffers.
+template <typename T, int CHI, bool GMEM = false, bool REAL = false>
 __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ meta, int n_images,
                                                    const cx<T>* __restrict__ arena,
                                                    const int32_t* __restrict__ bonds,
-                                                   cx<T>* __restrict__ renv, int64_t renv_stride,
-                                                   cx<T>* __restrict__ lenv,
+                                                   cx<T>* __restrict__ renv_c, int64_t renv_stride,
+                                                   cx<T>* __restrict__ lenv_c,
                                                    T* __restrict__ norm_out, unsigned char* __restrict__ gws) {
-    using Lay = PauliLayout<T, CHI>;
+    using E = std::conditional_t<REAL, T, cx<T>>;
+    using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
+    E* renv = reinterpret_cast<E*>(renv_c);
+    E* lenv = reinterpret_cast<E*>(lenv_c);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* raw = GMEM ? gws + (size_t)blockIdx.x * Lay::env_bytes : smem_raw;
     // one warp per image and one image per CTA (block-wide syncs are warp syncs)
@@ -509,78 +543,82 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
         if (!lenv || li >= n_images) return;
         const ImageMeta ml = meta[li];
         if (ml.flags & META_LENV)
-            lenv_image<T, CHI>(ml, arena, bonds, lenv + (size_t)li * renv_stride,
-                               reinterpret_cast<cx<T>*>(raw), lane);
+            lenv_image<E, CHI>(ml, arena, bonds, lenv + (size_t)li * renv_stride,
+                               reinterpret_cast<E*>(raw), lane);
         return;
     }
     const int img = blockIdx.x;
-    cx<T>* base = reinterpret_cast<cx<T>*>(raw);
+    E* base = reinterpret_cast<E*>(raw);
     const bool half_img = (meta[img].flags & META_HALF) != 0;
-    cx<T>* Abuf[2] = {base, base + 3 * MAT};   // site j in one, site j-1 arriving in the other
-    cx<T>* R = base + 2 * MAT;
-    cx<T>* S = base + 5 * MAT;                 // CHI rows of ZS (env_bytes)
+    E* Abuf[2] = {base, base + 3 * MAT};   // site j in one, site j-1 arriving in the other
+    E* R = base + 2 * MAT;
+    E* S = base + 5 * MAT;                 // CHI rows of ZS (env_bytes)
     const ImageMeta mt = meta[img];
     const int n = mt.n, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
     const cx<T>* sites = arena + mt.site_off;
-    cx<T>* rg = renv + (size_t)img * renv_stride;
+    E* rg = renv + (size_t)img * renv_stride;
     // site j -> dstA with cp.async, so that its load overlaps the transfer through site j+1
-    auto prefetch = [&](int j, cx<T>* dstA) {
+    // (plain loads into a global workspace, or converting to real elements)
+    auto prefetch = [&](int j, E* dstA) {
         const int Dl = bd[j], Dr = bd[j + 1];
         const cx<T>* src = sites + (size_t)j * 2 * ld * ld;
-        if constexpr (GMEM) {
-            team_for_2d<32, 4>(2 * Dl, Dr, lane, [&](int row, int r) { dstA[row * CS + r] = src[row * ld + r]; });
+        if constexpr (GMEM || REAL) {
+            team_for_2d<32, 4>(2 * Dl, Dr, lane, [&](int row, int r) { dstA[row * CS + r] = to_elem<E>(src[row * ld + r]); });
         } else {
             team_for_2d<32, 4>(2 * Dl, Dr, lane, [&](int row, int r) { cp_async_elem(dstA + row * CS + r, src + row * ld + r); });
             cp_async_commit();
         }
     };
-    if (lane == 0) R[0] = mk<T>(T(1), T(0));
+    if (lane == 0) R[0] = eone<E>();
     if (n > 0) prefetch(n - 1, Abuf[0]);
     int cb = 0;
     for (int j = n - 1; j >= 0; --j) {
         const int Dl = bd[j], Dr = bd[j + 1];
-        cx<T>* dst = rg + (size_t)j * CHI * CHI;
+        E* dst = rg + (size_t)j * CHI * CHI;
         team_for_2d<32, 4>(Dr, Dr, lane, [&](int r, int c) { dst[r * CHI + c] = R[r * CS + c]; });
-        if constexpr (!GMEM) cp_async_wait_all();
+        if constexpr (!(GMEM || REAL)) cp_async_wait_all();
         __syncwarp();
         if (j > 0) prefetch(j - 1, Abuf[cb ^ 1]);
-        transfer<T, CHI, 1, 32, 2>(R, Abuf[cb], S, Dl, Dr, lane, half_img && j < n - 1 && Dr >= HALF_SPLIT_MIN);
+        transfer<E, CHI, 1, 32, 2>(R, Abuf[cb], S, Dl, Dr, lane, half_img && j < n - 1 && Dr >= HALF_SPLIT_MIN);
         cb ^= 1;
     }
-    if (lane == 0) norm_out[img] = R[0].re;
+    if (lane == 0) norm_out[img] = ereal(R[0]);
 }
 
 // One (image, column) unit of the Pauli kernel, worked on by the CTA's UW warps with
 // its workspace at smem_raw.
-template <typename T, int CHI, int UW, bool DIAG>
+template <typename T, int CHI, int UW, bool DIAG, bool REAL>
 __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, const ImageMeta* __restrict__ meta,
                                            const int32_t* __restrict__ unit_image,
                                            const cx<T>* __restrict__ arena, const int32_t* __restrict__ bonds,
-                                           const cx<T>* __restrict__ renv, int64_t renv_stride,
-                                           const cx<T>* __restrict__ lenv, const T* __restrict__ norms,
+                                           const cx<T>* __restrict__ renv_c, int64_t renv_stride,
+                                           const cx<T>* __restrict__ lenv_c, const T* __restrict__ norms,
                                            T* __restrict__ out) {
-    using Lay = PauliLayout<T, CHI>;
+    using E = std::conditional_t<REAL, T, cx<T>>;
+    using Lay = PauliLayout<E, CHI>;
+    const E* renv = reinterpret_cast<const E*>(renv_c);
+    const E* lenv = reinterpret_cast<const E*>(lenv_c);
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
     constexpr int NTHR = 32 * UW;
     constexpr bool diag = DIAG;   // both diagonal pair sets as well (a separate instantiation)
     const int lane = threadIdx.x;
     const int img = unit_image[2 * unit], c = unit_image[2 * unit + 1];
-    cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
+    E* base = reinterpret_cast<E*>(smem_raw);
     T* red = reinterpret_cast<T*>(base + Lay::ELEMS + (diag ? 2 * MAT : 0));
-    cx<T>* A = base;               // 2 MAT
-    cx<T>* R = base + 2 * MAT;
-    cx<T>* C = base + 3 * MAT;     // 2 MAT: M = C_X + i C_Y, C_Z
-    cx<T>* S = base + 5 * MAT;     // GEMM scratch
-    cx<T>* Cd = base + Lay::ELEMS; // 2 MAT (diagonal pairs only)
+    E* A = base;               // 2 MAT
+    E* R = base + 2 * MAT;
+    E* C = base + 3 * MAT;     // 2 MAT: M = C_X + i C_Y, C_Z
+    E* S = base + 5 * MAT;     // GEMM scratch
+    E* Cd = base + Lay::ELEMS; // 2 MAT (diagonal pairs only)
     const ImageMeta mt = meta[img];
     const int p = mt.p, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
     const cx<T>* sites = arena + mt.site_off;
-    const cx<T>* rg = renv + (size_t)img * renv_stride;
+    const E* rg = renv + (size_t)img * renv_stride;
     // left environments (images whose MPS is not left-canonical), same layout as renv
-    const cx<T>* lgb = (lenv && (mt.flags & META_LENV)) ? lenv + (size_t)img * renv_stride : nullptr;
-    auto lenv_of = [lgb](int i) -> const cx<T>* { return lgb ? lgb + (size_t)i * CHI * CHI : nullptr; };
+    const E* lgb = (lenv && (mt.flags & META_LENV)) ? lenv + (size_t)img * renv_stride : nullptr;
+    auto lenv_of = [lgb](int i) -> const E* { return lgb ? lgb + (size_t)i * CHI * CHI : nullptr; };
     // half-structured sites (META_HALF): every site but the last.  half_at: the compact
     // left blocks (one product either way); half_tr: the contractions that split into
     // one product per physical index, from bond HALF_SPLIT_MIN on
@@ -610,13 +648,13 @@ __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, co
     for (int row = p - 1; row >= 0; --row) {
         const int j = row * p + c;
         const int Dl = bd[j], Dr = bd[j + 1];
-        load_site_p<T, CS, NTHR>(A, sites + (size_t)j * 2 * ld * ld, ld, Dl, Dr, lane);
-        load_mat<T, CS, NTHR>(R, rg + (size_t)j * CHI * CHI, CHI, Dr, lane);
+        load_site_p<E, CS, NTHR>(A, sites + (size_t)j * 2 * ld * ld, ld, Dl, Dr, lane);
+        load_mat<E, CS, NTHR>(R, rg + (size_t)j * CHI * CHI, CHI, Dr, lane);
         team_sync();
         // site j as the left site: single-site terms and the vertical pair (j, j+p)
-        left_blocks_env<T, CHI, NTHR>(A, lenv_of(j), S, Dl, Dr, lane, half_at(j));
+        left_blocks_env<E, CHI, NTHR>(A, lenv_of(j), S, Dl, Dr, lane, half_at(j));
         team_sync();
-        left_dots<T, CHI, NTHR>(S, row < p - 1 ? C : nullptr, R, Dr, d, red, lane, half_at(j));
+        left_dots<E, CHI, NTHR>(S, row < p - 1 ? C : nullptr, R, Dr, d, red, lane, half_at(j));
         T single_j[3];
         for (int a = 0; a < 3; ++a) single_j[a] = d[4 * a + 3] * inv_norm;
         if (row < p - 1) write_pair(nh + j, single_j, single_up, d);
@@ -626,29 +664,29 @@ __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, co
         if (has_dd) {
             for (int o = lane; o < 2 * MAT; o += NTHR) Cd[o] = C[o];
             team_sync();
-            transfer<T, CHI, 2, NTHR>(Cd, A, S, Dl, Dr, lane, half_tr(j));
+            transfer<E, CHI, 2, NTHR>(Cd, A, S, Dl, Dr, lane, half_tr(j));
         }
         // closings of site j as a right site
-        right_closings<T, CHI, NTHR>(A, R, C, S, Dl, Dr, lane, half_tr(j));
+        right_closings<E, CHI, NTHR>(A, R, C, S, Dl, Dr, lane, half_tr(j));
         T single_prev[3];
         for (int b = 0; b < 3; ++b) { single_prev[b] = single_up[b]; single_up[b] = single_j[b]; }
         if (c == 0 && row == 0) break;
         // next site to the left: horizontal pair (j-1, j) and the first carry step
         const int k0 = j - 1;
         const int Dl0 = bd[k0];   // left bond of site k0; its right bond is Dl
-        load_site_p<T, CS, NTHR>(A, sites + (size_t)k0 * 2 * ld * ld, ld, Dl0, Dl, lane);
+        load_site_p<E, CS, NTHR>(A, sites + (size_t)k0 * 2 * ld * ld, ld, Dl0, Dl, lane);
         team_sync();
         if (c > 0) {
-            load_mat<T, CS, NTHR>(R, rg + (size_t)k0 * CHI * CHI, CHI, Dl, lane);
+            load_mat<E, CS, NTHR>(R, rg + (size_t)k0 * CHI * CHI, CHI, Dl, lane);
             team_sync();
-            left_blocks_env<T, CHI, NTHR>(A, lenv_of(k0), S, Dl0, Dl, lane, half_at(k0));
+            left_blocks_env<E, CHI, NTHR>(A, lenv_of(k0), S, Dl0, Dl, lane, half_at(k0));
             team_sync();
-            left_dots<T, CHI, NTHR>(S, C, R, Dl, d, red, lane, half_at(k0));
+            left_dots<E, CHI, NTHR>(S, C, R, Dl, d, red, lane, half_at(k0));
             T single_k[3];
             for (int a = 0; a < 3; ++a) single_k[a] = d[4 * a + 3] * inv_norm;
             write_pair(row * (p - 1) + (c - 1), single_k, single_j, d);
             if (has_dd) {
-                left_dots<T, CHI, NTHR>(S, Cd, R, Dl, dd, red, lane, half_at(k0));
+                left_dots<E, CHI, NTHR>(S, Cd, R, Dl, dd, red, lane, half_at(k0));
                 write_pair(base_dd + row * (p - 1) + (c - 1), single_k, single_prev, dd);
             }
             team_sync();
@@ -658,16 +696,16 @@ __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, co
         for (int k = k0; k > j - p; --k) {
             const int Dlk = bd[k], Drk = bd[k + 1];
             if (k != k0) {
-                load_site_p<T, CS, NTHR>(A, sites + (size_t)k * 2 * ld * ld, ld, Dlk, Drk, lane);
+                load_site_p<E, CS, NTHR>(A, sites + (size_t)k * 2 * ld * ld, ld, Dlk, Drk, lane);
                 team_sync();
             }
             if (diag && k == j - p + 1 && c <= p - 2) {
                 // anti-diagonal (row-1, c+1)-(row, c): site k is the left site
-                load_mat<T, CS, NTHR>(R, rg + (size_t)k * CHI * CHI, CHI, Drk, lane);
+                load_mat<E, CS, NTHR>(R, rg + (size_t)k * CHI * CHI, CHI, Drk, lane);
                 team_sync();
-                left_blocks_env<T, CHI, NTHR>(A, lenv_of(k), S, Dlk, Drk, lane, half_at(k));
+                left_blocks_env<E, CHI, NTHR>(A, lenv_of(k), S, Dlk, Drk, lane, half_at(k));
                 team_sync();
-                left_dots<T, CHI, NTHR>(S, C, R, Drk, dd, red, lane, half_at(k));
+                left_dots<E, CHI, NTHR>(S, C, R, Drk, dd, red, lane, half_at(k));
                 T single_k[3];
                 for (int a = 0; a < 3; ++a) single_k[a] = dd[4 * a + 3] * inv_norm;
                 write_pair(base_da + (row - 1) * (p - 1) + c, single_k, single_j, dd);
@@ -676,7 +714,7 @@ __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, co
             // the last transfer brings the closings to site j - p, where they close in full;
             // before it, their next use is the transfer through site k - 1 (H+V pairs)
             const bool dout = !diag && k > j - p + 1 && half_tr(k - 1);
-            transfer<T, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane, half_tr(k), dout);
+            transfer<E, CHI, 2, NTHR>(C, A, S, Dlk, Drk, lane, half_tr(k), dout);
         }
     }
 }
@@ -684,7 +722,7 @@ __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, co
 
 // One (image, column) unit per CTA (GMEM: bonds above 32, workspace in global memory,
 // Lay::team_bytes per CTA, the CTAs stepping through the units).
-template <typename T, int CHI, int UW, bool DIAG, bool GMEM = false>
+template <typename T, int CHI, int UW, bool DIAG, bool GMEM = false, bool REAL = false>
 __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16) ? 9 : 8) / (sizeof(T) == 8 ? 2 : 1)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
                                                     const int32_t* __restrict__ unit_image,
                                                     const cx<T>* __restrict__ arena,
@@ -695,16 +733,18 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
                                                     unsigned char* __restrict__ gws) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (GMEM) {
-        constexpr size_t ws = (PauliLayout<T, CHI>::team_bytes(UW, DIAG) + 255) & ~size_t(255);
+        constexpr size_t ws = (PauliLayout<std::conditional_t<REAL, T, cx<T>>, CHI>::team_bytes(UW, DIAG) + 255) &
+                              ~size_t(255);
         unsigned char* raw = gws + (size_t)blockIdx.x * ws;
         for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
-            pauli_unit<T, CHI, UW, DIAG>(unit, raw, meta, unit_image, arena, bonds, renv, renv_stride, lenv, norms, out);
+            pauli_unit<T, CHI, UW, DIAG, REAL>(unit, raw, meta, unit_image, arena, bonds, renv, renv_stride, lenv,
+                                               norms, out);
             __syncthreads();
         }
     } else {
         if ((int)blockIdx.x >= n_units) return;
-        pauli_unit<T, CHI, UW, DIAG>(blockIdx.x, smem_raw, meta, unit_image, arena, bonds, renv, renv_stride, lenv,
-                                     norms, out);
+        pauli_unit<T, CHI, UW, DIAG, REAL>(blockIdx.x, smem_raw, meta, unit_image, arena, bonds, renv, renv_stride,
+                                           lenv, norms, out);
     }
 }
 

@@ -10,7 +10,7 @@ namespace {
 template <typename T, int CHI, int UW, bool DIAG>
 mps_status launch_pauli_uw(mps_batch* b, void* out) {
     constexpr bool diag = DIAG;
-    using Lay = PauliLayout<T, CHI>;
+    using Lay = PauliLayout<cx<T>, CHI>;
     const int limit = smem_optin_limit();
     const size_t smem = Lay::team_bytes(UW, diag);
     if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "Pauli kernel shared memory %zu B", smem);
@@ -30,7 +30,7 @@ mps_status launch_pauli_uw(mps_batch* b, void* out) {
 
 template <typename T, int CHI>
 mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
-    using Lay = PauliLayout<T, CHI>;
+    using Lay = PauliLayout<cx<T>, CHI>;
     const int limit = smem_optin_limit();
     const size_t smem = Lay::env_bytes;
     if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "environment kernel shared memory %zu B", smem);
@@ -57,6 +57,8 @@ mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
 
 template <typename T>
 mps_status dispatch_pauli(mps_batch* b, void* out, bool diag) {
+    // a real state (paper ansatz) up to bond 32: real-element kernels
+    if (sizeof(T) == 4 && b->real && b->chi_tpl <= 32) return launch_pauli_real(b, out, diag);
     switch (b->chi_tpl) {
         case 4: return launch_pauli<T, 4>(b, out, diag);
         case 8: return launch_pauli<T, 8>(b, out, diag);

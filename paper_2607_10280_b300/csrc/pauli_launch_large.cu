@@ -12,7 +12,7 @@ namespace {
 template <typename T, int CHI>
 mps_status launch_large(mps_batch* b, void* out, bool diag) {
     if (diag) return fail(MPS_ERR_UNSUPPORTED, "the diagonal pair sets are built for bonds up to 32");
-    using Lay = PauliLayout<T, CHI>;
+    using Lay = PauliLayout<cx<T>, CHI>;
     constexpr int UW = 4;
     const int renv_ctas = b->any_lenv ? 2 * b->B : b->B;
     int dev = 0, sms = 0;

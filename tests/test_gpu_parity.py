@@ -654,3 +654,33 @@ def test_large_bonds_refuse_the_diagonal_pair_set():
         b.pauli_cache(pair_set="hvd")
     assert e.value.status == 5
     b.close()
+
+
+@pytest.mark.parametrize("pair_set", ["hv", "hvd"])
+def test_paper_ansatz_real_kernels(pair_set):
+    """The paper ansatz (H, R_Y(2 pi x - pi), CNOT: all real) gives a real state; the
+    mixed path then runs real-element environment and Pauli kernels.  Against the
+    complex kernels (set_real_arithmetic(False)) to rounding, against the oracle within
+    1e-5, and every Pauli with one Y exactly zero."""
+    from paper_2607_10280_b300.api import Batch
+    p, B, chi = 5, 6, 16
+    X = synth.garment_pixels(B, p, seed=61)
+    px = torch.tensor(X.reshape(-1), dtype=torch.float64, device="cuda")
+    for L in (2, 3):      # operator-product path (2^L <= chi), then rank-bounded splits
+        res = {}
+        for real in (True, False):
+            b = Batch(np.full(B, p, np.int32), chi, "mixed")
+            b.set_real_arithmetic(real)
+            b.set_layer_pipeline(L == 2)
+            b.apply_circuit(px, L, "paper")
+            out = b.pauli_cache(pair_set=pair_set)
+            b.sync()
+            res[real] = out.double().cpu().numpy().reshape(B, -1, 16)
+            b.close()
+        assert np.max(np.abs(res[True] - res[False])) < 1e-6
+        one_y = [4 * a + b for a in range(4) for b in range(4) if (a == 2) != (b == 2)]
+        assert np.all(res[True][:, :, one_y] == 0.0)
+        for i in (0, B - 1):
+            ref = o_mps.simulate(o_circ.build_circuit("paper", X[i], L), p * p, chi).pair_paulis(
+                o_pairs.image_pairs(p, pair_set == "hvd"))
+            assert np.max(np.abs(res[True][i] - ref)) < TOL["mixed"], (L, i)
