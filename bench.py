@@ -827,8 +827,8 @@ def _oracle_serve_job(job):
 def run_serve(args):
     """Poisson arrivals at 2000 requests/s of single images with p in 6..16, L in 1..4,
     chi in {4,8,16,32}; p = 7 requests also get ANO (84 x 16) and a linear layer 84 -> 784.
-    Four slots, one of them reserved for requests whose circuit truncates (they run a
-    complex128 chain).  Latency per (L, chi), per p and per lane, device time per wave;
+    Four slots, two of them reserved for requests whose circuit truncates (they run a
+    complex128 chain, on 128-thread teams).  Latency per (L, chi), per p and per lane, device time per wave;
     every result against the batched FP64 path afterwards, and a stratified sample (one
     request of every (p, L, chi) class that occurred, and more of the truncating and the
     16x16 ones) against the CPU oracle."""
@@ -844,7 +844,7 @@ def run_serve(args):
     epi = {7: (torch.tensor(synth.observable_params(m7), dtype=torch.float32, device="cuda"),
                torch.tensor(W, dtype=torch.float32, device="cuda"), torch.tensor(b, dtype=torch.float32,
                                                                                 device="cuda"))}
-    srv = Server(params, epi, slots=4, max_images_per_wave=64, budget_bytes=4 << 30, long_slots=1)
+    srv = Server(params, epi, slots=4, max_images_per_wave=64, budget_bytes=4 << 30, long_slots=2)
     # warm the slots (kernel attributes, first launches)
     warm = [srv.submit(Request(r["p"], r["L"], r["chi"], r["pixels"])) for r in reqs[:64]]
     srv.start()

@@ -263,8 +263,10 @@ uint64_t mps_launch_count(void);
  *   images_per_cta   images per CTA of the circuit kernel when it runs one warp per
  *                    image, 1..8
  *   circuit_threads  threads that share one image in the circuit kernel: 32, 64 or 128
- *                    (wider teams are compiled for the mixed path at bond bucket 16
- *                    without truncation; elsewhere one warp per image runs)
+ *                    (64: the mixed path at bond bucket 16 without truncation; 128:
+ *                    the complex128 truncation chains up to bond 16, which then use the
+ *                    SM's four FP64 pipes for one image, for latency when few images
+ *                    run at once; elsewhere one warp per image runs)
  *   pauli_threads    threads that share one (image, grid column) unit of the Pauli
  *                    kernel: 32, 64 or 128 (the pair set with diagonals always runs
  *                    with 64)

@@ -101,6 +101,12 @@ mps_status launch_circuit(mps_batch* b, const double* pixels, int ansatz) {
     if constexpr (CHI == 16 && !TRUNC && sizeof(T) == 4 && sizeof(TQ) == 4) {
         if (b->circuit_threads == 64) return launch_circuit_team<T, TQ, CHI, TRUNC, 64>(b, pixels, ansatz);
     }
+    // FP64 truncation chains up to bond 16 on 128-thread teams: the chain's FP64 work
+    // spreads over the SM's four FP64 pipes instead of one, which shortens each chain
+    // when few images run at once (serving); full batches keep one warp per image
+    if constexpr (TRUNC && sizeof(T) == 8 && CHI <= 16) {
+        if (b->circuit_threads == 128) return launch_circuit_team<T, TQ, CHI, TRUNC, 128>(b, pixels, ansatz);
+    }
     return launch_circuit_team<T, TQ, CHI, TRUNC, 32>(b, pixels, ansatz);
     }
 }

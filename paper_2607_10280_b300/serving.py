@@ -131,7 +131,8 @@ class Server:
 
     def __init__(self, params: torch.Tensor, epilogue: dict = None, slots: int = 4,
                  max_images_per_wave: int = 64, budget_bytes: int = 2 << 30, precision: str = "mixed",
-                 launch_shape=None, max_p: int = 16, max_chi: int = 32, long_slots: int = None):
+                 launch_shape=None, max_p: int = 16, max_chi: int = 32, long_slots: int = None,
+                 long_launch_shape=(0, 128, 0)):
         self.params = params
         self.epilogue = epilogue or {}
         self.precision = precision
@@ -147,8 +148,11 @@ class Server:
         if long_slots is None:
             long_slots = 1 if slots >= 2 else 0
         self.long_slots = max(0, min(long_slots, slots - 1))
+        # the long lane's truncation chains run on 128-thread teams (shorter chains when
+        # a wave holds few images)
         self.slots = [_Slot(i, precision, max_images_per_wave, max_p, max_chi,
-                            max_images_per_wave * pair_count(max_p), epi_m, epi_out, launch_shape,
+                            max_images_per_wave * pair_count(max_p), epi_m, epi_out,
+                            long_launch_shape if i >= slots - self.long_slots else launch_shape,
                             params.shape[0], long_lane=i >= slots - self.long_slots)
                       for i in range(slots)]
         self.pending = collections.deque()        # requests for the short lane

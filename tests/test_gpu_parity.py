@@ -684,3 +684,24 @@ def test_paper_ansatz_real_kernels(pair_set):
             ref = o_mps.simulate(o_circ.build_circuit("paper", X[i], L), p * p, chi).pair_paulis(
                 o_pairs.image_pairs(p, pair_set == "hvd"))
             assert np.max(np.abs(res[True][i] - ref)) < TOL["mixed"], (L, i)
+
+
+def test_fp64_chain_team_widths_agree():
+    """The complex128 truncation chain on one warp per image and on 128-thread teams
+    (mps_set_launch_shape circuit_threads = 128): the same FP64 arithmetic in another
+    summation order, so the two agree to FP64 rounding, and both match the oracle."""
+    p, L, chi, B = 5, 4, 4, 8
+    X = synth.garment_pixels(B, p, seed=95)
+    params = synth.circuit_params(L, p * p, seed=96)
+    a, _, da = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=(0, 32, 0))
+    b, _, db = run_gpu(list(X), [p] * B, L, chi, "mixed", params=params, shape=(0, 128, 0))
+    f, _, _ = run_gpu(list(X), [p] * B, L, chi, "fp64", params=params, shape=(0, 128, 0))
+    for i in range(B):
+        st = o_mps.simulate(o_circ.build_circuit("ladder", X[i], L, params), p * p, chi)
+        if st.min_gap < TIE_GAP:
+            continue
+        ref = st.pair_paulis(o_pairs.image_pairs(p))
+        assert np.max(np.abs(a[i] - b[i])) < 1e-6
+        assert np.max(np.abs(b[i] - ref)) < TOL["mixed"]
+        assert np.max(np.abs(f[i] - ref)) < TOL["fp64"]
+        assert abs(da[i] - db[i]) < 1e-12
