@@ -256,6 +256,20 @@ mps_status mps_bond_dims(mps_batch* batch, int32_t* out);
  * the last circuit to the host, out [n_images].  Synchronous. */
 mps_status mps_discarded_weight(mps_batch* batch, double* out);
 
+/* How mps_apply_circuit would run one image, computed on the host alone (no device
+ * work; usable without a GPU).  out [4], host:
+ *   out[0] route: 0 operator product (nothing truncates, 1 <= L <= 4, 2^L <= chi, bond
+ *          2^L at every inner cut), 1 layer-pipelined (ladder, nothing truncates,
+ *          L <= 4), 2 sequential kernel in the batch's precision, 3 sequential kernel on
+ *          a complex128 state (a lossy truncation under MPS_MIXED / MPS_MIXED_ORTH64)
+ *   out[1] largest bond of the image's MPS
+ *   out[2] 1 if some step keeps fewer singular values than the rank (lossy), else 0
+ *   out[3] site padding (power of two) the image gets in a batch
+ * with layer_pipeline as set by mps_set_layer_pipeline.  MPS_ERR_INVALID_ARG for bad
+ * arguments, MPS_ERR_UNSUPPORTED (out filled) when the bond exceeds MPS_BOND_LIMIT. */
+mps_status mps_plan_image(int32_t p, int32_t L, int32_t chi, int32_t ansatz, int32_t prec,
+                          int32_t layer_pipeline, int32_t* out);
+
 /* Kernels this library has launched since it was loaded (all batches). */
 uint64_t mps_launch_count(void);
 
@@ -331,10 +345,11 @@ mps_status mps_kernel_times(mps_batch* batch, double* ms, int64_t* launches);
  * mps_pauli_cache for n_images images of one size, MPS_MIXED precision (a circuit
  * that truncates lossily runs on a complex128 state, as there), the ladder ansatz
  * and the horizontal + vertical pair set, using the same kernels.  All working
- * memory (site tensors, their complex128 copies for a truncating circuit,
- * environments, bond dimensions, per-image records, the status word) lives in one
- * fixed array inside this library's device memory (about 44 MiB, held on every GPU
- * that loads the library until the process exits).
+ * memory (site tensors, their complex128 copies for a truncating circuit, the
+ * workspace of a truncation at bond 32, environments, bond dimensions, per-image
+ * records, the status word) lives in one fixed array inside this library's device
+ * memory (about 62 MiB, held on every GPU that loads the library until the process
+ * exits).
  *   n_images  1..64
  *   p, chi, L image side 2..16, bond cap 1..32, layers >= 0
  *   pixels    device float64 [n_images][p*p], values in [0, 1]

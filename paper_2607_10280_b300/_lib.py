@@ -64,6 +64,8 @@ SIGNATURES = {
     "mps_bond_dims": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_int32)]),
     "mps_discarded_weight": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_double)]),
     "mps_launch_count": (_c.c_uint64, []),
+    "mps_plan_image": (_c.c_int, [_c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32,
+                                  _c.POINTER(_c.c_int32)]),
     "mps_set_launch_shape": (_c.c_int, [_c.c_void_p, _c.c_int32, _c.c_int32, _c.c_int32]),
     "mps_set_timing": (_c.c_int, [_c.c_void_p, _c.c_int32]),
     "mps_set_layer_pipeline": (_c.c_int, [_c.c_void_p, _c.c_int32]),

@@ -26,6 +26,22 @@ def pair_count(p: int, pair_set: str = "hv") -> int:
     return int(lib().mps_pair_count(int(p), PAIR_SET[pair_set]))
 
 
+ROUTES = ("operator_product", "layer_pipelined", "sequential", "sequential_complex128")
+
+
+def plan_image(p: int, L: int, chi: int, ansatz: str = "ladder", precision: str = "mixed",
+               layer_pipeline: bool = True) -> dict:
+    """How the library would run one image (host-side, no GPU needed): kernel route,
+    largest bond, whether a step truncates lossily, and the site padding."""
+    out = (ctypes.c_int32 * 4)()
+    st = lib().mps_plan_image(int(p), int(L), int(chi), ANSATZ[ansatz], PRECISION[precision],
+                              1 if layer_pipeline else 0, out)
+    if st not in (0, 5):
+        check(st)
+    return {"route": ROUTES[out[0]], "bond": int(out[1]), "lossy": bool(out[2]), "padding": int(out[3]),
+            "supported": st == 0}
+
+
 def launch_count() -> int:
     return int(lib().mps_launch_count())
 

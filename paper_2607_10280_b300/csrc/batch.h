@@ -51,6 +51,7 @@ struct mps_batch {
     // exceed a block's shared memory)
     void* gws = nullptr;
     size_t cap_gws = 0;
+    bool gws_fixed = false;                // gws is caller-provided scratch: never (re)allocate it
     int gate_n = 0;                        // qubit stride of the gate table
     bool gates_owned = true;               // false when gates points into static scratch
     int circuit_threads = 32;              // threads per image in the circuit kernel
@@ -131,8 +132,22 @@ mps_status launch_gate_table(mps_batch* b, int ansatz, int L_max, const double* 
 // bond; *svd is set when some step truncates lossily (an SVD split to chi below the
 // rank bound 2^c of its cut).
 int dry_run_bonds(int n, int L, int chi, int ansatz, bool* svd);
-// Smallest compiled bond bucket (4, 8, 16, 32) holding bond mx, or -1.
+// Smallest compiled bond bucket (4, 8, 16, 32, 64, 128) holding bond mx, or -1.
 int chi_bucket(int mx);
+// Default cap of the site padding (a batch is laid out again for larger bonds).
+constexpr int LD_DEFAULT_CAP = 32;
+// Kernel route of one image in mps_apply_circuit: operator product, layer-pipelined,
+// sequential in the batch's precision, sequential on a complex128 state (a lossy
+// truncation under the mixed precisions).
+enum Route { ROUTE_MPO = 0, ROUTE_WAVE = 1, ROUTE_SEQ = 2, ROUTE_CHAIN64 = 3 };
+struct ImagePlan {
+    int route;
+    int bond;     // largest bond of the image's MPS (2^L at every inner cut for ROUTE_MPO)
+    bool lossy;   // some step keeps fewer singular values than the rank
+};
+ImagePlan plan_image(int n, int L, int chi, int ld, int ansatz, int prec, bool layer_pipeline);
+// Site padding of an image with n qubits and bond cap chi once a circuit needing `bond` ran.
+int site_padding(int n, int chi, int bond);
 // Rounds the complex128 sites that an FP64 chain wrote to src64 into b->arena
 // (complex64, same offsets) for the images b->run_order[0 .. run_count) (run_order
 // NULL: images 0 .. run_count-1).

@@ -72,10 +72,10 @@ struct CircuitLayout {
     static constexpr size_t off_ord = off_lam + (TRUNC ? sizeof(double) * K : 0);
     static constexpr size_t off_red = (off_ord + (TRUNC ? sizeof(int) * K : 0) + 15) & ~size_t(15);
     static constexpr size_t off_flag = off_red + sizeof(double) * 8;   // team reductions (<= 256 threads)
-    // FP64 truncation (up to bond 16 in shared memory, above 32 in global memory): the
-    // eigen-decomposition starts from FP32 Jacobi vectors, made orthonormal in FP64 in the
-    // buffer W (see svd_truncate); bond 32 has no room for W
-    static constexpr bool REFINE = TRUNC && sizeof(TQ) == 8 && (CHI <= 16 || CHI > 32);
+    // FP64 truncation: the eigen-decomposition starts from FP32 Jacobi vectors, made
+    // orthonormal in FP64 in the buffer W (see svd_truncate); from bond 32 on the layout
+    // exceeds a block's shared memory and the kernel runs on a global-memory workspace
+    static constexpr bool REFINE = TRUNC && sizeof(TQ) == 8;
     static constexpr size_t off_w = (off_flag + sizeof(int) + 15) & ~size_t(15);
     static constexpr size_t bytes = (off_w + (REFINE ? sizeof(cx<double>) * K * LDK : 0) + 15) & ~size_t(15);
     // the new centre (in cur) is written from V, so the two must not overlap

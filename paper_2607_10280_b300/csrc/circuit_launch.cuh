@@ -89,10 +89,15 @@ mps_status launch_circuit_wave(mps_batch* b, const double* pixels) {
 // Wider teams are compiled only for the mixed path at bond bucket 16 without
 // truncation (the benchmark shape); measured on B300 they do not beat one warp per
 // image, so every other combination runs one warp per image.
+// Shared memory of one block on B300 (opt-in); layouts above it run on a global-memory
+// workspace, one 256-thread team per image.
+constexpr size_t SMEM_BLOCK_MAX = 232448;
+
 template <typename T, typename TQ, int CHI, bool TRUNC>
 mps_status launch_circuit(mps_batch* b, const double* pixels, int ansatz) {
-    if constexpr (CHI > 32) {
-        // bonds above 32: one 256-thread team per image, workspace in global memory
+    if constexpr (CHI > 32 || CircuitLayout<T, TQ, CHI, TRUNC>::bytes > SMEM_BLOCK_MAX) {
+        // bonds above 32, and FP64 truncation at bond 32 (its refined eigen-decomposition
+        // needs about 270 KB): one 256-thread team per image, workspace in global memory
         return launch_circuit_team<T, TQ, CHI, TRUNC, 256>(b, pixels, ansatz);
     } else {
     if constexpr (!TRUNC) {

@@ -201,6 +201,26 @@ int dry_run_bonds(int n, int L, int chi, int ansatz, bool* svd) {
     return mx;
 }
 
+ImagePlan plan_image(int n, int L, int chi, int ld, int ansatz, int prec, bool layer_pipeline) {
+    bool t = false;
+    const int bi = dry_run_bonds(n, L, chi, ansatz, &t);
+    const bool fast = layer_pipeline && !t && L >= 1 && L <= WAVE_LAYERS;   // nothing truncates
+    if (fast && (1 << L) <= std::min(ld, chi) && (1 << L) <= 16) return {ROUTE_MPO, 1 << L, false};
+    if (fast && ansatz == MPS_ANSATZ_LADDER) return {ROUTE_WAVE, bi, false};
+    if (t && (prec == MPS_MIXED || prec == MPS_MIXED_ORTH64)) return {ROUTE_CHAIN64, bi, true};
+    return {ROUTE_SEQ, bi, t};
+}
+
+int site_padding(int n, int chi, int bond) {
+    int cap = 1;
+    while (cap < chi && cap < (1 << std::min(n / 2, 20))) cap <<= 1;
+    cap = std::min(std::min(cap, chi), LD_DEFAULT_CAP);
+    if (bond > cap && bond <= MPS_BOND_LIMIT) cap = bond;   // laid out again for a larger bond
+    int ld = 4;
+    while (ld < cap) ld <<= 1;
+    return ld;
+}
+
 int chi_bucket(int mx) {
     for (int c : {4, 8, 16, 32, 64, 128})
         if (mx <= c) return c;
@@ -209,6 +229,9 @@ int chi_bucket(int mx) {
 
 mps_status ensure_gws(mps_batch* b, size_t bytes) {
     if (b->gws && b->cap_gws >= bytes) return MPS_OK;
+    if (b->gws_fixed)
+        return fail(MPS_ERR_INVALID_ARG, "kernel workspace of %zu B exceeds the fixed scratch of %zu B", bytes,
+                    b->cap_gws);
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     cudaFree(b->gws);
     b->gws = nullptr;
@@ -304,9 +327,8 @@ namespace {
 
 // Host-side layout of an image list: per-image records, Pauli work units and sizes.
 // Site padding: a power of two >= 4 holding the largest bond the image can reach,
-// min(chi, 2^floor(n/2)), by default at most 32; ld_min (optional, per image) raises
-// it for a circuit that needs a larger bond (up to MPS_BOND_LIMIT).
-constexpr int LD_DEFAULT_CAP = 32;
+// min(chi, 2^floor(n/2)), by default at most LD_DEFAULT_CAP; ld_min (optional, per
+// image) raises it for a circuit that needs a larger bond (up to MPS_BOND_LIMIT).
 mps_status layout_images(mps_batch* b, int32_t n_images, const int32_t* p, const int32_t* chi, int32_t chi_all,
                          const int32_t* ld_min = nullptr) {
     if (n_images <= 0) return fail(MPS_ERR_INVALID_ARG, "n_images must be positive, got %d", n_images);
@@ -519,6 +541,27 @@ mps_status mps_destroy_batch(mps_batch* b) {
     return MPS_OK;
 }
 
+mps_status mps_plan_image(int32_t p, int32_t L, int32_t chi, int32_t ansatz, int32_t prec, int32_t layer_pipeline,
+                          int32_t* out) {
+    if (!out) return fail(MPS_ERR_INVALID_ARG, "out is NULL");
+    if (p < 2 || p > 16) return fail(MPS_ERR_INVALID_ARG, "p = %d outside 2..16", p);
+    if (chi < 1 || chi > MPS_CHI_LIMIT) return fail(MPS_ERR_INVALID_ARG, "chi = %d outside 1..%d", chi, MPS_CHI_LIMIT);
+    if (L < 0 || L > 64) return fail(MPS_ERR_INVALID_ARG, "L = %d outside 0..64", L);
+    if (ansatz != MPS_ANSATZ_LADDER && ansatz != MPS_ANSATZ_PAPER) return fail(MPS_ERR_INVALID_ARG, "unknown ansatz %d", ansatz);
+    if (prec < MPS_FP64 || prec > MPS_MIXED_FAST) return fail(MPS_ERR_INVALID_ARG, "unknown precision %d", prec);
+    const int n = p * p;
+    bool t = false;
+    const int raw = dry_run_bonds(n, L, chi, ansatz, &t);
+    const int ld = site_padding(n, chi, raw);
+    const ImagePlan pl = plan_image(n, L, chi, ld, ansatz, prec, layer_pipeline != 0);
+    out[0] = pl.route;
+    out[1] = pl.bond;
+    out[2] = pl.lossy ? 1 : 0;
+    out[3] = ld;
+    if (pl.bond > MPS_BOND_LIMIT) return fail(MPS_ERR_UNSUPPORTED, "bond %d > %d", pl.bond, MPS_BOND_LIMIT);
+    return MPS_OK;
+}
+
 mps_status mps_reserve(mps_batch* b, int32_t L_max) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
     if (L_max < 0 || L_max > 64) return fail(MPS_ERR_INVALID_ARG, "L_max = %d outside 0..64", L_max);
@@ -622,26 +665,23 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     const bool chain64_on = b->prec == MPS_MIXED || b->prec == MPS_MIXED_ORTH64;
     std::vector<char> wave(b->B, 0), mpo(b->B, 0), c64(b->B, 0);
     int n_wave = 0, n_mpo = 0, n_64 = 0;
+    (void)chain64_on;
     for (int i = 0; i < b->B; ++i) {
         ImageMeta& m = b->meta_h[i];
         const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
         if (m.L != L) { m.L = L; b->meta_dirty = true; }
-        bool t = false;
-        int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
+        const ImagePlan pl = plan_image(m.n, L, m.chi, m.ld, circ->ansatz, b->prec, b->layer_pipeline);
+        const bool t = pl.lossy;
+        const int bi = pl.bond;
         if (bi > m.ld) return fail(MPS_ERR_UNSUPPORTED, "image %d reaches bond %d > padding %d", i, bi, m.ld);
-        const bool fast = b->layer_pipeline && !t && L >= 1 && L <= WAVE_LAYERS;   // nothing truncates
-        const bool pipe = fast && circ->ansatz == MPS_ANSATZ_LADDER;
-        mpo[i] = fast && (1 << L) <= std::min(m.ld, m.chi) && (1 << L) <= 16;
+        mpo[i] = pl.route == ROUTE_MPO;
         const int32_t fl =
             mpo[i] ? (META_LENV | (circ->ansatz == MPS_ANSATZ_LADDER && b->half_structure ? META_HALF : 0)) : 0;
         if (m.flags != fl) { m.flags = fl; b->meta_dirty = true; }
-        if (mpo[i]) {
-            bi = 1 << L;
-            ++n_mpo;
-        }
+        if (mpo[i]) ++n_mpo;
         mx = std::max(mx, bi);
-        wave[i] = pipe && !mpo[i];
-        c64[i] = !mpo[i] && !wave[i] && t && chain64_on;
+        wave[i] = pl.route == ROUTE_WAVE;
+        c64[i] = pl.route == ROUTE_CHAIN64;
         if (wave[i]) {
             ++n_wave;
             mx_wave = std::max(mx_wave, bi);

@@ -23,6 +23,9 @@ constexpr size_t NA_GATE_BYTES = size_t(512) << 10;   // one-qubit gate table (c
 // of the mixed precision), twice the complex64 sizes
 constexpr size_t NA_ARENA64_BYTES = 2 * NA_ARENA_BYTES;
 constexpr size_t NA_GATE64_BYTES = 2 * NA_GATE_BYTES;
+// per-image workspace of a truncation at bond 32 on a complex128 state (about 270 KB,
+// more than a block's shared memory), for up to 64 images
+constexpr size_t NA_GWS_BYTES = size_t(18) << 20;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t OFF_META = 0;
@@ -37,11 +40,12 @@ constexpr size_t OFF_RENV = align256(OFF_ARENA + NA_ARENA_BYTES);
 constexpr size_t OFF_GATES = align256(OFF_RENV + NA_RENV_BYTES);
 constexpr size_t OFF_ARENA64 = align256(OFF_GATES + NA_GATE_BYTES);
 constexpr size_t OFF_GATES64 = align256(OFF_ARENA64 + NA_ARENA64_BYTES);
-constexpr size_t NA_TOTAL = align256(OFF_GATES64 + NA_GATE64_BYTES);
+constexpr size_t OFF_GWS = align256(OFF_GATES64 + NA_GATE64_BYTES);
+constexpr size_t NA_TOTAL = align256(OFF_GWS + NA_GWS_BYTES);
 
 }  // namespace
 
-// The scratch array.  Every GPU that loads this library holds it (about 44 MiB)
+// The scratch array.  Every GPU that loads this library holds it (about 62 MiB)
 // until the process exits.  Host code must not use its name as an address: the
 // device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_TOTAL];
@@ -159,6 +163,9 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
     b.gates_owned = false;
     b.gate_n = n;
     b.queue_d = reinterpret_cast<int*>(base + OFF_QUEUE);
+    b.gws = base + OFF_GWS;   // global-memory workspace of the bond-32 complex128 chain
+    b.cap_gws = NA_GWS_BYTES;
+    b.gws_fixed = true;
     b.order_d = nullptr;   // equal sizes: images in index order
     b.run_order = nullptr;
     b.run_count = n_images;
