@@ -28,6 +28,7 @@ struct mps_batch {
     void* lenv = nullptr;                  // left environments (operator-product ladder images), as renv
     size_t cap_lenv = 0;
     bool any_lenv = false;                 // some image of the last circuit is flagged META_LENV
+    bool all_half = false;                 // every image of the last circuit is flagged META_HALF
     void* norms = nullptr;
     int32_t* bonds_d = nullptr;
     double* discarded_d = nullptr;

@@ -15,6 +15,7 @@ template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { cx<T> z; z
 template <typename T> __device__ __forceinline__ cx<T> czero() { return mk<T>(T(0), T(0)); }
 template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk<T>(a.re + b.re, a.im + b.im); }
 template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk<T>(a.re - b.re, a.im - b.im); }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a) { return mk<T>(-a.re, -a.im); }
 // Products that the compiler may not fuse into a neighbouring add: with every
 // multiply of the complex helpers either an explicit fma or one of these, each
 // kernel instantiation computes the same bits from the same inputs.

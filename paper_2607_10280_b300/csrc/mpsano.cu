@@ -708,6 +708,8 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         if (se != MPS_OK) return se;
     }
     b->any_lenv = n_mpo > 0;
+    b->all_half = true;
+    for (int i = 0; i < b->B; ++i) b->all_half = b->all_half && (b->meta_h[i].flags & META_HALF) != 0;
     if (order != b->order_h) {
         CUDA_TRY(cudaStreamSynchronize(b->stream));  // pinned staging may still be in flight
         std::memcpy(b->order_pinned, order.data(), sizeof(int32_t) * b->B);

@@ -45,14 +45,17 @@ namespace mpsano {
 // two products of depth D/2 cost more in launch overhead than they save.
 constexpr int HALF_SPLIT_MIN = 8;
 
-template <typename E, int CHI>
+// HALF: every image of the launch is half-structured (META_HALF), whose contractions
+// never need more than 2 CHI rows of S (the dense left blocks of a site with a right
+// bond above CHI/2 would; the Pauli kernel checks it), so S shrinks by a third.
+template <typename E, int CHI, bool HALF = false>
 struct PauliLayout {
     using T = typename elem_traits<E>::scalar;
     static constexpr int CS = CHI + 1;
     static constexpr int MAT = CHI * CS;
     static constexpr int ZS = 2 * CHI + 1;
-    static constexpr int SROWS = 3 * CHI;
-    // A (2 MAT), R (1 MAT), C (2 MAT: M = C_X + i C_Y, C_Z), S (3 CHI rows x ZS);
+    static constexpr int SROWS = HALF ? 2 * CHI : 3 * CHI;
+    // A (2 MAT), R (1 MAT), C (2 MAT: M = C_X + i C_Y, C_Z), S (SROWS rows x ZS);
     // with diagonal pairs also Cd (2 MAT, the carried closings one site further)
     static constexpr int ELEMS = 5 * MAT + SROWS * ZS;
     static constexpr size_t bytes = sizeof(E) * ELEMS;
@@ -86,12 +89,13 @@ struct Tile {
 
 // out[m][n] = sum_{seg < NSEG} sum_{k < K} opA(Ab[ao(m) + seg*as_seg + k*as])
 //                                          * Bb[bo(n) + seg*bs_seg + k*bs]
+// (NEG1: segment 1 enters with a minus sign; only with CONJA)
 // for m < M, n < N, delivered through store(m, so(n), value); the column offsets
 // ao, bo and so are evaluated once per tile row / column.
 // KU: unroll factor of the k loop (1 keeps the Pauli kernel's code small enough for
 // the instruction cache; the environment kernel, one warp per image, prefers 2).
-template <typename E, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, int KU, class AO, class BO, class SO,
-          class ST>
+template <typename E, int MT, int NT, int TM, int TN, int NSEG, bool CONJA, int KU, bool NEG1 = false, class AO,
+          class BO, class SO, class ST>
 __device__ __forceinline__ void team_gemm(const E* Ab, AO ao, int as, int as_seg,
                                           const E* Bb, BO bo, int bs, int bs_seg,
                                           int M, int N, int K, SO so, ST store, int lane) {
@@ -130,7 +134,8 @@ __device__ __forceinline__ void team_gemm(const E* Ab, AO ao, int as, int as_seg
                     for (int i = 0; i < TM; ++i)
 #pragma unroll
                         for (int j = 0; j < TN; ++j) {
-                            if (CONJA) cmac_cj(acc[i][j], a[i], b[j]);
+                            if (NEG1 && seg == 1) cmac_cj(acc[i][j], -a[i], b[j]);   // segment 1 subtracted
+                            else if (CONJA) cmac_cj(acc[i][j], a[i], b[j]);
                             else cmac(acc[i][j], a[i], b[j]);
                         }
                 }
@@ -393,7 +398,9 @@ __device__ __forceinline__ void left_dots(const E* S, const E* C, const E* R, in
 // Closings of a right site A (Dl x 2 x Dr) with right environment R:
 //   G[2l+s][2l'+s'] = sum_r conj(A[2l+s][r]) (R A^{s'T})[r][l'],
 //   C_X = G01 + G10, C_Y = i (G10 - G01), C_Z = G00 - G11  (Dl x Dl each); into C go
-//   M = C_X + i C_Y = 2 G01 and C_Z.
+//   M = C_X + i C_Y = 2 G01 and C_Z, each formed directly from S = R A^T (G itself is
+//   never stored): M from the even rows of A and the odd columns of S, C_Z as one
+//   two-segment product, the odd segment subtracted.
 template <typename E, int CHI, int NTHR>
 __device__ __forceinline__ void right_closings(const E* A, const E* R, E* C, E* S,
                                                int Dl, int Dr, int lane, bool half = false) {
@@ -401,29 +408,16 @@ __device__ __forceinline__ void right_closings(const E* A, const E* R, E* C, E* 
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
     times_site_t<E, CHI, 1, NTHR>(R, A, S, Dl, Dr, lane, half);   // S[r][n] = (R A^T)[r][n]
     team_sync();
-    E* G = S + CHI * ZS;
-    if (half) {
-        // rows 2l+s of G contract r over half s only (see times_site_t)
-        const int h = Dr >> 1;
-        using Tl = Tile<E, CHI, 2 * CHI, NTHR>;
-        for (int s = 0; s < 2; ++s)
-            team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
-                A, [s, h](int l) { return (2 * l + s) * CS + s * h; }, 1, 0, S + s * h * ZS, [](int n) { return n; },
-                ZS, 0, Dl, 2 * Dl, h, [](int n) { return n; },
-                [G, s](int l, int sn, E v) { G[(2 * l + s) * ZS + sn] = v; }, lane);
-    } else {
-        using Tl = Tile<E, 2 * CHI, 2 * CHI, NTHR>;
-        team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
-            A, [](int m) { return m * CS; }, 1, 0, S, [](int n) { return n; }, ZS, 0, 2 * Dl, 2 * Dl, Dr,
-            [](int n) { return n; }, [G](int m, int sn, E v) { G[m * ZS + sn] = v; }, lane);
-    }
-    team_sync();
-    team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int l, int lp) {
-        const E g00 = G[(2 * l) * ZS + 2 * lp], g01 = G[(2 * l) * ZS + 2 * lp + 1];
-        const E g11 = G[(2 * l + 1) * ZS + 2 * lp + 1];
-        C[l * CS + lp] = g01 + g01;
-        C[MAT + l * CS + lp] = g00 - g11;
-    });
+    // rows 2l+s contract r over half s only when the site is half-structured
+    const int K = half ? Dr >> 1 : Dr;
+    const int h = half ? Dr >> 1 : 0;
+    using Tl = Tile<E, CHI, CHI, NTHR>;
+    team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
+        A, [](int l) { return 2 * l * CS; }, 1, 0, S, [](int n) { return 2 * n + 1; }, ZS, 0, Dl, Dl, K,
+        [](int n) { return n; }, [C](int l, int sn, E v) { C[l * CS + sn] = v + v; }, lane);
+    team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, 1, true>(
+        A, [](int l) { return 2 * l * CS; }, 1, CS + h, S, [](int n) { return 2 * n; }, ZS, 1 + h * ZS, Dl, Dl, K,
+        [](int n) { return n; }, [C](int l, int sn, E v) { C[MAT + l * CS + sn] = v; }, lane);
     team_sync();
 }
 
@@ -588,15 +582,15 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
 
 // One (image, column) unit of the Pauli kernel, worked on by the CTA's UW warps with
 // its workspace at smem_raw.
-template <typename T, int CHI, int UW, bool DIAG, bool REAL>
+template <typename T, int CHI, int UW, bool DIAG, bool REAL, bool HALF = false>
 __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, const ImageMeta* __restrict__ meta,
                                            const int32_t* __restrict__ unit_image,
                                            const cx<T>* __restrict__ arena, const int32_t* __restrict__ bonds,
                                            const cx<T>* __restrict__ renv_c, int64_t renv_stride,
                                            const cx<T>* __restrict__ lenv_c, const T* __restrict__ norms,
-                                           T* __restrict__ out) {
+                                           T* __restrict__ out, int* status) {
     using E = std::conditional_t<REAL, T, cx<T>>;
-    using Lay = PauliLayout<E, CHI>;
+    using Lay = PauliLayout<E, CHI, HALF>;
     const E* renv = reinterpret_cast<const E*>(renv_c);
     const E* lenv = reinterpret_cast<const E*>(lenv_c);
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
@@ -623,6 +617,14 @@ __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, co
     // left blocks (one product either way); half_tr: the contractions that split into
     // one product per physical index, from bond HALF_SPLIT_MIN on
     const bool half_img = (mt.flags & META_HALF) != 0;
+    if constexpr (HALF) {
+        // the reduced scratch holds only half-structured images (the host launches this
+        // variant when every image is one)
+        if (!half_img) {
+            if (threadIdx.x == 0) raise_status(status, DEV_BAD_SHAPE);
+            return;
+        }
+    }
     auto half_at = [half_img, &mt, bd](int i) { return half_img && i < mt.n - 1 && bd[i + 1] >= 2; };
     auto half_tr = [half_img, &mt, bd](int i) { return half_img && i < mt.n - 1 && bd[i + 1] >= HALF_SPLIT_MIN; };
     const T inv_norm = T(1) / norms[img];
@@ -722,15 +724,20 @@ __device__ __forceinline__ void pauli_unit(int unit, unsigned char* smem_raw, co
 
 // One (image, column) unit per CTA (GMEM: bonds above 32, workspace in global memory,
 // Lay::team_bytes per CTA, the CTAs stepping through the units).
-template <typename T, int CHI, int UW, bool DIAG, bool GMEM = false, bool REAL = false>
-__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16) ? 9 : 8) / (sizeof(T) == 8 ? 2 : 1)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
+// Resident CTAs per SM the compiler is asked to fit for the half-structured variant
+// (64-thread teams): 10 fit its 19.4 KB of shared memory and 96 registers per thread.
+#ifndef PAULI_HALF_MIN_BLOCKS
+#define PAULI_HALF_MIN_BLOCKS 10
+#endif
+template <typename T, int CHI, int UW, bool DIAG, bool GMEM = false, bool REAL = false, bool HALF = false>
+__global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16) ? (HALF ? PAULI_HALF_MIN_BLOCKS : 9) : 8) / (sizeof(T) == 8 ? 2 : 1)) pauli_kernel(const ImageMeta* __restrict__ meta, int n_units,
                                                     const int32_t* __restrict__ unit_image,
                                                     const cx<T>* __restrict__ arena,
                                                     const int32_t* __restrict__ bonds,
                                                     const cx<T>* __restrict__ renv, int64_t renv_stride,
                                                     const cx<T>* __restrict__ lenv,
                                                     const T* __restrict__ norms, T* __restrict__ out,
-                                                    unsigned char* __restrict__ gws) {
+                                                    unsigned char* __restrict__ gws, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (GMEM) {
         constexpr size_t ws = (PauliLayout<std::conditional_t<REAL, T, cx<T>>, CHI>::team_bytes(UW, DIAG) + 255) &
@@ -738,13 +745,13 @@ __global__ void __launch_bounds__(32 * UW, (UW == 4 ? 4 : (UW == 2 && CHI <= 16)
         unsigned char* raw = gws + (size_t)blockIdx.x * ws;
         for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
             pauli_unit<T, CHI, UW, DIAG, REAL>(unit, raw, meta, unit_image, arena, bonds, renv, renv_stride, lenv,
-                                               norms, out);
+                                               norms, out, status);
             __syncthreads();
         }
     } else {
         if ((int)blockIdx.x >= n_units) return;
-        pauli_unit<T, CHI, UW, DIAG, REAL>(blockIdx.x, smem_raw, meta, unit_image, arena, bonds, renv, renv_stride,
-                                           lenv, norms, out);
+        pauli_unit<T, CHI, UW, DIAG, REAL, HALF>(blockIdx.x, smem_raw, meta, unit_image, arena, bonds, renv,
+                                                 renv_stride, lenv, norms, out, status);
     }
 }
 

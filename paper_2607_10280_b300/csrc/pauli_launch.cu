@@ -7,21 +7,21 @@
 namespace mpsano {
 namespace {
 
-template <typename T, int CHI, int UW, bool DIAG>
+template <typename T, int CHI, int UW, bool DIAG, bool HALF = false>
 mps_status launch_pauli_uw(mps_batch* b, void* out) {
     constexpr bool diag = DIAG;
-    using Lay = PauliLayout<cx<T>, CHI>;
+    using Lay = PauliLayout<cx<T>, CHI, HALF>;
     const int limit = smem_optin_limit();
     const size_t smem = Lay::team_bytes(UW, diag);
     if (smem > (size_t)limit) return fail(MPS_ERR_UNSUPPORTED, "Pauli kernel shared memory %zu B", smem);
-    auto pk = pauli_kernel<T, CHI, UW, DIAG>;
+    auto pk = pauli_kernel<T, CHI, UW, DIAG, false, false, HALF>;
     CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     timing_begin(b, KIND_PAULI);
     pk<<<b->n_units, 32 * UW, smem, b->stream>>>(
         b->meta_d, b->n_units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
         reinterpret_cast<const cx<T>*>(b->any_lenv ? b->lenv : nullptr),
-        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out), nullptr);
+        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out), nullptr, b->status_d);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
@@ -48,6 +48,11 @@ mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
     count_launch();
     // the diagonal pair sets are compiled for 2-warp teams only
     if (diag) return launch_pauli_uw<T, CHI, 2, true>(b, out);
+    // every image half-structured (operator-product ladder images): the smaller scratch,
+    // more resident teams
+    if constexpr (sizeof(T) == 4) {
+        if (b->all_half && b->pauli_warps == 2) return launch_pauli_uw<T, CHI, 2, false, true>(b, out);
+    }
     switch (b->pauli_warps) {
         case 1: return launch_pauli_uw<T, CHI, 1, false>(b, out);
         case 4: return launch_pauli_uw<T, CHI, 4, false>(b, out);

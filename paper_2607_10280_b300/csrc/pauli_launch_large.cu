@@ -37,7 +37,8 @@ mps_status launch_large(mps_batch* b, void* out, bool diag) {
         b->meta_d, b->n_units, b->units_d, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<T>*>(b->renv), b->renv_stride,
         reinterpret_cast<const cx<T>*>(b->any_lenv ? b->lenv : nullptr),
-        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out), static_cast<unsigned char*>(b->gws));
+        reinterpret_cast<const T*>(b->norms), reinterpret_cast<T*>(out), static_cast<unsigned char*>(b->gws),
+        b->status_d);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();

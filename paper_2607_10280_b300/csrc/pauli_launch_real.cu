@@ -36,7 +36,7 @@ mps_status launch_real(mps_batch* b, void* out) {
         b->meta_d, b->n_units, b->units_d, reinterpret_cast<const cx<float>*>(b->arena), b->bonds_d,
         reinterpret_cast<const cx<float>*>(b->renv), b->renv_stride,
         reinterpret_cast<const cx<float>*>(b->any_lenv ? b->lenv : nullptr),
-        reinterpret_cast<const float*>(b->norms), reinterpret_cast<float*>(out), nullptr);
+        reinterpret_cast<const float*>(b->norms), reinterpret_cast<float*>(out), nullptr, b->status_d);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
