@@ -38,6 +38,8 @@ PROFILED = {
                 ("ladder_mpo.cu", "circuit.cuh", "common.cuh")),
     "renv": ("profiles/renv_kernel_7x7_L4_chi16_b1024.md",
              ("pauli.cuh", "pauli_launch.cu", "linalg.cuh", "common.cuh")),
+    "chain": ("profiles/circuit_kernel_fp64_chain_7x7_L4_chi8_b1024.md",
+              ("circuit.cuh", "circuit_launch.cuh", "linalg.cuh", "common.cuh")),
 }
 
 
@@ -598,7 +600,8 @@ def run_trunc(args):
     peak64, peak32 = 1.25, 148 * 128 * 2 * 2.032e9 / 1e12
     achieved = B * f["fp64"] / (circ_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
-                "frac": achieved / peak64, "traffic": None, "kernel": "circuit (FP64 chain + rounding)",
+                "frac": achieved / peak64, "traffic": profiled_traffic("chain"),
+                "kernel": "circuit (FP64 chain + rounding)",
                 "peak_note": "nominal FP64 rate of B300 (1.25 TFLOP/s, about 2 DFMA per SM and clock at 2032 MHz)",
                 "fp32_side": {"achieved": B * f["fp32"] / (circ_ms / 1e3) / 1e12, "peak": peak32,
                               "note": "FP32 Jacobi that starts each eigen-decomposition"},
