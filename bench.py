@@ -32,8 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 # DRAM traffic a capture recorded is reported only while these files are unchanged
 # (the summary carries their hash).
 PROFILED = {
-    "pauli": ("profiles/pauli_kernel_7x7_L4_chi16_b1024.md",
-              ("pauli.cuh", "pauli_launch.cu", "linalg.cuh", "common.cuh")),
+    "pauli": ("profiles/pauli_sweep_kernel_7x7_L4_chi16_b1024.md",
+              ("pauli_sweep.cuh", "pauli_launch_sweep.cu", "pauli.cuh", "linalg.cuh", "common.cuh")),
     "circuit": ("profiles/ladder_mpo_kernel_7x7_L4_chi16_b1024.md",
                 ("ladder_mpo.cu", "circuit.cuh", "common.cuh")),
     "renv": ("profiles/renv_kernel_7x7_L4_chi16_b1024.md",
@@ -105,6 +105,8 @@ def parse():
                          "batch, the 16x16 batch, the serving run, training on cached Paulis and the "
                          "156-pair layout with diagonals")
     ap.add_argument("--requests", type=int, default=20000, help="serving run: number of requests (10 s at 2000/s)")
+    ap.add_argument("--pauli-kernel", default="default", choices=["default", "sweep", "column"],
+                    help="Pauli-cache kernel at bonds up to 16 (mps_set_pauli_sweep); default: the library's")
     return ap.parse_args()
 
 
@@ -226,6 +228,8 @@ def run_ours(args):
     from paper_2607_10280_b300 import api, flops, synth
     from paper_2607_10280_b300.build import build
     build()
+    if PAULI_KERNEL != "default":
+        api.Batch.pauli_sweep_default = PAULI_KERNEL == "sweep"
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -320,9 +324,10 @@ def run_ours(args):
                      "clocks": clk_sus.summary(local)}
 
     # ---------------- roofline of the dominant kernel (ALU bound, FP32 pipe)
-    f = flops.image_flops(P, L, CHI)
+    fk = "column" if PAULI_KERNEL == "column" else "sweep"
+    f = flops.image_flops(P, L, CHI, kernel=fk)
     # the same contraction without exploiting the half-structured sites (context only)
-    f_dense = flops.image_flops(P, L, CHI, dense=True)
+    f_dense = flops.image_flops(P, L, CHI, dense=True, kernel=fk)
     dom = max(("circuit", "renv", "pauli"), key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / max(1, kt[dom][1])
     achieved = BATCH * f[dom] / (dom_ms / 1e3) / 1e12
@@ -466,12 +471,18 @@ def run_diag(args):
     print(json.dumps(line), flush=True)
 
 
+PAULI_KERNEL = "default"
+
+
 def _setup_torch():
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     from paper_2607_10280_b300.build import build
     build()
+    if PAULI_KERNEL != "default":
+        from paper_2607_10280_b300 import api
+        api.Batch.pauli_sweep_default = PAULI_KERNEL == "sweep"
     return torch
 
 
@@ -998,6 +1009,7 @@ def run_train(args):
 
 if __name__ == "__main__":
     a = parse()
+    PAULI_KERNEL = a.pauli_kernel
     if a.impl == "reference":
         run_reference(a)
     elif a.config == "headline":

@@ -313,6 +313,17 @@ mps_status mps_set_layer_pipeline(mps_batch* batch, int32_t enable);
  * exactly that.  Takes effect at the next mps_apply_circuit. */
 mps_status mps_set_half_structure(mps_batch* batch, int32_t enable);
 
+/* Pauli-cache kernel choice under the mixed precisions at bonds up to 16 (enable != 0:
+ * the per-image sweep, the default; 0: the column walk).  The sweep gives one CTA a
+ * whole image and walks its chain from the last site to the first, carrying the right
+ * environment and the closings of every pair still open (Sec. II.C, Eq. 5), so each
+ * transfer through a site is one stacked product over all of them; the column walk
+ * carries one column's closings per team and reads right environments from a separate
+ * pass.  Both accumulate every sum in the same order: the results are bit-identical.
+ * The sweep is skipped (column walk) where its shared memory would not fit a block.
+ * Takes effect at the next mps_pauli_cache. */
+mps_status mps_set_pauli_sweep(mps_batch* batch, int32_t enable);
+
 /* Real-element environment and Pauli kernels for a real state (enable != 0: on, the
  * default).  The paper ansatz's gates (H, R_Y(2 pi x - pi), CNOT) are real, so its state
  * is real in every amplitude; under the mixed precisions the environment and Pauli

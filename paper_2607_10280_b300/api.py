@@ -49,6 +49,9 @@ def launch_count() -> int:
 class Batch:
     """A batch of images, one MPS each (Sec. II.B, Eq. 3), on one CUDA stream."""
 
+    # Pauli-cache kernel of new batches (set_pauli_sweep): True = the library default
+    pauli_sweep_default = True
+
     def __init__(self, p, chi, precision: str = "mixed", stream=None):
         p = np.atleast_1d(np.asarray(p, dtype=np.int32))
         self.n_images = len(p)
@@ -66,6 +69,8 @@ class Batch:
         self._h = handle
         self.pixel_offsets = np.concatenate([[0], np.cumsum(self.n)])
         self.pair_offsets = np.concatenate([[0], np.cumsum([pair_count(int(q)) for q in p])])
+        if not Batch.pauli_sweep_default:
+            self.set_pauli_sweep(False)
 
     def reshape(self, p, chi):
         """New image list for this batch, reusing its device memory when it fits."""
@@ -162,6 +167,11 @@ class Batch:
         """Real-element environment and Pauli kernels for a real state (paper ansatz,
         mixed precisions); results agree with the complex kernels to rounding."""
         check(lib().mps_set_real_arithmetic(self._h, 1 if enable else 0))
+
+    def set_pauli_sweep(self, enable: bool = True):
+        """Per-image sweep Pauli kernel (default) or the column walk, bonds up to 16 under
+        the mixed precisions; the two give bit-identical caches."""
+        check(lib().mps_set_pauli_sweep(self._h, 1 if enable else 0))
 
     def set_timing(self, enable: bool = True):
         check(lib().mps_set_timing(self._h, 1 if enable else 0))

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmpsano.so")
 SOURCES = (["circuit_fp64_t1_c128.cu", "circuit_fp64_t1_c64.cu", "circuit_mixed_t1_c128.cu", "circuit_mixed_t1_c64.cu",
             "circuit_fp64_t1_c32.cu", "circuit_fp64_t1_c16.cu", "circuit_orth64_t1_c32.cu", "circuit_orth64_t1_c16.cu",
-            "pauli_launch.cu", "pauli_launch_large.cu", "pauli_launch_real.cu"]
+            "pauli_launch_sweep.cu", "pauli_launch.cu", "pauli_launch_large.cu", "pauli_launch_real.cu"]
            + [f"circuit_{p}_t0_c{c}.cu" for p in ("fp64", "mixed") for c in (64, 128)]
            + [f"circuit_{p}_t{t}_c{c}.cu" for p in ("mixed", "fp64", "orth64") for t in (0, 1) for c in (4, 8, 16, 32)
               if not (t == 1 and p != "mixed" and c >= 16)]

@@ -605,6 +605,12 @@ mps_status mps_set_half_structure(mps_batch* b, int32_t enable) {
     return MPS_OK;
 }
 
+mps_status mps_set_pauli_sweep(mps_batch* b, int32_t enable) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    b->pauli_sweep = enable != 0;
+    return MPS_OK;
+}
+
 mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circuit* circ) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
     if (!pixels) return fail(MPS_ERR_INVALID_ARG, "pixels is NULL");

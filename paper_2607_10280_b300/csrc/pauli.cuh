@@ -265,11 +265,11 @@ __device__ __forceinline__ void left_blocks(const E* A, E* S, int Dl, int Dr, in
         [](int n) { return n; }, [F](int m, int sn, E v) { F[m * ZS + sn] = v; }, lane);
 }
 
-// The same blocks with a left environment L (Dl x Dl, row stride CHI, read from
-// global memory; NULL: the identity, left_blocks):
+// The same blocks with a left environment L (Dl x Dl, row stride LS: CHI as stored in
+// global memory, or a shared-memory copy; NULL: the identity, left_blocks):
 // F[m][n] = sum_{l,l'} conj(A[2l+s_m][r_m]) L[l][l'] A[2l'+s_n][r_n], through
 // T[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r] in S rows 0 .. Dl.
-template <typename E, int CHI, int NTHR>
+template <typename E, int CHI, int NTHR, int LS = CHI>
 __device__ __forceinline__ void left_blocks_env(const E* A, const E* Lg, E* S, int Dl, int Dr,
                                                 int lane, bool half = false) {
     if (!Lg) {
@@ -284,7 +284,7 @@ __device__ __forceinline__ void left_blocks_env(const E* A, const E* Lg, E* S, i
         {
             using Tl = Tile<E, CHI, CHI, NTHR>;
             team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
-                Lg, [](int l) { return l * CHI; }, 1, 0, A, off, 2 * CS, 0, Dl, Dr, Dl,
+                Lg, [](int l) { return l * LS; }, 1, 0, A, off, 2 * CS, 0, Dl, Dr, Dl,
                 [](int nn) { return nn; }, [S](int l, int sn, E v) { S[l * ZS + sn] = v; }, lane);
         }
         team_sync();
@@ -298,7 +298,7 @@ __device__ __forceinline__ void left_blocks_env(const E* A, const E* Lg, E* S, i
     {
         using Tl = Tile<E, CHI, 2 * CHI, NTHR>;
         team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
-            Lg, [](int l) { return l * CHI; }, 1, 0, A, [Dr](int nn) { return (nn / Dr) * CS + (nn % Dr); }, 2 * CS, 0,
+            Lg, [](int l) { return l * LS; }, 1, 0, A, [Dr](int nn) { return (nn / Dr) * CS + (nn % Dr); }, 2 * CS, 0,
             Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, E v) { S[l * ZS + sn] = v; }, lane);
     }
     team_sync();
@@ -311,77 +311,85 @@ __device__ __forceinline__ void left_blocks_env(const E* A, const E* Lg, E* S, i
 
 // <E_a, Y> for a = X, Y, Z (from the blocks F_{ss'} in S) and Y in {C_X, C_Y, C_Z, R}:
 // out[4(a-1) + y], with C_X, C_Y unpacked from M = C[0] and C_Z = C[MAT].  C may be
-// null (then only the R column is formed).  Warp 0 alone
-// forms the sums, so the summation order (and every bit of the result) does not
-// depend on the team size; the other warps read the sums from red.
-template <typename E, int CHI, int NTHR>
-__device__ __forceinline__ void left_dots(const E* S, const E* C, const E* R, int D,
-                                          typename elem_traits<E>::scalar* out,
-                                          typename elem_traits<E>::scalar* red, int lane, bool half = false) {
+// null (then only the R column is formed).  One warp (lane < 32) forms every sum in a
+// fixed order, so the bits of the result depend on neither the team size nor on which
+// warp runs it; every lane receives the sums.
+template <typename E, int CHI>
+__device__ __forceinline__ void left_dots_warp(const E* S, const E* C, const E* R, int D,
+                                               typename elem_traits<E>::scalar* out, int lane,
+                                               bool half = false) {
     using T = typename elem_traits<E>::scalar;
     using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
     const E* F = S + CHI * ZS;
     const int h = D >> 1;
-    if (lane < 32) {
-        T acc[12];
+    T acc[12];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) acc[i] = T(0);
-        team_for_2d<32, 4>(D, D, lane, [&](int r, int rp) {
-          if constexpr (elem_traits<E>::real) {
-            // a real state (no half-structured sites): E_X, E_Z, C_X, C_Z and R are real,
-            // E_Y = i (F10 - F01) and C_Y = -i (M - M^T) / 2 imaginary, so the entries with
-            // one Y vanish and <E_Y, C_Y> = sum (F10 - F01) (M - M^T) / 2
+    for (int i = 0; i < 12; ++i) acc[i] = T(0);
+    team_for_2d<32, 4>(D, D, lane, [&](int r, int rp) {
+      if constexpr (elem_traits<E>::real) {
+        // a real state (no half-structured sites): E_X, E_Z, C_X, C_Z and R are real,
+        // E_Y = i (F10 - F01) and C_Y = -i (M - M^T) / 2 imaginary, so the entries with
+        // one Y vanish and <E_Y, C_Y> = sum (F10 - F01) (M - M^T) / 2
+        const E f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
+        const E f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
+        const E ex = f01 + f10, ey = f10 - f01, ez = f00 - f11;
+        const E rr = R[r * CS + rp];
+        acc[3] = fma(ex, rr, acc[3]);
+        acc[11] = fma(ez, rr, acc[11]);
+        if (C) {
+            const E m1 = C[r * CS + rp], m2 = C[rp * CS + r];
+            const E yx = T(0.5) * (m1 + m2), yy = T(0.5) * (m1 - m2), yz = C[MAT + r * CS + rp];
+            acc[0] = fma(ex, yx, acc[0]);
+            acc[2] = fma(ex, yz, acc[2]);
+            acc[5] = fma(ey, yy, acc[5]);
+            acc[8] = fma(ez, yx, acc[8]);
+            acc[10] = fma(ez, yz, acc[10]);
+        }
+      } else {
+        E e[3];
+        if (half) {
+            // compact F' (left_blocks): the one nonzero block at (r, r') is F_{s s'}
+            // with s = r >= h, s' = r' >= h; the same values as the full form
+            const E f = F[r * ZS + rp], z = ezero<E>();
+            const int s0 = r >= h, s1 = rp >= h;
+            e[0] = s0 != s1 ? f : z;                                                   // X
+            e[1] = s0 == s1 ? z : (s0 ? mk<T>(-f.im, f.re) : mk<T>(f.im, -f.re));      // Y
+            e[2] = s0 != s1 ? z : (s0 ? mk<T>(-f.re, -f.im) : f);                      // Z
+        } else {
             const E f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
             const E f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
-            const E ex = f01 + f10, ey = f10 - f01, ez = f00 - f11;
-            const E rr = R[r * CS + rp];
-            acc[3] = fma(ex, rr, acc[3]);
-            acc[11] = fma(ez, rr, acc[11]);
-            if (C) {
-                const E m1 = C[r * CS + rp], m2 = C[rp * CS + r];
-                const E yx = T(0.5) * (m1 + m2), yy = T(0.5) * (m1 - m2), yz = C[MAT + r * CS + rp];
-                acc[0] = fma(ex, yx, acc[0]);
-                acc[2] = fma(ex, yz, acc[2]);
-                acc[5] = fma(ey, yy, acc[5]);
-                acc[8] = fma(ez, yx, acc[8]);
-                acc[10] = fma(ez, yz, acc[10]);
-            }
-          } else {
-            E e[3];
-            if (half) {
-                // compact F' (left_blocks): the one nonzero block at (r, r') is F_{s s'}
-                // with s = r >= h, s' = r' >= h; the same values as the full form
-                const E f = F[r * ZS + rp], z = ezero<E>();
-                const int s0 = r >= h, s1 = rp >= h;
-                e[0] = s0 != s1 ? f : z;                                                   // X
-                e[1] = s0 == s1 ? z : (s0 ? mk<T>(-f.im, f.re) : mk<T>(f.im, -f.re));      // Y
-                e[2] = s0 != s1 ? z : (s0 ? mk<T>(-f.re, -f.im) : f);                      // Z
-            } else {
-                const E f00 = F[r * ZS + rp], f01 = F[r * ZS + D + rp];
-                const E f10 = F[(D + r) * ZS + rp], f11 = F[(D + r) * ZS + D + rp];
-                e[0] = f01 + f10;                                     // X
-                e[1] = mk<T>(f01.im - f10.im, f10.re - f01.re);       // Y: i (F10 - F01)
-                e[2] = f00 - f11;                                     // Z
-            }
-            E y[4];
-            y[3] = R[r * CS + rp];
-            if (C) {
-                const E m1 = C[r * CS + rp], m2 = conj(C[rp * CS + r]);
-                const E u = m1 + m2, v = m1 - m2;
-                y[0] = mk<T>(T(0.5) * u.re, T(0.5) * u.im);       // (M + M^H) / 2
-                y[1] = mk<T>(T(0.5) * v.im, T(-0.5) * v.re);      // (M - M^H) / (2i)
-                y[2] = C[MAT + r * CS + rp];
-            }
+            e[0] = f01 + f10;                                     // X
+            e[1] = mk<T>(f01.im - f10.im, f10.re - f01.re);       // Y: i (F10 - F01)
+            e[2] = f00 - f11;                                     // Z
+        }
+        E y[4];
+        y[3] = R[r * CS + rp];
+        if (C) {
+            const E m1 = C[r * CS + rp], m2 = conj(C[rp * CS + r]);
+            const E u = m1 + m2, v = m1 - m2;
+            y[0] = mk<T>(T(0.5) * u.re, T(0.5) * u.im);       // (M + M^H) / 2
+            y[1] = mk<T>(T(0.5) * v.im, T(-0.5) * v.re);      // (M - M^H) / (2i)
+            y[2] = C[MAT + r * CS + rp];
+        }
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    if (C || b == 3) acc[4 * a + b] = fma(-e[a].im, y[b].im, fma(e[a].re, y[b].re, acc[4 * a + b]));
-          }
-        });
+            for (int b = 0; b < 4; ++b)
+                if (C || b == 3) acc[4 * a + b] = fma(-e[a].im, y[b].im, fma(e[a].re, y[b].re, acc[4 * a + b]));
+      }
+    });
 #pragma unroll
-        for (int i = 0; i < 12; ++i) out[i] = warp_sum(acc[i]);
+    for (int i = 0; i < 12; ++i) out[i] = warp_sum(acc[i]);
+}
+
+// left_dots_warp run by warp 0 of a team, the sums handed to the other warps through red.
+template <typename E, int CHI, int NTHR>
+__device__ __forceinline__ void left_dots(const E* S, const E* C, const E* R, int D,
+                                          typename elem_traits<E>::scalar* out,
+                                          typename elem_traits<E>::scalar* red, int lane, bool half = false) {
+    if (lane < 32) {
+        left_dots_warp<E, CHI>(S, C, R, D, out, lane, half);
         if (NTHR > 32 && lane == 0)
 #pragma unroll
             for (int i = 0; i < 12; ++i) red[i] = out[i];
@@ -437,6 +445,26 @@ template <typename T>
 __device__ __forceinline__ void cp_async_elem(cx<T>* dst, const cx<T>* src) {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
     if constexpr (sizeof(cx<T>) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+// The real part alone (4 or 8 B) into a real element.
+template <typename T>
+__device__ __forceinline__ void cp_async_re(T* dst, const cx<T>* src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(&src->re) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(&src->re) : "memory");
+}
+// An element of E from global memory of the same type (4, 8 or 16 B).
+template <typename E>
+__device__ __forceinline__ void cp_async_same(E* dst, const E* src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if constexpr (sizeof(E) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+    else if constexpr (sizeof(E) == 8)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
@@ -510,7 +538,8 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
     }
 }
 
-// CTA i < n_images: the right environments of image i; with lenv, CTA n_images + i:
+// CTA i < n_images (after first_block is added): the right environments of image i;
+// with lenv, CTA n_images + i:
 // the left environments of image i when it is flagged META_LENV (the two chains are
 // independent and latency-bound, so one launch runs them side by side).
 // GMEM (bonds above 32): the workspace is a slice of global memory, env_bytes per CTA.
@@ -522,7 +551,8 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
                                                    const int32_t* __restrict__ bonds,
                                                    cx<T>* __restrict__ renv_c, int64_t renv_stride,
                                                    cx<T>* __restrict__ lenv_c,
-                                                   T* __restrict__ norm_out, unsigned char* __restrict__ gws) {
+                                                   T* __restrict__ norm_out, unsigned char* __restrict__ gws,
+                                                   int first_block) {
     using E = std::conditional_t<REAL, T, cx<T>>;
     using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
@@ -530,10 +560,12 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
     E* lenv = reinterpret_cast<E*>(lenv_c);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* raw = GMEM ? gws + (size_t)blockIdx.x * Lay::env_bytes : smem_raw;
-    // one warp per image and one image per CTA (block-wide syncs are warp syncs)
+    // one warp per image and one image per CTA (block-wide syncs are warp syncs);
+    // first_block = n_images: the left environments alone
     const int lane = threadIdx.x;
-    if ((int)blockIdx.x >= n_images) {
-        const int li = blockIdx.x - n_images;
+    const int bid = blockIdx.x + first_block;
+    if (bid >= n_images) {
+        const int li = bid - n_images;
         if (!lenv || li >= n_images) return;
         const ImageMeta ml = meta[li];
         if (ml.flags & META_LENV)
@@ -541,7 +573,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
                                reinterpret_cast<E*>(raw), lane);
         return;
     }
-    const int img = blockIdx.x;
+    const int img = bid;
     E* base = reinterpret_cast<E*>(raw);
     const bool half_img = (meta[img].flags & META_HALF) != 0;
     E* Abuf[2] = {base, base + 3 * MAT};   // site j in one, site j-1 arriving in the other

@@ -42,7 +42,7 @@ mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
     rk<<<b->any_lenv ? 2 * b->B : b->B, 32, smem, b->stream>>>(
         b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<cx<T>*>(b->renv), b->renv_stride,
-        reinterpret_cast<cx<T>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<T*>(b->norms), nullptr);
+        reinterpret_cast<cx<T>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<T*>(b->norms), nullptr, 0);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();
@@ -62,6 +62,12 @@ mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
 
 template <typename T>
 mps_status dispatch_pauli(mps_batch* b, void* out, bool diag) {
+    if constexpr (sizeof(T) == 4) {
+        // bonds up to 16: one sweep per image (pauli_sweep.cuh), where its buffers fit
+        bool taken = false;
+        const mps_status st = launch_pauli_sweep(b, out, diag, &taken);
+        if (taken || st != MPS_OK) return st;
+    }
     // a real state (paper ansatz) up to bond 32: real-element kernels
     if (sizeof(T) == 4 && b->real && b->chi_tpl <= 32) return launch_pauli_real(b, out, diag);
     switch (b->chi_tpl) {

@@ -16,6 +16,8 @@ circuit  per two-qubit step on theta = (2 Dl) x (2 Dr) with inner bond Dm:
 renv     per site                                 8 * (2 Dl Dr^2 + 2 Dl^2 Dr)
 pauli    per column unit: E_a and closings at its sites, the carried closing
          matrices through p - 1 sites per row     3 * 8 * (2 Dl Dr^2 + 2 Dl^2 Dr)
+sweep    per site of the per-image sweep (sweep_flops): E_a once, the closing sums,
+         and one stacked transfer of R and every carried (M, C_Z) pair
 
 Circuits without truncation and 2^L <= min(chi, padding, 16) take the
 operator-product path (ladder_mpo.cu): bond 2^L at every inner cut, the circuit
@@ -219,6 +221,65 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
     return f
 
 
+def sweep_flops(p: int, bonds, lenv: bool = False, half: bool = False, diag: bool = False) -> float:
+    """Flops of the per-image sweep Pauli kernel (pauli_sweep.cuh) for one image, step by
+    step as it runs: left blocks E_a of each site once (with L_k first when lenv), the
+    closing sums, and the stacked transfer of R and of every carried closing matrix
+    (M, C_Z), with the closings of the site formed from the R rows."""
+    n = p * p
+    ns = p + (1 if diag else 0)
+
+    def half_tr(i):
+        return half and i < n - 1 and bonds[i + 1] >= HALF_SPLIT_MIN
+
+    def half_at(i):
+        return half and i < n - 1 and bonds[i + 1] >= 2
+
+    def uses(o):
+        r, c = divmod(o, p)
+        u = []
+        if c >= 1:
+            u.append(o - 1)
+        if r >= 1:
+            u.append(o - p)
+        if diag and r >= 1 and c <= p - 2:
+            u.append(o - p + 1)
+        if diag and r >= 1 and c >= 1:
+            u.append(o - p - 1)
+        return u
+
+    f = 0.0
+    for k in range(n - 1, -1, -1):
+        Dl, Dr = bonds[k], bonds[k + 1]
+        row, col = divmod(k, p)
+        if half_at(k):   # compact F' (Dr x Dr over Dl), after T' = L A' (Dl x Dr over Dl)
+            f += 8.0 * Dr * Dr * Dl + (8.0 * Dl * Dl * Dr if lenv else 0.0)
+        else:            # the four blocks F_ss' (2Dr x 2Dr over Dl), after T = L A
+            f += 8.0 * 4 * Dr * Dr * Dl + (8.0 * Dl * Dl * 2 * Dr if lenv else 0.0)
+        sets = (col < p - 1) + (row < p - 1) + (diag and row < p - 1 and col < p - 1) + \
+            (diag and row < p - 1 and col >= 1)
+        f += 4.0 * Dr * Dr * (3 + 12 * sets)          # Re(E_a Y) sums
+        htr = half_tr(k)
+        K1 = Dr // 2 if htr else Dr
+        dg = k >= 1 and half_tr(k - 1) and Dl % 2 == 0
+        carried = [o for o in range(k + 1, min(k + ns - 1, n - 1) + 1) if uses(o) and min(uses(o)) < k]
+        f += 8.0 * 2 * (Dr + 2 * len(carried) * K1) * Dl * K1          # first product, both planes
+        f += 8.0 * Dl * Dl * 2 * K1                                      # R_{k-1}
+        for o in carried:
+            full = (not dg) or (k - 1) in uses(o)
+            f += 2 * 8.0 * Dl * Dl * (1.0 if full else 0.5) * 2 * K1
+        if k >= 1 and uses(k):
+            f += 8.0 * Dl * Dl * K1 + 8.0 * Dl * Dl * 2 * K1              # M_k, C_Z,k
+    return f
+
+
+def lenv_flops(bonds, half: bool = False) -> float:
+    """Left-environment chain of one image (renv_kernel's second half)."""
+    n = len(bonds) - 1
+    return sum(8.0 * (2 * bonds[j] ** 2 * bonds[j + 1] + 2 * bonds[j] * bonds[j + 1] ** 2)
+               * (0.5 if half and j < n - 1 else 1.0) for j in range(n))
+
+
 def padding(p: int, chi: int) -> int:
     """Site padding of an image (the library's layout rule)."""
     n = p * p
@@ -239,8 +300,12 @@ def operator_product_path(p: int, L: int, chi: int, ansatz: str = "ladder") -> b
     return 1 <= L <= 4 and (1 << L) <= min(padding(p, chi), chi, 16)
 
 
-def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder", dense: bool = False) -> dict:
-    """dense: count the operator-product path's contractions without the half-structure."""
+def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder", dense: bool = False,
+                kernel: str = "sweep") -> dict:
+    """dense: count the operator-product path's contractions without the half-structure.
+    kernel: the Pauli-cache kernel ("sweep": the per-image sweep, which forms the right
+    environments itself, so the environment launch runs only the left chains; "column":
+    the column walk after the right and left chains)."""
     n = p * p
     if operator_product_path(p, L, chi, ansatz):
         D = 1 << L
@@ -252,12 +317,14 @@ def image_flops(p: int, L: int, chi: int, ansatz: str = "ladder", dense: bool = 
                 circ += 32.0 * dl * dr
                 dl = dl if k == 0 else 2 * dl
                 dr = dr if k == n - 1 else 2 * dr
-        # environments: right (half-structured sites for the ladder) and left, in one launch
         half = ansatz == "ladder" and not dense
         # left chain: L A on the needed half, block-diagonal result (half the dense work)
-        lenv = sum(8.0 * (2 * bonds[j] ** 2 * bonds[j + 1] + 2 * bonds[j] * bonds[j + 1] ** 2)
-                   * (0.5 if half and j < n - 1 else 1.0) for j in range(n))
+        lenv = lenv_flops(bonds, half)
+        if kernel == "sweep":
+            return {"circuit": circ, "renv": lenv, "pauli": sweep_flops(p, bonds, lenv=True, half=half)}
         return {"circuit": circ, "renv": renv_flops(bonds, half) + lenv,
                 "pauli": pauli_flops(p, bonds, lenv=True, half=half)}
     _, bonds = circuit_schedule(n, L, chi, ansatz)
+    if kernel == "sweep":
+        return {"circuit": circuit_flops(n, L, chi, ansatz), "renv": 0.0, "pauli": sweep_flops(p, bonds)}
     return {"circuit": circuit_flops(n, L, chi, ansatz), "renv": renv_flops(bonds), "pauli": pauli_flops(p, bonds)}
