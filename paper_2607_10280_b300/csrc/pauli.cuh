@@ -309,19 +309,18 @@ __device__ __forceinline__ void left_blocks_env(const E* A, const E* Lg, E* S, i
         2 * Dr, 2 * Dr, Dl, [](int nn) { return nn; }, [F](int m, int sn, E v) { F[m * ZS + sn] = v; }, lane);
 }
 
-// <E_a, Y> for a = X, Y, Z (from the blocks F_{ss'} in S) and Y in {C_X, C_Y, C_Z, R}:
-// out[4(a-1) + y], with C_X, C_Y unpacked from M = C[0] and C_Z = C[MAT].  C may be
-// null (then only the R column is formed).  One warp (lane < 32) forms every sum in a
-// fixed order, so the bits of the result depend on neither the team size nor on which
-// warp runs it; every lane receives the sums.
+// <E_a, Y> for a = X, Y, Z (from the blocks F_{ss'} at F, row stride ZS) and Y in
+// {C_X, C_Y, C_Z, R}: out[4(a-1) + y], with C_X, C_Y unpacked from M = C[0] and
+// C_Z = C[MAT].  C may be null (then only the R column is formed).  One warp (lane < 32)
+// forms every sum in a fixed order, so the bits of the result depend on neither the team
+// size nor on which warp runs it; every lane receives the sums.
 template <typename E, int CHI>
-__device__ __forceinline__ void left_dots_warp(const E* S, const E* C, const E* R, int D,
+__device__ __forceinline__ void left_dots_warp(const E* F, int ZS, const E* C, const E* R, int D,
                                                typename elem_traits<E>::scalar* out, int lane,
                                                bool half = false) {
     using T = typename elem_traits<E>::scalar;
     using Lay = PauliLayout<E, CHI>;
-    constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    const E* F = S + CHI * ZS;
+    constexpr int CS = Lay::CS, MAT = Lay::MAT;
     const int h = D >> 1;
     T acc[12];
 #pragma unroll
@@ -389,7 +388,7 @@ __device__ __forceinline__ void left_dots(const E* S, const E* C, const E* R, in
                                           typename elem_traits<E>::scalar* out,
                                           typename elem_traits<E>::scalar* red, int lane, bool half = false) {
     if (lane < 32) {
-        left_dots_warp<E, CHI>(S, C, R, D, out, lane, half);
+        left_dots_warp<E, CHI>(S + CHI * PauliLayout<E, CHI>::ZS, PauliLayout<E, CHI>::ZS, C, R, D, out, lane, half);
         if (NTHR > 32 && lane == 0)
 #pragma unroll
             for (int i = 0; i < 12; ++i) red[i] = out[i];
@@ -474,28 +473,49 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Left environments of one image (a warp): L_0 = 1 and L_{k+1}[r][r'] =
 // sum_{l,l',s} conj(A_k[l][s][r]) L_k[l][l'] A_k[l'][s][r'], stored like the right
-// environments (L_k, D_k x D_k, at k * CHI * CHI of the image's block).
-template <typename E, int CHI>
+// environments (L_k, D_k x D_k, at k * CHI * CHI of the image's block).  At a
+// half-structured site the product formed on the way is the compact left block
+// F'_k[r][r'] = sum_{l,l'} conj(A_k[l][s(r)][r]) L_k[l][l'] A_k[l'][s(r')][r'] of the
+// Pauli kernels (left_blocks_env), of which L_{k+1} keeps the diagonal blocks; with fg
+// it is stored too (at k * CHI * CHI of fg).  ASYNC: site k+1 arrives by cp.async in a
+// second buffer while site k is contracted (shared-memory workspace only).
+template <typename E, int CHI, bool ASYNC = false>
 __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
                                            const cx<typename elem_traits<E>::scalar>* __restrict__ arena,
-                                           const int32_t* __restrict__ bonds, E* lg, E* base,
+                                           const int32_t* __restrict__ bonds, E* lg, E* fg, E* base,
                                            int lane) {
     using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    E* A = base;             // 2 MAT
+    E* Abuf[2] = {base, base + 3 * MAT + CHI * ZS};   // 2 MAT each (the second within env_bytes)
     E* Lm = base + 2 * MAT;  // MAT
     E* S = base + 3 * MAT;   // CHI rows of ZS
     const int n = mt.n, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
     const cx<typename elem_traits<E>::scalar>* sites = arena + mt.site_off;
+    auto prefetch = [=](int k, E* dstA) {
+        const auto* src = sites + (size_t)k * 2 * ld * ld;
+        team_for_2d<32, 4>(2 * bd[k], bd[k + 1], lane, [=](int r, int c) {
+            if constexpr (elem_traits<E>::real) cp_async_re(dstA + r * CS + c, src + r * ld + c);
+            else cp_async_same(dstA + r * CS + c, src + r * ld + c);
+        });
+        cp_async_commit();
+    };
     if (lane == 0) Lm[0] = eone<E>();
+    if (ASYNC && n > 0) prefetch(0, Abuf[0]);
     __syncwarp();
     const bool half_img = (mt.flags & META_HALF) != 0;
     for (int k = 0; k < n; ++k) {
         const int Dl = bd[k], Dr = bd[k + 1];
         E* dst = lg + (size_t)k * CHI * CHI;
+        E* A = ASYNC ? Abuf[k & 1] : Abuf[0];
         team_for_2d<32, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
-        load_site_p<E, CS, 32>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
+        if constexpr (ASYNC) {
+            cp_async_wait_all();
+            __syncwarp();
+            if (k + 1 < n) prefetch(k + 1, Abuf[(k + 1) & 1]);
+        } else {
+            load_site_p<E, CS, 32>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
+        }
         __syncwarp();
         if (half_img && k < n - 1 && Dr >= 2) {
             // half-structured site: L A is needed only at (s, r) with r in half s
@@ -512,9 +532,13 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
             __syncwarp();
             {
                 using Tl = Tile<E, CHI, CHI, 32>;
+                E* fk = fg ? fg + (size_t)k * CHI * CHI : nullptr;
                 team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
                     A, off, 2 * CS, 0, S, [](int nn) { return nn; }, ZS, 0, Dr, Dr, Dl, [](int nn) { return nn; },
-                    [Lm, h](int r, int sn, E v) { Lm[r * CS + sn] = (r >= h) == (sn >= h) ? v : ezero<E>(); }, lane);
+                    [Lm, h, fk](int r, int sn, E v) {
+                        Lm[r * CS + sn] = (r >= h) == (sn >= h) ? v : ezero<E>();
+                        if (fk) fk[r * CHI + sn] = v;
+                    }, lane);
             }
             __syncwarp();
             continue;
@@ -541,7 +565,8 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
 // CTA i < n_images (after first_block is added): the right environments of image i;
 // with lenv, CTA n_images + i:
 // the left environments of image i when it is flagged META_LENV (the two chains are
-// independent and latency-bound, so one launch runs them side by side).
+// independent and latency-bound, so one launch runs them side by side), and with
+// fblk the compact left blocks of its half-structured sites (lenv_image).
 // GMEM (bonds above 32): the workspace is a slice of global memory, env_bytes per CTA.
 // REAL: a real state (every amplitude real): real elements, environments stored as
 // reals in the same buffers.
@@ -552,7 +577,7 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
                                                    cx<T>* __restrict__ renv_c, int64_t renv_stride,
                                                    cx<T>* __restrict__ lenv_c,
                                                    T* __restrict__ norm_out, unsigned char* __restrict__ gws,
-                                                   int first_block) {
+                                                   int first_block, cx<T>* __restrict__ fblk_c) {
     using E = std::conditional_t<REAL, T, cx<T>>;
     using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
@@ -568,9 +593,10 @@ __global__ void __launch_bounds__(32) renv_kernel(const ImageMeta* __restrict__ 
         const int li = bid - n_images;
         if (!lenv || li >= n_images) return;
         const ImageMeta ml = meta[li];
+        E* fg = fblk_c ? reinterpret_cast<E*>(fblk_c) + (size_t)li * renv_stride : nullptr;
         if (ml.flags & META_LENV)
-            lenv_image<E, CHI>(ml, arena, bonds, lenv + (size_t)li * renv_stride,
-                               reinterpret_cast<E*>(raw), lane);
+            lenv_image<E, CHI, !GMEM>(ml, arena, bonds, lenv + (size_t)li * renv_stride, fg,
+                                      reinterpret_cast<E*>(raw), lane);
         return;
     }
     const int img = bid;

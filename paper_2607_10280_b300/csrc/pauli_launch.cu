@@ -42,7 +42,7 @@ mps_status launch_pauli(mps_batch* b, void* out, bool diag) {
     rk<<<b->any_lenv ? 2 * b->B : b->B, 32, smem, b->stream>>>(
         b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<cx<T>*>(b->renv), b->renv_stride,
-        reinterpret_cast<cx<T>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<T*>(b->norms), nullptr, 0);
+        reinterpret_cast<cx<T>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<T*>(b->norms), nullptr, 0, nullptr);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();

@@ -28,7 +28,7 @@ mps_status launch_large(mps_batch* b, void* out, bool diag) {
         b->meta_d, b->B, reinterpret_cast<const cx<T>*>(b->arena), b->bonds_d,
         reinterpret_cast<cx<T>*>(b->renv), b->renv_stride,
         reinterpret_cast<cx<T>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<T*>(b->norms),
-        static_cast<unsigned char*>(b->gws), 0);
+        static_cast<unsigned char*>(b->gws), 0, nullptr);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();

@@ -23,7 +23,7 @@ mps_status launch_real(mps_batch* b, void* out) {
     rk<<<b->any_lenv ? 2 * b->B : b->B, 32, Lay::env_bytes, b->stream>>>(
         b->meta_d, b->B, reinterpret_cast<const cx<float>*>(b->arena), b->bonds_d,
         reinterpret_cast<cx<float>*>(b->renv), b->renv_stride,
-        reinterpret_cast<cx<float>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<float*>(b->norms), nullptr, 0);
+        reinterpret_cast<cx<float>*>(b->any_lenv ? b->lenv : nullptr), reinterpret_cast<float*>(b->norms), nullptr, 0, nullptr);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());
     count_launch();

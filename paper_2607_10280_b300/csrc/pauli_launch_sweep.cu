@@ -24,9 +24,12 @@ mps_status launch_sweep(mps_batch* b, void* out, int ns, size_t smem) {
         auto rk = renv_kernel<float, CHI, false, REAL>;
         CUDA_TRY(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lp::env_bytes));
         timing_begin(b, KIND_RENV);
+        // left chains of the operator-product images, storing the compact left blocks of
+        // their half-structured sites in the (otherwise unused) right-environment buffer
         rk<<<b->B, 32, Lp::env_bytes, b->stream>>>(
             b->meta_d, b->B, reinterpret_cast<const cx<float>*>(b->arena), b->bonds_d, nullptr, b->renv_stride,
-            reinterpret_cast<cx<float>*>(b->lenv), reinterpret_cast<float*>(b->norms), nullptr, b->B);
+            reinterpret_cast<cx<float>*>(b->lenv), reinterpret_cast<float*>(b->norms), nullptr, b->B,
+            reinterpret_cast<cx<float>*>(b->renv));
         timing_end(b);
         CUDA_TRY(cudaGetLastError());
         count_launch();
@@ -36,7 +39,8 @@ mps_status launch_sweep(mps_batch* b, void* out, int ns, size_t smem) {
     timing_begin(b, KIND_PAULI);
     sk<<<b->B, SWEEP_THREADS, smem, b->stream>>>(
         b->meta_d, b->B, reinterpret_cast<const cx<float>*>(b->arena), b->bonds_d,
-        reinterpret_cast<const cx<float>*>(b->any_lenv ? b->lenv : nullptr), b->renv_stride,
+        reinterpret_cast<const cx<float>*>(b->any_lenv ? b->lenv : nullptr),
+        reinterpret_cast<const cx<float>*>(b->any_lenv ? b->renv : nullptr), b->renv_stride,
         reinterpret_cast<float*>(b->norms), reinterpret_cast<float*>(out), ns, b->n_max, b->status_d);
     timing_end(b);
     CUDA_TRY(cudaGetLastError());

@@ -11,7 +11,8 @@
 //          close further left, each carried to the bond (k, k+1): origins k+1 .. k+p
 //          with the H+V pairs, k+1 .. k+p+1 with the diagonal sets as well (slot o mod ns),
 // and then
-//   1. forms the left blocks E_a of site k (with L_k for a META_LENV image);
+//   1. forms the left blocks E_a of site k (with L_k for a META_LENV image; at its
+//      half-structured sites the left chain stored them, F'_k, on its way);
 //   2. closes, one warp per closing, <E_a, R_k> (the single-site terms) and the pairs
 //      (k, o) for o = k+1 (horizontal), k+p (vertical), k+p+1 and k+p-1 (the diagonal
 //      sets), with the closings of o as carried;
@@ -93,8 +94,8 @@ __device__ __forceinline__ int sweep_div(int t, int m) { return (t * m) >> 16; }
 template <typename T, int CHI, int NTHR, bool DIAG, bool REAL, bool HALF>
 __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16) ? 3 : 1) pauli_sweep_kernel(
         const ImageMeta* __restrict__ meta, int n_images, const cx<T>* __restrict__ arena,
-        const int32_t* __restrict__ bonds, const cx<T>* __restrict__ lenv_c, int64_t env_stride,
-        T* __restrict__ norms, T* __restrict__ out, int ns, int n_max, int* status) {
+        const int32_t* __restrict__ bonds, const cx<T>* __restrict__ lenv_c, const cx<T>* __restrict__ fblk_c,
+        int64_t env_stride, T* __restrict__ norms, T* __restrict__ out, int ns, int n_max, int* status) {
     using E = std::conditional_t<REAL, T, cx<T>>;
     using Lay = SweepLayout<E, CHI, HALF>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT;
@@ -130,6 +131,8 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16) ? 3 : 1) p
     const cx<T>* sites = arena + mt.site_off;
     const E* lenv = reinterpret_cast<const E*>(lenv_c);
     const E* lgb = (lenv && (mt.flags & META_LENV)) ? lenv + (size_t)img * env_stride : nullptr;
+    // the compact left blocks F'_k the left chain stored for the half-structured sites
+    const E* fgb = (lgb && fblk_c) ? reinterpret_cast<const E*>(fblk_c) + (size_t)img * env_stride : nullptr;
     // site k into A buffer (n-1-k) % 2 and L_k into Ls, by cp.async (real elements take
     // the real parts of the complex64 storage)
     auto prefetch_site = [=](int k) {
@@ -140,11 +143,15 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16) ? 3 : 1) p
             else cp_async_same(dstA + r * CS + c, src + r * ld + c);
         });
     };
-    auto prefetch_lenv = [=](int k) {
-        const E* src = lgb + (size_t)k * CHI * CHI;
-        team_for_2d<NTHR, 4>(bd[k], bd[k], tid, [=](int r, int c) { cp_async_same(Ls + r * CS + c, src + r * CHI + c); });
-    };
     auto half_at = [half_img, n, bd](int i) { return half_img && i < n - 1 && bd[i + 1] >= 2; };
+    // site k's left blocks come ready from the left chain (F'_k), or are formed here from L_k
+    auto fpre = [=](int k) { return fgb != nullptr && half_at(k); };
+    auto prefetch_lenv = [=](int k) {
+        const bool f = fpre(k);
+        const E* src = (f ? fgb : lgb) + (size_t)k * CHI * CHI;
+        const int D = f ? bd[k + 1] : bd[k];
+        team_for_2d<NTHR, 4>(D, D, tid, [=](int r, int c) { cp_async_same(Ls + r * CS + c, src + r * CHI + c); });
+    };
     auto half_tr = [half_img, n, bd](int i) { return half_img && i < n - 1 && bd[i + 1] >= HALF_SPLIT_MIN; };
     T* outp = out + (size_t)(DIAG ? mt.pair_off_d : mt.pair_off) * 16;
     const int nh = p * (p - 1);
@@ -240,34 +247,25 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16) ? 3 : 1) p
         // site k-1 into the other A buffer (last read by the transfer through site k+1)
         if (k >= 1) prefetch_site(k - 1);
         cp_async_commit();
-        // 1. left blocks of site k (S is free here)
-        left_blocks_env<E, CHI, NTHR, CS>(A, lgb ? Ls : nullptr, S, Dl, Dr, tid, half_at(k));
-        __syncthreads();
-        // L_k has been read: L_{k-1} into its buffer
-        if (lgb && k >= 1) prefetch_lenv(k - 1);
-        cp_async_commit();
-        // 2. closings, one warp per set
+        // 1. left blocks of site k: F'_k as stored by the left chain (in Ls), or formed here
+        //    into S (from L_k in Ls, or the identity)
+        const bool fp = fpre(k);
+        if (!fp) {
+            left_blocks_env<E, CHI, NTHR, CS>(A, lgb ? Ls : nullptr, S, Dl, Dr, tid, half_at(k));
+            __syncthreads();
+        }
+        // 2. closings, one warp per set (sums into dots, written out after the next barrier)
         const int nsets = tab[SW_NSETS];
         for (int set = warp; set < nsets; set += NTHR / 32) {
             const E* C = set == 0 ? nullptr : base + slot_of(tab[SW_ORIG + set - 1]);
             T d[12];
-            left_dots_warp<E, CHI>(S, C, R, Dr, d, lane, half_at(k));
+            left_dots_warp<E, CHI>(fp ? Ls : S + CHI * Lay::ZS, fp ? CS : Lay::ZS, C, R, Dr, d, lane, half_at(k));
             if (lane == 0)
 #pragma unroll
                 for (int i = 0; i < 12; ++i) dots[12 * set + i] = d[i];
         }
-        __syncthreads();
-        if (tid < 3) singles[3 * k + tid] = dots[4 * tid + 3];
-        if (tid < 16 * (nsets - 1)) {
-            const int set = 1 + (tid >> 4), e = tid & 15, a = e >> 2, b = e & 3;
-            const int o = tab[SW_ORIG + set - 1];
-            T v;
-            if (a == 0 && b == 0) v = T(1);
-            else if (b == 0) v = dots[4 * (a - 1) + 3];
-            else if (a == 0) v = singles[3 * o + b - 1];
-            else v = dots[12 * set + 4 * (a - 1) + (b - 1)];
-            outp[(size_t)tab[SW_PAIR + set - 1] * 16 + e] = v;
-        }
+        // the first product overwrites S (which holds the blocks unless they came stored)
+        if (!fp) __syncthreads();
         // 3. transfer through site k
         const int g1 = tab[SW_NG1];
         const int Ms = Dr + (g1 - 1) * K1;
@@ -299,6 +297,20 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16) ? 3 : 1) p
                 [](int nn) { return nn; }, [=](int m, int sn, E v) { S[s * plane + m * CS + sn] = v; }, gl);
         }
         __syncthreads();
+        // Ls has been read: the left blocks (or L) of site k-1 into it
+        if (lgb && k >= 1) prefetch_lenv(k - 1);
+        cp_async_commit();
+        if (tid < 3) singles[3 * k + tid] = dots[4 * tid + 3];
+        if (tid < 16 * (nsets - 1)) {
+            const int set = 1 + (tid >> 4), e = tid & 15, a = e >> 2, b = e & 3;
+            const int o = tab[SW_ORIG + set - 1];
+            T v;
+            if (a == 0 && b == 0) v = T(1);
+            else if (b == 0) v = dots[4 * (a - 1) + 3];
+            else if (a == 0) v = singles[3 * o + b - 1];
+            else v = dots[12 * set + 4 * (a - 1) + (b - 1)];
+            outp[(size_t)tab[SW_PAIR + set - 1] * 16 + e] = v;
+        }
         {
             // second product, rows l in half q of the left bond (one half of the CTA each)
             const int nf = tab[SW_NF], nd = tab[SW_ND];

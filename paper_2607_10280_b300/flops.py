@@ -223,9 +223,10 @@ def pauli_flops(p: int, bonds, lenv: bool = False, half: bool = False) -> float:
 
 def sweep_flops(p: int, bonds, lenv: bool = False, half: bool = False, diag: bool = False) -> float:
     """Flops of the per-image sweep Pauli kernel (pauli_sweep.cuh) for one image, step by
-    step as it runs: left blocks E_a of each site once (with L_k first when lenv), the
-    closing sums, and the stacked transfer of R and of every carried closing matrix
-    (M, C_Z), with the closings of the site formed from the R rows."""
+    step as it runs: left blocks E_a of each site once (with L_k first when lenv; stored
+    by the left chain at half-structured sites), the closing sums, and the stacked
+    transfer of R and of every carried closing matrix (M, C_Z), with the closings of the
+    site formed from the R rows."""
     n = p * p
     ns = p + (1 if diag else 0)
 
@@ -252,8 +253,10 @@ def sweep_flops(p: int, bonds, lenv: bool = False, half: bool = False, diag: boo
     for k in range(n - 1, -1, -1):
         Dl, Dr = bonds[k], bonds[k + 1]
         row, col = divmod(k, p)
-        if half_at(k):   # compact F' (Dr x Dr over Dl), after T' = L A' (Dl x Dr over Dl)
-            f += 8.0 * Dr * Dr * Dl + (8.0 * Dl * Dl * Dr if lenv else 0.0)
+        if half_at(k):
+            # compact F' (Dr x Dr over Dl): with left environments the left chain stores it
+            # on its way (lenv_flops), else formed here
+            f += 0.0 if lenv else 8.0 * Dr * Dr * Dl
         else:            # the four blocks F_ss' (2Dr x 2Dr over Dl), after T = L A
             f += 8.0 * 4 * Dr * Dr * Dl + (8.0 * Dl * Dl * 2 * Dr if lenv else 0.0)
         sets = (col < p - 1) + (row < p - 1) + (diag and row < p - 1 and col < p - 1) + \
