@@ -71,15 +71,16 @@ struct PauliLayout {
 
 // Register-tile shape for an M x N output (compile-time bounds) computed by NTHR
 // threads: MT x NT threads, TM x TN complex accumulators per thread, at most 48
-// (float) or 24 (double).
-template <typename E, int M_HINT, int N_HINT, int NTHR = 32>
+// (float) or 24 (double), or CAPX when given.
+template <typename E, int M_HINT, int N_HINT, int NTHR = 32, int CAPX = 0>
 struct Tile {
     using T = typename elem_traits<E>::scalar;
     static constexpr int MT = (NTHR == 32) ? ((M_HINT >= 2 * N_HINT) ? 8 : 4)
                                            : ((M_HINT >= 2 * N_HINT) ? 16 : (M_HINT * 2 > N_HINT ? 8 : 4));
     static constexpr int NT = NTHR / MT;
     // register tile cap; products of bonds above 32 (hints above 64) take small tiles
-    static constexpr int CAP = (M_HINT > 64 || N_HINT > 64) ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 48 : 24);
+    static constexpr int CAP = CAPX > 0 ? CAPX
+                               : (M_HINT > 64 || N_HINT > 64) ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 48 : 24);
     static constexpr int TM0 = (M_HINT + MT - 1) / MT;
     static constexpr int TM = TM0 < 1 ? 1 : (TM0 > CAP ? CAP : TM0);
     static constexpr int TN0 = (N_HINT + NT - 1) / NT;
@@ -478,15 +479,17 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // F'_k[r][r'] = sum_{l,l'} conj(A_k[l][s(r)][r]) L_k[l][l'] A_k[l'][s(r')][r'] of the
 // Pauli kernels (left_blocks_env), of which L_{k+1} keeps the diagonal blocks; with fg
 // it is stored too (at k * CHI * CHI of fg).  ASYNC: site k+1 arrives by cp.async in a
-// second buffer while site k is contracted (shared-memory workspace only).
-template <typename E, int CHI, bool ASYNC = false>
+// second buffer while site k is contracted (shared-memory workspace only).  A team of
+// NTHR threads (lane = its thread index) runs the chain.
+template <typename E, int CHI, bool ASYNC = false, int NTHR = 32>
 __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
                                            const cx<typename elem_traits<E>::scalar>* __restrict__ arena,
                                            const int32_t* __restrict__ bonds, E* lg, E* fg, E* base,
                                            int lane) {
     using Lay = PauliLayout<E, CHI>;
     constexpr int CS = Lay::CS, MAT = Lay::MAT, ZS = Lay::ZS;
-    E* Abuf[2] = {base, base + 3 * MAT + CHI * ZS};   // 2 MAT each (the second within env_bytes)
+    E* const A0 = base;                      // 2 MAT each (the second within env_bytes)
+    E* const A1 = base + 3 * MAT + CHI * ZS;
     E* Lm = base + 2 * MAT;  // MAT
     E* S = base + 3 * MAT;   // CHI rows of ZS
     const int n = mt.n, ld = mt.ld;
@@ -494,29 +497,29 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
     const cx<typename elem_traits<E>::scalar>* sites = arena + mt.site_off;
     auto prefetch = [=](int k, E* dstA) {
         const auto* src = sites + (size_t)k * 2 * ld * ld;
-        team_for_2d<32, 4>(2 * bd[k], bd[k + 1], lane, [=](int r, int c) {
+        team_for_2d<NTHR, 4>(2 * bd[k], bd[k + 1], lane, [=](int r, int c) {
             if constexpr (elem_traits<E>::real) cp_async_re(dstA + r * CS + c, src + r * ld + c);
             else cp_async_same(dstA + r * CS + c, src + r * ld + c);
         });
         cp_async_commit();
     };
     if (lane == 0) Lm[0] = eone<E>();
-    if (ASYNC && n > 0) prefetch(0, Abuf[0]);
-    __syncwarp();
+    if (ASYNC && n > 0) prefetch(0, A0);
+    tsync<NTHR>();
     const bool half_img = (mt.flags & META_HALF) != 0;
     for (int k = 0; k < n; ++k) {
         const int Dl = bd[k], Dr = bd[k + 1];
         E* dst = lg + (size_t)k * CHI * CHI;
-        E* A = ASYNC ? Abuf[k & 1] : Abuf[0];
-        team_for_2d<32, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
+        E* A = (ASYNC && (k & 1)) ? A1 : A0;
+        team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
         if constexpr (ASYNC) {
             cp_async_wait_all();
-            __syncwarp();
-            if (k + 1 < n) prefetch(k + 1, Abuf[(k + 1) & 1]);
+            tsync<NTHR>();
+            if (k + 1 < n) prefetch(k + 1, (k & 1) ? A0 : A1);
         } else {
-            load_site_p<E, CS, 32>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
+            load_site_p<E, CS, NTHR>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
         }
-        __syncwarp();
+        tsync<NTHR>();
         if (half_img && k < n - 1 && Dr >= 2) {
             // half-structured site: L A is needed only at (s, r) with r in half s
             // (T'[l][r] = sum_l' L[l][l'] A[2l'+s(r)][r]), and L_{k+1} is block diagonal
@@ -524,14 +527,14 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
             const int h = Dr >> 1;
             auto off = [h](int r) { return (r >= h ? CS : 0) + r; };
             {
-                using Tl = Tile<E, CHI, CHI, 32>;
+                using Tl = Tile<E, CHI, CHI, NTHR>;
                 team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
                     Lm, [](int l) { return l * CS; }, 1, 0, A, off, 2 * CS, 0, Dl, Dr, Dl,
                     [](int nn) { return nn; }, [S](int l, int sn, E v) { S[l * ZS + sn] = v; }, lane);
             }
-            __syncwarp();
+            tsync<NTHR>();
             {
-                using Tl = Tile<E, CHI, CHI, 32>;
+                using Tl = Tile<E, CHI, CHI, NTHR>;
                 E* fk = fg ? fg + (size_t)k * CHI * CHI : nullptr;
                 team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, true, 1>(
                     A, off, 2 * CS, 0, S, [](int nn) { return nn; }, ZS, 0, Dr, Dr, Dl, [](int nn) { return nn; },
@@ -540,25 +543,25 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
                         if (fk) fk[r * CHI + sn] = v;
                     }, lane);
             }
-            __syncwarp();
+            tsync<NTHR>();
             continue;
         }
         // S[l][s Dr + r] = sum_l' L[l][l'] A[2l'+s][r]
         {
-            using Tl = Tile<E, CHI, 2 * CHI, 32>;
+            using Tl = Tile<E, CHI, 2 * CHI, NTHR>;
             team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
                 Lm, [](int l) { return l * CS; }, 1, 0, A, [Dr](int nn) { return (nn / Dr) * CS + (nn % Dr); }, 2 * CS, 0,
                 Dl, 2 * Dr, Dl, [](int nn) { return nn; }, [S](int l, int sn, E v) { S[l * ZS + sn] = v; }, lane);
         }
-        __syncwarp();
+        tsync<NTHR>();
         // L'[r][r'] = sum_{l,s} conj(A[2l+s][r]) S[l][s Dr + r']
         {
-            using Tl = Tile<E, CHI, CHI, 32>;
+            using Tl = Tile<E, CHI, CHI, NTHR>;
             team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, 1>(
                 A, [](int r) { return r; }, 2 * CS, CS, S, [](int nn) { return nn; }, ZS, Dr, Dr, Dr, Dl,
                 [](int nn) { return nn; }, [Lm](int r, int sn, E v) { Lm[r * CS + sn] = v; }, lane);
         }
-        __syncwarp();
+        tsync<NTHR>();
     }
 }
 

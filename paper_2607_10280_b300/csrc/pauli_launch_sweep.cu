@@ -13,23 +13,26 @@ namespace {
 #define MPS_SWEEP_THREADS 128
 #endif
 constexpr int SWEEP_THREADS = MPS_SWEEP_THREADS;
+// threads per left chain
+#ifndef MPS_LENV_THREADS
+#define MPS_LENV_THREADS 64
+#endif
+constexpr int LENV_THREADS = MPS_LENV_THREADS;
 
 template <int CHI, bool DIAG, bool REAL, bool HALF>
 mps_status launch_sweep(mps_batch* b, void* out, int ns, size_t smem) {
     using E = std::conditional_t<REAL, float, cx<float>>;
     if (b->any_lenv) {
-        // the left environments of the operator-product images (the sweep forms the
-        // right ones itself)
+        // left chains of the operator-product images (the sweep forms the right
+        // environments itself), storing the compact left blocks of their half-structured
+        // sites in the otherwise unused right-environment buffer
         using Lp = PauliLayout<E, CHI>;
-        auto rk = renv_kernel<float, CHI, false, REAL>;
-        CUDA_TRY(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lp::env_bytes));
+        auto lk = lenv_kernel<float, CHI, LENV_THREADS, REAL>;
+        CUDA_TRY(cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lp::env_bytes));
         timing_begin(b, KIND_RENV);
-        // left chains of the operator-product images, storing the compact left blocks of
-        // their half-structured sites in the (otherwise unused) right-environment buffer
-        rk<<<b->B, 32, Lp::env_bytes, b->stream>>>(
-            b->meta_d, b->B, reinterpret_cast<const cx<float>*>(b->arena), b->bonds_d, nullptr, b->renv_stride,
-            reinterpret_cast<cx<float>*>(b->lenv), reinterpret_cast<float*>(b->norms), nullptr, b->B,
-            reinterpret_cast<cx<float>*>(b->renv));
+        lk<<<b->B, LENV_THREADS, Lp::env_bytes, b->stream>>>(
+            b->meta_d, b->B, reinterpret_cast<const cx<float>*>(b->arena), b->bonds_d,
+            reinterpret_cast<cx<float>*>(b->lenv), reinterpret_cast<cx<float>*>(b->renv), b->renv_stride);
         timing_end(b);
         CUDA_TRY(cudaGetLastError());
         count_launch();

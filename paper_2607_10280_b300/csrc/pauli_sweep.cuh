@@ -34,6 +34,14 @@
 
 namespace mpsano {
 
+// Register-tile caps (complex accumulators per thread) of the first and second product.
+#ifndef MPS_SWEEP_TILE1
+#define MPS_SWEEP_TILE1 16
+#endif
+#ifndef MPS_SWEEP_TILE2
+#define MPS_SWEEP_TILE2 24
+#endif
+
 // Carried-closing slots for images of side p: origins k+1 .. k+p are live at site k with
 // the H+V pairs (the last one closes there), one more with the diagonal sets.
 __host__ __device__ constexpr int sweep_slots(int p, bool diag) { return p + (diag ? 1 : 0); }
@@ -87,6 +95,26 @@ enum : int {
 // error t (m - 2^16 / d) / 2^16 < 1/32 <= 1/d never carries across an integer.
 __host__ __device__ __forceinline__ int sweep_recip(int d) { return (65536 + d - 1) / d; }
 __device__ __forceinline__ int sweep_div(int t, int m) { return (t * m) >> 16; }
+
+// Left chains of the META_LENV images for the sweep, one CTA of NTHR threads per image
+// (the environment kernel gives a chain one warp and runs it beside the right chain):
+// L_k into lenv and the compact left blocks F'_k of the half-structured sites into fblk,
+// env_stride elements per image.
+template <typename T, int CHI, int NTHR, bool REAL>
+__global__ void __launch_bounds__(NTHR) lenv_kernel(const ImageMeta* __restrict__ meta, int n_images,
+                                                    const cx<T>* __restrict__ arena,
+                                                    const int32_t* __restrict__ bonds, cx<T>* __restrict__ lenv_c,
+                                                    cx<T>* __restrict__ fblk_c, int64_t env_stride) {
+    using E = std::conditional_t<REAL, T, cx<T>>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int img = blockIdx.x;
+    if (img >= n_images) return;
+    const ImageMeta mt = meta[img];
+    if (!(mt.flags & META_LENV)) return;
+    lenv_image<E, CHI, true, NTHR>(mt, arena, bonds, reinterpret_cast<E*>(lenv_c) + (size_t)img * env_stride,
+                                   reinterpret_cast<E*>(fblk_c) + (size_t)img * env_stride,
+                                   reinterpret_cast<E*>(smem_raw), threadIdx.x);
+}
 
 // One CTA of NTHR threads per image.  lenv: left environments (META_LENV images), as
 // written by renv_kernel; norms: <psi|psi> per image (written here); out: the Pauli
@@ -280,7 +308,9 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16) ? 3 : 1) p
             // rows of its odd segment at the same plane offset
             const int s = grp;
             const int mk = sweep_recip(K1);
-            using Tl = Tile<E, 8 * CHI, CHI, HT>;
+            // tile rows: the R block and 2 (ns - 1) carried blocks of half a bond each at a
+            // half-structured site (7 CHI rows for 7 x 7 images with H+V pairs)
+            using Tl = Tile<E, (DIAG ? 8 : 7) * CHI, CHI, HT, MPS_SWEEP_TILE1>;
             const int* g1src = tab + SW_G1;
             team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 2>(
                 base,
@@ -331,7 +361,9 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16) ? 3 : 1) p
                 lp = q0 + t - db * g;
                 return nf + db;
             };
-            using Tl = Tile<E, CHI / 2, 9 * CHI, HT>;
+            // columns: R_{k-1}, one full carried pair and the rest diagonal-only (8 CHI for
+            // 7 x 7 images with H+V pairs)
+            using Tl = Tile<E, CHI / 2, (DIAG ? 9 : 8) * CHI, HT, MPS_SWEEP_TILE2>;
             team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 2, true, 2>(
                 A, [=](int l) { return 2 * (q0 + l) * CS; }, 1, CS + hs,
                 S, [=](int nn) { int lp; const int b = colb(nn, lp); return rowb[b] * CS + lp; }, CS, plane, Mq, Nq,
