@@ -36,8 +36,8 @@ PROFILED = {
               ("pauli_sweep.cuh", "pauli_launch_sweep.cu", "pauli.cuh", "linalg.cuh", "common.cuh")),
     "circuit": ("profiles/ladder_mpo_kernel_7x7_L4_chi16_b1024.md",
                 ("ladder_mpo.cu", "circuit.cuh", "common.cuh")),
-    "renv": ("profiles/renv_kernel_7x7_L4_chi16_b1024.md",
-             ("pauli.cuh", "pauli_launch.cu", "linalg.cuh", "common.cuh")),
+    "renv": ("profiles/lenv_kernel_7x7_L4_chi16_b1024.md",
+             ("pauli_sweep.cuh", "pauli_launch_sweep.cu", "pauli.cuh", "linalg.cuh", "common.cuh")),
     "chain": ("profiles/circuit_kernel_fp64_chain_7x7_L4_chi8_b1024.md",
               ("circuit.cuh", "circuit_launch.cuh", "linalg.cuh", "common.cuh")),
 }
