@@ -229,7 +229,7 @@ def run_ours(args):
     from paper_2607_10280_b300.build import build
     build()
     if PAULI_KERNEL != "default":
-        api.Batch.pauli_sweep_default = PAULI_KERNEL == "sweep"
+        api.Batch.pauli_kernel_default = PAULI_KERNEL
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -482,7 +482,7 @@ def _setup_torch():
     build()
     if PAULI_KERNEL != "default":
         from paper_2607_10280_b300 import api
-        api.Batch.pauli_sweep_default = PAULI_KERNEL == "sweep"
+        api.Batch.pauli_kernel_default = PAULI_KERNEL
     return torch
 
 

@@ -313,16 +313,24 @@ mps_status mps_set_layer_pipeline(mps_batch* batch, int32_t enable);
  * exactly that.  Takes effect at the next mps_apply_circuit. */
 mps_status mps_set_half_structure(mps_batch* batch, int32_t enable);
 
-/* Pauli-cache kernel choice under the mixed precisions at bonds up to 16 (enable != 0:
- * the per-image sweep, the default; 0: the column walk).  The sweep gives one CTA a
- * whole image and walks its chain from the last site to the first, carrying the right
- * environment and the closings of every pair still open (Sec. II.C, Eq. 5), so each
- * transfer through a site is one stacked product over all of them; the column walk
- * carries one column's closings per team and reads right environments from a separate
- * pass.  Both accumulate every sum in the same order: the results are bit-identical.
- * The sweep is skipped (column walk) where its shared memory would not fit a block.
- * Takes effect at the next mps_pauli_cache. */
-mps_status mps_set_pauli_sweep(mps_batch* batch, int32_t enable);
+/* Pauli-cache kernel choice under the mixed precisions at bonds up to 16:
+ *   MPS_PAULI_COLUMN  one team per (image, grid column) walking the column, after
+ *                     separate right and left environment chains;
+ *   MPS_PAULI_SWEEP   one CTA per image walking its chain from the last site to the
+ *                     first, carrying the right environment and the closings of every
+ *                     pair still open (Sec. II.C, Eq. 5), so each transfer through a
+ *                     site is one stacked product over all of them;
+ *   MPS_PAULI_AUTO    (default) the sweep for batches of equal-size images whose sites
+ *                     are all half-structured (operator-product ladder circuits), the
+ *                     column walk otherwise (it measured faster on dense sites and on
+ *                     mixed sizes).
+ * The two kernels accumulate every sum in the same order: the results are
+ * bit-identical.  A sweep that would not fit a block's shared memory runs the column
+ * walk.  Takes effect at the next mps_pauli_cache. */
+#define MPS_PAULI_COLUMN 0
+#define MPS_PAULI_SWEEP 1
+#define MPS_PAULI_AUTO 2
+mps_status mps_set_pauli_sweep(mps_batch* batch, int32_t mode);
 
 /* Real-element environment and Pauli kernels for a real state (enable != 0: on, the
  * default).  The paper ansatz's gates (H, R_Y(2 pi x - pi), CNOT) are real, so its state

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "MPS_OK", 1: "MPS_ERR_INVALID_ARG", 2: "MPS_ERR_OOM", 3: "MPS
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_orth64": 2, "mixed_fast": 3}
 ANSATZ = {"ladder": 0, "paper": 1}
 PAIR_SET = {"hv": 0, "hvd": 1}
+PAULI_KERNEL = {"column": 0, "sweep": 1, "auto": 2}
 
 
 class MpsError(RuntimeError):

@@ -9,7 +9,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import ANSATZ, PAIR_SET, PRECISION, check, lib, mps_circuit
+from ._lib import ANSATZ, PAIR_SET, PAULI_KERNEL, PRECISION, check, lib, mps_circuit
 
 
 def _stream_handle(stream) -> ctypes.c_void_p:
@@ -49,8 +49,8 @@ def launch_count() -> int:
 class Batch:
     """A batch of images, one MPS each (Sec. II.B, Eq. 3), on one CUDA stream."""
 
-    # Pauli-cache kernel of new batches (set_pauli_sweep): True = the library default
-    pauli_sweep_default = True
+    # Pauli-cache kernel of new batches (set_pauli_sweep): None = the library default
+    pauli_kernel_default = None
 
     def __init__(self, p, chi, precision: str = "mixed", stream=None):
         p = np.atleast_1d(np.asarray(p, dtype=np.int32))
@@ -69,8 +69,8 @@ class Batch:
         self._h = handle
         self.pixel_offsets = np.concatenate([[0], np.cumsum(self.n)])
         self.pair_offsets = np.concatenate([[0], np.cumsum([pair_count(int(q)) for q in p])])
-        if not Batch.pauli_sweep_default:
-            self.set_pauli_sweep(False)
+        if Batch.pauli_kernel_default is not None:
+            self.set_pauli_sweep(Batch.pauli_kernel_default)
 
     def reshape(self, p, chi):
         """New image list for this batch, reusing its device memory when it fits."""
@@ -168,10 +168,16 @@ class Batch:
         mixed precisions); results agree with the complex kernels to rounding."""
         check(lib().mps_set_real_arithmetic(self._h, 1 if enable else 0))
 
-    def set_pauli_sweep(self, enable: bool = True):
-        """Per-image sweep Pauli kernel (default) or the column walk, bonds up to 16 under
-        the mixed precisions; the two give bit-identical caches."""
-        check(lib().mps_set_pauli_sweep(self._h, 1 if enable else 0))
+    def set_pauli_sweep(self, mode="auto"):
+        """Pauli-cache kernel at bonds up to 16 under the mixed precisions: "sweep" (one
+        sweep per image), "column" (the column walk) or "auto" (the default: the sweep for
+        equal-size half-structured batches); True / False stand for "sweep" / "column".
+        The kernels give bit-identical caches."""
+        if mode is True:
+            mode = "sweep"
+        elif mode is False:
+            mode = "column"
+        check(lib().mps_set_pauli_sweep(self._h, PAULI_KERNEL[mode]))
 
     def set_timing(self, enable: bool = True):
         check(lib().mps_set_timing(self._h, 1 if enable else 0))

@@ -60,7 +60,7 @@ struct mps_batch {
     bool half_structure = true;            // exploit half-structured sites (META_HALF)
     bool real = false;                     // the last circuit's state is real (paper ansatz)
     bool real_allowed = true;              // real-element kernels for real states (mps_set_real_arithmetic)
-    bool pauli_sweep = true;               // per-image sweep Pauli kernel where it applies (mps_set_pauli_sweep)
+    int pauli_sweep = MPS_PAULI_AUTO;      // Pauli-cache kernel choice (mps_set_pauli_sweep)
     int L_max = 0;                         // most layers of any image in the last circuit
     // images of the next circuit launch: run_order[0 .. run_count), and whether the
     // layer-pipelined kernel runs them
@@ -165,7 +165,7 @@ mps_status launch_pauli_real(mps_batch* b, void* out, bool diag);
 mps_status ensure_gws(mps_batch* b, size_t bytes);
 mps_status launch_pauli_mixed(mps_batch* b, void* out, bool diag = false);
 // Left environments and the per-image sweep Pauli kernel (mixed precisions, bonds up
-// to 16, b->pauli_sweep); *taken = false (and nothing launched) where it does not apply.
+// to 16, per b->pauli_sweep); *taken = false (and nothing launched) where it does not apply.
 mps_status launch_pauli_sweep(mps_batch* b, void* out, bool diag, bool* taken);
 
 }  // namespace mpsano

@@ -605,9 +605,11 @@ mps_status mps_set_half_structure(mps_batch* b, int32_t enable) {
     return MPS_OK;
 }
 
-mps_status mps_set_pauli_sweep(mps_batch* b, int32_t enable) {
+mps_status mps_set_pauli_sweep(mps_batch* b, int32_t mode) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
-    b->pauli_sweep = enable != 0;
+    if (mode != MPS_PAULI_COLUMN && mode != MPS_PAULI_SWEEP && mode != MPS_PAULI_AUTO)
+        return fail(MPS_ERR_INVALID_ARG, "Pauli kernel mode %d (0, 1 or 2)", mode);
+    b->pauli_sweep = mode;
     return MPS_OK;
 }
 

@@ -170,7 +170,7 @@ extern "C" mps_status mps_pauli_cache_noalloc(int32_t n_images, int32_t p, int32
     b.run_order = nullptr;
     b.run_count = n_images;
     b.use_wave = false;
-    b.pauli_sweep = false;   // the column-walk Pauli kernel: its environments fit the scratch as laid out
+    b.pauli_sweep = MPS_PAULI_COLUMN;   // the column walk: its environments fit the scratch as laid out
 
     const int threads = 128;
     const int work = std::max(n_images * p, n_images);

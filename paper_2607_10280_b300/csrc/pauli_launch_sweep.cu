@@ -81,9 +81,17 @@ mps_status try_sweep(mps_batch* b, void* out, int ns, bool* taken) {
 
 mps_status launch_pauli_sweep(mps_batch* b, void* out, bool diag, bool* taken) {
     *taken = false;
-    if (!b->pauli_sweep || b->B == 0) return MPS_OK;
-    int p_max = 1;
-    for (const ImageMeta& m : b->meta_h) p_max = std::max(p_max, (int)m.p);
+    if (b->pauli_sweep == MPS_PAULI_COLUMN || b->B == 0) return MPS_OK;
+    int p_max = 1, p_min = 1 << 30;
+    for (const ImageMeta& m : b->meta_h) {
+        p_max = std::max(p_max, (int)m.p);
+        p_min = std::min(p_min, (int)m.p);
+    }
+    // the automatic choice: batches of equal-size half-structured images (operator-product
+    // ladder images), where the sweep's stacked products and stored left blocks pay; the
+    // column walk measured faster on dense sites (fewer sweep CTAs fit an SM) and on
+    // mixed sizes (slots sized for the largest image, whose chain sets the time)
+    if (b->pauli_sweep == MPS_PAULI_AUTO && (!b->all_half || p_min != p_max)) return MPS_OK;
     const int ns = sweep_slots(p_max, diag);
     switch (b->chi_tpl) {
         case 4: return diag ? try_sweep<4, true>(b, out, ns, taken) : try_sweep<4, false>(b, out, ns, taken);
