@@ -93,7 +93,7 @@ WORKLOAD = {"workload": "7x7 garment-like images (49 qubits), ladder ansatz L=4,
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400, help="timed steps (400 headline steps take about 1 s)")
+    ap.add_argument("--steps", type=int, default=600, help="timed steps (600 headline steps take about 1.1 s)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
