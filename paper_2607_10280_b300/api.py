@@ -26,6 +26,13 @@ def pair_count(p: int, pair_set: str = "hv") -> int:
     return int(lib().mps_pair_count(int(p), PAIR_SET[pair_set]))
 
 
+def _pair_offsets(p: np.ndarray, pair_set: str = "hv") -> np.ndarray:
+    """Prefix sums of the images' pair counts (the library's count, once per distinct side)."""
+    sides, inv = np.unique(p, return_inverse=True)
+    counts = np.array([pair_count(int(q), pair_set) for q in sides], dtype=np.int64)
+    return np.concatenate([[0], np.cumsum(counts[inv.reshape(-1)])])
+
+
 ROUTES = ("operator_product", "layer_pipelined", "sequential", "sequential_complex128")
 
 
@@ -68,7 +75,8 @@ class Batch:
             _stream_handle(self.stream), ctypes.byref(handle)))
         self._h = handle
         self.pixel_offsets = np.concatenate([[0], np.cumsum(self.n)])
-        self.pair_offsets = np.concatenate([[0], np.cumsum([pair_count(int(q)) for q in p])])
+        self._pair_offs = {"hv": _pair_offsets(p, "hv")}
+        self.pair_offsets = self._pair_offs["hv"]
         if Batch.pauli_kernel_default is not None:
             self.set_pauli_sweep(Batch.pauli_kernel_default)
 
@@ -81,7 +89,8 @@ class Batch:
         self.n_images, self.p, self.chi = len(p), p, chi_arr
         self.n = p.astype(np.int64) ** 2
         self.pixel_offsets = np.concatenate([[0], np.cumsum(self.n)])
-        self.pair_offsets = np.concatenate([[0], np.cumsum([pair_count(int(q)) for q in p])])
+        self._pair_offs = {"hv": _pair_offsets(p, "hv")}
+        self.pair_offsets = self._pair_offs["hv"]
 
     def reserve(self, L_max: int):
         """Allocate every buffer a circuit of up to L_max layers may need on this layout
@@ -125,7 +134,9 @@ class Batch:
         check(lib().mps_apply_circuit(self._h, _ptr(pixels), ctypes.byref(c)))
 
     def pair_offsets_for(self, pair_set: str = "hv") -> np.ndarray:
-        return np.concatenate([[0], np.cumsum([pair_count(int(q), pair_set) for q in self.p])])
+        if pair_set not in self._pair_offs:
+            self._pair_offs[pair_set] = _pair_offsets(self.p, pair_set)
+        return self._pair_offs[pair_set]
 
     def pauli_cache(self, out: torch.Tensor = None, pair_set: str = "hv") -> torch.Tensor:
         """Pauli cache [sum m_i][16] (Sec. II.C, Eq. 5), float64 (fp64) or float32.

@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -648,14 +649,28 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
     //  - everything else: the sequential kernel in the batch's own precision.
     // an image whose circuit needs a bond above its site padding (above 32) gets a
     // larger padding: the batch is laid out again (its state is reset by this call anyway)
+    // An image's plan depends on its shape alone (sites, layers, cap, padding; the
+    // ansatz and precision are the call's), and a batch holds few distinct shapes: each
+    // is planned once per call (n < 2^20, L <= 64, chi < 2^20, ld < 2^16).
+    auto shape_key = [](int n, int L, int chi, int ld) {
+        return (uint64_t)(uint32_t)n | (uint64_t)(uint32_t)L << 20 | (uint64_t)(uint32_t)chi << 28 |
+               (uint64_t)(uint32_t)ld << 48;
+    };
+    std::unordered_map<uint64_t, int> bonds_memo;
+    std::unordered_map<uint64_t, ImagePlan> plan_memo;
     {
         std::vector<int32_t> need(b->B, 0);
         bool grow_ld = false;
         for (int i = 0; i < b->B; ++i) {
             const ImageMeta& m = b->meta_h[i];
             const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
-            bool t = false;
-            const int bi = dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t);
+            const uint64_t key = shape_key(m.n, L, m.chi, 0);
+            auto it = bonds_memo.find(key);
+            if (it == bonds_memo.end()) {
+                bool t = false;
+                it = bonds_memo.emplace(key, dry_run_bonds(m.n, L, m.chi, circ->ansatz, &t)).first;
+            }
+            const int bi = it->second;
             need[i] = std::max(bi, m.ld);
             if (bi > m.ld && bi <= MPS_BOND_LIMIT) grow_ld = true;
         }
@@ -678,7 +693,11 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         ImageMeta& m = b->meta_h[i];
         const int L = circ->L_per_image ? circ->L_per_image[i] : circ->L;
         if (m.L != L) { m.L = L; b->meta_dirty = true; }
-        const ImagePlan pl = plan_image(m.n, L, m.chi, m.ld, circ->ansatz, b->prec, b->layer_pipeline);
+        const uint64_t key = shape_key(m.n, L, m.chi, m.ld);
+        auto it = plan_memo.find(key);
+        if (it == plan_memo.end())
+            it = plan_memo.emplace(key, plan_image(m.n, L, m.chi, m.ld, circ->ansatz, b->prec, b->layer_pipeline)).first;
+        const ImagePlan pl = it->second;
         const bool t = pl.lossy;
         const int bi = pl.bond;
         if (bi > m.ld) return fail(MPS_ERR_UNSUPPORTED, "image %d reaches bond %d > padding %d", i, bi, m.ld);

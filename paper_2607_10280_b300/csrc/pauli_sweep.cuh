@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NTHR) lenv_kernel(const ImageMeta* __restrict_
 // written by renv_kernel; norms: <psi|psi> per image (written here); out: the Pauli
 // cache; ns, n_max: the slots and the most sites of any image the launch was sized for.
 template <typename T, int CHI, int NTHR, bool DIAG, bool REAL, bool HALF>
-__global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16) ? 3 : 1) pauli_sweep_kernel(
+__global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 && CHI <= 16 && NTHR <= 128) ? 3 : 1) pauli_sweep_kernel(
         const ImageMeta* __restrict__ meta, int n_images, const cx<T>* __restrict__ arena,
         const int32_t* __restrict__ bonds, const cx<T>* __restrict__ lenv_c, const cx<T>* __restrict__ fblk_c,
         int64_t env_stride, T* __restrict__ norms, T* __restrict__ out, int ns, int n_max, int* status) {
