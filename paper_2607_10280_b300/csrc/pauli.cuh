@@ -495,6 +495,9 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
     const int n = mt.n, ld = mt.ld;
     const int32_t* bd = bonds + mt.bond_off;
     const cx<typename elem_traits<E>::scalar>* sites = arena + mt.site_off;
+    const bool half_img = (mt.flags & META_HALF) != 0;
+    // site k is half-structured: row 2l+s of A_k is zero outside column half s
+    auto half_site = [=](int k) { return half_img && k < n - 1 && bd[k + 1] >= 2; };
     auto prefetch = [=](int k, E* dstA) {
         const auto* src = sites + (size_t)k * 2 * ld * ld;
         team_for_2d<NTHR, 4>(2 * bd[k], bd[k + 1], lane, [=](int r, int c) {
@@ -506,12 +509,13 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
     if (lane == 0) Lm[0] = eone<E>();
     if (ASYNC && n > 0) prefetch(0, A0);
     tsync<NTHR>();
-    const bool half_img = (mt.flags & META_HALF) != 0;
     for (int k = 0; k < n; ++k) {
         const int Dl = bd[k], Dr = bd[k + 1];
         E* dst = lg + (size_t)k * CHI * CHI;
         E* A = (ASYNC && (k & 1)) ? A1 : A0;
-        team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
+        // L_k (with fg, a half-structured site keeps F'_k instead, which is what is read there)
+        if (!(fg && half_site(k)))
+            team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
         if constexpr (ASYNC) {
             cp_async_wait_all();
             tsync<NTHR>();
@@ -520,13 +524,28 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
             load_site_p<E, CS, NTHR>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
         }
         tsync<NTHR>();
-        if (half_img && k < n - 1 && Dr >= 2) {
+        if (half_site(k)) {
             // half-structured site: L A is needed only at (s, r) with r in half s
             // (T'[l][r] = sum_l' L[l][l'] A[2l'+s(r)][r]), and L_{k+1} is block diagonal
             // over the two halves (zero between them, as the full form gives)
             const int h = Dr >> 1;
             auto off = [h](int r) { return (r >= h ? CS : 0) + r; };
-            {
+            if (k >= 1 && Dl >= 2) {
+                // the previous site was half-structured too, so L_k is block diagonal over
+                // the halves of its bond: row l of T' sums over the l' of its own half only
+                // (the zero block adds nothing); one half of the team per half of the rows
+                constexpr int HT = NTHR >= 64 ? NTHR / 2 : NTHR;
+                using Tl = Tile<E, CHI / 2, CHI, HT>;
+                const int g = Dl >> 1;
+                for (int q = NTHR >= 64 ? lane / HT : 0; q < 2; q += NTHR >= 64 ? 2 : 1) {
+                    const int q0 = q ? g : 0, Mq = q ? Dl - g : g;
+                    team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
+                        Lm, [q0](int l) { return (q0 + l) * CS + q0; }, 1, 0, A,
+                        [off, q0](int r) { return off(r) + q0 * 2 * CS; }, 2 * CS, 0, Mq, Dr, Mq,
+                        [](int nn) { return nn; }, [S, q0](int l, int sn, E v) { S[(q0 + l) * ZS + sn] = v; },
+                        lane & (HT - 1));
+                }
+            } else {
                 using Tl = Tile<E, CHI, CHI, NTHR>;
                 team_gemm<E, Tl::MT, Tl::NT, Tl::TM, Tl::TN, 1, false, 1>(
                     Lm, [](int l) { return l * CS; }, 1, 0, A, off, 2 * CS, 0, Dl, Dr, Dl,
