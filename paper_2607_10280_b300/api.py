@@ -257,34 +257,49 @@ class Pipeline:
     Every step copies the pixels from (pinned) host memory to the device, runs the
     circuit, the Pauli cache, the ANO features and the linear layer, and copies the
     Pauli cache, the features and the reconstruction back to pinned host buffers.
-    Uploads and downloads run on two copy streams of their own and the kernels on the
-    compute stream, with `depth` sets of device and host buffers, so that the copies
-    of one step overlap the kernels of the next (one copy stream for both would queue
-    the next step's upload behind this step's download, which waits for this step's
-    kernels, and stall the compute stream): submit() enqueues a step and returns its slot, result(slot)
-    waits for that step's results.  A slot's host buffers stay valid until the slot
-    is submitted again (`depth` submits later).  run() is submit() then result().
+    Uploads and downloads run on two copy streams of their own, with `depth` sets of
+    device and host buffers, so that the copies of one step overlap the kernels of the
+    next (one copy stream for both would queue the next step's upload behind this
+    step's download, which waits for this step's kernels, and stall the kernels).
+    With overlap (the default) every buffer set also has its own batch and compute
+    stream, so the kernels of consecutive steps overlap too: the next step's circuit
+    and environment chains (latency-bound, few resources) and its first Pauli CTAs run
+    on the SMs that the last wave of this step's Pauli kernel leaves idle.  That takes
+    `depth` batches of device memory; overlap=False keeps one batch and one compute
+    stream (the stream argument).  Every step is ordered after the work queued on the
+    stream argument when it is submitted.  submit() enqueues a step and returns its
+    slot, result(slot) waits for that step's results.  A slot's host buffers stay valid
+    until the slot is submitted again (`depth` submits later).  run() is submit() then
+    result().
     """
 
     def __init__(self, p, chi, L, precision, params, abd, W=None, bias=None, ansatz="ladder", stream=None,
-                 depth: int = 2):
+                 depth: int = 2, overlap: bool = True):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.batch = Batch(p, chi, precision, self.stream)
         self.L, self.ansatz = L, ansatz
         self.params, self.abd, self.W, self.bias = params, abd, W, bias
         p = np.atleast_1d(np.asarray(p))
         if len(set(p.tolist())) != 1:
             raise ValueError("Pipeline needs images of one size (one pair layout for the ANO layer)")
         self.m = pair_count(int(p[0]))
-        n_px = int(self.batch.pixel_offsets[-1])
         dev = torch.device("cuda", torch.cuda.current_device())
+        depth = max(1, depth)
+        if overlap:
+            streams = [torch.cuda.Stream(device=dev) for _ in range(depth)]
+            batches = [Batch(p, chi, precision, s) for s in streams]
+        else:
+            streams = [self.stream] * depth
+            batches = [Batch(p, chi, precision, self.stream)] * depth
+        self.batch = batches[0]
+        self.batches = batches if overlap else batches[:1]
+        n_px = int(self.batch.pixel_offsets[-1])
         self.copy_stream = torch.cuda.Stream(device=dev)       # host -> device
         self.d2h_stream = torch.cuda.Stream(device=dev)        # device -> host
         dt = torch.float64 if precision == "fp64" else torch.float32
         B = self.batch.n_images
         n_pairs = int(self.batch.pair_offsets[-1])
         self.slots = []
-        for _ in range(max(1, depth)):
+        for i in range(depth):
             sl = {"px": torch.empty(n_px, dtype=torch.float64, device=dev),
                   "pauli": torch.empty((n_pairs, 16), dtype=dt, device=dev),
                   "feats": torch.empty((B, self.m), dtype=torch.float32, device=dev),
@@ -292,7 +307,9 @@ class Pipeline:
                   "pauli_h": torch.empty((n_pairs, 16), dtype=dt).pin_memory(),
                   "feats_h": torch.empty((B, self.m), dtype=torch.float32).pin_memory(),
                   "out_h": None if W is None else torch.empty((B, W.shape[0]), dtype=torch.float32).pin_memory(),
-                  "ev_in": torch.cuda.Event(), "ev_comp": torch.cuda.Event(), "ev_out": torch.cuda.Event()}
+                  "batch": batches[i], "stream": streams[i],
+                  "ev_in": torch.cuda.Event(), "ev_comp": torch.cuda.Event(), "ev_out": torch.cuda.Event(),
+                  "ev_user": torch.cuda.Event()}
             self.slots.append(sl)
         self._next = 0
         self.h2d_bytes = n_px * 8
@@ -300,23 +317,34 @@ class Pipeline:
         self.d2h_bytes = (sl["pauli_h"].numel() * sl["pauli_h"].element_size() + sl["feats_h"].numel() * 4
                           + (0 if sl["out_h"] is None else sl["out_h"].numel() * 4))
 
+    def set_launch_shape(self, images_per_cta: int = 0, circuit_threads: int = 0, pauli_threads: int = 0):
+        for b in self.batches:
+            b.set_launch_shape(images_per_cta, circuit_threads, pauli_threads)
+
+    def sync(self):
+        """Wait for every submitted step; raises if a kernel reported an error."""
+        for b in self.batches:
+            b.sync()
+
     def submit(self, host_pixels: torch.Tensor) -> int:
         k = self._next
         self._next = (k + 1) % len(self.slots)
         sl = self.slots[k]
         sl["ev_out"].synchronize()          # the previous results of this slot have been read back
-        cs = self.copy_stream
+        cs, st, b = self.copy_stream, sl["stream"], sl["batch"]
         with torch.cuda.stream(cs):
             cs.wait_event(sl["ev_comp"])     # the previous step of this slot no longer reads its pixels
             sl["px"].copy_(host_pixels, non_blocking=True)
             sl["ev_in"].record(cs)
-        with torch.cuda.stream(self.stream):
-            self.stream.wait_event(sl["ev_in"])
-            self.batch.apply_circuit(sl["px"], self.L, self.ansatz, self.params)
-            self.batch.pauli_cache(sl["pauli"])
-            ano_features(sl["pauli"], self.m, self.abd, self.W, self.bias, self.stream,
-                         feats=sl["feats"], out=sl["out"])
-            sl["ev_comp"].record(self.stream)
+        with torch.cuda.stream(st):
+            if st is not self.stream:
+                sl["ev_user"].record(self.stream)
+                st.wait_event(sl["ev_user"])
+            st.wait_event(sl["ev_in"])
+            b.apply_circuit(sl["px"], self.L, self.ansatz, self.params)
+            b.pauli_cache(sl["pauli"])
+            ano_features(sl["pauli"], self.m, self.abd, self.W, self.bias, st, feats=sl["feats"], out=sl["out"])
+            sl["ev_comp"].record(st)
         ds = self.d2h_stream
         with torch.cuda.stream(ds):
             ds.wait_event(sl["ev_comp"])

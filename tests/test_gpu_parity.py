@@ -427,9 +427,11 @@ def test_layer_pipeline_falls_back_when_a_step_truncates():
         assert np.array_equal(a[i], b[i])
 
 
-def test_pipeline_overlapped_steps_keep_their_results():
-    """Pipeline.submit/result with two buffer sets: steps whose copies overlap the next
-    step's kernels return exactly what each step gives when run alone."""
+@pytest.mark.parametrize("overlap", [True, False])
+def test_pipeline_overlapped_steps_keep_their_results(overlap):
+    """Pipeline.submit/result with two buffer sets: steps whose copies (and, with
+    overlap, kernels on a compute stream and batch per buffer set) overlap the next
+    step's return exactly what each step gives when run alone."""
     from paper_2607_10280_b300 import api
     p, B, L, chi = 5, 16, 2, 4
     m = api.pair_count(p)
@@ -438,7 +440,8 @@ def test_pipeline_overlapped_steps_keep_their_results():
     W, b = synth.linear_params(40, m, seed=103)
     W = torch.tensor(W, dtype=torch.float32, device="cuda")
     b = torch.tensor(b, dtype=torch.float32, device="cuda")
-    pipe = api.Pipeline(np.full(B, p, np.int32), chi, L, "mixed", params, abd, W, b)
+    pipe = api.Pipeline(np.full(B, p, np.int32), chi, L, "mixed", params, abd, W, b, overlap=overlap)
+    assert len(pipe.batches) == (2 if overlap else 1)
     host = [torch.tensor(synth.garment_pixels(B, p, seed=110 + s).reshape(-1), dtype=torch.float64).pin_memory()
             for s in range(3)]
     alone = [[t.clone() for t in pipe.run(h)] for h in host]
@@ -452,6 +455,7 @@ def test_pipeline_overlapped_steps_keep_their_results():
         for g, r in zip(got, ref):
             assert torch.equal(g, r)
     assert not torch.equal(r0[0], r1[0])
+    pipe.sync()
 
 
 def test_bond_caps_above_the_exact_bond_change_nothing():
