@@ -517,13 +517,15 @@ __device__ __forceinline__ void lenv_image(const ImageMeta& mt,
         if (!(fg && half_site(k)))
             team_for_2d<NTHR, 4>(Dl, Dl, lane, [&](int r, int c) { dst[r * CHI + c] = Lm[r * CS + c]; });
         if constexpr (ASYNC) {
+            // site k has landed for every thread, and the buffer of site k-1 (read before
+            // the last barrier) takes site k+1
             cp_async_wait_all();
             tsync<NTHR>();
             if (k + 1 < n) prefetch(k + 1, (k & 1) ? A0 : A1);
         } else {
             load_site_p<E, CS, NTHR>(A, sites + (size_t)k * 2 * ld * ld, ld, Dl, Dr, lane);
+            tsync<NTHR>();
         }
-        tsync<NTHR>();
         if (half_site(k)) {
             // half-structured site: L A is needed only at (s, r) with r in half s
             // (T'[l][r] = sum_l' L[l][l'] A[2l'+s(r)][r]), and L_{k+1} is block diagonal

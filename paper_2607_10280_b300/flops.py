@@ -277,10 +277,20 @@ def sweep_flops(p: int, bonds, lenv: bool = False, half: bool = False, diag: boo
 
 
 def lenv_flops(bonds, half: bool = False) -> float:
-    """Left-environment chain of one image (renv_kernel's second half)."""
+    """Left-environment chain of one image (lenv_image).  half: at a half-structured site
+    (right bond >= 2, not the last) each product contracts one half of the site, and once
+    the site before was half-structured too, L_k is block diagonal and the first product
+    sums over half of the left bond."""
     n = len(bonds) - 1
-    return sum(8.0 * (2 * bonds[j] ** 2 * bonds[j + 1] + 2 * bonds[j] * bonds[j + 1] ** 2)
-               * (0.5 if half and j < n - 1 else 1.0) for j in range(n))
+    tot = 0.0
+    for j in range(n):
+        dl, dr = bonds[j], bonds[j + 1]
+        if half and j < n - 1 and dr >= 2:
+            first = dl * dl * dr * (0.5 if j >= 1 and dl >= 2 else 1.0)
+            tot += 8.0 * (first + dl * dr * dr)
+        else:
+            tot += 8.0 * (2 * dl * dl * dr + 2 * dl * dr * dr)
+    return tot
 
 
 def padding(p: int, chi: int) -> int:
