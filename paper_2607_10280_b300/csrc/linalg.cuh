@@ -244,6 +244,7 @@ __device__ int team_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int tid, int 
     // rotate while |G_pq| exceeds the rounding level of the pair's diagonal
     const T eps = sizeof(T) == 4 ? T(3e-7) : T(1e-15);
     const T abs_tol = (sizeof(T) == 4 ? T(3e-8) : T(1e-17)) * (tr > T(0) ? tr : T(1));
+    const T eps2 = eps * eps, abs_tol2 = abs_tol * abs_tol;
     const int Kp = (K + 1) & ~1;          // even number of slots; slot K (if K odd) is a dummy
     const int npairs = Kp / 2;
     int LP = 1;                           // threads per pair
@@ -264,45 +265,62 @@ __device__ int team_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int tid, int 
                 if (p > q) { int tmp = p; p = q; q = tmp; }
                 if (q >= K) p = -1;  // pair with the dummy slot
             }
-            T c = T(1), s = T(0);
-            cx<T> e = mk<T>(T(1), T(0));  // e^{-i phi}
+            // J = [[c, conj(z)], [-z, c]] with c real, c^2 + |z|^2 = 1, zeroes G[p][q] = g:
+            // z = c (t / |g|) conj(g), t the tangent of the rotation angle,
+            // t / |g| = 2 sgn(d) / (|d| + sqrt(d^2 + 4 |g|^2)), d = G[q][q] - G[p][p].
+            // For |g| < 5e-4 |d| (every rotation of a warm-started solve) the series
+            // t / |g| = w (1 - q + 2 q^2), c = 1 - t^2 / 2 + 3 t^4 / 8 (w = 1 / d,
+            // q = |g|^2 w^2 < 2.5e-7; the truncation errors are below 1e-19) need one
+            // division and no square root.  |g| itself is never formed: the threshold
+            // compares squares.
+            T c = T(1);
+            cx<T> z = czero<T>();
             bool rot = false;
             if (p >= 0) {
                 const T a = G[p * ld + p].re, b = G[q * ld + q].re;
                 const cx<T> g = G[q * ld + p];  // G[p][q]
-                const T ag = sqrt(norm2(g));
-                if (ag > abs_tol && ag > eps * sqrt(fabs(a * b))) {
+                const T gg = norm2(g);
+                if (gg > abs_tol2 && gg > eps2 * fabs(a * b)) {
                     rot = true;
-                    e = mk<T>(g.re / ag, -g.im / ag);
-                    const T tau = (b - a) / (T(2) * ag);
-                    const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(fma(tau, tau, T(1))));
-                    c = T(1) / sqrt(fma(t, t, T(1)));
-                    s = t * c;
+                    const T d = b - a;
+                    T tg, t2;
+                    if (T(4) * gg < T(1e-6) * d * d) {
+                        const T w = T(1) / d, qq = gg * w * w;
+                        tg = w * fma(qq, fma(T(2), qq, T(-1)), T(1));
+                        t2 = gg * tg * tg;
+                        c = fma(t2, fma(T(0.375), t2, T(-0.5)), T(1));
+                    } else {
+                        tg = (d >= T(0) ? T(2) : T(-2)) / (fabs(d) + sqrt(fma(d, d, T(4) * gg)));
+                        t2 = gg * tg * tg;
+                        if constexpr (sizeof(T) == 8) c = rsqrt(T(1) + t2);
+                        else c = T(1) / sqrt(T(1) + t2);
+                    }
+                    const T f = c * tg;
+                    z = mk<T>(f * g.re, -f * g.im);
                 }
             }
             rotated |= rot;
-            const cx<T> se = mk<T>(s * e.re, s * e.im), ce = mk<T>(c * e.re, c * e.im);
             tsync<NTHR>();
-            // columns of G and V: G <- G J, V <- V J,
-            // J(p,p) = c, J(p,q) = s, J(q,p) = -s e, J(q,q) = c e, e = e^{-i phi}
+            // columns of G and V: G <- G J, V <- V J
             if (rot) {
+                const cx<T> zc = conj(z);
                 for (int r = sub; r < K; r += LP) {
                     const cx<T> gp = G[p * ld + r], gq = G[q * ld + r];
-                    G[p * ld + r] = rot_minus(c, gp, se, gq);
-                    G[q * ld + r] = rot_plus(s, gp, ce, gq);
+                    G[p * ld + r] = rot_minus(c, gp, z, gq);
+                    G[q * ld + r] = rot_plus(c, gq, zc, gp);
                     const cx<T> vp = V[p * ld + r], vq = V[q * ld + r];
-                    V[p * ld + r] = rot_minus(c, vp, se, vq);
-                    V[q * ld + r] = rot_plus(s, vp, ce, vq);
+                    V[p * ld + r] = rot_minus(c, vp, z, vq);
+                    V[q * ld + r] = rot_plus(c, vq, zc, vp);
                 }
             }
             tsync<NTHR>();
-            // rows of G: G <- J^H G
+            // rows of G: G <- J^H G, J^H = [[c, -conj(z)], [z, c]]
             if (rot) {
-                const cx<T> sec = conj(se), cec = conj(ce);
+                const cx<T> zc = conj(z);
                 for (int col = sub; col < K; col += LP) {
                     const cx<T> gp = G[col * ld + p], gq = G[col * ld + q];
-                    G[col * ld + p] = rot_minus(c, gp, sec, gq);
-                    G[col * ld + q] = rot_plus(s, gp, cec, gq);
+                    G[col * ld + p] = rot_minus(c, gp, zc, gq);
+                    G[col * ld + q] = rot_plus(c, gq, z, gp);
                 }
             }
             tsync<NTHR>();
