@@ -861,6 +861,9 @@ def run_serve(args):
     every result against the batched FP64 path afterwards, and a stratified sample (one
     request of every (p, L, chi) class that occurred, and more of the truncating and the
     16x16 ones) against the CPU oracle."""
+    # a serving process loads every kernel when CUDA starts: a kernel loaded lazily at its
+    # first launch stalls the launching thread until the device's running work allows it
+    os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
     torch = _setup_torch()
     from paper_2607_10280_b300 import api, synth
     from paper_2607_10280_b300.flops import lossy
@@ -883,6 +886,17 @@ def run_serve(args):
     srv.completed.clear()
     srv.wave_log.clear()
     srv.waves = 0
+    # Python's collector pauses every thread, the scheduler's included: record each pause
+    import gc
+    gc_pauses = []
+    gc_t = {}
+
+    def _gc_cb(phase, info):
+        if phase == "start":
+            gc_t["t"] = time.perf_counter()
+        elif "t" in gc_t:
+            gc_pauses.append((info.get("generation", -1), (time.perf_counter() - gc_t.pop("t")) * 1e3))
+    gc.callbacks.append(_gc_cb)
     srv.start()
     t0 = time.perf_counter()
     submitted = []
@@ -895,16 +909,31 @@ def run_serve(args):
         q.event.wait()
     t1 = max(q.t_done for q in submitted)
     srv.stop()
+    gc.callbacks.remove(_gc_cb)
     rep = latency_report(submitted)
     waves = np.array([w[3] for w in srv.wave_log])
     lanes = {}
     for name, flag in (("short", False), ("long", True)):
         ws = np.array([w[3] for w in srv.wave_log if w[2] == flag])
         sz = np.array([w[1] for w in srv.wave_log if w[2] == flag])
+        hs = np.array([w[4] for w in srv.wave_log if w[2] == flag])
         if len(ws):
             lanes[name] = {"waves": int(len(ws)), "device_ms_p50": float(np.percentile(ws, 50)),
                            "device_ms_p99": float(np.percentile(ws, 99)), "device_ms_max": float(ws.max()),
+                           "host_launch_ms_p50": float(np.percentile(hs, 50)),
+                           "host_launch_ms_p99": float(np.percentile(hs, 99)), "host_launch_ms_max": float(hs.max()),
                            "images_per_wave_mean": float(sz.mean())}
+    # latency = queueing (arrival -> wave launch) + service (launch -> result on the host)
+    split = {}
+    for name in ("short", "long"):
+        rs = [q for q in submitted if q.lane == name]
+        if rs:
+            qw = np.array([q.t_launch - q.t_submit for q in rs]) * 1e3
+            sv = np.array([q.t_done - q.t_launch for q in rs]) * 1e3
+            split[name] = {"queue_ms_p50": float(np.percentile(qw, 50)), "queue_ms_p99": float(np.percentile(qw, 99)),
+                           "service_ms_p50": float(np.percentile(sv, 50)),
+                           "service_ms_p99": float(np.percentile(sv, 99))}
+    gcp = np.array([g[1] for g in gc_pauses]) if gc_pauses else np.zeros(1)
 
     # every result against the batched FP64 path, by (p, L, chi) group
     groups = {}
@@ -951,6 +980,9 @@ def run_serve(args):
             "arrival_rate_hz": 2000.0, "waves": srv.waves, "max_wave": srv.max_wave,
             "device_ms_per_wave": {"p50": float(np.percentile(waves, 50)), "p99": float(np.percentile(waves, 99)),
                                    "max": float(waves.max()), "lanes": lanes},
+            "latency_split_by_lane": split,
+            "gc_pauses": {"count": len(gc_pauses), "max_ms": float(gcp.max()), "total_ms": float(gcp.sum()),
+                          "gen2": sum(1 for g in gc_pauses if g[0] == 2)},
             "max_inflight_bytes": srv.max_inflight_bytes, "budget_bytes": srv.budget,
             "check_all_vs_fp64_gpu": {"requests": len(reqs), "max_abs": float(err.max()),
                                       "over_1e-5": int((err > 1e-5).sum())},

@@ -21,10 +21,19 @@ behind a truncating chain.
 
 Each image's arithmetic is independent of the other images in its wave, so a
 request's result does not depend on the mix it was served in.
+
+The scheduler is a Python thread, and Python's cyclic garbage collector stops every
+thread while it walks the heap: a full collection over a process that holds torch,
+the server and a few thousand requests took about 100 ms, during which no wave was
+launched or retired.  With ``freeze_gc`` (the default) ``start()`` moves every object
+that exists at that moment into the collector's permanent generation
+(``gc.freeze``), so the collections that run while serving walk only the objects
+created since; ``stop()`` hands them back (``gc.unfreeze``).
 """
 from __future__ import annotations
 
 import collections
+import gc
 import threading
 import time
 from dataclasses import dataclass, field
@@ -80,6 +89,7 @@ class Request:
     pixels: np.ndarray
     id: int = 0
     t_submit: float = 0.0
+    t_launch: float = 0.0   # when its wave was handed to the GPU (queueing = t_launch - t_submit)
     t_done: float = 0.0
     pauli: np.ndarray = None
     features: np.ndarray = None
@@ -118,6 +128,7 @@ class _Slot:
         self.started = torch.cuda.Event(enable_timing=True)
         self.done = torch.cuda.Event(enable_timing=True)
         self.wave = None
+        self.host_ms = 0.0
         self.footprint = 0
 
 
@@ -132,8 +143,10 @@ class Server:
     def __init__(self, params: torch.Tensor, epilogue: dict = None, slots: int = 4,
                  max_images_per_wave: int = 64, budget_bytes: int = 2 << 30, precision: str = "mixed",
                  launch_shape=None, max_p: int = 16, max_chi: int = 32, long_slots: int = None,
-                 long_launch_shape=(0, 128, 0)):
+                 long_launch_shape=(0, 128, 0), freeze_gc: bool = True):
         self.params = params
+        self.freeze_gc = freeze_gc
+        self._frozen = False
         self.epilogue = epilogue or {}
         self.precision = precision
         self.max_images = max_images_per_wave
@@ -157,7 +170,8 @@ class Server:
                       for i in range(slots)]
         self.pending = collections.deque()        # requests for the short lane
         self.pending_long = collections.deque()   # requests that run a truncating chain
-        self.wave_log = []                        # (slot, images, long lane, device ms) per wave
+        # (slot, images, long lane, device ms, host ms spent launching) per wave
+        self.wave_log = []
         self.lock = threading.Lock()
         self.inflight_bytes = 0
         self.completed = []
@@ -190,6 +204,10 @@ class Server:
         return self.pending_long if self._is_long(req) else self.pending
 
     def start(self):
+        if self.freeze_gc and not self._frozen:
+            gc.collect()
+            gc.freeze()
+            self._frozen = True
         self._stop = False
         self._thread = threading.Thread(target=self._loop, daemon=True)
         self._thread.start()
@@ -205,6 +223,9 @@ class Server:
         self._stop = True
         if self._thread:
             self._thread.join()
+        if self._frozen:
+            gc.unfreeze()
+            self._frozen = False
 
     # -------------------------------------------------------------- server loop
     def _loop(self):
@@ -242,11 +263,13 @@ class Server:
 
     def _launch(self, s: _Slot, admitted):
         wave, foot = admitted
+        t_launch = time.perf_counter()
         # images with an epilogue first, grouped by size, so that each group's Pauli
         # blocks are contiguous
         wave.sort(key=lambda r: (0 if r.p in self.epilogue else 1, r.p))
         for r in wave:
             r.lane = "long" if s.long_lane else "short"
+            r.t_launch = t_launch
         ps = np.array([r.p for r in wave], np.int32)
         chis = np.array([r.chi for r in wave], np.int32)
         Ls = np.array([r.L for r in wave], np.int32)
@@ -280,6 +303,7 @@ class Server:
                 i = j
             s.done.record(s.stream)
         s.wave = (wave, epi)
+        s.host_ms = (time.perf_counter() - t_launch) * 1e3
         s.footprint = foot
         self.waves += 1
         self.max_wave = max(self.max_wave, len(wave))
@@ -297,7 +321,7 @@ class Server:
         for r in wave:
             r.t_done = now
             r.event.set()
-        self.wave_log.append((s.idx, len(wave), s.long_lane, s.started.elapsed_time(s.done)))
+        self.wave_log.append((s.idx, len(wave), s.long_lane, s.started.elapsed_time(s.done), s.host_ms))
         with self.lock:
             self.inflight_bytes -= s.footprint
             self.completed.extend(wave)
