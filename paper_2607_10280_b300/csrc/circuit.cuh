@@ -354,6 +354,7 @@ struct CircuitTeam {
             tsync<NTHR>();
         };
         bool fp64_vectors = sizeof(TQ) == 8;
+        bool cross = false;   // the refined solve decoupled the kept part only
         const cx<double>* Vd = V;   // FP64 eigenvectors (columns), when fp64_vectors
         if constexpr (sizeof(TQ) == 8) {
             if constexpr (Lay::REFINE) {
@@ -417,7 +418,18 @@ struct CircuitTeam {
                     G[j * LDK + i] = acc;
                 });
                 tsync<NTHR>();
-                team_jacobi_eigh<NTHR, double>(G, W, LDK, K, lane, 40, red, true);
+                // diag(G) now holds FP64 Rayleigh quotients of the FP32 vectors (error
+                // ~eps_32 lambda_1 at worst, inside a cluster).  Where they put the cut in a
+                // gap wider than 1e-5 lambda_1 that split is certain, and FP64 Jacobi only
+                // has to decouple the kept from the dropped directions (team_jacobi_cross:
+                // the rotations inside either part change nothing a truncation uses);
+                // otherwise the full FP64 eigen-decomposition ranks them.
+                for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
+                tsync<NTHR>();
+                rank_lam();
+                cross = lam[ord[keep - 1]] - lam[ord[keep]] >= 1e-5 * lam[ord[0]];
+                if (cross) team_jacobi_cross<NTHR, double>(G, W, LDK, K, ord, keep, lane, 40, red);
+                else team_jacobi_eigh<NTHR, double>(G, W, LDK, K, lane, 40, red, true);
                 Vd = W;
             } else {
                 team_jacobi_eigh<NTHR, double>(G, V, LDK, K, lane, 40, red);
@@ -425,7 +437,8 @@ struct CircuitTeam {
             tsync<NTHR>();
             for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
             tsync<NTHR>();
-            rank_lam();
+            // after the block solve ord keeps its split (kept part first)
+            if (!cross) rank_lam();
         } else {
             team_for_2d<NTHR>(K, K, lane, [&](int c, int r) { G32[c * LDK + r] = cvt<float>(G[c * LDK + r]); });
             tsync<NTHR>();

@@ -224,6 +224,101 @@ __device__ __forceinline__ cx<T> rot_plus(T s, cx<T> a, cx<T> g, cx<T> b) {
     return mk<T>(fma(s, a.re, tr), fma(s, a.im, ti));
 }
 
+// One round of a parallel Jacobi method on the K x K Hermitian matrix G (column-major,
+// ld) with the accumulated basis V: the calling thread belongs to the group of LP
+// threads (sub = its index there) that owns the pair (p, q), p < q (p < 0: no pair),
+// and every pair of the round is disjoint from the others.  The rotation
+// J = [[c, conj(z)], [-z, c]] (c real, c^2 + |z|^2 = 1) zeroes G[p][q] = g:
+// z = c (t / |g|) conj(g), t the tangent of the rotation angle,
+// t / |g| = 2 sgn(d) / (|d| + sqrt(d^2 + 4 |g|^2)), d = G[q][q] - G[p][p].  For
+// |g| < 5e-4 |d| (every rotation of a warm-started solve) the series
+// t / |g| = w (1 - q + 2 q^2), c = 1 - t^2 / 2 + 3 t^4 / 8 (w = 1 / d,
+// q = |g|^2 w^2 < 2.5e-7; the truncation errors are below 1e-19) need one division and
+// no square root.  |g| itself is never formed: the rotate-or-not test compares
+// |g|^2 with abs_tol2 and eps2 |G_pp G_qq|.  Returns whether this pair rotated.
+template <int NTHR, typename T>
+__device__ __forceinline__ bool jacobi_round(cx<T>* G, cx<T>* V, int ld, int K, int p, int q, int sub, int LP,
+                                             T eps2, T abs_tol2) {
+    T c = T(1);
+    cx<T> z = czero<T>();
+    bool rot = false;
+    if (p >= 0) {
+        const T a = G[p * ld + p].re, b = G[q * ld + q].re;
+        const cx<T> g = G[q * ld + p];  // G[p][q]
+        const T gg = norm2(g);
+        if (gg > abs_tol2 && gg > eps2 * fabs(a * b)) {
+            rot = true;
+            const T d = b - a;
+            T tg, t2;
+            if (T(4) * gg < T(1e-6) * d * d) {
+                const T w = T(1) / d, qq = gg * w * w;
+                tg = w * fma(qq, fma(T(2), qq, T(-1)), T(1));
+                t2 = gg * tg * tg;
+                c = fma(t2, fma(T(0.375), t2, T(-0.5)), T(1));
+            } else {
+                tg = (d >= T(0) ? T(2) : T(-2)) / (fabs(d) + sqrt(fma(d, d, T(4) * gg)));
+                t2 = gg * tg * tg;
+                if constexpr (sizeof(T) == 8) c = rsqrt(T(1) + t2);
+                else c = T(1) / sqrt(T(1) + t2);
+            }
+            const T f = c * tg;
+            z = mk<T>(f * g.re, -f * g.im);
+        }
+    }
+    tsync<NTHR>();
+    // columns of G and V: G <- G J, V <- V J
+    if (rot) {
+        const cx<T> zc = conj(z);
+        for (int r = sub; r < K; r += LP) {
+            const cx<T> gp = G[p * ld + r], gq = G[q * ld + r];
+            G[p * ld + r] = rot_minus(c, gp, z, gq);
+            G[q * ld + r] = rot_plus(c, gq, zc, gp);
+            const cx<T> vp = V[p * ld + r], vq = V[q * ld + r];
+            V[p * ld + r] = rot_minus(c, vp, z, vq);
+            V[q * ld + r] = rot_plus(c, vq, zc, vp);
+        }
+    }
+    tsync<NTHR>();
+    // rows of G: G <- J^H G, J^H = [[c, -conj(z)], [z, c]]
+    if (rot) {
+        const cx<T> zc = conj(z);
+        for (int col = sub; col < K; col += LP) {
+            const cx<T> gp = G[col * ld + p], gq = G[col * ld + q];
+            G[col * ld + p] = rot_minus(c, gp, zc, gq);
+            G[col * ld + q] = rot_plus(c, gq, z, gp);
+        }
+    }
+    tsync<NTHR>();
+    if (rot && sub == 0) {  // the 2x2 block is diagonal in exact arithmetic
+        G[q * ld + p] = czero<T>();
+        G[p * ld + q] = czero<T>();
+        G[p * ld + p].im = T(0);
+        G[q * ld + q].im = T(0);
+    }
+    tsync<NTHR>();
+    return rot;
+}
+
+// Rotation thresholds of the Jacobi solvers: rotate while |G_pq| exceeds the rounding
+// level of the pair's diagonal (eps) or of the trace (abs_tol); returned squared.
+template <int NTHR, typename T>
+__device__ __forceinline__ void jacobi_thresholds(const cx<T>* G, int ld, int K, int tid, double* red, T* eps2,
+                                                  T* abs_tol2) {
+    T tr = T(0);
+    for (int r = tid; r < K; r += NTHR) tr += fabs(G[r * ld + r].re);
+    tr = team_sum<NTHR>(tr, red, tid);
+    const T eps = sizeof(T) == 4 ? T(3e-7) : T(1e-15);
+    const T abs_tol = (sizeof(T) == 4 ? T(3e-8) : T(1e-17)) * (tr > T(0) ? tr : T(1));
+    *eps2 = eps * eps;
+    *abs_tol2 = abs_tol * abs_tol;
+}
+
+template <int NTHR>
+__device__ __forceinline__ bool team_any(bool v) {
+    if constexpr (NTHR == 32) return __any_sync(0xffffffffu, v);
+    else return __syncthreads_or(v) != 0;
+}
+
 // Cyclic parallel (round-robin) Jacobi eigensolver for the K x K Hermitian matrix G
 // (column-major, ld), K <= 2 NTHR, run by a team of NTHR threads in the arithmetic of
 // T.  On return diag(G) holds the eigenvalues and the columns of V (K x K, ld) the
@@ -238,13 +333,8 @@ __device__ int team_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int tid, int 
     if (!v_given)
         for (int c = 0; c < K; ++c)
             for (int r = tid; r < K; r += NTHR) V[c * ld + r] = mk<T>(r == c ? T(1) : T(0), T(0));
-    T tr = T(0);
-    for (int r = tid; r < K; r += NTHR) tr += fabs(G[r * ld + r].re);
-    tr = team_sum<NTHR>(tr, red, tid);
-    // rotate while |G_pq| exceeds the rounding level of the pair's diagonal
-    const T eps = sizeof(T) == 4 ? T(3e-7) : T(1e-15);
-    const T abs_tol = (sizeof(T) == 4 ? T(3e-8) : T(1e-17)) * (tr > T(0) ? tr : T(1));
-    const T eps2 = eps * eps, abs_tol2 = abs_tol * abs_tol;
+    T eps2, abs_tol2;
+    jacobi_thresholds<NTHR, T>(G, ld, K, tid, red, &eps2, &abs_tol2);
     const int Kp = (K + 1) & ~1;          // even number of slots; slot K (if K odd) is a dummy
     const int npairs = Kp / 2;
     int LP = 1;                           // threads per pair
@@ -253,7 +343,7 @@ __device__ int team_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int tid, int 
     int sweep = 0;
     tsync<NTHR>();
     for (; sweep < max_sweeps; ++sweep) {
-        int rotated = 0;
+        bool rotated = false;
         for (int round = 0; round < Kp - 1; ++round) {
             // round-robin pairing: slot 0 fixed, slots 1..Kp-1 rotate
             int p = -1, q = -1;
@@ -265,77 +355,50 @@ __device__ int team_jacobi_eigh(cx<T>* G, cx<T>* V, int ld, int K, int tid, int 
                 if (p > q) { int tmp = p; p = q; q = tmp; }
                 if (q >= K) p = -1;  // pair with the dummy slot
             }
-            // J = [[c, conj(z)], [-z, c]] with c real, c^2 + |z|^2 = 1, zeroes G[p][q] = g:
-            // z = c (t / |g|) conj(g), t the tangent of the rotation angle,
-            // t / |g| = 2 sgn(d) / (|d| + sqrt(d^2 + 4 |g|^2)), d = G[q][q] - G[p][p].
-            // For |g| < 5e-4 |d| (every rotation of a warm-started solve) the series
-            // t / |g| = w (1 - q + 2 q^2), c = 1 - t^2 / 2 + 3 t^4 / 8 (w = 1 / d,
-            // q = |g|^2 w^2 < 2.5e-7; the truncation errors are below 1e-19) need one
-            // division and no square root.  |g| itself is never formed: the threshold
-            // compares squares.
-            T c = T(1);
-            cx<T> z = czero<T>();
-            bool rot = false;
-            if (p >= 0) {
-                const T a = G[p * ld + p].re, b = G[q * ld + q].re;
-                const cx<T> g = G[q * ld + p];  // G[p][q]
-                const T gg = norm2(g);
-                if (gg > abs_tol2 && gg > eps2 * fabs(a * b)) {
-                    rot = true;
-                    const T d = b - a;
-                    T tg, t2;
-                    if (T(4) * gg < T(1e-6) * d * d) {
-                        const T w = T(1) / d, qq = gg * w * w;
-                        tg = w * fma(qq, fma(T(2), qq, T(-1)), T(1));
-                        t2 = gg * tg * tg;
-                        c = fma(t2, fma(T(0.375), t2, T(-0.5)), T(1));
-                    } else {
-                        tg = (d >= T(0) ? T(2) : T(-2)) / (fabs(d) + sqrt(fma(d, d, T(4) * gg)));
-                        t2 = gg * tg * tg;
-                        if constexpr (sizeof(T) == 8) c = rsqrt(T(1) + t2);
-                        else c = T(1) / sqrt(T(1) + t2);
-                    }
-                    const T f = c * tg;
-                    z = mk<T>(f * g.re, -f * g.im);
-                }
-            }
-            rotated |= rot;
-            tsync<NTHR>();
-            // columns of G and V: G <- G J, V <- V J
-            if (rot) {
-                const cx<T> zc = conj(z);
-                for (int r = sub; r < K; r += LP) {
-                    const cx<T> gp = G[p * ld + r], gq = G[q * ld + r];
-                    G[p * ld + r] = rot_minus(c, gp, z, gq);
-                    G[q * ld + r] = rot_plus(c, gq, zc, gp);
-                    const cx<T> vp = V[p * ld + r], vq = V[q * ld + r];
-                    V[p * ld + r] = rot_minus(c, vp, z, vq);
-                    V[q * ld + r] = rot_plus(c, vq, zc, vp);
-                }
-            }
-            tsync<NTHR>();
-            // rows of G: G <- J^H G, J^H = [[c, -conj(z)], [z, c]]
-            if (rot) {
-                const cx<T> zc = conj(z);
-                for (int col = sub; col < K; col += LP) {
-                    const cx<T> gp = G[col * ld + p], gq = G[col * ld + q];
-                    G[col * ld + p] = rot_minus(c, gp, zc, gq);
-                    G[col * ld + q] = rot_plus(c, gq, z, gp);
-                }
-            }
-            tsync<NTHR>();
-            if (rot && sub == 0) {  // the 2x2 block is diagonal in exact arithmetic
-                G[q * ld + p] = czero<T>();
-                G[p * ld + q] = czero<T>();
-                G[p * ld + p].im = T(0);
-                G[q * ld + q].im = T(0);
-            }
-            tsync<NTHR>();
+            rotated |= jacobi_round<NTHR, T>(G, V, ld, K, p, q, sub, LP, eps2, abs_tol2);
         }
-        int any;
-        if constexpr (NTHR == 32) any = __any_sync(0xffffffffu, rotated);
-        else any = __syncthreads_or(rotated);
-        if (!any) break;
+        if (!team_any<NTHR>(rotated)) break;
+    }
+    return sweep;
+}
+
+// Block version for a truncation: the indices ord[0 .. keep) (kept) and
+// ord[keep .. K) (discarded) split G, and only pairs with one index in each part are
+// rotated, until G has no entry between the two parts above the rounding level.  The
+// kept columns of V then span the invariant subspace of the kept part's eigenvalues,
+// and the discarded part's diagonal sums to its eigenvalues, which is all a truncation
+// uses (the basis inside the kept subspace is a gauge of the new bond).  Round r pairs
+// index i of the smaller part with index (i + r) mod (size of the larger part) of the
+// other, so every cross pair appears once per sweep: keep (K - keep) rotations in
+// max(keep, K - keep) rounds, against K (K - 1) / 2 in K - 1 rounds for the full solve.
+// The split must not separate a cluster of eigenvalues (the caller checks the gap).
+template <int NTHR, typename T>
+__device__ int team_jacobi_cross(cx<T>* G, cx<T>* V, int ld, int K, const int* ord, int keep, int tid,
+                                 int max_sweeps, double* red) {
+    T eps2, abs_tol2;
+    jacobi_thresholds<NTHR, T>(G, ld, K, tid, red, &eps2, &abs_tol2);
+    const int nd = K - keep;
+    const int small = keep < nd ? keep : nd, large = keep < nd ? nd : keep;
+    int LP = 1;
+    while (LP * 2 * small <= NTHR) LP *= 2;
+    const int pair = tid / LP, sub = tid % LP;
+    int sweep = 0;
+    tsync<NTHR>();
+    for (; sweep < max_sweeps; ++sweep) {
+        bool rotated = false;
+        for (int round = 0; round < large; ++round) {
+            int p = -1, q = -1;
+            if (pair < small) {
+                int j = pair + round;
+                if (j >= large) j -= large;
+                const int x = keep <= nd ? ord[pair] : ord[j];
+                const int y = keep <= nd ? ord[keep + j] : ord[keep + pair];
+                p = x < y ? x : y;
+                q = x < y ? y : x;
+            }
+            rotated |= jacobi_round<NTHR, T>(G, V, ld, K, p, q, sub, LP, eps2, abs_tol2);
+        }
+        if (!team_any<NTHR>(rotated)) break;
     }
     return sweep;
 }
