@@ -323,8 +323,7 @@ struct CircuitTeam {
         const bool left = M <= N;      // Gram of the row space (M x M) or column space (N x N)
         const int K = left ? M : N;
         // G = theta theta^H (left) or theta^H theta, accumulated in FP64
-        team_for_2d<NTHR>(K, K, lane, [&](int i, int j) {   // G[i][j], column-major store G[j*LDK + i]
-            if (j < i) return;
+        team_for_upper<NTHR>(K, lane, [&](int i, int j) {   // G[i][j], column-major store G[j*LDK + i]
             cx<double> acc = czero<double>();
             if (left) {
                 for (int c = 0; c < N; ++c)
@@ -374,8 +373,7 @@ struct CircuitTeam {
                 tsync<NTHR>();
                 // C = W^H W (upper triangle, column-major in the V buffer), then C = R^H R
                 cx<double>* C = V;
-                team_for_2d<NTHR>(K, K, lane, [&](int j, int i) {
-                    if (i > j) return;
+                team_for_upper<NTHR>(K, lane, [&](int i, int j) {
                     cx<double> acc = czero<double>();
                     for (int r = 0; r < K; ++r) cmac_cj(acc, W[i * LDK + r], W[j * LDK + r]);
                     C[j * LDK + i] = acc;
@@ -389,18 +387,34 @@ struct CircuitTeam {
                         C[j * LDK + k] = j == k ? mk<double>(d, 0.0) : inv * C[j * LDK + k];
                     if (lane == 0) taud[k] = mk<double>(inv, 0.0);
                     tsync<NTHR>();
-                    team_for_2d<NTHR>(K - 1 - k, K - 1 - k, lane, [&](int jj, int ii) {
+                    team_for_upper<NTHR>(K - 1 - k, lane, [&](int ii, int jj) {
                         const int i = k + 1 + ii, j = k + 1 + jj;
-                        if (i <= j) cmsub(C[j * LDK + i], conj(C[i * LDK + k]), C[j * LDK + k]);
+                        cmsub(C[j * LDK + i], conj(C[i * LDK + k]), C[j * LDK + k]);
                     });
                     tsync<NTHR>();
                 }
-                // W <- W R^{-1}, row by row (forward substitution over the columns)
-                for (int r = lane; r < K; r += NTHR) {
-                    for (int c = 0; c < K; ++c) {
-                        cx<double> acc = W[c * LDK + r];
-                        for (int m = 0; m < c; ++m) cmsub(acc, W[m * LDK + r], C[c * LDK + m]);
-                        W[c * LDK + r] = taud[c].re * acc;
+                // W <- W R^{-1}, row by row (forward substitution over the columns).  A
+                // group of GS lanes takes a row (GS * K <= NTHR, GS <= 32), each lane the
+                // terms m = g (mod GS) of every column's sum, combined by xor-shuffles, so
+                // that no lane of a warp idles when K < NTHR.
+                {
+                    int GS = 1;
+                    while (GS < 32 && 2 * GS * K <= NTHR) GS *= 2;
+                    const int g = lane & (GS - 1), groups = NTHR / GS;
+                    for (int r0 = 0; r0 < K; r0 += groups) {
+                        const int r = r0 + lane / GS;
+                        const bool live = r < K;
+                        for (int c = 0; c < K; ++c) {
+                            cx<double> part = czero<double>();
+                            if (live)
+                                for (int m = g; m < c; m += GS) cmac(part, W[m * LDK + r], C[c * LDK + m]);
+                            for (int o = GS >> 1; o > 0; o >>= 1) {
+                                part.re += __shfl_xor_sync(0xffffffffu, part.re, o);
+                                part.im += __shfl_xor_sync(0xffffffffu, part.im, o);
+                            }
+                            if (live && g == 0) W[c * LDK + r] = taud[c].re * (W[c * LDK + r] - part);
+                            __syncwarp();
+                        }
                     }
                 }
                 tsync<NTHR>();
@@ -412,10 +426,13 @@ struct CircuitTeam {
                     Tm[c * LDK + r] = acc;
                 });
                 tsync<NTHR>();
-                team_for_2d<NTHR>(K, K, lane, [&](int j, int i) {
+                // W^H G W is Hermitian: the upper triangle, mirrored
+                team_for_upper<NTHR>(K, lane, [&](int i, int j) {
                     cx<double> acc = czero<double>();
                     for (int r = 0; r < K; ++r) cmac_cj(acc, W[i * LDK + r], Tm[j * LDK + r]);
+                    if (i == j) acc.im = 0.0;
                     G[j * LDK + i] = acc;
+                    G[i * LDK + j] = conj(acc);
                 });
                 tsync<NTHR>();
                 // diag(G) now holds FP64 Rayleigh quotients of the FP32 vectors (error

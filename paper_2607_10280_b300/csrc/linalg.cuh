@@ -51,6 +51,22 @@ __device__ __forceinline__ void team_for_2d(int R, int C, int tid, F f) {
     }
 }
 
+// Calls f(i, j) for every 0 <= i <= j < K (the upper triangle of a K x K matrix),
+// K (K + 1) / 2 calls spread evenly over the NTHR threads: t = j (j + 1) / 2 + i.
+// (team_for_2d over K x K with the lower half skipped leaves about half of every
+// warp's lanes idle, and an FP64 instruction costs its issue slots on the FP64 pipe
+// whether or not its lanes are active.)
+template <int NTHR, class F>
+__device__ __forceinline__ void team_for_upper(int K, int tid, F f) {
+    const int total = K * (K + 1) / 2;
+    for (int t = tid; t < total; t += NTHR) {
+        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (j * (j + 1) / 2 > t) --j;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        f(t - j * (j + 1) / 2, j);
+    }
+}
+
 // Largest power of two G <= 32 with G * nc <= NTHR (at least 1): threads per column
 // when nc columns are processed by the team.
 template <int NTHR>
