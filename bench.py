@@ -895,7 +895,8 @@ def run_serve(args):
         if phase == "start":
             gc_t["t"] = time.perf_counter()
         elif "t" in gc_t:
-            gc_pauses.append((info.get("generation", -1), (time.perf_counter() - gc_t.pop("t")) * 1e3))
+            t_end = time.perf_counter()
+            gc_pauses.append((info.get("generation", -1), (t_end - gc_t.pop("t")) * 1e3, t_end))
     gc.callbacks.append(_gc_cb)
     srv.start()
     t0 = time.perf_counter()
@@ -933,7 +934,9 @@ def run_serve(args):
             split[name] = {"queue_ms_p50": float(np.percentile(qw, 50)), "queue_ms_p99": float(np.percentile(qw, 99)),
                            "service_ms_p50": float(np.percentile(sv, 50)),
                            "service_ms_p99": float(np.percentile(sv, 99))}
-    gcp = np.array([g[1] for g in gc_pauses]) if gc_pauses else np.zeros(1)
+    # pauses while requests were in flight (t0 .. t1) and after
+    run_p = [g for g in gc_pauses if g[2] <= t1]
+    gcp = np.array([g[1] for g in run_p]) if run_p else np.zeros(1)
 
     # every result against the batched FP64 path, by (p, L, chi) group
     groups = {}
@@ -981,8 +984,9 @@ def run_serve(args):
             "device_ms_per_wave": {"p50": float(np.percentile(waves, 50)), "p99": float(np.percentile(waves, 99)),
                                    "max": float(waves.max()), "lanes": lanes},
             "latency_split_by_lane": split,
-            "gc_pauses": {"count": len(gc_pauses), "max_ms": float(gcp.max()), "total_ms": float(gcp.sum()),
-                          "gen2": sum(1 for g in gc_pauses if g[0] == 2)},
+            "gc_pauses": {"count": len(run_p), "max_ms": float(gcp.max()), "total_ms": float(gcp.sum()),
+                          "gen2": sum(1 for g in run_p if g[0] == 2),
+                          "after_last_result": [round(g[1], 2) for g in gc_pauses if g[2] > t1]},
             "max_inflight_bytes": srv.max_inflight_bytes, "budget_bytes": srv.budget,
             "check_all_vs_fp64_gpu": {"requests": len(reqs), "max_abs": float(err.max()),
                                       "over_1e-5": int((err > 1e-5).sum())},

@@ -380,8 +380,10 @@ struct CircuitTeam {
                 });
                 tsync<NTHR>();
                 for (int k = 0; k < K; ++k) {
-                    const double d = sqrt(C[k * LDK + k].re);
-                    const double inv = 1.0 / d;
+                    // 1/sqrt in one call (rsqrt, within about an ulp): the pivot is
+                    // 1 + O(eps_32), far from any range rsqrt treats specially
+                    const double inv = rsqrt(C[k * LDK + k].re);
+                    const double d = C[k * LDK + k].re * inv;
                     tsync<NTHR>();
                     for (int j = k + lane; j < K; j += NTHR)
                         C[j * LDK + k] = j == k ? mk<double>(d, 0.0) : inv * C[j * LDK + k];

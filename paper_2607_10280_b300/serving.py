@@ -27,8 +27,10 @@ thread while it walks the heap: a full collection over a process that holds torc
 the server and a few thousand requests took about 100 ms, during which no wave was
 launched or retired.  With ``freeze_gc`` (the default) ``start()`` moves every object
 that exists at that moment into the collector's permanent generation
-(``gc.freeze``), so the collections that run while serving walk only the objects
-created since; ``stop()`` hands them back (``gc.unfreeze``).
+(``gc.freeze``), and the scheduler does the same again every ``freeze_every`` retired
+waves, so the collections that run while serving walk only the objects created since
+the last freeze; ``stop()`` hands them back (``gc.unfreeze``).  Frozen objects are
+not searched for reference cycles until then; a request and its results form none.
 """
 from __future__ import annotations
 
@@ -143,9 +145,11 @@ class Server:
     def __init__(self, params: torch.Tensor, epilogue: dict = None, slots: int = 4,
                  max_images_per_wave: int = 64, budget_bytes: int = 2 << 30, precision: str = "mixed",
                  launch_shape=None, max_p: int = 16, max_chi: int = 32, long_slots: int = None,
-                 long_launch_shape=(0, 128, 0), freeze_gc: bool = True):
+                 long_launch_shape=(0, 128, 0), freeze_gc: bool = True, freeze_every: int = 256):
         self.params = params
         self.freeze_gc = freeze_gc
+        self.freeze_every = max(1, freeze_every)
+        self._retired_since_freeze = 0
         self._frozen = False
         self.epilogue = epilogue or {}
         self.precision = precision
@@ -321,6 +325,11 @@ class Server:
         for r in wave:
             r.t_done = now
             r.event.set()
+        if self._frozen:
+            self._retired_since_freeze += 1
+            if self._retired_since_freeze >= self.freeze_every:
+                gc.freeze()
+                self._retired_since_freeze = 0
         self.wave_log.append((s.idx, len(wave), s.long_lane, s.started.elapsed_time(s.done), s.host_ms))
         with self.lock:
             self.inflight_bytes -= s.footprint
