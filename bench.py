@@ -934,8 +934,9 @@ def run_serve(args):
             split[name] = {"queue_ms_p50": float(np.percentile(qw, 50)), "queue_ms_p99": float(np.percentile(qw, 99)),
                            "service_ms_p50": float(np.percentile(sv, 50)),
                            "service_ms_p99": float(np.percentile(sv, 99))}
-    # pauses while requests were in flight (t0 .. t1) and after
-    run_p = [g for g in gc_pauses if g[2] <= t1]
+    # pauses while requests were in flight (t0 .. t1; start() itself runs one full
+    # collection before t0) and after
+    run_p = [g for g in gc_pauses if t0 <= g[2] <= t1]
     gcp = np.array([g[1] for g in run_p]) if run_p else np.zeros(1)
 
     # every result against the batched FP64 path, by (p, L, chi) group
