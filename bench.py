@@ -105,6 +105,9 @@ def parse():
                          "batch, the 16x16 batch, the serving run, training on cached Paulis and the "
                          "156-pair layout with diagonals")
     ap.add_argument("--requests", type=int, default=20000, help="serving run: number of requests (10 s at 2000/s)")
+    ap.add_argument("--serve-slots", type=int, default=4, help="serving run: execution slots")
+    ap.add_argument("--serve-long-slots", type=int, default=2,
+                    help="serving run: slots reserved for requests that run a truncating chain")
     ap.add_argument("--pauli-kernel", default="default", choices=["default", "sweep", "column"],
                     help="Pauli-cache kernel at bonds up to 16 (mps_set_pauli_sweep); default: the library's")
     return ap.parse_args()
@@ -876,7 +879,8 @@ def run_serve(args):
     epi = {7: (torch.tensor(synth.observable_params(m7), dtype=torch.float32, device="cuda"),
                torch.tensor(W, dtype=torch.float32, device="cuda"), torch.tensor(b, dtype=torch.float32,
                                                                                 device="cuda"))}
-    srv = Server(params, epi, slots=4, max_images_per_wave=64, budget_bytes=4 << 30, long_slots=2)
+    srv = Server(params, epi, slots=args.serve_slots, max_images_per_wave=64, budget_bytes=4 << 30,
+                 long_slots=args.serve_long_slots)
     # warm the slots (kernel attributes, first launches)
     warm = [srv.submit(Request(r["p"], r["L"], r["chi"], r["pixels"])) for r in reqs[:64]]
     srv.start()
@@ -995,7 +999,7 @@ def run_serve(args):
                                        "max_abs": max(oerr) if oerr else None, "over_1e-5": int(sum(e > 1e-5 for e in oerr)),
                                        "skipped_ties": ties},
             "config": {"workload": "single images p~U{6..16}, L~U{1..4}, chi~U{4,8,16,32}, p=7 with ANO + "
-                                   "linear 84->784", "requests": len(submitted), "slots": 4,
+                                   "linear 84->784", "requests": len(submitted), "slots": len(srv.slots),
                        "long_slots": srv.long_slots}}
     print(json.dumps(line), flush=True)
     assert err.max() <= 1e-5 and (not oerr or max(oerr) <= 1e-5), "serving results exceed 1e-5"

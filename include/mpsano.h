@@ -313,6 +313,16 @@ mps_status mps_set_layer_pipeline(mps_batch* batch, int32_t enable);
  * exactly that.  Takes effect at the next mps_apply_circuit. */
 mps_status mps_set_half_structure(mps_batch* batch, int32_t enable);
 
+/* Block solve in FP64 truncations (enable != 0: on, the default).  A truncation at
+ * the orthogonality centre (Sec. II.B) keeps the span of the chi largest eigenvectors
+ * of the Gram matrix of theta; the basis inside that span is a gauge of the new bond.
+ * When FP64 Rayleigh quotients of the FP32-started eigenvectors place the cut in a gap
+ * wider than 1e-5 of the largest eigenvalue, FP64 Jacobi then rotates only pairs with
+ * one kept and one dropped direction.  With enable = 0 every FP64 truncation runs the
+ * full FP64 eigen-decomposition; the truncated states agree to rounding, and the
+ * switch exists to check exactly that.  Takes effect at the next mps_apply_circuit. */
+mps_status mps_set_block_truncation(mps_batch* batch, int32_t enable);
+
 /* Pauli-cache kernel choice under the mixed precisions at bonds up to 16:
  *   MPS_PAULI_COLUMN  one team per (image, grid column) walking the column, after
  *                     separate right and left environment chains;

@@ -71,6 +71,7 @@ SIGNATURES = {
     "mps_set_timing": (_c.c_int, [_c.c_void_p, _c.c_int32]),
     "mps_set_layer_pipeline": (_c.c_int, [_c.c_void_p, _c.c_int32]),
     "mps_set_half_structure": (_c.c_int, [_c.c_void_p, _c.c_int32]),
+    "mps_set_block_truncation": (_c.c_int, [_c.c_void_p, _c.c_int32]),
     "mps_set_real_arithmetic": (_c.c_int, [_c.c_void_p, _c.c_int32]),
     "mps_set_pauli_sweep": (_c.c_int, [_c.c_void_p, _c.c_int32]),
     "mps_kernel_times": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64)]),

@@ -174,6 +174,12 @@ class Batch:
         circuits built as operator products); results are bit-identical either way."""
         check(lib().mps_set_half_structure(self._h, 1 if enable else 0))
 
+    def set_block_truncation(self, enable: bool = True):
+        """FP64 truncations may decouple only the kept from the dropped directions when
+        the cut lies in a clear gap (the default); False runs the full FP64
+        eigen-decomposition every time.  The truncated states agree to rounding."""
+        check(lib().mps_set_block_truncation(self._h, 1 if enable else 0))
+
     def set_real_arithmetic(self, enable: bool = True):
         """Real-element environment and Pauli kernels for a real state (paper ansatz,
         mixed precisions); results agree with the complex kernels to rounding."""

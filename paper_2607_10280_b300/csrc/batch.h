@@ -58,6 +58,7 @@ struct mps_batch {
     int circuit_threads = 32;              // threads per image in the circuit kernel
     bool layer_pipeline = true;            // layer-pipelined kernel where it applies
     bool half_structure = true;            // exploit half-structured sites (META_HALF)
+    bool block_truncation = true;          // FP64 truncations may use the block solve (else META_FULL_EIGH)
     bool real = false;                     // the last circuit's state is real (paper ansatz)
     bool real_allowed = true;              // real-element kernels for real states (mps_set_real_arithmetic)
     int pauli_sweep = MPS_PAULI_AUTO;      // Pauli-cache kernel choice (mps_set_pauli_sweep)

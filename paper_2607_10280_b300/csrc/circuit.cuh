@@ -195,6 +195,7 @@ struct CircuitTeam {
     int* flag;    // team broadcast
     int lane, n, chi, ld;
     int keep;     // singular values an SVD truncation keeps
+    bool block_trunc;   // FP64 truncations may use the block solve (META_FULL_EIGH clear)
     cx<T>* sites;        // this image's site 0 in the arena
     double discarded;
     int* status;
@@ -446,7 +447,7 @@ struct CircuitTeam {
                 for (int i = lane; i < K; i += NTHR) lam[i] = G[i * LDK + i].re;
                 tsync<NTHR>();
                 rank_lam();
-                cross = lam[ord[keep - 1]] - lam[ord[keep]] >= 1e-5 * lam[ord[0]];
+                cross = block_trunc && lam[ord[keep - 1]] - lam[ord[keep]] >= 1e-5 * lam[ord[0]];
                 if (cross) team_jacobi_cross<NTHR, double>(G, W, LDK, K, ord, keep, lane, 40, red);
                 else team_jacobi_eigh<NTHR, double>(G, W, LDK, K, lane, 40, red, true);
                 Vd = W;
@@ -768,6 +769,7 @@ __global__ void __launch_bounds__(NTHR == 32 ? 256 : NTHR, NTHR == 32 ? 1 : 1024
         w.chi = mt.chi < CHI ? mt.chi : CHI;
         w.ld = mt.ld;
         w.sites = arena + mt.site_off;
+        w.block_trunc = (mt.flags & META_FULL_EIGH) == 0;
         w.discarded = 0.0;
         const double* px = pixels + mt.pixel_off;
         const int n = mt.n;
@@ -892,6 +894,7 @@ __device__ bool wave_step(unsigned char* buf, int t, int* bd, int k, int n, int 
     w.chi = CL;
     w.ld = ld;
     w.sites = sites;
+    w.block_trunc = true;
     w.discarded = 0.0;
     w.status = status;
     const int Dl = bd[k], Dm = bd[k + 1], Dr = bd[k + 2];

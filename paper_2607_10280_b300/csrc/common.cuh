@@ -132,6 +132,10 @@ constexpr int32_t META_LENV = 1;
 // r / (D_right / 2) == s: a ladder circuit built as an operator product), so the
 // contractions over a site's right index run over half of it (see times_site_t).
 constexpr int32_t META_HALF = 2;
+// ImageMeta::flags: FP64 truncations always run the full FP64 eigen-decomposition, never
+// the block solve that only decouples the kept from the dropped directions (both give
+// the same truncated state to rounding; the flag exists to check exactly that).
+constexpr int32_t META_FULL_EIGH = 4;
 
 // Device status word: first error wins.
 enum : int { DEV_OK = 0, DEV_BOND_OVERFLOW = 1, DEV_SMEM_OVERFLOW = 2, DEV_BAD_SHAPE = 3 };

@@ -600,6 +600,12 @@ mps_status mps_set_real_arithmetic(mps_batch* b, int32_t enable) {
     return MPS_OK;
 }
 
+mps_status mps_set_block_truncation(mps_batch* b, int32_t enable) {
+    if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
+    b->block_truncation = enable != 0;
+    return MPS_OK;
+}
+
 mps_status mps_set_half_structure(mps_batch* b, int32_t enable) {
     if (!b) return fail(MPS_ERR_INVALID_ARG, "batch is NULL");
     b->half_structure = enable != 0;
@@ -703,7 +709,8 @@ mps_status mps_apply_circuit(mps_batch* b, const double* pixels, const mps_circu
         if (bi > m.ld) return fail(MPS_ERR_UNSUPPORTED, "image %d reaches bond %d > padding %d", i, bi, m.ld);
         mpo[i] = pl.route == ROUTE_MPO;
         const int32_t fl =
-            mpo[i] ? (META_LENV | (circ->ansatz == MPS_ANSATZ_LADDER && b->half_structure ? META_HALF : 0)) : 0;
+            (mpo[i] ? (META_LENV | (circ->ansatz == MPS_ANSATZ_LADDER && b->half_structure ? META_HALF : 0)) : 0) |
+            (b->block_truncation ? 0 : META_FULL_EIGH);
         if (m.flags != fl) { m.flags = fl; b->meta_dirty = true; }
         if (mpo[i]) ++n_mpo;
         mx = std::max(mx, bi);
