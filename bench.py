@@ -105,8 +105,8 @@ def parse():
                          "batch, the 16x16 batch, the serving run, training on cached Paulis and the "
                          "156-pair layout with diagonals")
     ap.add_argument("--requests", type=int, default=20000, help="serving run: number of requests (10 s at 2000/s)")
-    ap.add_argument("--serve-slots", type=int, default=4, help="serving run: execution slots")
-    ap.add_argument("--serve-long-slots", type=int, default=2,
+    ap.add_argument("--serve-slots", type=int, default=6, help="serving run: execution slots")
+    ap.add_argument("--serve-long-slots", type=int, default=4,
                     help="serving run: slots reserved for requests that run a truncating chain")
     ap.add_argument("--pauli-kernel", default="default", choices=["default", "sweep", "column"],
                     help="Pauli-cache kernel at bonds up to 16 (mps_set_pauli_sweep); default: the library's")
@@ -859,14 +859,18 @@ def _oracle_serve_job(job):
 def run_serve(args):
     """Poisson arrivals at 2000 requests/s of single images with p in 6..16, L in 1..4,
     chi in {4,8,16,32}; p = 7 requests also get ANO (84 x 16) and a linear layer 84 -> 784.
-    Four slots, two of them reserved for requests whose circuit truncates (they run a
-    complex128 chain, on 128-thread teams).  Latency per (L, chi), per p and per lane, device time per wave;
+    Six slots (--serve-slots), four of them (--serve-long-slots) reserved for requests whose
+    circuit truncates (they run a complex128 chain, on 128-thread teams).  Latency per (L, chi), per p and per lane, device time per wave;
     every result against the batched FP64 path afterwards, and a stratified sample (one
     request of every (p, L, chi) class that occurred, and more of the truncating and the
     16x16 ones) against the CPU oracle."""
     # a serving process loads every kernel when CUDA starts: a kernel loaded lazily at its
     # first launch stalls the launching thread until the device's running work allows it
     os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
+    # every slot's stream on a hardware queue of its own: with the default of 8 queues
+    # streams share them, and an event on a short-lane slot's idle stream then waited
+    # behind a long-lane chain on the same queue (up to 75 ms, measured with 6 slots)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     torch = _setup_torch()
     from paper_2607_10280_b300 import api, synth
     from paper_2607_10280_b300.flops import lossy
@@ -927,6 +931,9 @@ def run_serve(args):
                            "device_ms_p99": float(np.percentile(ws, 99)), "device_ms_max": float(ws.max()),
                            "host_launch_ms_p50": float(np.percentile(hs, 50)),
                            "host_launch_ms_p99": float(np.percentile(hs, 99)), "host_launch_ms_max": float(hs.max()),
+                           "host_phase_ms_max": dict(zip(("reshape", "pixels", "circuit", "pauli", "epilogue"),
+                                                         np.max([w[5] for w in srv.wave_log if w[2] == flag],
+                                                                axis=0).round(2).tolist())),
                            "images_per_wave_mean": float(sz.mean())}
     # latency = queueing (arrival -> wave launch) + service (launch -> result on the host)
     split = {}

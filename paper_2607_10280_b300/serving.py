@@ -31,6 +31,13 @@ that exists at that moment into the collector's permanent generation
 waves, so the collections that run while serving walk only the objects created since
 the last freeze; ``stop()`` hands them back (``gc.unfreeze``).  Frozen objects are
 not searched for reference cycles until then; a request and its results form none.
+
+Two settings belong to the process, before CUDA starts: ``CUDA_DEVICE_MAX_CONNECTIONS=32``
+gives every slot's stream a hardware queue of its own (with the default 8, streams share
+queues, and work on a short-lane slot's idle stream waited behind a long-lane chain on
+the same queue: up to 75 ms of host time per launch with six slots), and
+``CUDA_MODULE_LOADING=EAGER`` loads every kernel at start-up instead of at its first
+launch.
 """
 from __future__ import annotations
 
@@ -131,6 +138,7 @@ class _Slot:
         self.done = torch.cuda.Event(enable_timing=True)
         self.wave = None
         self.host_ms = 0.0
+        self.phase_ms = ()
         self.footprint = 0
 
 
@@ -174,7 +182,8 @@ class Server:
                       for i in range(slots)]
         self.pending = collections.deque()        # requests for the short lane
         self.pending_long = collections.deque()   # requests that run a truncating chain
-        # (slot, images, long lane, device ms, host ms spent launching) per wave
+        # (slot, images, long lane, device ms, host ms spent launching, host ms per launch
+        # phase: reshape, pixel staging, circuit, Pauli cache, epilogue) per wave
         self.wave_log = []
         self.lock = threading.Lock()
         self.inflight_bytes = 0
@@ -280,14 +289,18 @@ class Server:
         with torch.cuda.stream(s.stream):
             s.started.record(s.stream)
             s.batch.reshape(ps, chis)
+            t_reshape = time.perf_counter()
             offs = s.batch.pixel_offsets
             for i, r in enumerate(wave):
                 s.px_host[offs[i]:offs[i + 1]] = torch.from_numpy(r.pixels)
             n_px = int(offs[-1])
             s.px_dev[:n_px].copy_(s.px_host[:n_px], non_blocking=True)
+            t_pixels = time.perf_counter()
             s.batch.apply_circuit(s.px_dev[:n_px], Ls, "ladder", self.params)
+            t_circuit = time.perf_counter()
             n_pairs = int(s.batch.pair_offsets[-1])
             s.batch.pauli_cache(s.pauli_dev[:n_pairs])
+            t_pauli = time.perf_counter()
             s.pauli_host[:n_pairs].copy_(s.pauli_dev[:n_pairs], non_blocking=True)
             epi = []
             i = 0
@@ -307,7 +320,12 @@ class Server:
                 i = j
             s.done.record(s.stream)
         s.wave = (wave, epi)
-        s.host_ms = (time.perf_counter() - t_launch) * 1e3
+        t_end = time.perf_counter()
+        s.host_ms = (t_end - t_launch) * 1e3
+        # host ms of each launch phase: reshape, pixel staging, circuit, Pauli cache, epilogue
+        s.phase_ms = tuple(1e3 * (b - a) for a, b in ((t_launch, t_reshape), (t_reshape, t_pixels),
+                                                       (t_pixels, t_circuit), (t_circuit, t_pauli),
+                                                       (t_pauli, t_end)))
         s.footprint = foot
         self.waves += 1
         self.max_wave = max(self.max_wave, len(wave))
@@ -330,7 +348,8 @@ class Server:
             if self._retired_since_freeze >= self.freeze_every:
                 gc.freeze()
                 self._retired_since_freeze = 0
-        self.wave_log.append((s.idx, len(wave), s.long_lane, s.started.elapsed_time(s.done), s.host_ms))
+        self.wave_log.append((s.idx, len(wave), s.long_lane, s.started.elapsed_time(s.done), s.host_ms,
+                              s.phase_ms))
         with self.lock:
             self.inflight_bytes -= s.footprint
             self.completed.extend(wave)
