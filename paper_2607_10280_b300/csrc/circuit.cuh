@@ -42,8 +42,9 @@ constexpr int MAX_QUBITS = 256;  // p <= 16
 // matrix and eigenvectors (G, V) of the SVD truncation: theta is formed from cur and
 // nxt before G is written, rb serves only the exact centre moves, and the new centre
 // is written to cur (inside G) only after the last read of U (held in G), from V.
-// That keeps the FP64 workspace of a bond-32 truncation (about 205 KB) within the
-// shared memory of one block.
+// That keeps the FP64 Gram and eigenvector workspace of a bond-32 truncation at about
+// 205 KB; with the FP64 basis W of the refined eigen-decomposition (REFINE) the layout
+// grows to about 270 KB, which launch_circuit places in global memory.
 template <typename T, typename TQ, int CHI, bool TRUNC>
 struct CircuitLayout {
     static constexpr int CS = CHI + 1;              // row stride of a site: element (l,s,r) at (2l+s)*CS + r
