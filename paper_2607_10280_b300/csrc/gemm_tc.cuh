@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict_
         // threads walk the operand's unit-stride index so the loads coalesce
         const bool x_kfast = xs_k == 1, w_kfast = ws_k == 1;
         // unrolled so that several global loads are in flight per thread (the staging
-        // is latency-bound: 32 loads per thread and operand per chunk)
-#pragma unroll 8
+        // is latency-bound: 32 loads per thread and operand per chunk; by 32 the index
+        // arithmetic takes 255 registers, by 16 it takes 60)
+#pragma unroll 16
         for (int e = tid; e < TC_M * TC_KC; e += 128) {
             const int row = x_kfast ? e / TC_KC : e % TC_M, k = x_kfast ? e % TC_KC : e / TC_M;
             const int kk = ch * TC_KC + k;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(128) linear_tc_kernel(const float* __restrict_
             *reinterpret_cast<uint32_t*>(a_hi + off) = xh;
             *reinterpret_cast<uint32_t*>(a_lo + off) = tf32_round(xa - __uint_as_float(xh));
         }
-#pragma unroll 8
+#pragma unroll 16
         for (int e = tid; e < TC_N * TC_KC; e += 128) {
             const int row = w_kfast ? e / TC_KC : e % TC_N, k = w_kfast ? e % TC_KC : e / TC_N;
             const int kk = ch * TC_KC + k;
