@@ -30,6 +30,8 @@
 // that renv_kernel writes beside the right ones (lenv_image), for the images marked
 // META_LENV.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "batch.h"
 #include "circuit.cuh"
@@ -125,8 +127,125 @@ __global__ void __launch_bounds__(32 * MPO_WARPS) ladder_mpo_kernel(
     }
 }
 
+// v <- u v with the rounding of cdot2 when one of its two terms is an exact zero (the
+// layered kernel's gate application at a half-structured site): each component is one
+// rounded product followed by one fma.
+template <typename T>
+__device__ __forceinline__ cx<T> mpo_mul(cx<T> u, cx<T> v) {
+    return mk<T>(fma(-u.im, v.im, mul_rn(u.re, v.re)), fma(u.im, v.re, mul_rn(u.re, v.im)));
+}
+
+// The ladder's site tensors in closed form, every element computed on its own (no shared
+// memory, no intermediate layers).  With l = sum_j a_j 2^(j-1) and r = sum_j b_j 2^(j-1)
+// (a_j, b_j the incoming and outgoing parities of layer j; a = 0 at site 0), an inner
+// site's element is zero unless s = b_L, and otherwise
+//     A[l][s][r] = y[a_1 xor b_1] * prod_{j = 2..L} U_j[a_j xor b_j][b_(j-1)],
+// y = U_1 (cos(pi x / 2), sin(pi x / 2)): before layer j's CNOT the physical index is
+// a_j xor b_j and after it b_j, which the next gate reads alone (the other physical
+// component is zero).  The last site has no right bond: its physical 2-vector goes
+// through v <- X^(a_j) U_j v.  The products are rounded in the layered kernel's order
+// (its gate applications add exact zeros), so both kernels write the same values.
+// Grid: (images, site groups of MPO_DIRECT_WARPS sites); one warp per site.
+constexpr int MPO_DIRECT_WARPS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * MPO_DIRECT_WARPS) ladder_mpo_direct_kernel(
+    const ImageMeta* __restrict__ meta, int n_images, const int32_t* __restrict__ order,
+    const double* __restrict__ pixels, const cx<T>* __restrict__ gates, int gn,
+    cx<T>* __restrict__ arena, int32_t* __restrict__ bonds_out, double* __restrict__ discarded_out,
+    int* status) {
+    constexpr int MAXL = 4;   // 2^L <= MPO_MAXB
+    const int slot = blockIdx.x;
+    if (slot >= n_images) return;
+    const int img = order ? order[slot] : slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const ImageMeta mt = meta[img];
+    const int n = mt.n, ld = mt.ld, L = mt.L;
+    if (L < 0 || L > MAXL || (1 << L) > MPO_MAXB || (1 << L) > ld) {   // the host routes by these bounds
+        if (threadIdx.x == 0) raise_status(status, DEV_BOND_OVERFLOW);
+        return;
+    }
+    const double* px = pixels + mt.pixel_off;
+    cx<T>* sites = arena + mt.site_off;
+    const int k = blockIdx.y * MPO_DIRECT_WARPS + warp;
+    if (k < n) {
+        T sn = T(0), cs = T(1);
+        encode_amplitudes(px[k], &sn, &cs);
+        const cx<T> x0 = mk<T>(cs, T(0)), x1 = mk<T>(sn, T(0));
+        Gate1<T> g[MAXL];
+#pragma unroll
+        for (int j = 0; j < MAXL; ++j)
+            if (j < L) g[j] = table_gate<T>(gates, gn, 0, j, img, k);
+        const int sl = k == 0 ? 0 : L, sr = k == n - 1 ? 0 : L;   // log2 of the bonds
+        cx<T>* dst = sites + (size_t)k * 2 * ld * ld;
+        if (k < n - 1) {
+            const cx<T> y0 = L > 0 ? cdot2(g[0].u00, x0, g[0].u01, x1) : x0;
+            const cx<T> y1 = L > 0 ? cdot2(g[0].u10, x0, g[0].u11, x1) : x1;
+            for (int e = lane; e < (2 << (sl + sr)); e += 32) {
+                const int row = e >> sr, r = e & ((1 << sr) - 1);
+                const int l = row >> 1, s = row & 1;
+                cx<T> v;
+                if (L == 0) {
+                    v = s ? x1 : x0;
+                } else if (s != ((r >> (L - 1)) & 1)) {
+                    v = czero<T>();
+                } else {
+                    v = ((l ^ r) & 1) ? y1 : y0;
+#pragma unroll
+                    for (int j = 1; j < MAXL; ++j) {
+                        if (j < L) {
+                            const int t = ((l ^ r) >> j) & 1, pb = (r >> (j - 1)) & 1;
+                            const cx<T> u = t ? (pb ? g[j].u11 : g[j].u10) : (pb ? g[j].u01 : g[j].u00);
+                            v = mpo_mul(u, v);
+                        }
+                    }
+                }
+                dst[row * ld + r] = v;
+            }
+        } else {
+            // last site: one 2-vector per left index l
+            for (int l = lane; l < (1 << sl); l += 32) {
+                cx<T> v0 = x0, v1 = x1;
+#pragma unroll
+                for (int j = 0; j < MAXL; ++j) {
+                    if (j < L) {
+                        const cx<T> w0 = cdot2(g[j].u00, v0, g[j].u01, v1);
+                        const cx<T> w1 = cdot2(g[j].u10, v0, g[j].u11, v1);
+                        const bool a = (l >> j) & 1;
+                        v0 = a ? w1 : w0;
+                        v1 = a ? w0 : w1;
+                    }
+                }
+                dst[(2 * l) * ld] = v0;
+                dst[(2 * l + 1) * ld] = v1;
+            }
+        }
+        if (lane == 0) bonds_out[mt.bond_off + k] = 1 << sl;
+    }
+    if (blockIdx.y == 0 && threadIdx.x == 0) {
+        bonds_out[mt.bond_off + n] = 1;
+        discarded_out[img] = 0.0;
+    }
+}
+
 template <typename T>
 mps_status launch_mpo_t(mps_batch* b, const double* pixels, int ansatz) {
+    // ladder circuits take the closed form; MPSANO_MPO=layered selects the layer-by-layer
+    // kernel for them too (the two write the same values; the tests compare them)
+    const char* mode = std::getenv("MPSANO_MPO");
+    if (ansatz == 0 && !(mode && std::strcmp(mode, "layered") == 0)) {
+        auto kd = ladder_mpo_direct_kernel<T>;
+        timing_begin(b, KIND_CIRCUIT);
+        const dim3 grid((unsigned)b->run_count, (unsigned)((b->n_max + MPO_DIRECT_WARPS - 1) / MPO_DIRECT_WARPS));
+        kd<<<grid, 32 * MPO_DIRECT_WARPS, 0, b->stream>>>(b->meta_d, b->run_count, b->run_order, pixels,
+                                                        reinterpret_cast<const cx<T>*>(b->gates), b->gate_n,
+                                                        reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
+                                                        b->discarded_d, b->status_d);
+        timing_end(b);
+        CUDA_TRY(cudaGetLastError());
+        count_launch();
+        return MPS_OK;
+    }
     auto k = ladder_mpo_kernel<T>;
     const size_t smem = sizeof(cx<T>) * 2 * MPO_BUF * MPO_WARPS;
     CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
