@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 PROFILED = {
     "pauli": ("profiles/pauli_sweep_kernel_7x7_L4_chi16_b1024.md",
               ("pauli_sweep.cuh", "pauli_launch_sweep.cu", "pauli.cuh", "linalg.cuh", "common.cuh")),
-    "circuit": ("profiles/ladder_mpo_kernel_7x7_L4_chi16_b1024.md",
+    "circuit": ("profiles/ladder_mpo_direct_kernel_7x7_L4_chi16_b1024.md",
                 ("ladder_mpo.cu", "circuit.cuh", "common.cuh")),
     "renv": ("profiles/lenv_kernel_7x7_L4_chi16_b1024.md",
              ("pauli_sweep.cuh", "pauli_launch_sweep.cu", "pauli.cuh", "linalg.cuh", "common.cuh")),
