@@ -143,15 +143,18 @@ __device__ __forceinline__ cx<T> mpo_mul(cx<T> u, cx<T> v) {
 // y = U_1 (cos(pi x / 2), sin(pi x / 2)): before layer j's CNOT the physical index is
 // a_j xor b_j and after it b_j, which the next gate reads alone (the other physical
 // component is zero).  The last site has no right bond: its physical 2-vector goes
-// through v <- X^(a_j) U_j v.  The products are rounded in the layered kernel's order
-// (its gate applications add exact zeros), so both kernels write the same values.
+// through v <- X^(a_j) U_j v.  The paper's brick-wall has the same form with the roles
+// of the two parities swapped at its even sites (X^a P_b: t = b before and a xor b after
+// the CNOTs), and |0> re-encoded by its per-image gate in every layer.  The products are
+// rounded in the layered kernel's order (its gate applications add exact zeros), so both
+// kernels write the same values.
 // Grid: (images, site groups of MPO_DIRECT_WARPS sites); one warp per site.
 constexpr int MPO_DIRECT_WARPS = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(32 * MPO_DIRECT_WARPS) ladder_mpo_direct_kernel(
     const ImageMeta* __restrict__ meta, int n_images, const int32_t* __restrict__ order,
-    const double* __restrict__ pixels, const cx<T>* __restrict__ gates, int gn,
+    const double* __restrict__ pixels, const cx<T>* __restrict__ gates, int gn, int ansatz,
     cx<T>* __restrict__ arena, int32_t* __restrict__ bonds_out, double* __restrict__ discarded_out,
     int* status) {
     constexpr int MAXL = 4;   // 2^L <= MPO_MAXB
@@ -169,13 +172,18 @@ __global__ void __launch_bounds__(32 * MPO_DIRECT_WARPS) ladder_mpo_direct_kerne
     cx<T>* sites = arena + mt.site_off;
     const int k = blockIdx.y * MPO_DIRECT_WARPS + warp;
     if (k < n) {
+        // ladder: the encoding R_Y(pi x) on |0>; paper: |0> (it encodes in every layer)
         T sn = T(0), cs = T(1);
-        encode_amplitudes(px[k], &sn, &cs);
+        if (ansatz == 0) encode_amplitudes(px[k], &sn, &cs);
         const cx<T> x0 = mk<T>(cs, T(0)), x1 = mk<T>(sn, T(0));
         Gate1<T> g[MAXL];
 #pragma unroll
         for (int j = 0; j < MAXL; ++j)
-            if (j < L) g[j] = table_gate<T>(gates, gn, 0, j, img, k);
+            if (j < L) g[j] = table_gate<T>(gates, gn, ansatz, j, img, k);
+        // physical index before (t) and after (p) each layer's CNOTs, as bits j of tb and
+        // pb: P_b X^a (ladder, odd brick-wall sites) t = a xor b, p = b; X^a P_b (even
+        // brick-wall sites) t = b, p = a xor b
+        const bool right_first = ansatz != 0 && (k & 1) == 0;
         const int sl = k == 0 ? 0 : L, sr = k == n - 1 ? 0 : L;   // log2 of the bonds
         cx<T>* dst = sites + (size_t)k * 2 * ld * ld;
         if (k < n - 1) {
@@ -184,17 +192,18 @@ __global__ void __launch_bounds__(32 * MPO_DIRECT_WARPS) ladder_mpo_direct_kerne
             for (int e = lane; e < (2 << (sl + sr)); e += 32) {
                 const int row = e >> sr, r = e & ((1 << sr) - 1);
                 const int l = row >> 1, s = row & 1;
+                const int tb = right_first ? r : (l ^ r), pbits = right_first ? (l ^ r) : r;
                 cx<T> v;
                 if (L == 0) {
                     v = s ? x1 : x0;
-                } else if (s != ((r >> (L - 1)) & 1)) {
+                } else if (s != ((pbits >> (L - 1)) & 1)) {
                     v = czero<T>();
                 } else {
-                    v = ((l ^ r) & 1) ? y1 : y0;
+                    v = (tb & 1) ? y1 : y0;
 #pragma unroll
                     for (int j = 1; j < MAXL; ++j) {
                         if (j < L) {
-                            const int t = ((l ^ r) >> j) & 1, pb = (r >> (j - 1)) & 1;
+                            const int t = (tb >> j) & 1, pb = (pbits >> (j - 1)) & 1;
                             const cx<T> u = t ? (pb ? g[j].u11 : g[j].u10) : (pb ? g[j].u01 : g[j].u00);
                             v = mpo_mul(u, v);
                         }
@@ -230,15 +239,15 @@ __global__ void __launch_bounds__(32 * MPO_DIRECT_WARPS) ladder_mpo_direct_kerne
 
 template <typename T>
 mps_status launch_mpo_t(mps_batch* b, const double* pixels, int ansatz) {
-    // ladder circuits take the closed form; MPSANO_MPO=layered selects the layer-by-layer
-    // kernel for them too (the two write the same values; the tests compare them)
+    // the closed form; MPSANO_MPO=layered selects the layer-by-layer kernel (the two
+    // write the same values; the tests compare them)
     const char* mode = std::getenv("MPSANO_MPO");
-    if (ansatz == 0 && !(mode && std::strcmp(mode, "layered") == 0)) {
+    if (!(mode && std::strcmp(mode, "layered") == 0)) {
         auto kd = ladder_mpo_direct_kernel<T>;
         timing_begin(b, KIND_CIRCUIT);
         const dim3 grid((unsigned)b->run_count, (unsigned)((b->n_max + MPO_DIRECT_WARPS - 1) / MPO_DIRECT_WARPS));
         kd<<<grid, 32 * MPO_DIRECT_WARPS, 0, b->stream>>>(b->meta_d, b->run_count, b->run_order, pixels,
-                                                        reinterpret_cast<const cx<T>*>(b->gates), b->gate_n,
+                                                        reinterpret_cast<const cx<T>*>(b->gates), b->gate_n, ansatz,
                                                         reinterpret_cast<cx<T>*>(b->arena), b->bonds_d,
                                                         b->discarded_d, b->status_d);
         timing_end(b);

@@ -1,5 +1,5 @@
-"""Ladder circuits as operator products: the closed-form site kernel against the
-layer-by-layer one (GPU tests).
+"""Circuits as operator products: the closed-form site kernel against the
+layer-by-layer one, ladder and brick-wall (GPU tests).
 
 Both build the exact MPS of L ladder layers (Sec. II.B) with bond 2^L; the closed form
 computes every site element as one product of gate entries and rounds it in the order
@@ -26,7 +26,7 @@ def cuda_ready():
     build.build()
 
 
-def run(X, p, L, chi, precision, params, layered):
+def run(X, p, L, chi, precision, params, layered, ansatz="ladder"):
     from paper_2607_10280_b300.api import Batch
     old = os.environ.get("MPSANO_MPO")
     if layered:
@@ -35,9 +35,9 @@ def run(X, p, L, chi, precision, params, layered):
         os.environ.pop("MPSANO_MPO", None)
     try:
         px = torch.tensor(np.concatenate(list(X)), dtype=torch.float64, device="cuda")
-        pr = torch.tensor(params, dtype=torch.float64, device="cuda").contiguous()
+        pr = None if params is None else torch.tensor(params, dtype=torch.float64, device="cuda").contiguous()
         b = Batch(np.full(len(X), p, np.int32), chi, precision)
-        b.apply_circuit(px, L, "ladder", pr)
+        b.apply_circuit(px, L, ansatz, pr)
         out = b.pauli_cache()
         b.sync()
         res = out.double().cpu().numpy().reshape(len(X), -1, 16)
@@ -64,4 +64,21 @@ def test_closed_form_matches_layered_kernel(precision, p, L, chi):
     tol = 1e-10 if precision == "fp64" else 1e-5
     for i in (0, B - 1):
         ref = o_pipe.pauli_cache(X[i], p, L, chi, "ladder", params)
+        assert np.max(np.abs(direct[i] - ref)) < tol, (i, np.max(np.abs(direct[i] - ref)))
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("p,L,chi", [(3, 1, 4), (4, 2, 4), (5, 3, 8), (7, 4, 16)])
+def test_closed_form_matches_layered_kernel_paper_ansatz(precision, p, L, chi):
+    """The paper's brick-wall circuit (H, R_Y(2 pi x - pi) every layer, CNOTs on the even
+    then the odd bonds): even sites take the CNOT on their right bond first."""
+    B = 4
+    X = synth.garment_pixels(B, p, seed=500 + p + L)
+    direct, bd = run(X, p, L, chi, precision, None, layered=False, ansatz="paper")
+    layered, bl = run(X, p, L, chi, precision, None, layered=True, ansatz="paper")
+    assert [list(x) for x in bd] == [list(x) for x in bl]
+    assert np.array_equal(direct, layered)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for i in (0, B - 1):
+        ref = o_pipe.pauli_cache(X[i], p, L, chi, "paper")
         assert np.max(np.abs(direct[i] - ref)) < tol, (i, np.max(np.abs(direct[i] - ref)))
